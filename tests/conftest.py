@@ -1,0 +1,22 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (B300, sm_103a) and the built CUDA library")
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _built_cpu_parts():
+    """Compile the generator and both oracle builds once per session (gcc, seconds)."""
+    import oracle
+    import synth
+
+    synth.build()
+    oracle.build()

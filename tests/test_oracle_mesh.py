@@ -1,0 +1,318 @@
+"""Pins of the oracle's meshing (Secs. IV, V-B..V-F) against what the paper and geometry fix.
+
+* an analytic sphere meshes into a closed, oriented 2-manifold with Euler characteristic 2,
+  no duplicate vertex, the right enclosed volume, vertices on the sphere and radial normals;
+* a planar patch has (w+1)(h+1) vertices and 2wh triangles (Sec. VI-B, golden fixture);
+* plain per-cube marching cubes with duplicated vertices, welded by position, gives exactly
+  the oracle's edge-owned mesh (the paper's "identical in theory" statement, Sec. VI-C);
+* the regular types and their Hamming distances are those printed in Sec. V-F (golden);
+* Eqs. 3-5 on hand-worked single cubes, and their postconditions on random cubes;
+* refinement does not raise the summed Hamming distance between face-adjacent cube types;
+* the incremental mesh equals a full re-extraction over the final TSDF; GC leaves the mesh
+  unchanged;
+* noise-free fused sequences put every vertex within about half a voxel of the surface.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.meshutil import (canonical_triangles, field_fill, index_mesh, manifold_report, signed_volume,
+                            sphere_fill)
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _mesh_of_fill(keys, tsdf, weight, l, mu, prec="f64", refine=False):
+    V = oracle.Volume(l, mu, prec=prec)
+    V.set_blocks(keys, tsdf, weight)
+    V.update_mesh(full=True, refine=refine)
+    return V, V.mesh()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("center,radius", [((0.013, -0.021, 0.007), 0.1), ((0.5, 0.31, -0.2), 0.173)])
+def test_analytic_sphere_is_a_closed_manifold(prec, center, radius):
+    l, mu = 0.01, 0.04
+    keys, tsdf, w = sphere_fill(center, radius, l, mu)
+    _, m = _mesh_of_fill(keys, tsdf, w, l, mu, prec)
+    assert len(np.unique(m["vkeys"])) == len(m["vkeys"])  # zero duplicate vertices
+    tris = index_mesh(m["vkeys"], m["tkeys"])
+    rep = manifold_report(tris)
+    assert rep["closed"] and rep["oriented"] and rep["degenerate"] == 0, rep
+    assert rep["euler"] == 2
+    vol = signed_volume(m["pos"], tris)
+    assert abs(vol / (4 / 3 * np.pi * radius ** 3) - 1) < 0.02
+    r = np.linalg.norm(m["pos"] - np.array(center), axis=1)
+    assert np.max(np.abs(r - radius)) < 0.1 * l
+    radial = (m["pos"] - np.array(center)) / r[:, None]
+    assert np.min(np.einsum("ij,ij->i", radial, m["nrm"])) > 0.95
+    # refcount == degree (Sec. V-E): number of triangles per vertex equals its uses
+    deg = np.bincount(tris.reshape(-1), minlength=len(m["vkeys"]))
+    assert deg.min() >= 3
+
+
+def test_planar_patch_counts_match_the_paper():
+    l, mu = 0.01, 0.04
+    rows = [list(map(int, ln.split())) for ln in open(os.path.join(GOLDEN, "planar_patch.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    for w, h, nv, nt in rows:
+        nbx, nby = (w + 1) // 8, (h + 1) // 8
+        keys = np.array([[x, y, 0] for y in range(nby) for x in range(nbx)], np.int32)
+        keys, tsdf, wt = field_fill(keys, lambda p: p[..., 2] - 0.0345, l, mu)
+        _, m = _mesh_of_fill(keys, tsdf, wt, l, mu)
+        assert (len(m["vkeys"]), len(m["tkeys"])) == (nv, nt)
+        assert nt == 2 * w * h and nv == (w + 1) * (h + 1)
+        assert len(m["tkeys"]) <= 2 * len(m["vkeys"])
+
+
+def _smooth_field(p, seed):
+    rng = np.random.default_rng(seed)
+    out = np.zeros(p.shape[:-1])
+    for _ in range(6):
+        k = rng.normal(size=3) * 25.0
+        out += np.sin(p @ k + rng.uniform(0, 6.28)) * rng.uniform(0.3, 1.0)
+    return out * 0.02 + 0.004
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_plain_marching_cubes_welded_by_position_equals_edge_owned_mesh(seed):
+    l, mu = 0.01, 0.04
+    keys = np.array([[x, y, z] for z in (-1, 0) for y in (-1, 0) for x in (-1, 0)], np.int32)
+    keys, tsdf, wt = field_fill(keys, lambda p: _smooth_field(p, seed), l, mu)
+    _, m = _mesh_of_fill(keys, tsdf, wt, l, mu, "f64")
+    n, t = oracle.mc_table()
+    # dense corner grid over the filled blocks (voxels -8 .. 7 on each axis)
+    grid = np.zeros((16, 16, 16))
+    for j, k in enumerate(keys):
+        blk = tsdf[j].reshape(8, 8, 8)  # [z][y][x]
+        o = (k + 1) * 8
+        grid[o[0]:o[0] + 8, o[1]:o[1] + 8, o[2]:o[2] + 8] = blk.transpose(2, 1, 0)
+    corner = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0], [0, 0, 1], [1, 0, 1], [1, 1, 1], [0, 1, 1]])
+    edge = [(0, 1), (1, 2), (3, 2), (0, 3), (4, 5), (5, 6), (7, 6), (4, 7), (0, 4), (1, 5), (2, 6), (3, 7)]
+    tri_pos = []
+    for x in range(15):
+        for y in range(15):
+            for z in range(15):
+                d = [grid[x + c[0], y + c[1], z + c[2]] for c in corner]
+                code = sum(1 << i for i in range(8) if d[i] < 0)
+                for tri in t[code, : n[code]]:
+                    pts = []
+                    for e in tri:
+                        a, b = edge[e]
+                        neg, pos_ = (a, b) if d[a] < 0 else (b, a)
+                        pn = (np.array([x, y, z]) + corner[neg] - 8) * l
+                        pp = (np.array([x, y, z]) + corner[pos_] - 8) * l
+                        s = d[neg] / (d[neg] - d[pos_])
+                        pts.append(pn + s * (pp - pn))
+                    tri_pos.append(pts)
+    tri_pos = np.array(tri_pos).reshape(-1, 3)
+    # weld by position onto the oracle's vertices
+    from scipy.spatial import cKDTree
+
+    dist, idx = cKDTree(m["pos"]).query(tri_pos)
+    assert dist.max() < 1e-9
+    brute = canonical_triangles(m["vkeys"][idx].reshape(-1, 3))
+    mine = canonical_triangles(m["tkeys"])
+    np.testing.assert_array_equal(brute, mine)
+    assert len(mine) > 200
+
+
+def _regular_types():
+    return [int(ln.strip(), 2) for ln in open(os.path.join(GOLDEN, "regular_types.txt"))
+            if ln.strip() and not ln.startswith("#")]
+
+
+def test_regular_types_and_their_distances():
+    R = _regular_types()
+    assert len(R) == 6
+    corner = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0], [0, 0, 1], [1, 0, 1], [1, 1, 1], [0, 1, 1]])
+    for a in range(6):
+        # each regular type marks the four corners of one cube face (a plane through the cube)
+        bits = [k for k in range(8) if (R[a] >> k) & 1]
+        assert len(bits) == 4 and any(len(set(corner[bits, ax])) == 1 for ax in range(3))
+        for b in range(6):
+            if a != b:
+                assert bin(R[a] ^ R[b]).count("1") in (4, 8)
+    # the oracle applies exactly these types: a raw type one flip away from each snaps back
+    for j, r in enumerate(R):
+        for k in range(8):
+            raw = r ^ (1 << k)
+            d = np.full(8, 0.5)
+            d[k] = 0.001
+            assert oracle.refine_code(raw, r, d, 0.002) == r
+
+
+def test_refinement_worked_examples():
+    eps = 0.002  # 0.2 l at l = 1 cm
+    # a z-plane through the cube: corners 0-3 below (d < 0), 4-7 above
+    d = np.array([-0.5, -0.5, -0.5, -0.5, 0.5, 0.5, 0.5, 0.5]) * 0.01
+    assert oracle.refine_code(0x0F, 0x0F, d, eps) == 0x0F
+    # corner 4 disturbed to a tiny negative value: raw 0x1F, previous 0x0F -> snapped back (Eqs. 3-5)
+    d1 = d.copy()
+    d1[4] = -0.0001
+    assert oracle.refine_code(0x1F, 0x0F, d1, eps) == 0x0F
+    # the same flip with |d| >= eps violates Eq. 5 -> kept
+    d2 = d.copy()
+    d2[4] = -0.003
+    assert oracle.refine_code(0x1F, 0x0F, d2, eps) == 0x1F
+    # previous type far away (Eq. 3 violated, d_H(0x1F, 0x00) = 5) -> kept
+    assert oracle.refine_code(0x1F, 0x00, d1, eps) == 0x1F
+    # two regular types at distance 2, both admissible: 0xE8 is 2 flips from 0xCC (t_r1) and from
+    # 0xF0 (t_r5); the tie goes to the first listed; a raw type 1 flip from 0xF0 goes to 0xF0
+    d3 = np.full(8, 0.0001)
+    assert bin(0xE8 ^ 0xCC).count("1") == 2 and bin(0xE8 ^ 0xF0).count("1") == 2
+    assert oracle.refine_code(0xE8, 0xE8, d3, eps) == 0xCC
+    assert oracle.refine_code(0xF1, 0xF1, d3, eps) == 0xF0
+    # empty and full cubes never snap (distance 4 to every regular type)
+    assert oracle.refine_code(0x00, 0x00, d3, eps) == 0x00
+    assert oracle.refine_code(0xFF, 0xFF, d3, eps) == 0xFF
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_refinement_postconditions_on_random_cubes(prec):
+    R = _regular_types()
+    rng = np.random.default_rng(3)
+    eps = 0.002
+    snapped = 0
+    for _ in range(20000):
+        d = rng.normal(size=8) * rng.choice([0.001, 0.003, 0.01])
+        raw = sum(1 << k for k in range(8) if d[k] < 0)
+        prev = int(rng.choice([raw, rng.integers(0, 256)] + R))
+        out = oracle.refine_code(raw, prev, d, eps, prec)
+        admissible = []
+        if bin(raw ^ prev).count("1") <= 3:
+            for j, r in enumerate(R):
+                diff = raw ^ r
+                if bin(diff).count("1") <= 3 and all(abs(d[k]) < eps for k in range(8) if (diff >> k) & 1):
+                    admissible.append((bin(diff).count("1"), j))
+        if admissible:
+            assert out == R[min(admissible)[1]]
+            snapped += out != raw
+        else:
+            assert out == raw
+    assert snapped > 100
+
+
+def _face_pair_hamming(codes, keys):
+    """Sum of d_H over face-adjacent cube pairs with at least one surface cube."""
+    idx = {tuple(k): i for i, k in enumerate(keys)}
+    total = 0
+    c = codes.reshape(-1, 8, 8, 8)  # [blk][z][y][x]
+    for i, k in enumerate(keys):
+        for ax in range(3):
+            a = np.moveaxis(c[i], 2 - ax, 0)
+            inner = (a[:-1], a[1:])
+            nb = list(k)
+            nb[ax] += 1
+            j = idx.get(tuple(nb))
+            pairs = [inner]
+            if j is not None:
+                pairs.append((a[-1:], np.moveaxis(c[j], 2 - ax, 0)[:1]))
+            for x, y in pairs:
+                surf = ((x != 0) & (x != 255)) | ((y != 0) & (y != 255))
+                total += int(np.unpackbits((x ^ y)[surf].astype(np.uint8)).sum())
+    return total
+
+
+@pytest.mark.parametrize("shape", ["tilted_plane", "steep_plane"])
+def test_refinement_does_not_raise_neighbour_hamming_distance(shape):
+    """Planar surfaces, the case Sec. V-F targets.  On curved surfaces (a sphere) the sum can
+    rise slightly; the paper claims nothing there, and the oracle's definition rules."""
+    l, mu = 0.01, 0.04
+    rng = np.random.default_rng(11)
+    keys = np.array([[x, y, z] for z in (-1, 0) for y in (-2, -1, 0, 1) for x in (-2, -1, 0, 1)], np.int32)
+    n = np.array([0.12, -0.07, 1.0])
+    n /= np.linalg.norm(n)
+    if shape == "steep_plane":
+        n = np.array([0.45, 0.3, 1.0])
+        n /= np.linalg.norm(n)
+    fn = lambda p: p @ n - 0.003
+    k, base, w = field_fill(keys, fn, l, mu)
+    V = oracle.Volume(l, mu, prec="f64")
+    V.set_blocks(k, base + rng.normal(size=base.shape) * 0.0004, w)
+    V.update_mesh(full=True)
+    noisy = base + rng.normal(size=base.shape) * 0.0004
+    V.set_blocks(k, noisy, w)
+    V.update_mesh(full=True)
+    b0 = V.blocks()
+    V.refine_mesh(full=True)
+    b1 = V.blocks()
+    assert np.any(b0["code_eff"] != b1["code_eff"])
+    before = _face_pair_hamming(b0["code_eff"], b0["keys"])
+    after = _face_pair_hamming(b1["code_eff"], b1["keys"])
+    assert after <= before, (before, after)
+
+
+def _run_sequence(scene, frames, prec="f32", refine=False, gc=True, check_gc=False):
+    V = oracle.Volume.from_config(scene.volume, prec=prec)
+    for k in range(frames):
+        T = scene.pose(k)
+        Ti = synth.pose_inverse_f64(T)
+        if prec == "f32":
+            T, Ti = T.astype(np.float32).astype(np.float64), Ti.astype(np.float32).astype(np.float64)
+        V.integrate(scene.depth(k), (scene.fx, scene.fy, scene.cx, scene.cy), T, Ti)
+        V.update_mesh(full=False, refine=refine)
+        if gc:
+            if check_gc:
+                m0 = V.mesh()
+            V.gc()
+            if check_gc:
+                m1 = V.mesh()
+                np.testing.assert_array_equal(canonical_triangles(m0["tkeys"]), canonical_triangles(m1["tkeys"]))
+                np.testing.assert_array_equal(m0["pos"], m1["pos"])
+    return V
+
+
+def test_incremental_mesh_equals_full_extraction_and_gc_keeps_the_mesh():
+    s = synth.small_room_scene(num_frames=8)
+    V = _run_sequence(s, 8, check_gc=True)
+    m_inc = V.mesh()
+    b = V.blocks()
+    F = oracle.Volume.from_config(s.volume, prec="f32")
+    F.set_blocks(b["keys"], b["tsdf"], b["weight"])
+    F.update_mesh(full=True)
+    m_full = F.mesh()
+    assert len(m_inc["tkeys"]) > 1000
+    np.testing.assert_array_equal(canonical_triangles(m_inc["tkeys"]), canonical_triangles(m_full["tkeys"]))
+    np.testing.assert_array_equal(m_inc["vkeys"], m_full["vkeys"])
+    np.testing.assert_array_equal(m_inc["pos"], m_full["pos"])
+    np.testing.assert_array_equal(m_inc["nrm"], m_full["nrm"])
+
+
+def test_gc_frees_blocks_and_keeps_every_triangle():
+    s = synth.small_room_scene(num_frames=8)
+    V = oracle.Volume.from_config(s.volume, prec="f32")
+    freed = 0
+    for k in range(8):
+        T = s.pose(k)
+        Ti = synth.pose_inverse_f64(T)
+        V.integrate(s.depth(k), (s.fx, s.fy, s.cx, s.cy), T.astype(np.float32).astype(np.float64),
+                    Ti.astype(np.float32).astype(np.float64))
+        V.update_mesh(refine=True)
+        before = V.num_blocks()
+        m0 = V.mesh()
+        freed += V.gc()
+        assert V.num_blocks() == before - (before - V.num_blocks())
+        m1 = V.mesh()
+        np.testing.assert_array_equal(canonical_triangles(m0["tkeys"]), canonical_triangles(m1["tkeys"]))
+    assert freed > 0
+
+
+def test_noise_free_sequence_vertices_lie_on_the_surface():
+    s = synth.sphere_scene(noise_sigma=0.0)
+    V = oracle.Volume.from_config(s.volume, prec="f64")
+    for k in range(s.num_frames):
+        T = s.pose(k)
+        V.integrate(s.depth(k), (s.fx, s.fy, s.cx, s.cy), T, synth.pose_inverse_f64(T))
+    V.update_mesh(full=True)
+    m = V.mesh()
+    p = m["pos"]
+    # exclude the sphere/ground contact crease and the ground square's rim and underside
+    keep = (np.linalg.norm(p, axis=1) > 2 * 0.04) & (np.abs(p[:, 0]) < 0.9) & (np.abs(p[:, 1]) < 0.9) & (p[:, 2] > -0.005)
+    err = np.abs(s.sdf(p[keep])) / s.volume.voxel_size
+    assert keep.sum() > 50000
+    assert np.quantile(err, 0.999) < 0.5
+    assert err.max() < 0.75
