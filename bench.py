@@ -1,0 +1,339 @@
+#!/usr/bin/env python3
+"""Benchmark: integrate + incremental mesh (+ refine + gc) per depth frame on one B300.
+
+Workload: the seeded 6 x 4 x 3 m room with 20 random primitives, 640 x 480 float32
+depth (fx = fy = 525), smooth random-walk trajectory, noise sigma = 0.0012 z^2 and 2 %
+dropped pixels; voxel 8 mm, truncation 3.2 cm, 2^20 hash buckets (synthetic stand-in for
+the RGB-D sequences of the paper's Sec. VI).  A step is one frame: vm_step =
+integrate_depth + update_mesh(refine) + gc, replayed from a CUDA graph, depth already
+resident in HBM.  L2 is flushed (256 MB write) before every timed frame; each frame is
+timed with CUDA events on the volume's stream.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl vmesh|reference]
+With N > 1 (torchrun, one rank per GPU) every rank runs an independent replica on its own
+seeded scene (no data-path collective); value = frames of all ranks / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "depth frames/s (integrate+incremental mesh) and voxels/s; % of HBM peak"
+UNIT = "frames/s"
+WORKLOAD = ("room 6x4x3 m, 20 primitives, 640x480 float32 depth, voxel 8 mm, trunc 3.2 cm, 2^20 buckets; "
+            "per frame integrate + incremental mesh + refine + gc")
+L2_FLUSH_BYTES = 256 << 20
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+# Algorithmic bytes per launch of the per-frame kernels (the minimum each must move):
+#   k_integrate   16 B per voxel of the collected blocks (d, W read + write) + 20 B per block
+#   k_mesh_types  11 B per voxel of the update set (d, W read; type read; previous type
+#                 write; vertex flags read)
+#   k_alloc       4 B per depth pixel + 16 B hash bucket per collected block
+#   k_triangles   1 B per cube of the update set (pending flag) + 36 B per changed cube
+#   k_gc_blocks   29 B per block pool slot ever used (key, epoch, counts, near flag)
+BYTES_MODEL = {
+    "k_integrate": lambda s: 16 * 512 * s["frame_blocks"] + 20 * s["frame_blocks"],
+    "k_mesh_types": lambda s: 11 * 512 * s["update_blocks"],
+    "k_alloc": lambda s: 4 * s["pixels"] + 16 * s["frame_blocks"],
+    "k_triangles": lambda s: 512 * s["update_blocks"] + 36 * s["changed"],
+    "k_gc_blocks": lambda s: 29 * s["high_water"],
+}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    def __init__(self, gpu_index: int, out_path: str | None = None):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out_path = out_path
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + CLOCK_QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.2)
+        return self
+
+    def __exit__(self, *exc):
+        self.text = ""
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.text, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                self.text = ""
+        if self.out_path and self.text:
+            with open(self.out_path, "w") as f:
+                f.write(self.text)
+
+    def summary(self):
+        rows = [r.split(",") for r in self.text.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def reduce_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def scene_for(rank: int, frames: int):
+    # rank 0 runs the canonical seeded room sequence; other replicas use their own seeds
+    return synth.room_scene(num_frames=frames, seed=synth.SEED_BASE + 2 + 1000 * rank)
+
+
+def oracle_frames(scene, frames, warmup=0):
+    """Time the float32 oracle (single-threaded C) over `frames` after `warmup` frames."""
+    import oracle
+
+    V = oracle.Volume.from_config(scene.volume, prec="f32")
+    K = (scene.fx, scene.fy, scene.cx, scene.cy)
+    depths = [scene.depth(k) for k in range(warmup + frames)]
+    poses = []
+    for k in range(warmup + frames):
+        T = scene.pose(k).astype(np.float32)
+        Ti = synth.pose_inverse_f64(scene.pose(k)).astype(np.float32)
+        poses.append((T.astype(np.float64), Ti.astype(np.float64)))
+    voxels = 0
+    t_total = 0.0
+    for k in range(warmup + frames):
+        t0 = time.perf_counter()
+        V.integrate(depths[k], K, *poses[k])
+        V.update_mesh(refine=True)
+        V.gc()
+        dt = time.perf_counter() - t0
+        if k >= warmup:
+            t_total += dt
+            voxels += 512 * V.stats()["frame_blocks"]
+    return frames / t_total, voxels / t_total, t_total
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    n = args.warmup + args.steps
+    scene = scene_for(0, n)
+    fps, vps, secs = oracle_frames(scene, args.steps, args.warmup)
+    sample = "frames %d..%d of the room sequence (after %d warm-up frames), integrate+update(refine)+gc each" % (
+        args.warmup, n - 1, args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 / fps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "impl": "float32 CPU oracle (plain single-threaded C)"},
+        "voxels_per_s": vps,
+        "cpu_baseline": {"value": fps, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": fps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_vmesh(args, rank, world, local):
+    import torch
+
+    from paper_1803_03949_b300 import Intrinsics, Volume
+
+    torch.cuda.set_device(local)
+    n = args.warmup + args.steps
+    scene = scene_for(rank, n)
+    H, W = scene.H, scene.W
+    depth_host = torch.empty((n, H, W), dtype=torch.float32).pin_memory()
+    for k in range(n):
+        depth_host[k].copy_(torch.from_numpy(scene.depth(k)))
+    depth_dev = depth_host.cuda()
+    poses = []
+    for k in range(n):
+        T = scene.pose(k)
+        poses.append((T.astype(np.float32), synth.pose_inverse_f64(T).astype(np.float32)))
+    K = Intrinsics(W, H, scene.fx, scene.fy, scene.cx, scene.cy)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def run(vol, timed_frames, e2e=False, collect=True):
+        """Warm-up then timed frames; returns per-frame ms and per-frame counters."""
+        per = []
+        res_host = torch.empty(2, dtype=torch.int32).pin_memory()
+        for f in range(args.warmup):
+            vol.step(depth_dev[f], K, *poses[f], refine=True, gc=True, graph=not args.no_graph)
+        torch.cuda.synchronize()
+        if collect:
+            vol.enable_timing(True)
+        ms, counters = [], []
+        prev = vol.stats()
+        dev_buf = torch.empty((H, W), dtype=torch.float32, device="cuda")
+        for f in timed_frames:
+            flush.fill_(f)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if e2e:
+                dev_buf.copy_(depth_host[f], non_blocking=True)
+                vol.step(dev_buf, K, *poses[f], refine=True, gc=True, graph=not args.no_graph)
+                vol.mesh_size_async(res_host)
+            else:
+                vol.step(depth_dev[f], K, *poses[f], refine=True, gc=True, graph=not args.no_graph)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            st = vol.stats()
+            counters.append(dict(frame_blocks=st["frame_blocks"], update_blocks=st["update_blocks"],
+                                 changed=st["changed_cubes"] - prev["changed_cubes"],
+                                 high_water=st["block_high_water"], pixels=W * H))
+            prev = st
+        kt = vol.kernel_times() if collect else {}
+        vol.check()
+        return ms, counters, kt
+
+    vol = Volume.from_config(scene.volume, stream=stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clock_path = os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else None
+    with ClockSampler(local, clock_path if rank == 0 else None) as cs:
+        ms, counters, kt = run(vol, range(args.warmup, n))
+        torch.cuda.synchronize()
+    barrier(world)
+    total_ms = sum(ms)
+    max_ms = reduce_max(total_ms, world)
+    value = world * args.steps / (max_ms / 1000.0)
+    voxels = sum(512 * c["frame_blocks"] for c in counters)
+    vps = voxels / (total_ms / 1000.0)
+
+    # roofline of the dominant kernel (largest device time in the timed region)
+    peak, peak_kind = load_peaks()
+    main = {k: v for k, v in kt.items() if k in BYTES_MODEL and v[1] > 0}
+    dom = max(main, key=lambda k: main[k][0]) if main else None
+    roof = None
+    if dom:
+        tot_ms_k, launches = kt[dom]
+        bytes_total = sum(BYTES_MODEL[dom](c) for c in counters)
+        achieved = bytes_total / (tot_ms_k / 1000.0) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                "bytes_per_launch": bytes_total / max(launches, 1), "avg_launch_us": 1000.0 * tot_ms_k / max(launches, 1)}
+    launches_total = sum(v[1] * (4 if k == "k_rehash" else 1) for k, v in kt.items())
+
+    # end to end through the public API: pinned host depth -> device, step, result -> host
+    vol_e2e = Volume.from_config(scene.volume, stream=stream)
+    ms_e2e, _, _ = run(vol_e2e, range(args.warmup, n), e2e=True, collect=False)
+    e2e_value = world * args.steps / (reduce_max(sum(ms_e2e), world) / 1000.0)
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.skip_cpu_baseline:
+        nframes = min(args.cpu_frames, n)
+        fps, cvps, secs = oracle_frames(scene_for(0, nframes), nframes)
+        cpu = {"value": fps, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "frames 0..%d of the same room sequence, integrate+update(refine)+gc each (%.1f s)" % (
+                   nframes - 1, secs), "voxels_per_s": cvps}
+    kernel_ms = {k: round(v[0] / max(len(ms), 1), 5) for k, v in kt.items() if v[1] > 0}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "frames": "%d..%d" % (args.warmup, n - 1),
+                   "graph": not args.no_graph, "l2": "flushed before every timed frame (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "voxels_per_s": vps,
+        "mean_blocks_per_frame": float(np.mean([c["frame_blocks"] for c in counters])),
+        "mean_update_blocks_per_frame": float(np.mean([c["update_blocks"] for c in counters])),
+        "kernel_ms_per_frame": kernel_ms,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * W * H, "d2h_bytes_per_step": 8},
+        "gpu_launches": int(launches_total),
+        "clocks": cs.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["vmesh", "reference"], default="vmesh")
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--skip-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-frames", type=int, default=200)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_vmesh(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

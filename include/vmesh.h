@@ -1,0 +1,205 @@
+/*
+ * vmesh -- incremental volumetric meshing on a spatial hash, B300 (sm_103a) CUDA.
+ *
+ * C ABI of the per-frame hot path of Dong, Shi, Tang, Wang, Zha, "An Efficient
+ * Volumetric Mesh Representation for Real-time Scene Reconstruction using Spatial
+ * Hashing" (arXiv 1803.03949):
+ *
+ *   integrate_depth   block collection (Sec. V-A, Eq. 1) + TSDF fusion (Sec. V-A, Eq. 2)
+ *   update_mesh       cube types (Sec. V-B), edge-owned vertices (Sec. V-C, Sec. IV),
+ *                     triangulation with type-change reuse (Sec. V-D)
+ *   refine_mesh       Hamming-distance cube-type refinement (Sec. V-F, Eqs. 3-5)
+ *   gc                reference-count recycling of vertices (Sec. V-E) plus triangle
+ *                     and block recycling
+ *   download_mesh     compaction of the live mesh into dense arrays (Sec. VI, the
+ *                     "compress" step before rendering)
+ *
+ * Conventions shared by every call
+ *   - Lattice: a voxel is a cube corner; global voxel g = (gx, gy, gz) sits at world
+ *     g * voxel_size; blocks hold 8 x 8 x 8 voxels, block key = floor(g / 8); inside a
+ *     block voxel (x, y, z) has index x + 8 y + 64 z.  Voxel g owns the three edges
+ *     g -> g + e_x, g + e_y, g + e_z and the vertices on them (Sec. IV).
+ *   - Camera: pinhole with OpenCV axes (x right, y down, z forward); depth is camera z
+ *     in metres; a pixel is valid when its depth is finite and > 0.  T_wc is the
+ *     camera-to-world pose, T_cw its inverse; both row-major 4 x 4 float32 on the host,
+ *     and the caller computes T_cw (the library never inverts a pose).
+ *   - Streams: every call enqueues work on the volume's stream (given at creation or by
+ *     vm_set_stream) and returns without waiting, except where a call says it
+ *     synchronises.  Device pointers must be valid on that stream when the work runs.
+ *   - Ownership: the caller owns depth frames and every output buffer; the library owns
+ *     the volume's device memory (hash table, voxel arrays, mesh pools), allocated in
+ *     vm_create_volume and released in vm_destroy_volume.
+ *   - Errors: a call returns VM_ERR_INVALID_ARG for a bad argument (null pointer,
+ *     non-finite or out-of-range value) before enqueuing anything, VM_ERR_CUDA when a
+ *     CUDA runtime call fails, and VM_OK otherwise.  Failures found on the device
+ *     (hash table or pool exhausted) are recorded in a sticky status word, never by
+ *     trapping; vm_last_error synchronises and returns it.  After a device failure the
+ *     volume's contents are unspecified but it can still be destroyed.
+ */
+#ifndef VMESH_H
+#define VMESH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vm_volume vm_volume;
+
+typedef enum {
+  VM_OK = 0,
+  VM_ERR_INVALID_ARG = 1, /* bad argument; nothing was enqueued */
+  VM_ERR_HASH_FULL = 2,   /* device: no free hash bucket for a new block */
+  VM_ERR_POOL_FULL = 3,   /* device: block, vertex, triangle pool or a work list exhausted */
+  VM_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+  VM_ERR_OOM = 5          /* device memory allocation failed */
+} vm_status;
+
+/* Volume parameters (Sec. VI: 8^3 blocks, cube size 8 mm .. 3 cm). */
+typedef struct {
+  float voxel_size;       /* cube side l in metres, >= 1e-4 */
+  float trunc;            /* truncation distance mu in metres, 0 < mu <= 32 l */
+  float eps_refine;       /* epsilon of Eq. 5 in metres (proportional to l; 0.2 l is typical), >= 0 */
+  float w_max;            /* cap of the fusion weight, >= 1 */
+  uint32_t hash_buckets;  /* power of two, 2^4 .. 2^30 */
+  uint32_t max_blocks;    /* block pool size, 1 .. 2^20 */
+  uint32_t max_vertices;  /* vertex pool size, 1 .. 2^30 */
+  uint32_t max_triangles; /* triangle pool size, 1 .. 2^30 */
+} vm_params;
+
+typedef struct {
+  int32_t width, height; /* pixels, 1 .. 16384 each */
+  float fx, fy, cx, cy;  /* pinhole intrinsics in pixels, fx, fy > 0; every pixel ray's
+                            slope |(u - cx) / fx|, |(v - cy) / fy| must be <= 64 */
+} vm_intrinsics;
+
+/* Per-call counters, filled by vm_get_stats (which synchronises). */
+typedef struct {
+  int64_t frame_blocks;      /* blocks collected by the last integrate_depth (N_t) */
+  int64_t new_blocks;        /* blocks allocated since the volume was created */
+  int64_t update_blocks;     /* blocks in the update set of the last mesh pass */
+  int64_t changed_cubes;     /* cubes whose effective type changed in the last mesh pass */
+  int64_t live_blocks;       /* allocated blocks */
+  int64_t live_vertices;     /* vertices in the pool (includes zero-reference ones awaiting gc) */
+  int64_t live_triangles;    /* triangles in the pool */
+  int64_t freed_blocks;      /* blocks recycled since the volume was created */
+  int64_t freed_vertices;    /* vertices recycled since the volume was created */
+  int64_t created_vertices;  /* vertices created since the volume was created */
+  int64_t hash_tombstones;   /* dead hash buckets awaiting a rehash */
+  int64_t block_high_water;  /* block pool slots ever used */
+} vm_frame_stats;
+
+/* Flags of vm_update_mesh / vm_step. */
+#define VM_FULL 1   /* process every allocated block, not only the frame's update set */
+#define VM_REFINE 2 /* apply the refinement of Eqs. 3-5 in the same pass */
+#define VM_GC 4     /* vm_step only: run gc after the mesh update */
+
+/* Create a volume: allocates and clears all of its device memory on `cuda_stream`
+ * (a cudaStream_t; NULL = legacy default stream).  *out receives the handle. */
+vm_status vm_create_volume(const vm_params* params, void* cuda_stream, vm_volume** out);
+
+/* Synchronise the volume's stream and free everything it owns.  NULL is accepted. */
+vm_status vm_destroy_volume(vm_volume* vol);
+
+/* Change the stream later calls enqueue on. */
+vm_status vm_set_stream(vm_volume* vol, void* cuda_stream);
+
+/* Sec. V-A.  depth_dev: device pointer to height x width float32, row-major, 0 or
+ * non-finite = invalid.  Collects every block crossed by the segment of camera depths
+ * [max(D - mu, 0.05), D + mu] on each valid pixel's ray (Eq. 1), allocates the new ones,
+ * then fuses the frame into every voxel of the collected blocks (Eq. 2): nearest pixel
+ * floor(u + 0.5), sdf = D - z_c, skip when sdf < -mu, d <- (d W + min(sdf, mu)) / (W + 1),
+ * W <- min(W + 1, w_max).  Blocks collected since the last vm_update_mesh accumulate
+ * into the next update set. */
+vm_status vm_integrate_depth(vm_volume* vol, const float* depth_dev, const vm_intrinsics* intr,
+                             const float T_wc[16], const float T_cw[16]);
+
+/* Secs. V-B..V-D.  Recomputes the cube types of the update set (blocks collected since
+ * the previous update plus their existing neighbours at offsets {0,-1}^3 \ {0}; all
+ * blocks with VM_FULL); a cube is valid when its 8 corners are allocated with W > 0,
+ * otherwise its type is 0.  Stores the previous effective type as t_{i-1}, keeps a
+ * cube's triangles when its type is unchanged, otherwise releases them and emits the
+ * marching-cubes triangles of the new type on edge-owned vertices, creating vertices
+ * on first use and updating the positions and normals of the update set's existing
+ * vertices.  VM_REFINE applies Eqs. 3-5 in the same pass (same result as a following
+ * vm_refine_mesh). */
+vm_status vm_update_mesh(vm_volume* vol, int flags);
+
+/* Sec. V-F, Eqs. 3-5, over the last update set (all blocks when full != 0): a valid
+ * cube whose raw type t_i is within Hamming distance 3 of its stored t_{i-1} takes the
+ * nearest regular type t_rj within distance 3 whose differing corners all have
+ * |d| < eps_refine (ties: the first in the paper's list); then re-triangulates. */
+vm_status vm_refine_mesh(vm_volume* vol, int full);
+
+/* Sec. V-E.  Recycles vertices whose reference count dropped to 0 and blocks that were
+ * not collected since the last update, carry no triangle (nor do their 7 lower
+ * neighbours), own no vertex, and whose voxels all have W = 0 or d >= mu.  Freed
+ * triangles were already recycled by the mesh passes. */
+vm_status vm_gc(vm_volume* vol);
+
+/* One frame: integrate_depth, then update_mesh(flags & (VM_FULL | VM_REFINE)), then gc
+ * when flags has VM_GC.  With use_graph != 0 the device work after the first call is
+ * replayed from a CUDA graph captured on that first call with the same flags. */
+vm_status vm_step(vm_volume* vol, const float* depth_dev, const vm_intrinsics* intr, const float T_wc[16],
+                  const float T_cw[16], int flags, int use_graph);
+
+/* Synchronises; counts of the vertices with a positive reference count and of the live
+ * triangles, i.e. the sizes vm_download_mesh writes. */
+vm_status vm_mesh_counts(vm_volume* vol, int64_t* n_vertices, int64_t* n_triangles);
+
+/* Synchronises; compacts the live mesh (Sec. VI "compress").  Buffers are device
+ * pointers when on_device != 0, host pointers otherwise, sized from vm_mesh_counts:
+ *   pos       n_vertices x 3 float32, world metres
+ *   nrm       n_vertices x 3 float32, unit normal (zero when undefined)
+ *   tris      n_triangles x 3 int32, indices into pos, oriented so that the normal
+ *             points from negative to positive TSDF
+ *   edge_keys n_vertices uint64 (optional, may be NULL): owner voxel coordinates biased
+ *             by 2^19 in bits 42-61, 22-41, 2-21 and the edge axis in bits 0-1
+ *   refcount  n_vertices int32 (optional, may be NULL): the vertex reference count */
+vm_status vm_download_mesh(vm_volume* vol, float* pos, float* nrm, int32_t* tris, uint64_t* edge_keys,
+                           int32_t* refcount, int on_device);
+
+/* Enqueues (without waiting) a copy of the live vertex and triangle counts, 2 x int32,
+ * to dst: pinned host memory when on_device == 0 (valid once the stream reaches the
+ * copy), device memory otherwise.  The counts include zero-reference vertices that the
+ * next gc will recycle. */
+vm_status vm_mesh_size_async(vm_volume* vol, int32_t* dst, int on_device);
+
+/* Synchronises and fills *stats. */
+vm_status vm_get_stats(vm_volume* vol, vm_frame_stats* stats);
+
+/* Synchronises and returns the sticky device status (VM_OK when none). */
+vm_status vm_last_error(vm_volume* vol);
+
+/* Synchronises; number of allocated blocks. */
+vm_status vm_num_blocks(vm_volume* vol, int64_t* n);
+
+/* Synchronises; copies every allocated block to host buffers sized from vm_num_blocks
+ * (any order): keys n x 3 int32, tsdf and weight n x 512 float32, code_eff and
+ * code_prev n x 512 uint8 (current and previous effective cube types).  Any output may
+ * be NULL. */
+vm_status vm_export_blocks(vm_volume* vol, int32_t* keys, float* tsdf, float* weight, uint8_t* code_eff,
+                           uint8_t* code_prev);
+
+/* Allocates the blocks `keys` (host, n x 3 int32, distinct) if needed and overwrites
+ * their voxels from host tsdf and weight (n x 512 float32 each); the blocks join the
+ * next update set as if collected by a frame.  For analytic fills. */
+vm_status vm_set_blocks(vm_volume* vol, const int32_t* keys, int64_t n, const float* tsdf,
+                        const float* weight);
+
+/* Device time of the library's kernels, accumulated while timing is on (CUDA events on
+ * the volume's stream around each launch; inside a vm_step CUDA graph they are event-record
+ * nodes, whose times are added when the next replay starts or vm_kernel_times is called).
+ * enable != 0 turns it on and clears the totals (a captured frame graph is re-captured).
+ * vm_kernel_times synchronises and writes up to `cap` entries of (name, total
+ * milliseconds, launches); returns the number of kernels in *n. */
+vm_status vm_enable_timing(vm_volume* vol, int enable);
+vm_status vm_kernel_times(vm_volume* vol, const char** names, double* total_ms, int64_t* launches, int cap,
+                          int* n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VMESH_H */

@@ -57,7 +57,10 @@
  *     they need no separate state here.  A block is freed when it was not
  *     collected since the last epoch change, no cube of it or of its 7 lower
  *     neighbours has triangles, none of its voxels owns a referenced edge, and
- *     every voxel has W = 0 or d >= mu.
+ *     every voxel has W = 0 or d >= mu.  The paper recycles vertices only; block
+ *     recycling is this implementation's addition.  A gc between a frame's
+ *     integration and its mesh update keeps the pending update set; a gc after the
+ *     mesh update empties the update set (a refinement pass after gc does nothing).
  */
 #include <math.h>
 #include <stdint.h>
@@ -652,9 +655,24 @@ int or_gc(void* h) {
   ovol* V = (ovol*)h;
   int* kill = (int*)calloc((size_t)(V->nblocks > 0 ? V->nblocks : 1), sizeof(int));
   int nk = 0;
+  /* Before the collected blocks are meshed, the pending update set (collected blocks and
+   * their lower neighbours) is kept whole; after a mesh update the update set is done with
+   * and emptied here. */
+  const int consumed = V->advance_pending;
+  for (int b = 0; b < V->nblocks; ++b) V->blocks[b]->mark = 0;
+  if (!consumed)
+    for (int j = 0; j < V->npending; ++j) {
+      oblock* P = V->blocks[V->pending[j]];
+      P->mark = 1;
+      for (int o = 0; o < 7; ++o) {
+        int n = find_block(V, P->key[0] + LOWER[o][0], P->key[1] + LOWER[o][1], P->key[2] + LOWER[o][2]);
+        if (n >= 0) V->blocks[n]->mark = 1;
+      }
+    }
   for (int b = 0; b < V->nblocks; ++b) {
     oblock* B = V->blocks[b];
     if (!B->alive || B->touch_epoch == V->epoch) continue;
+    if (!consumed && B->mark) continue;
     if (block_has_triangles(B)) continue;
     int near = 0;
     for (int i = 0; i < BV && !near; ++i)
@@ -673,6 +691,7 @@ int or_gc(void* h) {
   for (int b = 0; b < V->nblocks; ++b)
     if (kill[b]) V->blocks[b]->alive = 0;
   free(kill);
+  if (consumed) V->nlast = 0;
   if (nk) {
     /* compact the pending and last-update lists, then the map */
     int n = 0;

@@ -1,0 +1,223 @@
+// Mesh compaction for download (the "compress" step of Sec. VI) and the block
+// export / analytic-fill paths used by tests.  None of these run per frame.
+#pragma once
+
+#include "kernels_fusion.cuh"
+#include "vmesh_device.cuh"
+
+namespace vmk {
+
+constexpr int SCAN_ITEMS = 1024;  // items per CTA (256 threads x 4)
+
+// Phase 1: per-CTA count of live vertices (refcount > 0) or live triangles (x >= 0).
+template <bool TRI>
+__global__ void __launch_bounds__(256) k_count_live(Vol V, int* cta_counts) {
+  const int n = TRI ? min(__ldcg(&V.ctl->c[C_TRI_BUMP]), V.max_triangles)
+                    : min(__ldcg(&V.ctl->c[C_VTX_BUMP]), V.max_vertices);
+  const int base = blockIdx.x * SCAN_ITEMS;
+  int cnt = 0;
+  if (base < n) {
+    for (int j = threadIdx.x; j < SCAN_ITEMS && base + j < n; j += 256) {
+      bool live = TRI ? V.tris[base + j].x >= 0 : V.vref[base + j] > 0;
+      cnt += live;
+    }
+  }
+  __shared__ int s;
+  if (threadIdx.x == 0) s = 0;
+  __syncthreads();
+  atomicAdd(&s, cnt);
+  __syncthreads();
+  if (threadIdx.x == 0) cta_counts[blockIdx.x] = s;
+}
+
+// Phase 2 (one CTA): exclusive scan of the CTA counts in place; total to *total.
+__global__ void __launch_bounds__(1024) k_scan_counts(int* cta_counts, int n, int* total) {
+  __shared__ int carry;
+  __shared__ int warp_sums[32];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < n; base += 1024) {
+    int i = base + threadIdx.x;
+    int v = i < n ? cta_counts[i] : 0;
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      int s = warp_sums[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += y;
+      }
+      warp_sums[lane] = s;
+    }
+    __syncthreads();
+    int incl = x + (w > 0 ? warp_sums[w - 1] : 0);
+    if (i < n) cta_counts[i] = carry + incl - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+__device__ __forceinline__ uint64_t edge_key_of(const Vol& V, int e) {
+  const int ob = e / EPB, r = e - ob * EPB, ov = r / 3, a = r - ov * 3;
+  int4 k = V.bkey[ob];
+  int gx = k.x * BS + (ov & 7), gy = k.y * BS + ((ov >> 3) & 7), gz = k.z * BS + (ov >> 6);
+  return ((uint64_t)(uint32_t)(gx + (1 << 19)) << 42) | ((uint64_t)(uint32_t)(gy + (1 << 19)) << 22) |
+         ((uint64_t)(uint32_t)(gz + (1 << 19)) << 2) | (uint64_t)a;
+}
+
+// Phase 3 (vertices): stable compaction; remap[v] = new index (or -1).
+__global__ void __launch_bounds__(256) k_compact_vertices(Vol V, const int* cta_offsets, int* remap, float* pos,
+                                                          float* nrm, uint64_t* keys, int* refcount) {
+  const int n = min(__ldcg(&V.ctl->c[C_VTX_BUMP]), V.max_vertices);
+  const int base = blockIdx.x * SCAN_ITEMS;
+  if (base >= n) return;
+  __shared__ int warp_tot[8];
+  __shared__ int running;
+  if (threadIdx.x == 0) running = cta_offsets[blockIdx.x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int j0 = 0; j0 < SCAN_ITEMS; j0 += 256) {
+    int v = base + j0 + threadIdx.x;
+    bool live = v < n && V.vref[v] > 0;
+    unsigned b = __ballot_sync(0xffffffffu, live);
+    if (lane == 0) warp_tot[w] = __popc(b);
+    __syncthreads();
+    int off = running;
+    for (int q = 0; q < w; ++q) off += warp_tot[q];
+    off += __popc(b & ((1u << lane) - 1));
+    if (v < n) remap[v] = live ? off : -1;
+    if (live) {
+      float4 p = V.vpos[v], q4 = V.vnrm[v];
+      pos[3 * (size_t)off] = p.x; pos[3 * (size_t)off + 1] = p.y; pos[3 * (size_t)off + 2] = p.z;
+      nrm[3 * (size_t)off] = q4.x; nrm[3 * (size_t)off + 1] = q4.y; nrm[3 * (size_t)off + 2] = q4.z;
+      if (keys) keys[off] = edge_key_of(V, V.vedge[v]);
+      if (refcount) refcount[off] = V.vref[v];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int t = 0;
+      for (int q = 0; q < 8; ++q) t += warp_tot[q];
+      running += t;
+    }
+    __syncthreads();
+  }
+}
+
+// Phase 3 (triangles): stable compaction with vertex indices remapped.
+__global__ void __launch_bounds__(256) k_compact_triangles(Vol V, const int* cta_offsets, const int* remap,
+                                                           int* tris_out) {
+  const int n = min(__ldcg(&V.ctl->c[C_TRI_BUMP]), V.max_triangles);
+  const int base = blockIdx.x * SCAN_ITEMS;
+  if (base >= n) return;
+  __shared__ int warp_tot[8];
+  __shared__ int running;
+  if (threadIdx.x == 0) running = cta_offsets[blockIdx.x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int j0 = 0; j0 < SCAN_ITEMS; j0 += 256) {
+    int t = base + j0 + threadIdx.x;
+    int4 tr = t < n ? V.tris[t] : make_int4(-1, -1, -1, -1);
+    bool live = tr.x >= 0;
+    unsigned b = __ballot_sync(0xffffffffu, live);
+    if (lane == 0) warp_tot[w] = __popc(b);
+    __syncthreads();
+    int off = running;
+    for (int q = 0; q < w; ++q) off += warp_tot[q];
+    off += __popc(b & ((1u << lane) - 1));
+    if (live) {
+      tris_out[3 * (size_t)off] = remap[tr.x];
+      tris_out[3 * (size_t)off + 1] = tr.y >= 0 ? remap[tr.y] : -1;
+      tris_out[3 * (size_t)off + 2] = tr.z >= 0 ? remap[tr.z] : -1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int s = 0;
+      for (int q = 0; q < 8; ++q) s += warp_tot[q];
+      running += s;
+    }
+    __syncthreads();
+  }
+}
+
+// Export every live block (any order) into dense buffers.
+__global__ void __launch_bounds__(256) k_export_blocks(Vol V, int* counter, int* keys, float* tsdf, float* weight,
+                                                       uint8_t* ce, uint8_t* cp) {
+  const int hw = min(__ldcg(&V.ctl->c[C_BLK_BUMP]), V.max_blocks);
+  __shared__ int slot;
+  for (int blk = blockIdx.x; blk < hw; blk += gridDim.x) {
+    int4 k = V.bkey[blk];
+    if (k.w < 0) continue;
+    if (threadIdx.x == 0) slot = atomicAdd(counter, 1);
+    __syncthreads();
+    const int j = slot;
+    if (threadIdx.x == 0) {
+      keys[3 * j] = k.x; keys[3 * j + 1] = k.y; keys[3 * j + 2] = k.z;
+    }
+    for (int v = threadIdx.x; v < BV; v += blockDim.x) {
+      float2 q = V.tw[(size_t)blk * BV + v];
+      tsdf[(size_t)j * BV + v] = q.x;
+      weight[(size_t)j * BV + v] = q.y;
+      ce[(size_t)j * BV + v] = V.code_eff[(size_t)blk * BV + v];
+      cp[(size_t)j * BV + v] = V.code_prev[(size_t)blk * BV + v];
+    }
+    __syncthreads();
+  }
+}
+
+// Analytic fill, phase 1: insert the given keys as if collected by a frame.
+__global__ void __launch_bounds__(256) k_fill_insert(Vol V, const int* keys, int n, int advance_epoch) {
+  const uint32_t frame = (uint32_t)__ldcg(&V.ctl->c[C_FRAME]);
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    int x = keys[3 * j], y = keys[3 * j + 1], z = keys[3 * j + 2];
+    if (abs(x) > KEY_LIMIT || abs(y) > KEY_LIMIT || abs(z) > KEY_LIMIT) {
+      set_status(V, ST_INVALID);
+      continue;
+    }
+    int s = hash_insert(V, pack_key(x, y, z), x, y, z);
+    if (s >= 0) touch_bucket(V, s, frame);
+  }
+  if (last_block(V, C_DONE0)) {
+    if (threadIdx.x == 0) {
+      fold_top(V, C_BLK_TOP);
+      if (advance_epoch) {
+        V.ctl->c[C_EPOCH] += 1;
+        V.ctl->c[C_N_UPDATE] = 0;
+      }
+      V.ctl->c[C_DONE0] = 0;
+    }
+  }
+}
+
+// Analytic fill, phase 2 (after k_resolve): copy the voxel values, set the near flag.
+__global__ void __launch_bounds__(256) k_fill_copy(Vol V, const int* keys, const float* tsdf, const float* weight,
+                                                   int n) {
+  for (int j = blockIdx.x; j < n; j += gridDim.x) {
+    int blk = find_block(V, keys[3 * j], keys[3 * j + 1], keys[3 * j + 2]);
+    if (blk < 0) continue;
+    bool near = false;
+    for (int v = threadIdx.x; v < BV; v += blockDim.x) {
+      float d = tsdf[(size_t)j * BV + v], w = weight[(size_t)j * BV + v];
+      V.tw[(size_t)blk * BV + v] = make_float2(d, w);
+      near |= (w > 0.0f && d < V.mu);
+    }
+    int any = __syncthreads_or(near);
+    if (threadIdx.x == 0) V.bnear[blk] = (uint8_t)(any != 0);
+  }
+  if (last_block(V, C_DONE2)) {
+    if (threadIdx.x == 0) {
+      V.ctl->c[C_N_TOUCHED] = 0;
+      V.ctl->c[C_FRAME] += 1;
+      V.ctl->c[C_DONE2] = 0;
+    }
+  }
+}
+
+}  // namespace vmk

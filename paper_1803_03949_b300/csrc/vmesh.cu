@@ -1,0 +1,686 @@
+// C ABI of the vmesh library (declared in include/vmesh.h): volume lifetime, the
+// per-frame calls, CUDA-graph replay of a whole frame, per-kernel timing and the
+// download / export paths.  All device work is the kernels in this directory.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "vmesh.h"
+#include "kernels_fusion.cuh"
+#include "kernels_gc.cuh"
+#include "kernels_io.cuh"
+#include "kernels_mesh.cuh"
+#include "mc_table.h"
+#include "vmesh_device.cuh"
+
+using namespace vmk;
+
+namespace {
+
+enum KernelId {
+  K_SET_FRAME = 0, K_ALLOC, K_RESOLVE, K_INTEGRATE, K_LIST_ALL, K_MESH_TYPES, K_VERTICES, K_TRIANGLES,
+  K_GC_VERTICES, K_GC_BLOCKS, K_REHASH, K_COUNT_
+};
+const char* kKernelNames[K_COUNT_] = {"k_set_frame", "k_alloc",      "k_resolve",     "k_integrate",
+                                      "k_list_all",  "k_mesh_types", "k_vertices",    "k_triangles",
+                                      "k_gc_vertices", "k_gc_blocks", "k_rehash"};
+
+__global__ void k_set_frame(FrameParams* dst, FrameParams fp) { *dst = fp; }
+
+// Every allocated block joins the update set (full extraction).
+__global__ void __launch_bounds__(256) k_list_all(Vol V) {
+  const int hw = min(__ldcg(&V.ctl->c[C_BLK_BUMP]), V.max_blocks);
+  const uint32_t epoch = (uint32_t)__ldcg(&V.ctl->c[C_EPOCH]);
+  for (int blk = blockIdx.x * blockDim.x + threadIdx.x; blk < hw; blk += gridDim.x * blockDim.x) {
+    int4 k = V.bkey[blk];
+    if (k.w < 0) continue;
+    V.ustamp[k.w] = epoch;
+    list_push(V, V.update, C_N_UPDATE, V.list_cap_update, blk);
+  }
+}
+
+struct TimingRec {
+  int kernel;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct vm_volume {
+  vm_params p;
+  Vol V;
+  cudaStream_t stream = nullptr;
+  int num_sms = 148;
+  bool advance_pending = false;
+  std::vector<void*> allocs;
+  // download scratch
+  int* cta_counts = nullptr;
+  int* scan_total = nullptr;
+  int* remap = nullptr;
+  int cta_cap = 0;
+  // timing
+  bool timing = false;
+  bool capturing = false;
+  std::vector<TimingRec> recs;
+  std::vector<TimingRec> graph_recs;  // event-record nodes of the captured frame graph
+  bool graph_pending = false;         // a replay's node timings not yet collected
+  std::vector<cudaEvent_t> event_pool;
+  double tot_ms[K_COUNT_] = {0};
+  long long launches[K_COUNT_] = {0};
+  // graph replay of vm_step
+  cudaGraphExec_t graph_exec = nullptr;
+  int graph_flags = -1;
+  int graph_W = -1, graph_H = -1;
+};
+
+namespace {
+
+vm_status cuda_status(cudaError_t e) { return e == cudaSuccess ? VM_OK : VM_ERR_CUDA; }
+
+cudaEvent_t get_event(vm_volume* v) {
+  if (!v->event_pool.empty()) {
+    cudaEvent_t e = v->event_pool.back();
+    v->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Launch helper: records a pair of events around the launch while timing is on.  During
+// graph capture the records become event-record nodes of the graph (their timings are
+// collected after each replay).
+template <typename F>
+vm_status launch(vm_volume* v, int kid, F&& f) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (v->timing) {
+    a = get_event(v);
+    b = get_event(v);
+    if (v->capturing) cudaEventRecordWithFlags(a, v->stream, cudaEventRecordExternal);
+    else cudaEventRecord(a, v->stream);
+  }
+  f();
+  cudaError_t e = cudaGetLastError();
+  if (v->timing) {
+    if (v->capturing) {
+      cudaEventRecordWithFlags(b, v->stream, cudaEventRecordExternal);
+      v->graph_recs.push_back({kid, a, b});
+    } else {
+      cudaEventRecord(b, v->stream);
+      v->recs.push_back({kid, a, b});
+    }
+  }
+  return cuda_status(e);
+}
+
+// Add the timings of the last graph replay (waits for it).
+void collect_graph_timing(vm_volume* v) {
+  if (!v->graph_pending) return;
+  v->graph_pending = false;
+  for (auto& r : v->graph_recs) {
+    float ms = 0;
+    cudaEventSynchronize(r.b);
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      v->tot_ms[r.kernel] += ms;
+      v->launches[r.kernel] += 1;
+    }
+  }
+}
+
+template <typename T>
+bool dalloc(vm_volume* v, T** p, size_t count, int fill_byte) {
+  void* q = nullptr;
+  size_t bytes = count * sizeof(T);
+  if (bytes == 0) bytes = sizeof(T);
+  if (cudaMalloc(&q, bytes) != cudaSuccess) return false;
+  v->allocs.push_back(q);
+  if (cudaMemsetAsync(q, fill_byte, bytes, v->stream) != cudaSuccess) return false;
+  *p = static_cast<T*>(q);
+  return true;
+}
+
+bool finite_all(const float* a, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+bool make_frame(const vm_intrinsics* K, const float* Twc, const float* Tcw, const float* depth, FrameParams* fp) {
+  if (!K || !Twc || !Tcw || !depth) return false;
+  if (K->width < 1 || K->height < 1 || K->width > 16384 || K->height > 16384) return false;
+  if (!(K->fx > 0) || !(K->fy > 0) || !std::isfinite(K->fx) || !std::isfinite(K->fy) || !std::isfinite(K->cx) ||
+      !std::isfinite(K->cy))
+    return false;
+  if (!finite_all(Twc, 16) || !finite_all(Tcw, 16)) return false;
+  // bound the slope of every pixel ray (a field of view below ~178 degrees)
+  const double sx = std::fmax(std::fabs((double)K->cx), std::fabs(K->width - 1 - (double)K->cx)) / K->fx;
+  const double sy = std::fmax(std::fabs((double)K->cy), std::fabs(K->height - 1 - (double)K->cy)) / K->fy;
+  if (!(sx <= 64.0) || !(sy <= 64.0)) return false;
+  fp->depth = depth;
+  fp->W = K->width;
+  fp->H = K->height;
+  fp->fx = K->fx;
+  fp->fy = K->fy;
+  fp->cx = K->cx;
+  fp->cy = K->cy;
+  for (int i = 0; i < 12; ++i) {
+    fp->Twc[i] = Twc[i];
+    fp->Tcw[i] = Tcw[i];
+  }
+  return true;
+}
+
+int grid_for(vm_volume* v, int per_sm) { return v->num_sms * per_sm; }
+
+// ---- enqueue helpers (no validation)
+vm_status enqueue_integrate(vm_volume* v, const FrameParams& fp, bool set_frame) {
+  vm_status st = VM_OK;
+  Ctl* ctl = v->V.ctl;
+  if (set_frame) st = launch(v, K_SET_FRAME, [&] { k_set_frame<<<1, 1, 0, v->stream>>>(&ctl->fp, fp); });
+  if (st) return st;
+  const int adv = v->advance_pending ? 1 : 0;
+  dim3 g((fp.W + ALLOC_TILE_W - 1) / ALLOC_TILE_W, (fp.H + ALLOC_TILE_H - 1) / ALLOC_TILE_H);
+  st = launch(v, K_ALLOC, [&] { k_alloc<<<g, ALLOC_THREADS, 0, v->stream>>>(v->V, &ctl->fp, adv); });
+  if (st) return st;
+  st = launch(v, K_RESOLVE, [&] { k_resolve<<<grid_for(v, 4), 256, 0, v->stream>>>(v->V); });
+  if (st) return st;
+  st = launch(v, K_INTEGRATE, [&] { k_integrate<<<grid_for(v, 8), INTEG_THREADS, 0, v->stream>>>(v->V, &ctl->fp); });
+  v->advance_pending = false;
+  return st;
+}
+
+vm_status enqueue_list_all(vm_volume* v) {
+  cudaError_t e = cudaMemsetAsync(&v->V.ctl->c[C_N_UPDATE], 0, sizeof(int), v->stream);
+  if (e != cudaSuccess) return VM_ERR_CUDA;
+  return launch(v, K_LIST_ALL, [&] { k_list_all<<<grid_for(v, 4), 256, 0, v->stream>>>(v->V); });
+}
+
+vm_status enqueue_mesh_pass(vm_volume* v, int mode) {
+  vm_status st = launch(v, K_MESH_TYPES, [&] { k_mesh_types<<<grid_for(v, 8), MESH_THREADS, 0, v->stream>>>(v->V, mode); });
+  if (st) return st;
+  st = launch(v, K_VERTICES, [&] { k_vertices<<<grid_for(v, 4), 256, 0, v->stream>>>(v->V); });
+  if (st) return st;
+  return launch(v, K_TRIANGLES, [&] { k_triangles<<<grid_for(v, 8), MESH_THREADS, 0, v->stream>>>(v->V); });
+}
+
+vm_status enqueue_update(vm_volume* v, int flags) {
+  vm_status st = VM_OK;
+  if (flags & VM_FULL) st = enqueue_list_all(v);
+  if (st) return st;
+  st = enqueue_mesh_pass(v, M_UPDATE | ((flags & VM_REFINE) ? M_REFINE : 0));
+  v->advance_pending = true;
+  return st;
+}
+
+vm_status enqueue_gc(vm_volume* v) {
+  vm_status st = launch(v, K_GC_VERTICES, [&] { k_gc_vertices<<<grid_for(v, 2), 256, 0, v->stream>>>(v->V); });
+  if (st) return st;
+  const int consumed = v->advance_pending ? 1 : 0;
+  st = launch(v, K_GC_BLOCKS, [&] { k_gc_blocks<<<grid_for(v, 8), 256, 0, v->stream>>>(v->V, consumed); });
+  if (st) return st;
+  return launch(v, K_REHASH, [&] {
+    k_rehash_check<<<1, 32, 0, v->stream>>>(v->V);
+    k_rehash_wipe<<<grid_for(v, 4), 256, 0, v->stream>>>(v->V);
+    k_rehash_insert<<<grid_for(v, 4), 256, 0, v->stream>>>(v->V);
+    k_rehash_mark<<<grid_for(v, 2), 256, 0, v->stream>>>(v->V);
+  });
+}
+
+vm_status sync_status(vm_volume* v) {
+  if (cudaStreamSynchronize(v->stream) != cudaSuccess) return VM_ERR_CUDA;
+  return VM_OK;
+}
+
+int read_counter(vm_volume* v, int c) {
+  int x = 0;
+  cudaMemcpy(&x, &v->V.ctl->c[c], sizeof(int), cudaMemcpyDeviceToHost);
+  return x;
+}
+
+void drop_graph(vm_volume* v) {
+  if (v->graph_exec) {
+    cudaStreamSynchronize(v->stream);
+    cudaGraphExecDestroy(v->graph_exec);
+  }
+  v->graph_exec = nullptr;
+  v->graph_flags = -1;
+  v->graph_pending = false;
+  for (auto& r : v->graph_recs) {
+    v->event_pool.push_back(r.a);
+    v->event_pool.push_back(r.b);
+  }
+  v->graph_recs.clear();
+}
+
+void free_all(vm_volume* v) {
+  drop_graph(v);
+  for (auto& r : v->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : v->event_pool) cudaEventDestroy(e);
+  for (void* p : v->allocs) cudaFree(p);
+  v->allocs.clear();
+}
+
+// vertex / triangle counts through the scan kernels; leaves offsets in cta_counts
+vm_status count_live(vm_volume* v, bool tri, int* total_out) {
+  const int items = tri ? v->p.max_triangles : v->p.max_vertices;
+  const int nct = (items + SCAN_ITEMS - 1) / SCAN_ITEMS;
+  if (tri) k_count_live<true><<<nct, 256, 0, v->stream>>>(v->V, v->cta_counts);
+  else k_count_live<false><<<nct, 256, 0, v->stream>>>(v->V, v->cta_counts);
+  k_scan_counts<<<1, 1024, 0, v->stream>>>(v->cta_counts, nct, v->scan_total);
+  if (cudaGetLastError() != cudaSuccess) return VM_ERR_CUDA;
+  if (cudaMemcpyAsync(total_out, v->scan_total, sizeof(int), cudaMemcpyDeviceToHost, v->stream) != cudaSuccess)
+    return VM_ERR_CUDA;
+  return sync_status(v);
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+vm_status vm_create_volume(const vm_params* p, void* cuda_stream, vm_volume** out) {
+  if (!p || !out) return VM_ERR_INVALID_ARG;
+  *out = nullptr;
+  const uint32_t hb = p->hash_buckets;
+  if (!(p->voxel_size >= 1e-4f) || !std::isfinite(p->voxel_size) || !(p->trunc > 0) ||
+      !(p->trunc <= 32.0f * p->voxel_size) || !(p->eps_refine >= 0) || !std::isfinite(p->eps_refine) ||
+      !(p->w_max >= 1) || !std::isfinite(p->w_max) || hb < 16 || hb > (1u << 30) || (hb & (hb - 1)) ||
+      p->max_blocks < 1 || p->max_blocks > (1u << 20) || p->max_vertices < 1 || p->max_vertices > (1u << 30) ||
+      p->max_triangles < 1 || p->max_triangles > (1u << 30))
+    return VM_ERR_INVALID_ARG;
+  static vmk_host::McTable table;
+  static bool table_built = false;
+  if (!table_built) {
+    vmk_host::build_mc_table(table);
+    table_built = true;
+  }
+  if (!table.ok) return VM_ERR_INVALID_ARG;
+
+  vm_volume* v = new vm_volume();
+  v->p = *p;
+  v->stream = static_cast<cudaStream_t>(cuda_stream);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (v->num_sms <= 0) v->num_sms = 148;
+  if (cudaMemcpyToSymbol(c_ntri, table.ntri, sizeof(table.ntri)) != cudaSuccess ||
+      cudaMemcpyToSymbol(c_tri, table.tri, sizeof(table.tri)) != cudaSuccess ||
+      cudaMemcpyToSymbol(c_edgemask, table.edgemask, sizeof(table.edgemask)) != cudaSuccess) {
+    delete v;
+    return VM_ERR_CUDA;
+  }
+
+  Vol& V = v->V;
+  V.l = p->voxel_size;
+  V.mu = p->trunc;
+  V.eps = p->eps_refine;
+  V.wmax = p->w_max;
+  V.hmask = hb - 1;
+  V.max_blocks = (int)p->max_blocks;
+  V.max_vertices = (int)p->max_vertices;
+  V.max_triangles = (int)p->max_triangles;
+  for (int L = 1; L <= 5; ++L) V.run_cap[L - 1] = (int)(p->max_triangles / L) + 1;
+  V.list_cap_touched = (int)(p->max_blocks < hb ? p->max_blocks : hb);
+  V.list_cap_update = (int)p->max_blocks;
+  V.list_cap_newedge = (int)p->max_vertices;
+  V.list_cap_dead = (int)((2ull * p->max_vertices) < (1ull << 31) - 1 ? 2ull * p->max_vertices : (1ull << 31) - 1);
+  const size_t NB = p->max_blocks, NV = p->max_vertices, NT = p->max_triangles;
+  bool ok = dalloc(v, &V.keys, hb, 0xFF) && dalloc(v, &V.vals, hb, 0xFF) && dalloc(v, &V.stamp, hb, 0) &&
+            dalloc(v, &V.ustamp, hb, 0) && dalloc(v, &V.bkey, NB, 0xFF) && dalloc(v, &V.bntri, NB, 0) &&
+            dalloc(v, &V.bnvert, NB, 0) && dalloc(v, &V.bnear, NB, 0) && dalloc(v, &V.bepoch, NB, 0) &&
+            dalloc(v, &V.tw, NB * BV, 0) && dalloc(v, &V.code_eff, NB * BV, 0) &&
+            dalloc(v, &V.code_prev, NB * BV, 0) && dalloc(v, &V.vmask, NB * BV, 0) && dalloc(v, &V.chg, NB * BV, 0) &&
+            dalloc(v, &V.edge_vtx, NB * BV * 3, 0xFF) && dalloc(v, &V.tri_base, NB * BV, 0xFF) &&
+            dalloc(v, &V.vpos, NV, 0) && dalloc(v, &V.vnrm, NV, 0) && dalloc(v, &V.vref, NV, 0xFF) &&
+            dalloc(v, &V.vedge, NV, 0xFF) && dalloc(v, &V.tris, NT, 0xFF) && dalloc(v, &V.blk_free, NB, 0) &&
+            dalloc(v, &V.vtx_free, NV, 0) && dalloc(v, &V.touched, (size_t)V.list_cap_touched, 0) &&
+            dalloc(v, &V.touched_blk, (size_t)V.list_cap_touched, 0) && dalloc(v, &V.update, NB, 0) &&
+            dalloc(v, &V.newedge, NV, 0) && dalloc(v, &V.dead, (size_t)V.list_cap_dead, 0) &&
+            dalloc(v, &V.ctl, 1, 0);
+  for (int L = 0; L < 5 && ok; ++L) ok = dalloc(v, &V.run_free[L], (size_t)V.run_cap[L], 0);
+  if (!ok) {
+    free_all(v);
+    delete v;
+    return VM_ERR_OOM;
+  }
+  int init[3] = {0, 1, 1};  // status, frame, epoch
+  if (cudaMemcpyAsync(V.ctl->c, init, sizeof(init), cudaMemcpyHostToDevice, v->stream) != cudaSuccess ||
+      cudaStreamSynchronize(v->stream) != cudaSuccess) {
+    free_all(v);
+    delete v;
+    return VM_ERR_CUDA;
+  }
+  *out = v;
+  return VM_OK;
+}
+
+vm_status vm_destroy_volume(vm_volume* v) {
+  if (!v) return VM_OK;
+  cudaStreamSynchronize(v->stream);
+  free_all(v);
+  delete v;
+  return VM_OK;
+}
+
+vm_status vm_set_stream(vm_volume* v, void* s) {
+  if (!v) return VM_ERR_INVALID_ARG;
+  v->stream = static_cast<cudaStream_t>(s);
+  drop_graph(v);
+  return VM_OK;
+}
+
+vm_status vm_integrate_depth(vm_volume* v, const float* depth, const vm_intrinsics* K, const float Twc[16],
+                             const float Tcw[16]) {
+  if (!v) return VM_ERR_INVALID_ARG;
+  FrameParams fp;
+  if (!make_frame(K, Twc, Tcw, depth, &fp)) return VM_ERR_INVALID_ARG;
+  return enqueue_integrate(v, fp, true);
+}
+
+vm_status vm_update_mesh(vm_volume* v, int flags) {
+  if (!v || (flags & ~(VM_FULL | VM_REFINE))) return VM_ERR_INVALID_ARG;
+  return enqueue_update(v, flags);
+}
+
+vm_status vm_refine_mesh(vm_volume* v, int full) {
+  if (!v) return VM_ERR_INVALID_ARG;
+  vm_status st = VM_OK;
+  if (full) st = enqueue_list_all(v);
+  if (st) return st;
+  return enqueue_mesh_pass(v, M_REFINE);
+}
+
+vm_status vm_gc(vm_volume* v) {
+  if (!v) return VM_ERR_INVALID_ARG;
+  return enqueue_gc(v);
+}
+
+vm_status vm_step(vm_volume* v, const float* depth, const vm_intrinsics* K, const float Twc[16], const float Tcw[16],
+                  int flags, int use_graph) {
+  if (!v || (flags & ~(VM_FULL | VM_REFINE | VM_GC))) return VM_ERR_INVALID_ARG;
+  FrameParams fp;
+  if (!make_frame(K, Twc, Tcw, depth, &fp)) return VM_ERR_INVALID_ARG;
+  vm_status st = launch(v, K_SET_FRAME, [&] { k_set_frame<<<1, 1, 0, v->stream>>>(&v->V.ctl->fp, fp); });
+  if (st) return st;
+  auto body = [&]() -> vm_status {
+    vm_status s = enqueue_integrate(v, fp, false);
+    if (s) return s;
+    s = enqueue_update(v, flags & (VM_FULL | VM_REFINE));
+    if (s) return s;
+    if (flags & VM_GC) s = enqueue_gc(v);
+    return s;
+  };
+  // A frame graph is captured with the epoch advancing at its start, i.e. for frames that
+  // follow a mesh update; other frames run as plain launches.
+  if (!use_graph || !v->advance_pending) return body();
+  if (!v->graph_exec || v->graph_flags != flags || v->graph_W != fp.W || v->graph_H != fp.H) {
+    drop_graph(v);
+    cudaGraph_t g = nullptr;
+    v->capturing = true;
+    if (cudaStreamBeginCapture(v->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      v->capturing = false;
+      return VM_ERR_CUDA;
+    }
+    vm_status s = body();
+    cudaError_t e = cudaStreamEndCapture(v->stream, &g);
+    v->capturing = false;
+    if (s) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    if (e != cudaSuccess) return VM_ERR_CUDA;
+    e = cudaGraphInstantiate(&v->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      v->graph_exec = nullptr;
+      return VM_ERR_CUDA;
+    }
+    v->graph_flags = flags;
+    v->graph_W = fp.W;
+    v->graph_H = fp.H;
+  }
+  v->advance_pending = true;
+  collect_graph_timing(v);  // a previous replay's node events are about to be re-recorded
+  cudaError_t e = cudaGraphLaunch(v->graph_exec, v->stream);
+  v->graph_pending = v->timing && !v->graph_recs.empty();
+  return cuda_status(e);
+}
+
+vm_status vm_last_error(vm_volume* v) {
+  if (!v) return VM_ERR_INVALID_ARG;
+  if (sync_status(v)) return VM_ERR_CUDA;
+  int st = read_counter(v, C_STATUS);
+  return (vm_status)st;
+}
+
+static vm_status ensure_scan_scratch(vm_volume* v) {
+  if (v->remap) return VM_OK;
+  const int items = v->p.max_vertices > v->p.max_triangles ? v->p.max_vertices : v->p.max_triangles;
+  v->cta_cap = (items + SCAN_ITEMS - 1) / SCAN_ITEMS + 1;
+  if (!dalloc(v, &v->cta_counts, (size_t)v->cta_cap, 0) || !dalloc(v, &v->scan_total, 1, 0) ||
+      !dalloc(v, &v->remap, v->p.max_vertices, 0xFF))
+    return VM_ERR_OOM;
+  return VM_OK;
+}
+
+vm_status vm_mesh_counts(vm_volume* v, int64_t* nv, int64_t* nt) {
+  if (!v || !nv || !nt) return VM_ERR_INVALID_ARG;
+  vm_status st = ensure_scan_scratch(v);
+  if (st) return st;
+  int a = 0, b = 0;
+  if ((st = count_live(v, false, &a))) return st;
+  if ((st = count_live(v, true, &b))) return st;
+  *nv = a;
+  *nt = b;
+  return VM_OK;
+}
+
+vm_status vm_download_mesh(vm_volume* v, float* pos, float* nrm, int32_t* tris, uint64_t* keys, int32_t* refcount,
+                           int on_device) {
+  if (!v || !pos || !nrm || !tris) return VM_ERR_INVALID_ARG;
+  vm_status st = ensure_scan_scratch(v);
+  if (st) return st;
+  int nv = 0, nt = 0;
+  // vertices: count, scan, compact (writes remap)
+  if ((st = count_live(v, false, &nv))) return st;
+  float *dpos = pos, *dnrm = nrm;
+  int32_t* dtris = tris;
+  uint64_t* dkeys = keys;
+  int32_t* dref = refcount;
+  std::vector<void*> tmp;
+  auto tmp_alloc = [&](size_t bytes) -> void* {
+    void* q = nullptr;
+    if (cudaMalloc(&q, bytes ? bytes : 4) != cudaSuccess) return nullptr;
+    tmp.push_back(q);
+    return q;
+  };
+  auto cleanup = [&]() {
+    for (void* q : tmp) cudaFree(q);
+  };
+  if (!on_device) {
+    dpos = (float*)tmp_alloc((size_t)nv * 12);
+    dnrm = (float*)tmp_alloc((size_t)nv * 12);
+    dkeys = keys ? (uint64_t*)tmp_alloc((size_t)nv * 8) : nullptr;
+    dref = refcount ? (int32_t*)tmp_alloc((size_t)nv * 4) : nullptr;
+    if (!dpos || !dnrm || (keys && !dkeys) || (refcount && !dref)) {
+      cleanup();
+      return VM_ERR_OOM;
+    }
+  }
+  const int nctv = (v->p.max_vertices + SCAN_ITEMS - 1) / SCAN_ITEMS;
+  k_compact_vertices<<<nctv, 256, 0, v->stream>>>(v->V, v->cta_counts, v->remap, dpos, dnrm, dkeys, dref);
+  if (cudaGetLastError() != cudaSuccess) {
+    cleanup();
+    return VM_ERR_CUDA;
+  }
+  if ((st = count_live(v, true, &nt))) {
+    cleanup();
+    return st;
+  }
+  if (!on_device) {
+    dtris = (int32_t*)tmp_alloc((size_t)nt * 12);
+    if (!dtris) {
+      cleanup();
+      return VM_ERR_OOM;
+    }
+  }
+  const int nctt = (v->p.max_triangles + SCAN_ITEMS - 1) / SCAN_ITEMS;
+  k_compact_triangles<<<nctt, 256, 0, v->stream>>>(v->V, v->cta_counts, v->remap, dtris);
+  if (cudaGetLastError() != cudaSuccess) {
+    cleanup();
+    return VM_ERR_CUDA;
+  }
+  if (!on_device) {
+    cudaStreamSynchronize(v->stream);
+    bool ok = cudaMemcpy(pos, dpos, (size_t)nv * 12, cudaMemcpyDeviceToHost) == cudaSuccess &&
+              cudaMemcpy(nrm, dnrm, (size_t)nv * 12, cudaMemcpyDeviceToHost) == cudaSuccess &&
+              cudaMemcpy(tris, dtris, (size_t)nt * 12, cudaMemcpyDeviceToHost) == cudaSuccess &&
+              (!keys || cudaMemcpy(keys, dkeys, (size_t)nv * 8, cudaMemcpyDeviceToHost) == cudaSuccess) &&
+              (!refcount || cudaMemcpy(refcount, dref, (size_t)nv * 4, cudaMemcpyDeviceToHost) == cudaSuccess);
+    cleanup();
+    return ok ? VM_OK : VM_ERR_CUDA;
+  }
+  return sync_status(v);
+}
+
+vm_status vm_mesh_size_async(vm_volume* v, int32_t* dst, int on_device) {
+  if (!v || !dst) return VM_ERR_INVALID_ARG;
+  // live vertices and live triangles are adjacent counters
+  static_assert(C_LIVE_TRIS == C_LIVE_VERTS + 1, "counter layout");
+  return cuda_status(cudaMemcpyAsync(dst, &v->V.ctl->c[C_LIVE_VERTS], 2 * sizeof(int32_t),
+                                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, v->stream));
+}
+
+vm_status vm_get_stats(vm_volume* v, vm_frame_stats* s) {
+  if (!v || !s) return VM_ERR_INVALID_ARG;
+  if (sync_status(v)) return VM_ERR_CUDA;
+  int c[C_COUNT];
+  if (cudaMemcpy(c, v->V.ctl->c, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) return VM_ERR_CUDA;
+  s->frame_blocks = c[C_ST_FRAME_BLOCKS];
+  s->new_blocks = c[C_ST_NEW_BLOCKS];
+  s->update_blocks = c[C_ST_UPDATE_BLOCKS];
+  s->changed_cubes = c[C_ST_CHANGED];
+  s->live_blocks = c[C_LIVE_BLOCKS];
+  s->live_vertices = c[C_LIVE_VERTS];
+  s->live_triangles = c[C_LIVE_TRIS];
+  s->freed_blocks = c[C_ST_FREED_BLOCKS];
+  s->freed_vertices = c[C_ST_FREED_VERTS];
+  s->created_vertices = c[C_ST_NEW_VERTS];
+  s->hash_tombstones = c[C_TOMBS];
+  s->block_high_water = c[C_BLK_BUMP] < (int)v->p.max_blocks ? c[C_BLK_BUMP] : (int)v->p.max_blocks;
+  return VM_OK;
+}
+
+vm_status vm_num_blocks(vm_volume* v, int64_t* n) {
+  if (!v || !n) return VM_ERR_INVALID_ARG;
+  if (sync_status(v)) return VM_ERR_CUDA;
+  *n = read_counter(v, C_LIVE_BLOCKS);
+  return VM_OK;
+}
+
+vm_status vm_export_blocks(vm_volume* v, int32_t* keys, float* tsdf, float* weight, uint8_t* ce, uint8_t* cp) {
+  if (!v) return VM_ERR_INVALID_ARG;
+  if (sync_status(v)) return VM_ERR_CUDA;
+  const int n = read_counter(v, C_LIVE_BLOCKS);
+  void *dk = nullptr, *dt = nullptr, *dw = nullptr, *dce = nullptr, *dcp = nullptr, *cnt = nullptr;
+  const size_t nn = n > 0 ? (size_t)n : 1;
+  bool ok = cudaMalloc(&dk, nn * 12) == cudaSuccess && cudaMalloc(&dt, nn * BV * 4) == cudaSuccess &&
+            cudaMalloc(&dw, nn * BV * 4) == cudaSuccess && cudaMalloc(&dce, nn * BV) == cudaSuccess &&
+            cudaMalloc(&dcp, nn * BV) == cudaSuccess && cudaMalloc(&cnt, 4) == cudaSuccess;
+  if (ok) {
+    cudaMemsetAsync(cnt, 0, 4, v->stream);
+    k_export_blocks<<<grid_for(v, 8), 256, 0, v->stream>>>(v->V, (int*)cnt, (int*)dk, (float*)dt, (float*)dw,
+                                                           (uint8_t*)dce, (uint8_t*)dcp);
+    ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(v->stream) == cudaSuccess;
+    if (ok && n > 0) {
+      ok = (!keys || cudaMemcpy(keys, dk, (size_t)n * 12, cudaMemcpyDeviceToHost) == cudaSuccess) &&
+           (!tsdf || cudaMemcpy(tsdf, dt, (size_t)n * BV * 4, cudaMemcpyDeviceToHost) == cudaSuccess) &&
+           (!weight || cudaMemcpy(weight, dw, (size_t)n * BV * 4, cudaMemcpyDeviceToHost) == cudaSuccess) &&
+           (!ce || cudaMemcpy(ce, dce, (size_t)n * BV, cudaMemcpyDeviceToHost) == cudaSuccess) &&
+           (!cp || cudaMemcpy(cp, dcp, (size_t)n * BV, cudaMemcpyDeviceToHost) == cudaSuccess);
+    }
+  }
+  cudaFree(dk);
+  cudaFree(dt);
+  cudaFree(dw);
+  cudaFree(dce);
+  cudaFree(dcp);
+  cudaFree(cnt);
+  return ok ? VM_OK : VM_ERR_CUDA;
+}
+
+vm_status vm_set_blocks(vm_volume* v, const int32_t* keys, int64_t n, const float* tsdf, const float* weight) {
+  if (!v || n < 0 || (n > 0 && (!keys || !tsdf || !weight)) || n > (int64_t)v->p.max_blocks)
+    return VM_ERR_INVALID_ARG;
+  if (n == 0) return VM_OK;
+  void *dk = nullptr, *dt = nullptr, *dw = nullptr;
+  bool ok = cudaMalloc(&dk, (size_t)n * 12) == cudaSuccess && cudaMalloc(&dt, (size_t)n * BV * 4) == cudaSuccess &&
+            cudaMalloc(&dw, (size_t)n * BV * 4) == cudaSuccess;
+  if (ok) {
+    ok = cudaMemcpyAsync(dk, keys, (size_t)n * 12, cudaMemcpyHostToDevice, v->stream) == cudaSuccess &&
+         cudaMemcpyAsync(dt, tsdf, (size_t)n * BV * 4, cudaMemcpyHostToDevice, v->stream) == cudaSuccess &&
+         cudaMemcpyAsync(dw, weight, (size_t)n * BV * 4, cudaMemcpyHostToDevice, v->stream) == cudaSuccess;
+  }
+  if (ok) {
+    const int adv = v->advance_pending ? 1 : 0;
+    k_fill_insert<<<grid_for(v, 2), 256, 0, v->stream>>>(v->V, (const int*)dk, (int)n, adv);
+    k_resolve<<<grid_for(v, 4), 256, 0, v->stream>>>(v->V);
+    k_fill_copy<<<grid_for(v, 4), 256, 0, v->stream>>>(v->V, (const int*)dk, (const float*)dt, (const float*)dw,
+                                                       (int)n);
+    ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(v->stream) == cudaSuccess;
+    v->advance_pending = false;
+  }
+  cudaFree(dk);
+  cudaFree(dt);
+  cudaFree(dw);
+  return ok ? VM_OK : VM_ERR_CUDA;
+}
+
+vm_status vm_enable_timing(vm_volume* v, int enable) {
+  if (!v) return VM_ERR_INVALID_ARG;
+  cudaStreamSynchronize(v->stream);
+  if ((enable != 0) != v->timing) drop_graph(v);  // re-capture with / without event nodes
+  v->graph_pending = false;
+  for (auto& r : v->recs) {
+    v->event_pool.push_back(r.a);
+    v->event_pool.push_back(r.b);
+  }
+  v->recs.clear();
+  for (int k = 0; k < K_COUNT_; ++k) {
+    v->tot_ms[k] = 0;
+    v->launches[k] = 0;
+  }
+  v->timing = enable != 0;
+  return VM_OK;
+}
+
+vm_status vm_kernel_times(vm_volume* v, const char** names, double* total_ms, int64_t* launches, int cap, int* n) {
+  if (!v || !n) return VM_ERR_INVALID_ARG;
+  if (sync_status(v)) return VM_ERR_CUDA;
+  collect_graph_timing(v);
+  for (auto& r : v->recs) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      v->tot_ms[r.kernel] += ms;
+      v->launches[r.kernel] += 1;
+    }
+    v->event_pool.push_back(r.a);
+    v->event_pool.push_back(r.b);
+  }
+  v->recs.clear();
+  *n = K_COUNT_;
+  for (int k = 0; k < K_COUNT_ && k < cap; ++k) {
+    if (names) names[k] = kKernelNames[k];
+    if (total_ms) total_ms[k] = v->tot_ms[k];
+    if (launches) launches[k] = v->launches[k];
+  }
+  return VM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,269 @@
+// Device-side layout, constants and helpers of the vmesh CUDA library (sm_103a).
+//
+// HBM layout of a volume (all arrays owned by the library, cleared at creation):
+//   hash      keys u64[B] (packed block key, EMPTY / TOMB), vals i32[B] (block index),
+//             stamp u32[B] (integrate call that last collected the bucket's block),
+//             ustamp u32[B] (mesh epoch in which the block joined the update set)
+//   blocks    bkey int4[NB] (x, y, z, bucket; bucket < 0 = free), bntri/bnvert i32[NB]
+//             (triangles in its cubes / vertices it owns), bnear u8[NB] (some voxel
+//             has W > 0 and d < mu), bepoch u32[NB] (epoch it was last collected in)
+//   voxels    tw float2[NB*512] (TSDF d, weight W), code_eff/code_prev u8[NB*512],
+//             vmask u8[NB*512] (bits 0-2: owned edge has a vertex; bits 3-5: vertex
+//             requested in the current pass), chg u8[NB*512] (cube awaits triangles),
+//             edge_vtx i32[NB*512*3] (vertex on owned edge, -1 none), tri_base i32[NB*512]
+//   vertices  vpos float4[NV], vnrm float4[NV], vref i32[NV] (reference count, -1 free),
+//             vedge i32[NV] (owning edge id = block*1536 + voxel*3 + axis)
+//   triangles tris int4[NT] (three vertex ids, owning cube id; x < 0 = free)
+//   free lists block / vertex stacks and five triangle-run stacks (run length 1..5)
+//   work lists touched buckets, collected blocks, update set, new-edge requests,
+//             zero-reference vertices, plus a control block (counters, status, frame).
+#pragma once
+
+#include <cooperative_groups.h>
+#include <cooperative_groups/reduce.h>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vmk {
+
+namespace cg = cooperative_groups;
+
+constexpr int BS = 8;       // block side in voxels (Sec. VI: 8^3 in all configurations)
+constexpr int BV = 512;     // voxels per block
+constexpr int EPB = 1536;   // owned edges per block
+constexpr uint64_t KEY_EMPTY = ~0ull;
+constexpr uint64_t KEY_TOMB = ~0ull - 1ull;
+constexpr int KEY_BIAS = 1 << 20;
+constexpr int KEY_LIMIT = (1 << 20) - 2;  // |block coordinate| bound
+constexpr float Z_NEAR = 0.05f;           // nearest camera depth of a collection segment
+
+enum Status { ST_OK = 0, ST_INVALID = 1, ST_HASH_FULL = 2, ST_POOL_FULL = 3 };
+
+// counters of the control block (int slots of Ctl::c)
+enum Counter {
+  C_STATUS = 0,
+  C_FRAME,          // integrate calls so far + 1
+  C_EPOCH,          // mesh epoch, advanced by the first integrate after a mesh update
+  C_N_TOUCHED,      // buckets collected by the current integrate call
+  C_N_UPDATE,       // blocks in the update set
+  C_N_NEWEDGE,      // vertex requests of the current mesh pass
+  C_N_DEAD,         // zero-reference vertices awaiting gc
+  C_BLK_TOP, C_BLK_BUMP,
+  C_VTX_TOP, C_VTX_BUMP,
+  C_RUN_TOP0, C_RUN_TOP1, C_RUN_TOP2, C_RUN_TOP3, C_RUN_TOP4,
+  C_TRI_BUMP,
+  C_LIVE_BLOCKS, C_LIVE_VERTS, C_LIVE_TRIS,
+  C_TOMBS,
+  C_REHASH,         // 1 while a hash rebuild is under way
+  C_ST_FRAME_BLOCKS, C_ST_UPDATE_BLOCKS, C_ST_NEW_BLOCKS, C_ST_CHANGED, C_ST_FREED_BLOCKS, C_ST_FREED_VERTS, C_ST_NEW_VERTS,
+  C_DONE0, C_DONE1, C_DONE2, C_DONE3, C_DONE4, C_DONE5, C_DONE6, C_DONE7,
+  C_COUNT
+};
+
+struct FrameParams {
+  const float* depth;
+  int W, H;
+  float fx, fy, cx, cy;
+  float Twc[12];  // rows of [R | t], camera -> world
+  float Tcw[12];  // world -> camera
+};
+
+struct Ctl {
+  int c[C_COUNT];
+  FrameParams fp;
+};
+
+// Plain-old-data view of a volume passed by value to every kernel.
+struct Vol {
+  float l, mu, eps, wmax;
+  uint32_t hmask;
+  int max_blocks, max_vertices, max_triangles;
+  int run_cap[5];
+  int list_cap_touched, list_cap_update, list_cap_newedge, list_cap_dead;
+
+  uint64_t* keys;
+  int* vals;
+  uint32_t* stamp;
+  uint32_t* ustamp;
+
+  int4* bkey;
+  int* bntri;
+  int* bnvert;
+  uint8_t* bnear;
+  uint32_t* bepoch;
+
+  float2* tw;
+  uint8_t* code_eff;
+  uint8_t* code_prev;
+  uint8_t* vmask;
+  uint8_t* chg;
+  int* edge_vtx;
+  int* tri_base;
+
+  float4* vpos;
+  float4* vnrm;
+  int* vref;
+  int* vedge;
+
+  int4* tris;
+
+  int* blk_free;
+  int* vtx_free;
+  int* run_free[5];
+
+  int* touched;       // buckets collected by this integrate call
+  int* touched_blk;   // their blocks
+  int* update;        // update-set blocks
+  int* newedge;       // requested edge ids
+  int* dead;          // zero-reference vertex ids
+
+  Ctl* ctl;
+};
+
+// ------------------------------------------------------------------ cube tables
+// Corners in Bourke order; edge k joins the owner corner EDGE_LO[k] to EDGE_HI[k].
+__constant__ int8_t c_corner[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {0, 1, 0},
+                                      {0, 0, 1}, {1, 0, 1}, {1, 1, 1}, {0, 1, 1}};
+// owner corner offset and axis of each cube edge
+__constant__ int8_t c_edge_owner[12][4] = {{0, 0, 0, 0}, {1, 0, 0, 1}, {0, 1, 0, 0}, {0, 0, 0, 1},
+                                           {0, 0, 1, 0}, {1, 0, 1, 1}, {0, 1, 1, 0}, {0, 0, 1, 1},
+                                           {0, 0, 0, 2}, {1, 0, 0, 2}, {1, 1, 0, 2}, {0, 1, 0, 2}};
+__constant__ uint8_t c_ntri[256];
+__constant__ uint8_t c_tri[256][15];
+__constant__ uint16_t c_edgemask[256];
+// regular cube types of Sec. V-F, in the paper's order
+__constant__ uint8_t c_regular[6] = {0xCC, 0x33, 0x99, 0x66, 0xF0, 0x0F};
+
+// ------------------------------------------------------------------ small helpers
+__device__ __forceinline__ int floordiv8(int g) { return g >> 3; }  // arithmetic shift = floor
+
+__device__ __forceinline__ uint64_t pack_key(int x, int y, int z) {
+  return ((uint64_t)(uint32_t)(x + KEY_BIAS) << 42) | ((uint64_t)(uint32_t)(y + KEY_BIAS) << 21) |
+         (uint64_t)(uint32_t)(z + KEY_BIAS);
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {  // murmur3 finaliser
+  z = (z ^ (z >> 33)) * 0xFF51AFD7ED558CCDull;
+  z = (z ^ (z >> 33)) * 0xC4CEB9FE1A85EC53ull;
+  return z ^ (z >> 33);
+}
+
+__device__ __forceinline__ void set_status(const Vol& V, int st) { atomicCAS(&V.ctl->c[C_STATUS], 0, st); }
+
+// Hash lookup: bucket holding `key`, or -1.  Linear probing, at most hmask+1 probes.
+__device__ __forceinline__ int hash_find(const Vol& V, uint64_t key) {
+  uint32_t s = (uint32_t)mix64(key) & V.hmask;
+  for (uint32_t p = 0; p <= V.hmask; ++p) {
+    uint64_t k = __ldcg(&V.keys[s]);
+    if (k == key) return (int)s;
+    if (k == KEY_EMPTY) return -1;
+    s = (s + 1) & V.hmask;
+  }
+  return -1;
+}
+
+// Block index of block key (x, y, z), or -1.
+__device__ __forceinline__ int find_block(const Vol& V, int x, int y, int z) {
+  int s = hash_find(V, pack_key(x, y, z));
+  return s < 0 ? -1 : __ldcg(&V.vals[s]);
+}
+
+// Pop of `stride` consecutive ids per calling lane from a free stack of run starts backed
+// by a bump range, aggregated over the lanes that call it together.  Pops and pushes of
+// one stack never share a kernel; the popping kernel clamps the stack top at 0 when it
+// ends (fold_top).  Returns -1 (and sets POOL_FULL) when the pool is exhausted.
+__device__ __forceinline__ int pool_pop(const Vol& V, int* stack, int c_top, int c_bump, int cap, int stride = 1) {
+  cg::coalesced_group g = cg::coalesced_threads();
+  int n = (int)g.size(), rank = (int)g.thread_rank();
+  int old = 0, bump0 = 0, from_stack = 0;
+  if (rank == 0) {
+    old = atomicSub(&V.ctl->c[c_top], n);
+    from_stack = old <= 0 ? 0 : (old < n ? old : n);
+    if (from_stack < n) bump0 = atomicAdd(&V.ctl->c[c_bump], (n - from_stack) * stride);
+  }
+  old = g.shfl(old, 0);
+  from_stack = g.shfl(from_stack, 0);
+  bump0 = g.shfl(bump0, 0);
+  int id;
+  if (rank < from_stack) {
+    id = __ldcg(&stack[old - 1 - rank]);
+  } else {
+    long long b = (long long)bump0 + (long long)(rank - from_stack) * stride;
+    if (b + stride > cap) {
+      set_status(V, ST_POOL_FULL);
+      id = -1;
+    } else {
+      id = (int)b;
+    }
+  }
+  return id;
+}
+
+// Push of one id per calling lane, aggregated over the lanes that call it together.
+__device__ __forceinline__ void pool_push(const Vol& V, int* stack, int c_top, int cap, int id) {
+  cg::coalesced_group g = cg::coalesced_threads();
+  int base = 0;
+  if (g.thread_rank() == 0) base = atomicAdd(&V.ctl->c[c_top], (int)g.size());
+  base = g.shfl(base, 0) + (int)g.thread_rank();
+  if (base < cap) stack[base] = id;
+  else set_status(V, ST_POOL_FULL);
+}
+
+// Append to a work list, aggregated over the calling lanes; false (and POOL_FULL) on overflow.
+__device__ __forceinline__ bool list_push(const Vol& V, int* list, int c_count, int cap, int value) {
+  cg::coalesced_group g = cg::coalesced_threads();
+  int base = 0;
+  if (g.thread_rank() == 0) base = atomicAdd(&V.ctl->c[c_count], (int)g.size());
+  base = g.shfl(base, 0) + (int)g.thread_rank();
+  if (base < cap) {
+    list[base] = value;
+    return true;
+  }
+  set_status(V, ST_POOL_FULL);
+  return false;
+}
+
+// Add `v` to a counter, aggregated over the calling lanes.
+__device__ __forceinline__ void counter_add(const Vol& V, int c, int v) {
+  cg::coalesced_group g = cg::coalesced_threads();
+  int s = cg::reduce(g, v, cg::plus<int>());
+  if (g.thread_rank() == 0 && s != 0) atomicAdd(&V.ctl->c[c], s);
+}
+
+// Byte-granular atomic OR / AND on a u8 array (through the enclosing 32-bit word).
+__device__ __forceinline__ uint8_t atomic_or_u8(uint8_t* p, uint8_t bits) {
+  uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  unsigned* w = reinterpret_cast<unsigned*>(a & ~uintptr_t(3));
+  int sh = (int)(a & 3) * 8;
+  return (uint8_t)(atomicOr(w, (unsigned)bits << sh) >> sh);
+}
+__device__ __forceinline__ uint8_t atomic_and_u8(uint8_t* p, uint8_t bits) {
+  uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  unsigned* w = reinterpret_cast<unsigned*>(a & ~uintptr_t(3));
+  int sh = (int)(a & 3) * 8;
+  return (uint8_t)(atomicAnd(w, ~((unsigned)(uint8_t)~bits << sh)) >> sh);
+}
+
+// Last-block-done ticket: returns true in exactly one CTA of the grid, after every
+// other CTA has finished its work (threadfence reduction pattern; no waiting).
+__device__ __forceinline__ bool last_block(const Vol& V, int c_done) {
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = atomicAdd(&V.ctl->c[c_done], 1);
+    s_last = (t == (int)(gridDim.x * gridDim.y * gridDim.z) - 1);
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void fold_top(const Vol& V, int c_top) {
+  if (V.ctl->c[c_top] < 0) V.ctl->c[c_top] = 0;
+}
+
+}  // namespace vmk

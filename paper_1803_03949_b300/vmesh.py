@@ -1,0 +1,263 @@
+"""Python binding of the vmesh C ABI (``include/vmesh.h``): argument marshalling only.
+
+Every step of the per-frame path runs in the CUDA library ``libvmesh.so``; PyTorch only
+provides device memory (depth frames, download buffers) and the stream.  There is no
+CPU fallback: without the built library, or without a CUDA device, construction fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvmesh.so")
+
+VM_FULL, VM_REFINE, VM_GC = 1, 2, 4
+STATUS = {0: "VM_OK", 1: "VM_ERR_INVALID_ARG", 2: "VM_ERR_HASH_FULL", 3: "VM_ERR_POOL_FULL", 4: "VM_ERR_CUDA",
+          5: "VM_ERR_OOM"}
+
+
+class VmeshError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__("%s failed: %s" % (where, STATUS.get(code, code)))
+        self.code = code
+
+
+class vm_params(ctypes.Structure):
+    _fields_ = [("voxel_size", ctypes.c_float), ("trunc", ctypes.c_float), ("eps_refine", ctypes.c_float),
+                ("w_max", ctypes.c_float), ("hash_buckets", ctypes.c_uint32), ("max_blocks", ctypes.c_uint32),
+                ("max_vertices", ctypes.c_uint32), ("max_triangles", ctypes.c_uint32)]
+
+
+class vm_intrinsics(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float)]
+
+
+class vm_frame_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "frame_blocks", "new_blocks", "update_blocks", "changed_cubes", "live_blocks", "live_vertices",
+        "live_triangles", "freed_blocks", "freed_vertices", "created_vertices", "hash_tombstones",
+        "block_high_water")]
+
+
+_lib = None
+
+EXPORTS = ["vm_create_volume", "vm_destroy_volume", "vm_set_stream", "vm_integrate_depth", "vm_update_mesh",
+           "vm_refine_mesh", "vm_gc", "vm_step", "vm_mesh_counts", "vm_download_mesh", "vm_get_stats",
+           "vm_last_error", "vm_num_blocks", "vm_export_blocks", "vm_set_blocks", "vm_enable_timing",
+           "vm_kernel_times", "vm_mesh_size_async"]
+
+
+def load_library(path: str = LIB_PATH):
+    """Load ``libvmesh.so`` and declare its signatures (no CUDA call is made)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("vmesh CUDA library not built: %s (run paper_1803_03949_b300/build.py)" % path)
+    lib = ctypes.CDLL(path)
+    vp, i, i64, f = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_float
+    P = ctypes.POINTER
+    F16 = P(f)
+    sig = {
+        "vm_create_volume": [P(vm_params), vp, P(vp)],
+        "vm_destroy_volume": [vp],
+        "vm_set_stream": [vp, vp],
+        "vm_integrate_depth": [vp, vp, P(vm_intrinsics), F16, F16],
+        "vm_update_mesh": [vp, i],
+        "vm_refine_mesh": [vp, i],
+        "vm_gc": [vp],
+        "vm_step": [vp, vp, P(vm_intrinsics), F16, F16, i, i],
+        "vm_mesh_counts": [vp, P(i64), P(i64)],
+        "vm_download_mesh": [vp, vp, vp, vp, vp, vp, i],
+        "vm_get_stats": [vp, P(vm_frame_stats)],
+        "vm_last_error": [vp],
+        "vm_num_blocks": [vp, P(i64)],
+        "vm_export_blocks": [vp, vp, vp, vp, vp, vp],
+        "vm_set_blocks": [vp, vp, i64, vp, vp],
+        "vm_enable_timing": [vp, i],
+        "vm_kernel_times": [vp, P(ctypes.c_char_p), P(ctypes.c_double), P(i64), i, P(i)],
+        "vm_mesh_size_async": [vp, vp, i],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise VmeshError(code, where)
+
+
+def _f16(T) -> ctypes.Array:
+    a = np.ascontiguousarray(np.asarray(T, np.float32).reshape(16))
+    return (ctypes.c_float * 16)(*a.tolist())
+
+
+def _ptr(x) -> int:
+    """Data pointer of a torch tensor or numpy array (None -> 0)."""
+    if x is None:
+        return 0
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+@dataclass
+class Intrinsics:
+    width: int
+    height: int
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+
+    def c(self) -> vm_intrinsics:
+        return vm_intrinsics(self.width, self.height, self.fx, self.fy, self.cx, self.cy)
+
+
+class Volume:
+    """A spatially hashed TSDF volume with its incrementally maintained mesh (one GPU)."""
+
+    def __init__(self, voxel_size, trunc, hash_buckets, max_blocks, max_vertices, max_triangles,
+                 eps_refine=None, w_max=255.0, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("vmesh needs a CUDA device; no CPU fallback exists")
+        self._lib = load_library()
+        if eps_refine is None:
+            eps_refine = 0.2 * voxel_size
+        self.params = vm_params(voxel_size, trunc, eps_refine, w_max, hash_buckets, max_blocks, max_vertices,
+                                max_triangles)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        _check(self._lib.vm_create_volume(ctypes.byref(self.params), ctypes.c_void_p(self.stream.cuda_stream),
+                                          ctypes.byref(h)), "vm_create_volume")
+        self._h = h
+
+    @classmethod
+    def from_config(cls, vc, **kw):
+        return cls(vc.voxel_size, vc.trunc, vc.hash_buckets, vc.max_blocks, vc.max_vertices, vc.max_triangles,
+                   eps_refine=vc.eps_refine, w_max=vc.w_max, **kw)
+
+    def close(self):
+        h, self._h = getattr(self, "_h", None), None
+        if h is not None and h.value:
+            self._lib.vm_destroy_volume(h)
+
+    def __del__(self):
+        self.close()
+
+    # --------------------------------------------------------------- per-frame path
+    def integrate(self, depth, intr: Intrinsics, T_wc, T_cw):
+        """depth: CUDA float32 tensor (H, W); poses 4x4 (host, rounded to float32)."""
+        _check(self._lib.vm_integrate_depth(self._h, ctypes.c_void_p(_ptr(depth)), ctypes.byref(intr.c()),
+                                            _f16(T_wc), _f16(T_cw)), "vm_integrate_depth")
+
+    def update_mesh(self, full=False, refine=False):
+        _check(self._lib.vm_update_mesh(self._h, (VM_FULL if full else 0) | (VM_REFINE if refine else 0)),
+               "vm_update_mesh")
+
+    def refine_mesh(self, full=False):
+        _check(self._lib.vm_refine_mesh(self._h, int(bool(full))), "vm_refine_mesh")
+
+    def gc(self):
+        _check(self._lib.vm_gc(self._h), "vm_gc")
+
+    def step(self, depth, intr: Intrinsics, T_wc, T_cw, refine=True, gc=True, full=False, graph=False):
+        flags = (VM_FULL if full else 0) | (VM_REFINE if refine else 0) | (VM_GC if gc else 0)
+        _check(self._lib.vm_step(self._h, ctypes.c_void_p(_ptr(depth)), ctypes.byref(intr.c()), _f16(T_wc),
+                                 _f16(T_cw), flags, int(bool(graph))), "vm_step")
+
+    # --------------------------------------------------------------- queries
+    def last_error(self) -> int:
+        return self._lib.vm_last_error(self._h)
+
+    def check(self):
+        _check(self.last_error(), "device status")
+
+    def stats(self) -> dict:
+        s = vm_frame_stats()
+        _check(self._lib.vm_get_stats(self._h, ctypes.byref(s)), "vm_get_stats")
+        return {n: getattr(s, n) for n, _ in vm_frame_stats._fields_}
+
+    def num_blocks(self) -> int:
+        n = ctypes.c_int64()
+        _check(self._lib.vm_num_blocks(self._h, ctypes.byref(n)), "vm_num_blocks")
+        return n.value
+
+    def mesh_size_async(self, dst):
+        """Enqueue a copy of (live vertices, live triangles) into dst: a 2-element int32 torch
+        tensor, pinned host or CUDA; it holds the values once the stream reaches the copy."""
+        import torch
+
+        assert dst.dtype == torch.int32 and dst.numel() >= 2
+        _check(self._lib.vm_mesh_size_async(self._h, ctypes.c_void_p(dst.data_ptr()), int(dst.is_cuda)),
+               "vm_mesh_size_async")
+
+    def mesh_counts(self):
+        nv, nt = ctypes.c_int64(), ctypes.c_int64()
+        _check(self._lib.vm_mesh_counts(self._h, ctypes.byref(nv), ctypes.byref(nt)), "vm_mesh_counts")
+        return nv.value, nt.value
+
+    def download(self, device: bool = False):
+        """The live mesh: dict(pos (nv,3) f32, nrm (nv,3) f32, tris (nt,3) i32, keys (nv,) u64,
+        refcount (nv,) i32) as numpy arrays (host path) or torch CUDA tensors (device path)."""
+        import torch
+
+        nv, nt = self.mesh_counts()
+        if device:
+            dev = torch.device("cuda")
+            pos = torch.empty((nv, 3), dtype=torch.float32, device=dev)
+            nrm = torch.empty((nv, 3), dtype=torch.float32, device=dev)
+            tris = torch.empty((nt, 3), dtype=torch.int32, device=dev)
+            keys = torch.empty((nv,), dtype=torch.int64, device=dev)
+            ref = torch.empty((nv,), dtype=torch.int32, device=dev)
+        else:
+            pos = np.empty((nv, 3), np.float32)
+            nrm = np.empty((nv, 3), np.float32)
+            tris = np.empty((nt, 3), np.int32)
+            keys = np.empty((nv,), np.uint64)
+            ref = np.empty((nv,), np.int32)
+        _check(self._lib.vm_download_mesh(self._h, _ptr(pos), _ptr(nrm), _ptr(tris), _ptr(keys), _ptr(ref),
+                                          int(device)), "vm_download_mesh")
+        return dict(pos=pos, nrm=nrm, tris=tris, keys=keys, refcount=ref)
+
+    def blocks(self) -> dict:
+        """Every allocated block: keys (n,3) i32, tsdf/weight (n,512) f32, code_eff/code_prev (n,512) u8."""
+        n = self.num_blocks()
+        keys = np.empty((n, 3), np.int32)
+        tsdf = np.empty((n, 512), np.float32)
+        weight = np.empty((n, 512), np.float32)
+        ce = np.empty((n, 512), np.uint8)
+        cp = np.empty((n, 512), np.uint8)
+        _check(self._lib.vm_export_blocks(self._h, _ptr(keys), _ptr(tsdf), _ptr(weight), _ptr(ce), _ptr(cp)),
+               "vm_export_blocks")
+        return dict(keys=keys, tsdf=tsdf, weight=weight, code_eff=ce, code_prev=cp)
+
+    def set_blocks(self, keys, tsdf, weight):
+        k = np.ascontiguousarray(keys, np.int32).reshape(-1, 3)
+        t = np.ascontiguousarray(tsdf, np.float32).reshape(-1, 512)
+        w = np.ascontiguousarray(weight, np.float32).reshape(-1, 512)
+        _check(self._lib.vm_set_blocks(self._h, _ptr(k), k.shape[0], _ptr(t), _ptr(w)), "vm_set_blocks")
+
+    # --------------------------------------------------------------- timing
+    def enable_timing(self, on: bool = True):
+        _check(self._lib.vm_enable_timing(self._h, int(bool(on))), "vm_enable_timing")
+
+    def kernel_times(self) -> dict:
+        cap = 32
+        names = (ctypes.c_char_p * cap)()
+        ms = (ctypes.c_double * cap)()
+        cnt = (ctypes.c_int64 * cap)()
+        n = ctypes.c_int()
+        _check(self._lib.vm_kernel_times(self._h, names, ms, cnt, cap, ctypes.byref(n)), "vm_kernel_times")
+        return {names[i].decode(): (ms[i], cnt[i]) for i in range(n.value)}
