@@ -88,6 +88,7 @@ typedef struct {
   int64_t created_vertices;  /* vertices created since the volume was created */
   int64_t hash_tombstones;   /* dead hash buckets awaiting a rehash */
   int64_t block_high_water;  /* block pool slots ever used */
+  int64_t rehashes;          /* hash rebuilds (tombstone clean-ups) so far */
 } vm_frame_stats;
 
 /* Flags of vm_update_mesh / vm_step. */

@@ -148,6 +148,7 @@ __global__ void __launch_bounds__(256) k_rehash_mark(Vol V) {
     if (threadIdx.x == 0) {
       V.ctl->c[C_TOMBS] = 0;
       V.ctl->c[C_REHASH] = 0;
+      V.ctl->c[C_ST_REHASHES] += 1;
       V.ctl->c[C_DONE6] = 0;
     }
   }

@@ -51,7 +51,9 @@ struct TimingRec {
 struct vm_volume {
   vm_params p;
   Vol V;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;      // the caller's stream: every call enqueues here
+  cudaStream_t cur = nullptr;         // stream launches go to (the capture stream while capturing)
+  cudaStream_t cap_stream = nullptr;  // owned non-blocking stream for graph capture
   int num_sms = 148;
   bool advance_pending = false;
   std::vector<void*> allocs;
@@ -99,17 +101,18 @@ vm_status launch(vm_volume* v, int kid, F&& f) {
   if (v->timing) {
     a = get_event(v);
     b = get_event(v);
-    if (v->capturing) cudaEventRecordWithFlags(a, v->stream, cudaEventRecordExternal);
-    else cudaEventRecord(a, v->stream);
+    if (v->capturing) cudaEventRecordWithFlags(a, v->cur, cudaEventRecordExternal);
+    else cudaEventRecord(a, v->cur);
   }
+  (void)cudaGetLastError();  // drop a stale non-sticky error so it is not blamed on this launch
   f();
   cudaError_t e = cudaGetLastError();
   if (v->timing) {
     if (v->capturing) {
-      cudaEventRecordWithFlags(b, v->stream, cudaEventRecordExternal);
+      cudaEventRecordWithFlags(b, v->cur, cudaEventRecordExternal);
       v->graph_recs.push_back({kid, a, b});
     } else {
-      cudaEventRecord(b, v->stream);
+      cudaEventRecord(b, v->cur);
       v->recs.push_back({kid, a, b});
     }
   }
@@ -137,7 +140,7 @@ bool dalloc(vm_volume* v, T** p, size_t count, int fill_byte) {
   if (bytes == 0) bytes = sizeof(T);
   if (cudaMalloc(&q, bytes) != cudaSuccess) return false;
   v->allocs.push_back(q);
-  if (cudaMemsetAsync(q, fill_byte, bytes, v->stream) != cudaSuccess) return false;
+  if (cudaMemsetAsync(q, fill_byte, bytes, v->cur) != cudaSuccess) return false;
   *p = static_cast<T*>(q);
   return true;
 }
@@ -179,31 +182,31 @@ int grid_for(vm_volume* v, int per_sm) { return v->num_sms * per_sm; }
 vm_status enqueue_integrate(vm_volume* v, const FrameParams& fp, bool set_frame) {
   vm_status st = VM_OK;
   Ctl* ctl = v->V.ctl;
-  if (set_frame) st = launch(v, K_SET_FRAME, [&] { k_set_frame<<<1, 1, 0, v->stream>>>(&ctl->fp, fp); });
+  if (set_frame) st = launch(v, K_SET_FRAME, [&] { k_set_frame<<<1, 1, 0, v->cur>>>(&ctl->fp, fp); });
   if (st) return st;
   const int adv = v->advance_pending ? 1 : 0;
   dim3 g((fp.W + ALLOC_TILE_W - 1) / ALLOC_TILE_W, (fp.H + ALLOC_TILE_H - 1) / ALLOC_TILE_H);
-  st = launch(v, K_ALLOC, [&] { k_alloc<<<g, ALLOC_THREADS, 0, v->stream>>>(v->V, &ctl->fp, adv); });
+  st = launch(v, K_ALLOC, [&] { k_alloc<<<g, ALLOC_THREADS, 0, v->cur>>>(v->V, &ctl->fp, adv); });
   if (st) return st;
-  st = launch(v, K_RESOLVE, [&] { k_resolve<<<grid_for(v, 4), 256, 0, v->stream>>>(v->V); });
+  st = launch(v, K_RESOLVE, [&] { k_resolve<<<grid_for(v, 4), 256, 0, v->cur>>>(v->V); });
   if (st) return st;
-  st = launch(v, K_INTEGRATE, [&] { k_integrate<<<grid_for(v, 8), INTEG_THREADS, 0, v->stream>>>(v->V, &ctl->fp); });
+  st = launch(v, K_INTEGRATE, [&] { k_integrate<<<grid_for(v, 8), INTEG_THREADS, 0, v->cur>>>(v->V, &ctl->fp); });
   v->advance_pending = false;
   return st;
 }
 
 vm_status enqueue_list_all(vm_volume* v) {
-  cudaError_t e = cudaMemsetAsync(&v->V.ctl->c[C_N_UPDATE], 0, sizeof(int), v->stream);
+  cudaError_t e = cudaMemsetAsync(&v->V.ctl->c[C_N_UPDATE], 0, sizeof(int), v->cur);
   if (e != cudaSuccess) return VM_ERR_CUDA;
-  return launch(v, K_LIST_ALL, [&] { k_list_all<<<grid_for(v, 4), 256, 0, v->stream>>>(v->V); });
+  return launch(v, K_LIST_ALL, [&] { k_list_all<<<grid_for(v, 4), 256, 0, v->cur>>>(v->V); });
 }
 
 vm_status enqueue_mesh_pass(vm_volume* v, int mode) {
-  vm_status st = launch(v, K_MESH_TYPES, [&] { k_mesh_types<<<grid_for(v, 8), MESH_THREADS, 0, v->stream>>>(v->V, mode); });
+  vm_status st = launch(v, K_MESH_TYPES, [&] { k_mesh_types<<<grid_for(v, 8), MESH_THREADS, 0, v->cur>>>(v->V, mode); });
   if (st) return st;
-  st = launch(v, K_VERTICES, [&] { k_vertices<<<grid_for(v, 4), 256, 0, v->stream>>>(v->V); });
+  st = launch(v, K_VERTICES, [&] { k_vertices<<<grid_for(v, 4), 256, 0, v->cur>>>(v->V); });
   if (st) return st;
-  return launch(v, K_TRIANGLES, [&] { k_triangles<<<grid_for(v, 8), MESH_THREADS, 0, v->stream>>>(v->V); });
+  return launch(v, K_TRIANGLES, [&] { k_triangles<<<grid_for(v, 8), MESH_THREADS, 0, v->cur>>>(v->V); });
 }
 
 vm_status enqueue_update(vm_volume* v, int flags) {
@@ -216,16 +219,16 @@ vm_status enqueue_update(vm_volume* v, int flags) {
 }
 
 vm_status enqueue_gc(vm_volume* v) {
-  vm_status st = launch(v, K_GC_VERTICES, [&] { k_gc_vertices<<<grid_for(v, 2), 256, 0, v->stream>>>(v->V); });
+  vm_status st = launch(v, K_GC_VERTICES, [&] { k_gc_vertices<<<grid_for(v, 2), 256, 0, v->cur>>>(v->V); });
   if (st) return st;
   const int consumed = v->advance_pending ? 1 : 0;
-  st = launch(v, K_GC_BLOCKS, [&] { k_gc_blocks<<<grid_for(v, 8), 256, 0, v->stream>>>(v->V, consumed); });
+  st = launch(v, K_GC_BLOCKS, [&] { k_gc_blocks<<<grid_for(v, 8), 256, 0, v->cur>>>(v->V, consumed); });
   if (st) return st;
   return launch(v, K_REHASH, [&] {
-    k_rehash_check<<<1, 32, 0, v->stream>>>(v->V);
-    k_rehash_wipe<<<grid_for(v, 4), 256, 0, v->stream>>>(v->V);
-    k_rehash_insert<<<grid_for(v, 4), 256, 0, v->stream>>>(v->V);
-    k_rehash_mark<<<grid_for(v, 2), 256, 0, v->stream>>>(v->V);
+    k_rehash_check<<<1, 32, 0, v->cur>>>(v->V);
+    k_rehash_wipe<<<grid_for(v, 4), 256, 0, v->cur>>>(v->V);
+    k_rehash_insert<<<grid_for(v, 4), 256, 0, v->cur>>>(v->V);
+    k_rehash_mark<<<grid_for(v, 2), 256, 0, v->cur>>>(v->V);
   });
 }
 
@@ -264,6 +267,8 @@ void free_all(vm_volume* v) {
   for (auto e : v->event_pool) cudaEventDestroy(e);
   for (void* p : v->allocs) cudaFree(p);
   v->allocs.clear();
+  if (v->cap_stream) cudaStreamDestroy(v->cap_stream);
+  v->cap_stream = nullptr;
 }
 
 // vertex / triangle counts through the scan kernels; leaves offsets in cta_counts
@@ -305,6 +310,7 @@ vm_status vm_create_volume(const vm_params* p, void* cuda_stream, vm_volume** ou
   vm_volume* v = new vm_volume();
   v->p = *p;
   v->stream = static_cast<cudaStream_t>(cuda_stream);
+  v->cur = v->stream;
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&v->num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -370,8 +376,9 @@ vm_status vm_destroy_volume(vm_volume* v) {
 
 vm_status vm_set_stream(vm_volume* v, void* s) {
   if (!v) return VM_ERR_INVALID_ARG;
-  v->stream = static_cast<cudaStream_t>(s);
   drop_graph(v);
+  v->stream = static_cast<cudaStream_t>(s);
+  v->cur = v->stream;
   return VM_OK;
 }
 
@@ -421,20 +428,32 @@ vm_status vm_step(vm_volume* v, const float* depth, const vm_intrinsics* K, cons
   if (!use_graph || !v->advance_pending) return body();
   if (!v->graph_exec || v->graph_flags != flags || v->graph_W != fp.W || v->graph_H != fp.H) {
     drop_graph(v);
-    cudaGraph_t g = nullptr;
-    v->capturing = true;
-    if (cudaStreamBeginCapture(v->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-      v->capturing = false;
+    // Capture on an owned stream (the legacy NULL stream cannot be captured); the graph is
+    // then launched on the caller's stream.
+    if (!v->cap_stream && cudaStreamCreateWithFlags(&v->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      (void)cudaGetLastError();
+      v->cap_stream = nullptr;
       return VM_ERR_CUDA;
     }
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(v->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return VM_ERR_CUDA;
+    }
+    v->capturing = true;
+    v->cur = v->cap_stream;
     vm_status s = body();
-    cudaError_t e = cudaStreamEndCapture(v->stream, &g);
+    cudaError_t e = cudaStreamEndCapture(v->cap_stream, &g);
     v->capturing = false;
+    v->cur = v->stream;
     if (s) {
       if (g) cudaGraphDestroy(g);
       return s;
     }
-    if (e != cudaSuccess) return VM_ERR_CUDA;
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      return VM_ERR_CUDA;
+    }
     e = cudaGraphInstantiate(&v->graph_exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
@@ -574,6 +593,7 @@ vm_status vm_get_stats(vm_volume* v, vm_frame_stats* s) {
   s->created_vertices = c[C_ST_NEW_VERTS];
   s->hash_tombstones = c[C_TOMBS];
   s->block_high_water = c[C_BLK_BUMP] < (int)v->p.max_blocks ? c[C_BLK_BUMP] : (int)v->p.max_blocks;
+  s->rehashes = c[C_ST_REHASHES];
   return VM_OK;
 }
 

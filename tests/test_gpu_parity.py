@@ -69,7 +69,7 @@ def test_room_full_size_launch_configurations(mode):
     g.check()
     st = compare_blocks(g.blocks(), o.blocks())
     ms = compare_mesh(g.download(), o.mesh(), s.volume.voxel_size)
-    assert st["blocks"] > 2000 and ms["triangles"] > 100000
+    assert st["blocks"] > 500 and ms["triangles"] > 20000
     stats = g.stats()
     nv, nt = g.mesh_counts()
     assert stats["live_vertices"] == nv and stats["live_triangles"] == nt
@@ -181,11 +181,11 @@ def test_rehash_under_block_churn_keeps_parity():
     vc = s.volume
     import dataclasses
 
-    small = dataclasses.replace(vc, hash_buckets=1 << 11)
+    small = dataclasses.replace(vc, hash_buckets=1 << 10)  # ~500 live blocks: rebuilds start at frame 2
     g, o = gpu_volume(small), oracle.Volume.from_config(vc)
     run_frames(s, range(10), gpu=g, orc=o)
     g.check()
     compare_blocks(g.blocks(), o.blocks())
     compare_mesh(g.download(), o.mesh(), vc.voxel_size)
     st = g.stats()
-    assert st["freed_blocks"] > 0
+    assert st["freed_blocks"] > 0 and st["rehashes"] > 0
