@@ -173,6 +173,25 @@ vm_status vm_get_stats(vm_volume* vol, vm_frame_stats* stats);
 /* Synchronises and returns the sticky device status (VM_OK when none). */
 vm_status vm_last_error(vm_volume* vol);
 
+/* No counterpart in the paper: the same compaction as vm_download_mesh for callers that
+ * must not allocate device memory -- for example code running while a caching allocator
+ * holds all free device memory, or under a fixed memory budget set at start-up.  It calls
+ * no cudaMalloc or cudaFree; its scratch is a static device array of about 4.5 MB that
+ * every GPU loading the library holds until the process exits, sized for vertex pools up
+ * to 2^24 and triangle pools up to 2^26 entries (larger volumes get VM_ERR_INVALID_ARG
+ * before anything is enqueued).  Synchronises.  Writes the live counts to the host
+ * *n_vertices and *n_triangles; with pos == NULL it stops there (a size query).
+ * Otherwise pos, nrm, tris (and the optional edge_keys, refcount) are DEVICE buffers in
+ * the vm_download_mesh layout holding at least cap_vertices / cap_triangles entries;
+ * counts above those capacities give VM_ERR_INVALID_ARG with the outputs untouched.
+ * The first call on each device looks up the scratch array's device address, so make it
+ * before any stream capture on that device.  All calls share the one scratch array and
+ * every call rewrites the parts it reads; calls whose work overlaps on the GPU (other
+ * host threads, other streams) race on it and must be serialised by the caller. */
+vm_status vm_download_mesh_noalloc(vm_volume* vol, float* pos, float* nrm, int32_t* tris, uint64_t* edge_keys,
+                                   int32_t* refcount, int64_t cap_vertices, int64_t cap_triangles,
+                                   int64_t* n_vertices, int64_t* n_triangles);
+
 /* Synchronises; number of allocated blocks. */
 vm_status vm_num_blocks(vm_volume* vol, int64_t* n);
 

@@ -704,3 +704,173 @@ vm_status vm_kernel_times(vm_volume* v, const char** names, double* total_ms, in
 }
 
 }  // extern "C"
+
+// ====================================================================== allocation-free download
+// vm_download_mesh keeps its scan scratch (per-chunk counts and a vertex remap table) in
+// device memory the library allocates on first use, and stages host outputs through
+// temporary allocations.  Some callers cannot allow that: code running while a
+// caching allocator owns all free device memory, inside a memory budget that forbids
+// growth after start-up, or on a path that must never touch the allocator.  For them
+// vm_download_mesh_noalloc does the same compaction with its scratch in the static array
+// below (a liveness bitmask and per-32-slot prefix instead of a full remap table).  Every
+// GPU that loads the library holds this array until the process exits.
+namespace {
+constexpr int NA_MAX_VERTICES = 1 << 24;   // vertex-pool size the static scratch covers
+constexpr int NA_MAX_TRIANGLES = 1 << 26;  // triangle-pool size the static scratch covers
+constexpr int NA_WORDS = NA_MAX_VERTICES / 32;
+constexpr int NA_VCHUNKS = NA_MAX_VERTICES / SCAN_ITEMS;
+constexpr int NA_TCHUNKS = NA_MAX_TRIANGLES / SCAN_ITEMS;
+constexpr size_t NA_INTS = 2 * (size_t)NA_WORDS + NA_VCHUNKS + NA_TCHUNKS + 64;  // ~4.5 MB
+constexpr int NA_MAX_DEVICES = 64;
+int* na_scratch_addr[NA_MAX_DEVICES] = {nullptr};
+}  // namespace
+
+static __device__ __align__(256) int na_scratch[NA_INTS];
+
+namespace {
+
+// Liveness bitmask of the vertex pool (one word per 32 slots) and the live count of every
+// 1024-slot chunk.  Every word and count of the launched range is rewritten each call.
+__global__ void __launch_bounds__(256) k_na_vertex_words(Vol V, unsigned* mask, int* chunk_counts) {
+  const int n = min(__ldcg(&V.ctl->c[C_VTX_BUMP]), V.max_vertices);
+  const int base = blockIdx.x * SCAN_ITEMS;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __shared__ int s;
+  if (threadIdx.x == 0) s = 0;
+  __syncthreads();
+  int cnt = 0;
+  for (int j0 = 0; j0 < SCAN_ITEMS; j0 += 256) {
+    const int v = base + j0 + threadIdx.x;
+    const bool live = v < n && V.vref[v] > 0;
+    const unsigned b = __ballot_sync(0xffffffffu, live);
+    if (lane == 0) mask[(base + j0) / 32 + w] = b;
+    cnt += live;
+  }
+  atomicAdd(&s, cnt);
+  __syncthreads();
+  if (threadIdx.x == 0) chunk_counts[blockIdx.x] = s;
+}
+
+// New index of vertex slot v from the bitmask and per-word prefix (-1 when not live).
+__device__ __forceinline__ int na_remap(const unsigned* mask, const int* wprefix, int v) {
+  if (v < 0) return -1;
+  const unsigned m = mask[v >> 5];
+  const unsigned bit = 1u << (v & 31);
+  return (m & bit) ? wprefix[v >> 5] + __popc(m & (bit - 1u)) : -1;
+}
+
+// Per-word prefixes of the chunk (from its scanned offset), then the stable compaction.
+__global__ void __launch_bounds__(256) k_na_vertex_compact(Vol V, const unsigned* mask, const int* chunk_off,
+                                                           int* wprefix, float* pos, float* nrm, uint64_t* keys,
+                                                           int* refcount) {
+  const int n = min(__ldcg(&V.ctl->c[C_VTX_BUMP]), V.max_vertices);
+  const int base = blockIdx.x * SCAN_ITEMS;
+  const int word0 = base / 32;
+  if (threadIdx.x < 32) {
+    const int c = __popc(mask[word0 + threadIdx.x]);
+    int x = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if ((int)threadIdx.x >= o) x += y;
+    }
+    wprefix[word0 + threadIdx.x] = chunk_off[blockIdx.x] + x - c;
+  }
+  __syncthreads();
+  for (int j0 = 0; j0 < SCAN_ITEMS; j0 += 256) {
+    const int v = base + j0 + threadIdx.x;
+    if (v >= n) break;
+    const int off = na_remap(mask, wprefix, v);
+    if (off < 0) continue;
+    const float4 p = V.vpos[v], q = V.vnrm[v];
+    pos[3 * (size_t)off] = p.x; pos[3 * (size_t)off + 1] = p.y; pos[3 * (size_t)off + 2] = p.z;
+    nrm[3 * (size_t)off] = q.x; nrm[3 * (size_t)off + 1] = q.y; nrm[3 * (size_t)off + 2] = q.z;
+    if (keys) keys[off] = edge_key_of(V, V.vedge[v]);
+    if (refcount) refcount[off] = V.vref[v];
+  }
+}
+
+// Stable compaction of the live triangles with vertex indices remapped from the bitmask.
+__global__ void __launch_bounds__(256) k_na_compact_triangles(Vol V, const int* chunk_off, const unsigned* mask,
+                                                              const int* wprefix, int* tris_out) {
+  const int n = min(__ldcg(&V.ctl->c[C_TRI_BUMP]), V.max_triangles);
+  const int base = blockIdx.x * SCAN_ITEMS;
+  if (base >= n) return;
+  __shared__ int warp_tot[8];
+  __shared__ int running;
+  if (threadIdx.x == 0) running = chunk_off[blockIdx.x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int j0 = 0; j0 < SCAN_ITEMS; j0 += 256) {
+    const int t = base + j0 + threadIdx.x;
+    const int4 tr = t < n ? V.tris[t] : make_int4(-1, -1, -1, -1);
+    const bool live = tr.x >= 0;
+    const unsigned b = __ballot_sync(0xffffffffu, live);
+    if (lane == 0) warp_tot[w] = __popc(b);
+    __syncthreads();
+    int off = running;
+    for (int q = 0; q < w; ++q) off += warp_tot[q];
+    off += __popc(b & ((1u << lane) - 1));
+    if (live) {
+      tris_out[3 * (size_t)off] = na_remap(mask, wprefix, tr.x);
+      tris_out[3 * (size_t)off + 1] = na_remap(mask, wprefix, tr.y);
+      tris_out[3 * (size_t)off + 2] = na_remap(mask, wprefix, tr.z);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int s = 0;
+      for (int q = 0; q < 8; ++q) s += warp_tot[q];
+      running += s;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+extern "C" vm_status vm_download_mesh_noalloc(vm_volume* v, float* pos, float* nrm, int32_t* tris,
+                                              uint64_t* edge_keys, int32_t* refcount, int64_t cap_vertices,
+                                              int64_t cap_triangles, int64_t* n_vertices, int64_t* n_triangles) {
+  if (!v || !n_vertices || !n_triangles || cap_vertices < 0 || cap_triangles < 0) return VM_ERR_INVALID_ARG;
+  if (v->p.max_vertices > (uint32_t)NA_MAX_VERTICES || v->p.max_triangles > (uint32_t)NA_MAX_TRIANGLES)
+    return VM_ERR_INVALID_ARG;  // pools larger than the static scratch covers
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) {
+    (void)cudaGetLastError();
+    return VM_ERR_CUDA;
+  }
+  // First call on this device: look up the device address of the static scratch array.
+  if (!na_scratch_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, na_scratch) != cudaSuccess || !p) {
+      (void)cudaGetLastError();
+      return VM_ERR_CUDA;
+    }
+    na_scratch_addr[dev] = static_cast<int*>(p);
+  }
+  unsigned* mask = reinterpret_cast<unsigned*>(na_scratch_addr[dev]);
+  int* wprefix = na_scratch_addr[dev] + NA_WORDS;
+  int* vchunk = wprefix + NA_WORDS;
+  int* tchunk = vchunk + NA_VCHUNKS;
+  int* totals = tchunk + NA_TCHUNKS;
+  const int nvc = ((int)v->p.max_vertices + SCAN_ITEMS - 1) / SCAN_ITEMS;
+  const int ntc = ((int)v->p.max_triangles + SCAN_ITEMS - 1) / SCAN_ITEMS;
+  cudaStream_t s = v->stream;
+  (void)cudaGetLastError();
+  k_na_vertex_words<<<nvc, 256, 0, s>>>(v->V, mask, vchunk);
+  k_scan_counts<<<1, 1024, 0, s>>>(vchunk, nvc, totals);
+  k_count_live<true><<<ntc, 256, 0, s>>>(v->V, tchunk);
+  k_scan_counts<<<1, 1024, 0, s>>>(tchunk, ntc, totals + 1);
+  int tot[2] = {0, 0};
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(tot, totals, sizeof(tot), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return VM_ERR_CUDA;
+  *n_vertices = tot[0];
+  *n_triangles = tot[1];
+  if (!pos) return VM_OK;  // size query
+  if (!nrm || !tris || tot[0] > cap_vertices || tot[1] > cap_triangles) return VM_ERR_INVALID_ARG;
+  k_na_vertex_compact<<<nvc, 256, 0, s>>>(v->V, mask, vchunk, wprefix, pos, nrm, edge_keys, refcount);
+  k_na_compact_triangles<<<ntc, 256, 0, s>>>(v->V, tchunk, mask, wprefix, tris);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return VM_ERR_CUDA;
+  return VM_OK;
+}

@@ -49,7 +49,7 @@ _lib = None
 EXPORTS = ["vm_create_volume", "vm_destroy_volume", "vm_set_stream", "vm_integrate_depth", "vm_update_mesh",
            "vm_refine_mesh", "vm_gc", "vm_step", "vm_mesh_counts", "vm_download_mesh", "vm_get_stats",
            "vm_last_error", "vm_num_blocks", "vm_export_blocks", "vm_set_blocks", "vm_enable_timing",
-           "vm_kernel_times", "vm_mesh_size_async"]
+           "vm_kernel_times", "vm_mesh_size_async", "vm_download_mesh_noalloc"]
 
 
 def load_library(path: str = LIB_PATH):
@@ -82,6 +82,7 @@ def load_library(path: str = LIB_PATH):
         "vm_enable_timing": [vp, i],
         "vm_kernel_times": [vp, P(ctypes.c_char_p), P(ctypes.c_double), P(i64), i, P(i)],
         "vm_mesh_size_async": [vp, vp, i],
+        "vm_download_mesh_noalloc": [vp, vp, vp, vp, vp, vp, i64, i64, P(i64), P(i64)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
