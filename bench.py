@@ -248,7 +248,12 @@ def run_vmesh(args, rank, world, local):
         vol.check()
         return ms, counters, kt
 
-    vol = Volume.from_config(scene.volume, stream=stream)
+    vc = scene.volume
+    if args.small_pools:  # same workload, smaller pool allocations (profiling captures)
+        import dataclasses
+
+        vc = dataclasses.replace(vc, max_blocks=1 << 15, max_vertices=1 << 21, max_triangles=1 << 22)
+    vol = Volume.from_config(vc, stream=stream)
     torch.cuda.synchronize()
     barrier(world)
     clock_path = os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(
@@ -278,7 +283,7 @@ def run_vmesh(args, rank, world, local):
     launches_total = sum(v[1] * (4 if k == "k_rehash" else 1) for k, v in kt.items())
 
     # end to end through the public API: pinned host depth -> device, step, result -> host
-    vol_e2e = Volume.from_config(scene.volume, stream=stream)
+    vol_e2e = Volume.from_config(vc, stream=stream)
     ms_e2e, _, _ = run(vol_e2e, range(args.warmup, n), e2e=True, collect=False)
     e2e_value = world * args.steps / (reduce_max(sum(ms_e2e), world) / 1000.0)
 
@@ -320,6 +325,7 @@ def main():
     ap.add_argument("--impl", choices=["vmesh", "reference"], default="vmesh")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
+    ap.add_argument("--small-pools", action="store_true", help="smaller pool allocations (ncu captures)")
     ap.add_argument("--cpu-frames", type=int, default=200)
     args = ap.parse_args()
     if args.warmup < 3:
