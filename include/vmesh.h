@@ -89,6 +89,9 @@ typedef struct {
   int64_t hash_tombstones;   /* dead hash buckets awaiting a rehash */
   int64_t block_high_water;  /* block pool slots ever used */
   int64_t rehashes;          /* hash rebuilds (tombstone clean-ups) so far */
+  int64_t emitted_triangles; /* triangles written by mesh passes so far */
+  int64_t released_triangles;/* triangles released by mesh passes so far */
+  int64_t refreshed_vertices;/* vertex positions and normals recomputed so far */
 } vm_frame_stats;
 
 /* Flags of vm_update_mesh / vm_step. */
@@ -211,7 +214,9 @@ vm_status vm_set_blocks(vm_volume* vol, const int32_t* keys, int64_t n, const fl
 /* Device time of the library's kernels, accumulated while timing is on (CUDA events on
  * the volume's stream around each launch; inside a vm_step CUDA graph they are event-record
  * nodes, whose times are added when the next replay starts or vm_kernel_times is called).
- * enable != 0 turns it on and clears the totals (a captured frame graph is re-captured).
+ * `enable` is a kernel mask: bit k times the k-th kernel in vm_kernel_times order, -1 all
+ * of them, 0 none; the call clears the totals, and a captured frame graph is re-captured
+ * on the next vm_step (event nodes cost device time, so time only what is needed).
  * vm_kernel_times synchronises and writes up to `cap` entries of (name, total
  * milliseconds, launches); returns the number of kernels in *n. */
 vm_status vm_enable_timing(vm_volume* vol, int enable);

@@ -10,15 +10,16 @@
 namespace vmk {
 
 // ------------------------------------------------------------------ block collection
-constexpr int ALLOC_TILE_W = 64;     // pixels per tile row (16 threads x 4 pixels)
+constexpr int ALLOC_TILE_W = 64;     // pixels per tile row (one pixel per thread)
 constexpr int ALLOC_TILE_H = 16;     // tile rows
-constexpr int ALLOC_THREADS = 256;
-constexpr int ALLOC_SET = 2048;      // CTA-local set of block keys (power of two)
+constexpr int ALLOC_THREADS = ALLOC_TILE_W * ALLOC_TILE_H;
+constexpr int ALLOC_SET = 1024;      // CTA-local set of block keys (power of two)
 constexpr int DDA_MAX_CELLS = 1 << 16;
 
 // Insert `key` into the global hash; returns its bucket or -1.  A new key takes a block
-// from the block pool; its index is published in vals[] for later kernels.
-__device__ int hash_insert(const Vol& V, uint64_t key, int bx, int by, int bz) {
+// from the block pool (stamped with the creating integrate call); its index is published
+// in vals[] for later kernels.
+__device__ int hash_insert(const Vol& V, uint64_t key, int bx, int by, int bz, uint32_t frame) {
   uint32_t s = (uint32_t)mix64(key) & V.hmask;
   for (uint32_t p = 0; p <= V.hmask; ++p) {
     uint64_t k = __ldcg(&V.keys[s]);
@@ -41,6 +42,7 @@ __device__ int hash_insert(const Vol& V, uint64_t key, int bx, int by, int bz) {
         V.vals[s] = blk;
         if (blk >= 0) {
           V.bkey[blk] = make_int4(bx, by, bz, (int)s);
+          V.bborn[blk] = frame;
           atomicAdd(&V.ctl->c[C_LIVE_BLOCKS], 1);
           atomicAdd(&V.ctl->c[C_ST_NEW_BLOCKS], 1);
         }
@@ -64,8 +66,8 @@ __device__ __forceinline__ void touch_bucket(const Vol& V, int s, uint32_t frame
   }
 }
 
-__device__ __forceinline__ void smem_set_insert(unsigned long long* set, int* overflow, const Vol& V,
-                                                uint64_t key, int bx, int by, int bz, uint32_t frame) {
+__device__ __forceinline__ void smem_set_insert(unsigned long long* set, const Vol& V, uint64_t key, int bx, int by,
+                                                int bz, uint32_t frame) {
   uint32_t h = (uint32_t)(mix64(key) >> 20) & (ALLOC_SET - 1);
   for (int p = 0; p < 32; ++p) {
     unsigned long long old = atomicCAS(&set[h], (unsigned long long)KEY_EMPTY, (unsigned long long)key);
@@ -73,105 +75,99 @@ __device__ __forceinline__ void smem_set_insert(unsigned long long* set, int* ov
     h = (h + 1) & (ALLOC_SET - 1);
   }
   // CTA set saturated: insert directly
-  *overflow = 1;
-  int s = hash_insert(V, key, bx, by, bz);
+  int s = hash_insert(V, key, bx, by, bz, frame);
   if (s >= 0) touch_bucket(V, s, frame);
 }
 
-// Walk the block cells of one pixel's segment (Eq. 1) into the CTA set.
+// DDA set-up along one axis: start cell c, remaining steps rem, step direction, the ray
+// parameter of the first boundary crossing (tmax) and between crossings (tdel).
+__device__ __forceinline__ void dda_axis(float a, float b, int& c, int& rem, int& step, float& tmax, float& tdel) {
+  c = (int)floorf(a);
+  const int e = (int)floorf(b);
+  const float dir = b - a;
+  if (dir > 0.0f) {
+    step = 1;
+    tdel = 1.0f / dir;
+    tmax = (((float)c + 1.0f) - a) / dir;
+  } else if (dir < 0.0f) {
+    step = -1;
+    tdel = 1.0f / (-dir);
+    tmax = (a - (float)c) / (-dir);
+  } else {
+    step = 0;
+    tdel = __int_as_float(0x7f800000);
+    tmax = __int_as_float(0x7f800000);
+  }
+  rem = abs(e - c);
+}
+
+// Walk the block cells of one pixel's segment (Eq. 1) into the CTA set; `last` holds the
+// key this thread inserted most recently (neighbouring pixels mostly cross the same cells).
 __device__ __forceinline__ void collect_pixel(const Vol& V, const FrameParams& fp, int u, int v, float D,
-                                              unsigned long long* set, int* overflow, uint32_t frame) {
+                                              unsigned long long* set, uint32_t frame, uint64_t& last) {
   if (!(D > 0.0f) || !isfinite(D)) return;
-  float xn = ((float)u - fp.cx) / fp.fx;
-  float yn = ((float)v - fp.cy) / fp.fy;
+  const float xn = ((float)u - fp.cx) / fp.fx;
+  const float yn = ((float)v - fp.cy) / fp.fy;
   float z0 = D - V.mu;
   if (z0 < Z_NEAR) z0 = Z_NEAR;
-  float z1 = D + V.mu;
-  float pa[3] = {xn * z0, yn * z0, z0};
-  float pb[3] = {xn * z1, yn * z1, z1};
-  float bs = V.l * (float)BS;
+  const float z1 = D + V.mu;
+  const float pa0 = xn * z0, pa1 = yn * z0, pa2 = z0;
+  const float pb0 = xn * z1, pb1 = yn * z1, pb2 = z1;
+  const float bs = V.l * (float)BS;
   float A[3], B[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    float wa = ((fp.Twc[4 * i] * pa[0] + fp.Twc[4 * i + 1] * pa[1]) + fp.Twc[4 * i + 2] * pa[2]) + fp.Twc[4 * i + 3];
-    float wb = ((fp.Twc[4 * i] * pb[0] + fp.Twc[4 * i + 1] * pb[1]) + fp.Twc[4 * i + 2] * pb[2]) + fp.Twc[4 * i + 3];
+    float wa = ((fp.Twc[4 * i] * pa0 + fp.Twc[4 * i + 1] * pa1) + fp.Twc[4 * i + 2] * pa2) + fp.Twc[4 * i + 3];
+    float wb = ((fp.Twc[4 * i] * pb0 + fp.Twc[4 * i + 1] * pb1) + fp.Twc[4 * i + 2] * pb2) + fp.Twc[4 * i + 3];
     A[i] = wa / bs;
     B[i] = wb / bs;
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i)
     if (!isfinite(A[i]) || !isfinite(B[i]) || fabsf(A[i]) > (float)KEY_LIMIT || fabsf(B[i]) > (float)KEY_LIMIT) return;
-  // 3D DDA over block cells, from floor(A) to floor(B); ties step x before y before z
-  int c[3], rem[3], step[3];
-  float tmax[3], tdel[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    c[i] = (int)floorf(A[i]);
-    int e = (int)floorf(B[i]);
-    float dir = B[i] - A[i];
-    if (dir > 0.0f) {
-      step[i] = 1;
-      tdel[i] = 1.0f / dir;
-      tmax[i] = (((float)c[i] + 1.0f) - A[i]) / dir;
-    } else if (dir < 0.0f) {
-      step[i] = -1;
-      tdel[i] = 1.0f / (-dir);
-      tmax[i] = (A[i] - (float)c[i]) / (-dir);
-    } else {
-      step[i] = 0;
-      tdel[i] = __int_as_float(0x7f800000);
-      tmax[i] = __int_as_float(0x7f800000);
-    }
-    rem[i] = abs(e - c[i]);
-  }
-  // The walk has rem_x + rem_y + rem_z + 1 cells; the parameter limits checked on the host
+  // 3D DDA over block cells from floor(A) to floor(B): one step at a time along the axis
+  // whose next boundary comes first among the axes with steps left (ties x, then y, then z)
+  int cx, cy, cz, rx, ry, rz, sx, sy, sz;
+  float mx, my, mz, dx, dy, dz;
+  dda_axis(A[0], B[0], cx, rx, sx, mx, dx);
+  dda_axis(A[1], B[1], cy, ry, sy, my, dy);
+  dda_axis(A[2], B[2], cz, rz, sz, mz, dz);
+  // The walk has rx + ry + rz + 1 cells; the parameter limits checked on the host
   // (voxel >= 0.1 mm, mu <= 32 voxels, |pixel ray slope| <= 64) keep it far below the cap,
   // which only guards against a runaway loop.
   for (int it = 0; it < DDA_MAX_CELLS; ++it) {
-    smem_set_insert(set, overflow, V, pack_key(c[0], c[1], c[2]), c[0], c[1], c[2], frame);
-    if (rem[0] + rem[1] + rem[2] == 0) break;
-    int best = -1;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-      if (rem[i] > 0 && (best < 0 || tmax[i] < tmax[best])) best = i;
-    c[best] += step[best];
-    tmax[best] += tdel[best];
-    rem[best]--;
+    const uint64_t key = pack_key(cx, cy, cz);
+    if (key != last) {
+      smem_set_insert(set, V, key, cx, cy, cz, frame);
+      last = key;
+    }
+    if (rx + ry + rz == 0) break;
+    int best = rx > 0 ? 0 : -1;
+    float bt = mx;
+    if (ry > 0 && (best < 0 || my < bt)) { best = 1; bt = my; }
+    if (rz > 0 && (best < 0 || mz < bt)) { best = 2; }
+    if (best == 0) { cx += sx; mx += dx; --rx; }
+    else if (best == 1) { cy += sy; my += dy; --ry; }
+    else { cz += sz; mz += dz; --rz; }
   }
 }
 
-// One CTA per 64 x 16 pixel tile: each thread reads 4 consecutive depths (one float4 when
-// the row is 16-byte aligned), walks their segments into a CTA-local key set, then the
-// set's unique keys are inserted into the global hash and recorded as collected.
-// The last CTA clamps the block free-stack top and, when `advance_epoch`, starts a new
-// mesh epoch with an empty update set.
+// One CTA per 64 x 16 pixel tile, one pixel per thread: walk the pixel's segment into a
+// CTA-local key set, then insert the set's unique keys into the global hash and record
+// them as collected.  The last CTA clamps the block free-stack top and, when
+// `advance_epoch`, starts a new mesh epoch with an empty update set.
 __global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(Vol V, const FrameParams* __restrict__ fpp,
                                                          int advance_epoch) {
   __shared__ unsigned long long set[ALLOC_SET];
-  __shared__ int overflow;
-  const FrameParams fp = *fpp;
+  const FrameParams& fp = *fpp;
   const uint32_t frame = (uint32_t)__ldcg(&V.ctl->c[C_FRAME]);
   for (int i = threadIdx.x; i < ALLOC_SET; i += blockDim.x) set[i] = KEY_EMPTY;
-  if (threadIdx.x == 0) overflow = 0;
+  const int u = blockIdx.x * ALLOC_TILE_W + (threadIdx.x & (ALLOC_TILE_W - 1));
+  const int v = blockIdx.y * ALLOC_TILE_H + threadIdx.x / ALLOC_TILE_W;
+  const float D = (u < fp.W && v < fp.H) ? __ldg(fp.depth + (size_t)v * fp.W + u) : 0.0f;
   __syncthreads();
-
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int u0 = blockIdx.x * ALLOC_TILE_W + tx * 4;
-  const int v = blockIdx.y * ALLOC_TILE_H + ty;
-  if (v < fp.H && u0 < fp.W) {
-    const float* row = fp.depth + (size_t)v * fp.W;
-    float d[4];
-    if (u0 + 3 < fp.W && ((reinterpret_cast<uintptr_t>(row + u0) & 15) == 0)) {
-      float4 q = __ldg(reinterpret_cast<const float4*>(row + u0));
-      d[0] = q.x; d[1] = q.y; d[2] = q.z; d[3] = q.w;
-    } else {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) d[j] = (u0 + j < fp.W) ? __ldg(row + u0 + j) : 0.0f;
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if (u0 + j < fp.W) collect_pixel(V, fp, u0 + j, v, d[j], set, &overflow, frame);
-  }
+  uint64_t last = KEY_EMPTY;
+  if (u < fp.W && v < fp.H) collect_pixel(V, fp, u, v, D, set, frame, last);
   __syncthreads();
   for (int i = threadIdx.x; i < ALLOC_SET; i += blockDim.x) {
     uint64_t key = set[i];
@@ -179,7 +175,7 @@ __global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(Vol V, const FrameParam
     int bx = (int)((key >> 42) & 0x1FFFFF) - KEY_BIAS;
     int by = (int)((key >> 21) & 0x1FFFFF) - KEY_BIAS;
     int bz = (int)(key & 0x1FFFFF) - KEY_BIAS;
-    int s = hash_insert(V, key, bx, by, bz);
+    int s = hash_insert(V, key, bx, by, bz, frame);
     if (s >= 0) touch_bucket(V, s, frame);
   }
   if (last_block(V, C_DONE0)) {
@@ -194,95 +190,103 @@ __global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(Vol V, const FrameParam
   }
 }
 
-// Collected buckets -> blocks; each collected block and its existing neighbours at
-// offsets {0,-1}^3 join the update set once per epoch.  8 lanes per collected bucket.
-__global__ void __launch_bounds__(256) k_resolve(Vol V) {
-  const int n = __ldcg(&V.ctl->c[C_N_TOUCHED]);
-  const uint32_t epoch = (uint32_t)__ldcg(&V.ctl->c[C_EPOCH]);
-  const int total = (n < V.list_cap_touched ? n : V.list_cap_touched) * 8;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-    int i = t >> 3, o = t & 7;
-    int s = V.touched[i];
-    int blk = __ldcg(&V.vals[s]);
-    if (o == 0) {
-      V.touched_blk[i] = blk;
-      if (blk >= 0) V.bepoch[blk] = epoch;
-    }
-    if (blk < 0) continue;
-    int4 k = V.bkey[blk];
-    int ns = o == 0 ? s : hash_find(V, pack_key(k.x - (o & 1), k.y - ((o >> 1) & 1), k.z - ((o >> 2) & 1)));
-    if (ns < 0) continue;
-    int nb = __ldcg(&V.vals[ns]);
-    if (nb < 0) continue;
-    if (__ldcg(&V.ustamp[ns]) == epoch) continue;
-    if (atomicExch(&V.ustamp[ns], epoch) != epoch) list_push(V, V.update, C_N_UPDATE, V.list_cap_update, nb);
+// Resolve one collected bucket (threads 0..15 of the calling CTA):
+//   - the block and its existing neighbours at offsets {0,-1}^3 join the update set once
+//     per epoch (their cubes read corners in the collected block);
+//   - a block created by this integrate call links itself into the neighbour table (and
+//     its neighbours to it), looking its neighbours up in the hash.
+// Old blocks read their lower neighbours from the table.  A new block's table entries may
+// race with an old neighbour reading them, but new blocks are collected themselves, so no
+// update-set member is lost.
+__device__ __forceinline__ void resolve_block(const Vol& V, int blk, int4 key, uint32_t frame, uint32_t epoch) {
+  const int t = threadIdx.x;
+  if (t >= 16) return;
+  const bool is_new = __ldcg(&V.bborn[blk]) == frame;
+  const int o = t & 7;
+  const int sgn = t < 8 ? -1 : 1;  // threads 0..7: lower neighbours (and self), 8..15: upper
+  int nb;
+  if (o == 0) {
+    nb = blk;
+  } else if (is_new) {
+    nb = find_block(V, key.x + sgn * (o & 1), key.y + sgn * ((o >> 1) & 1), key.z + sgn * ((o >> 2) & 1));
+    // table: my slot for this offset, and the neighbour's slot for the opposite offset
+    V.nbr[blk * 16 + (sgn > 0 ? o : 8 + o)] = nb;
+    if (nb >= 0) V.nbr[nb * 16 + (sgn > 0 ? 8 + o : o)] = blk;
+  } else {
+    nb = sgn < 0 ? __ldcg(&V.nbr[blk * 16 + 8 + o]) : -1;
   }
-  if (last_block(V, C_DONE1)) {
-    if (threadIdx.x == 0) {
-      V.ctl->c[C_ST_FRAME_BLOCKS] = n;
-      V.ctl->c[C_DONE1] = 0;
-    }
-  }
+  if (t == 0) V.bepoch[blk] = epoch;
+  if (sgn > 0 || nb < 0) return;
+  const int ns = o == 0 ? key.w : __ldcg(&V.bkey[nb].w);
+  if (ns < 0) return;
+  if (__ldcg(&V.ustamp[ns]) == epoch) return;
+  if (atomicExch(&V.ustamp[ns], epoch) != epoch) list_push(V, V.update, C_N_UPDATE, V.list_cap_update, nb);
 }
 
 // ------------------------------------------------------------------ fusion (Eq. 2)
 constexpr int INTEG_THREADS = 128;  // 4 voxels per thread, one block per CTA iteration
 
-// Fuse the frame into every voxel of each collected block.  Voxels stream as float2
-// (d, W) pairs, 32 bytes per thread per block; depth is gathered through the read-only
-// path.  Also records whether any voxel of the block has W > 0 and d < mu (used by gc).
-// The last CTA resets the collected list and advances the frame counter.
+// Per collected bucket: resolve it (update set, neighbour table), then (FUSE) fuse the frame
+// into every voxel of its block.  Voxels stream as float2 (d, W) pairs, 32 bytes per
+// thread; depth is gathered through the read-only path.  Also records whether any voxel
+// of the block has W > 0 and d < mu (used by gc).  The last CTA empties the collected list
+// and advances the integrate-call counter.
+template <bool FUSE>
 __global__ void __launch_bounds__(INTEG_THREADS) k_integrate(Vol V, const FrameParams* __restrict__ fpp) {
-  const FrameParams fp = *fpp;
   const int n = min(__ldcg(&V.ctl->c[C_N_TOUCHED]), V.list_cap_touched);
+  const uint32_t frame = (uint32_t)__ldcg(&V.ctl->c[C_FRAME]);
+  const uint32_t epoch = (uint32_t)__ldcg(&V.ctl->c[C_EPOCH]);
   const float mu = V.mu, l = V.l, wmax = V.wmax;
   const int v0 = threadIdx.x * 4;
   const int lx = v0 & 7, ly = (v0 >> 3) & 7, lz = v0 >> 6;
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
-    int blk = V.touched_blk[i];
+    const int blk = __ldcg(&V.vals[V.touched[i]]);
     if (blk < 0) continue;
-    int4 key = V.bkey[blk];
+    const int4 key = V.bkey[blk];
+    resolve_block(V, blk, key, frame, epoch);
+    if (!FUSE) continue;
+    const FrameParams& fp = *fpp;
     float4* p = reinterpret_cast<float4*>(V.tw + (size_t)blk * BV + v0);
-    float4 q0 = __ldcs(p), q1 = __ldcs(p + 1);
+    float4 q0 = __ldcg(p), q1 = __ldcg(p + 1);
     float dd[4] = {q0.x, q0.z, q1.x, q1.z};
     float ww[4] = {q0.y, q0.w, q1.y, q1.w};
     bool changed = false;
-    const int gy = key.y * BS + ly, gz = key.z * BS + lz;
-    const float py = (float)gy * l, pz = (float)gz * l;
+    const float py = (float)(key.y * BS + ly) * l, pz = (float)(key.z * BS + lz) * l;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      float px = (float)(key.x * BS + lx + j) * l;
-      float xc = ((fp.Tcw[0] * px + fp.Tcw[1] * py) + fp.Tcw[2] * pz) + fp.Tcw[3];
-      float yc = ((fp.Tcw[4] * px + fp.Tcw[5] * py) + fp.Tcw[6] * pz) + fp.Tcw[7];
-      float zc = ((fp.Tcw[8] * px + fp.Tcw[9] * py) + fp.Tcw[10] * pz) + fp.Tcw[11];
+      const float px = (float)(key.x * BS + lx + j) * l;
+      const float xc = ((fp.Tcw[0] * px + fp.Tcw[1] * py) + fp.Tcw[2] * pz) + fp.Tcw[3];
+      const float yc = ((fp.Tcw[4] * px + fp.Tcw[5] * py) + fp.Tcw[6] * pz) + fp.Tcw[7];
+      const float zc = ((fp.Tcw[8] * px + fp.Tcw[9] * py) + fp.Tcw[10] * pz) + fp.Tcw[11];
       if (!(zc > 0.0f)) continue;
-      float us = ((fp.fx * xc) / zc + fp.cx) + 0.5f;
-      float vs = ((fp.fy * yc) / zc + fp.cy) + 0.5f;
+      const float us = ((fp.fx * xc) / zc + fp.cx) + 0.5f;
+      const float vs = ((fp.fy * yc) / zc + fp.cy) + 0.5f;
       if (!(us >= 0.0f && us < (float)fp.W && vs >= 0.0f && vs < (float)fp.H)) continue;
-      int iu = (int)floorf(us), iv = (int)floorf(vs);
-      float D = __ldg(fp.depth + (size_t)iv * fp.W + iu);
+      const int iu = (int)floorf(us), iv = (int)floorf(vs);
+      const float D = __ldg(fp.depth + (size_t)iv * fp.W + iu);
       if (!(D > 0.0f) || !isfinite(D)) continue;
-      float sdf = D - zc;
+      const float sdf = D - zc;
       if (sdf < -mu) continue;
-      float dt = sdf < mu ? sdf : mu;
-      float num = dd[j] * ww[j] + dt;
-      float den = ww[j] + 1.0f;
+      const float dt = sdf < mu ? sdf : mu;
+      const float num = dd[j] * ww[j] + dt;
+      const float den = ww[j] + 1.0f;
       dd[j] = num / den;
       ww[j] = den < wmax ? den : wmax;
       changed = true;
     }
     if (changed) {
-      __stcs(p, make_float4(dd[0], ww[0], dd[1], ww[1]));
-      __stcs(p + 1, make_float4(dd[2], ww[2], dd[3], ww[3]));
+      p[0] = make_float4(dd[0], ww[0], dd[1], ww[1]);
+      p[1] = make_float4(dd[2], ww[2], dd[3], ww[3]);
     }
     bool near = false;
 #pragma unroll
     for (int j = 0; j < 4; ++j) near |= (ww[j] > 0.0f && dd[j] < mu);
-    int any = __syncthreads_or(near);
+    const int any = __syncthreads_or(near);
     if (threadIdx.x == 0) V.bnear[blk] = (uint8_t)(any != 0);
   }
   if (last_block(V, C_DONE2)) {
     if (threadIdx.x == 0) {
+      V.ctl->c[C_ST_FRAME_BLOCKS] = n;
       V.ctl->c[C_N_TOUCHED] = 0;
       V.ctl->c[C_FRAME] += 1;
       V.ctl->c[C_DONE2] = 0;

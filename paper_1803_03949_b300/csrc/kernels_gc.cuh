@@ -1,36 +1,97 @@
 // Garbage collection (Sec. V-E): vertices whose reference count (= vertex degree)
-// dropped to zero are recycled, and so are blocks that carry no surface any more.
-// Triangles are recycled by the mesh passes as soon as their cube changes type.
+// dropped to zero are recycled, so are the triangle runs the mesh pass released and the
+// blocks that carry no surface any more.
 #pragma once
 
 #include "vmesh_device.cuh"
 
 namespace vmk {
 
-// Zero-reference vertices: claim with CAS(0 -> -1) so a vertex listed twice, or one that
-// regained a reference in a later pass, is freed at most once and only when unreferenced.
+// Push a triangle run onto the free stack of its length, aggregated over lanes with the
+// same length.
+__device__ __forceinline__ void run_push(const Vol& V, int L, int base) {
+  cg::coalesced_group g0 = cg::coalesced_threads();
+  cg::coalesced_group g = cg::labeled_partition(g0, L);
+  int slot = 0;
+  if (g.thread_rank() == 0) slot = atomicAdd(&V.ctl->c[C_RUN_TOP0 + L - 1], (int)g.size());
+  slot = g.shfl(slot, 0) + (int)g.thread_rank();
+  if (slot < V.run_cap[L - 1]) V.run_free[L - 1][slot] = base;
+  else set_status(V, ST_POOL_FULL);
+}
+
+// Zero-reference vertices: claim with CAS(0 -> -1), so a vertex listed twice, or one that
+// regained a reference after it was listed, is freed at most once and only when
+// unreferenced; a vertex still attached to its edge is detached.  Released triangle runs
+// go back to their free stacks.
 __global__ void __launch_bounds__(256) k_gc_vertices(Vol V) {
   const int n = min(__ldcg(&V.ctl->c[C_N_DEAD]), V.list_cap_dead);
+  const int nr = min(__ldcg(&V.ctl->c[C_N_DEADRUN]), V.list_cap_deadrun);
   int freed = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int vid = V.dead[i];
     if (atomicCAS(&V.vref[vid], 0, -1) != 0) continue;
     const int e = V.vedge[vid];
-    const int ob = e / EPB, r = e - ob * EPB, ov = r / 3, a = r - ov * 3;
-    V.edge_vtx[e] = -1;
-    atomic_and_u8(V.vmask + (size_t)ob * BV + ov, (uint8_t)~(9 << a));
-    atomicSub(&V.bnvert[ob], 1);
+    if (e >= 0) {
+      const int ob = e / EPB, r = e - ob * EPB, ov = r / 3, a = r - ov * 3;
+      V.edge_vtx[e] = -1;
+      atomic_and_u8(V.vmask + (size_t)ob * BV + ov, (uint8_t)~(1 << a));
+      atomicSub(&V.bnvert[ob], 1);
+      ++freed;
+    }
     pool_push(V, V.vtx_free, C_VTX_TOP, V.max_vertices, vid);
-    ++freed;
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
+    const int2 r = V.deadrun[i];
+    if (r.y >= 1 && r.y <= 5) run_push(V, r.y, r.x);
   }
   if (freed) {
-    atomicSub(&V.ctl->c[C_LIVE_VERTS], freed);
-    atomicAdd(&V.ctl->c[C_ST_FREED_VERTS], freed);
+    counter_add(V, C_LIVE_VERTS, -freed);
+    counter_add(V, C_ST_FREED_VERTS, freed);
   }
   if (last_block(V, C_DONE5)) {
     if (threadIdx.x == 0) {
       V.ctl->c[C_N_DEAD] = 0;
+      V.ctl->c[C_N_DEADRUN] = 0;
       V.ctl->c[C_DONE5] = 0;
+    }
+  }
+}
+
+// Rebuild the hash without tombstones (one CTA): empty every bucket, re-insert every live
+// block from the block array (bkey holds its key; its new bucket is written back), then
+// re-mark the pending update set so no block is listed twice.
+__device__ void rehash_in_cta(const Vol& V, bool mark_update) {
+  for (uint32_t s = threadIdx.x; s <= V.hmask; s += blockDim.x) {
+    V.keys[s] = KEY_EMPTY;
+    V.vals[s] = -1;
+    V.stamp[s] = 0;
+    V.ustamp[s] = 0;
+  }
+  __threadfence();
+  __syncthreads();
+  const int hw = min(__ldcg(&V.ctl->c[C_BLK_BUMP]), V.max_blocks);
+  for (int blk = threadIdx.x; blk < hw; blk += blockDim.x) {
+    const int4 k = V.bkey[blk];
+    if (k.w < 0) continue;
+    const uint64_t key = pack_key(k.x, k.y, k.z);
+    uint32_t s = (uint32_t)mix64(key) & V.hmask;
+    for (uint32_t p = 0; p <= V.hmask; ++p) {
+      const unsigned long long old = atomicCAS((unsigned long long*)&V.keys[s], (unsigned long long)KEY_EMPTY,
+                                               (unsigned long long)key);
+      if (old == KEY_EMPTY) break;
+      s = (s + 1) & V.hmask;
+    }
+    V.vals[s] = blk;
+    V.bkey[blk].w = (int)s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (mark_update) {
+    const int n = min(__ldcg(&V.ctl->c[C_N_UPDATE]), V.list_cap_update);
+    const uint32_t epoch = (uint32_t)__ldcg(&V.ctl->c[C_EPOCH]);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int4 k = V.bkey[V.update[i]];
+      if (k.w >= 0) V.ustamp[k.w] = epoch;
     }
   }
 }
@@ -38,10 +99,11 @@ __global__ void __launch_bounds__(256) k_gc_vertices(Vol V) {
 // Block recycling, one warp per pool slot.  A block is freed when it was not collected in
 // the current epoch, has no triangles and owns no vertex, all of its voxels have W = 0 or
 // d >= mu, and none of its 7 lower neighbours (whose cubes reach into it) has triangles.
-// Its bucket becomes a tombstone, its voxels are cleared, its index returns to the pool.
-// `consumed` says the update set has been meshed since it was collected: then it is
-// emptied here; otherwise its blocks are kept so that the pending update never lists a
-// recycled (and possibly reallocated) block index.
+// Its bucket becomes a tombstone, its voxels are cleared, its neighbours forget it, its
+// index returns to the pool.  `consumed` says the update set has been meshed since it was
+// collected: then it is emptied here; otherwise its blocks are kept so that the pending
+// update never lists a recycled (and possibly reallocated) block index.  The last CTA
+// rebuilds the hash when live plus dead buckets pass half the table.
 __global__ void __launch_bounds__(256) k_gc_blocks(Vol V, int consumed) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -51,36 +113,36 @@ __global__ void __launch_bounds__(256) k_gc_blocks(Vol V, int consumed) {
   int freed = 0;
   for (int blk = warp; blk < hw; blk += nwarps) {
     const int4 key = V.bkey[blk];
-    bool cand = key.w >= 0 && V.bepoch[blk] != epoch && V.bntri[blk] == 0 && V.bnvert[blk] == 0 &&
-                V.bnear[blk] == 0 && (consumed || V.ustamp[key.w] != epoch);
+    const bool cand = key.w >= 0 && V.bepoch[blk] != epoch && V.bntri[blk] == 0 && V.bnvert[blk] == 0 &&
+                      V.bnear[blk] == 0 && (consumed || V.ustamp[key.w] != epoch);
     if (!cand) continue;  // warp-uniform
     bool lower_tri = false;
     if (lane >= 1 && lane < 8) {
-      int o = lane;
-      int nbk = find_block(V, key.x - (o & 1), key.y - ((o >> 1) & 1), key.z - ((o >> 2) & 1));
+      const int nbk = V.nbr[blk * 16 + 8 + lane];
       lower_tri = nbk >= 0 && V.bntri[nbk] != 0;
     }
     if (__any_sync(0xffffffffu, lower_tri)) continue;
     // free it
     float4* tw = reinterpret_cast<float4*>(V.tw + (size_t)blk * BV);
     for (int j = lane; j < BV / 2; j += 32) tw[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-    uint4* ce = reinterpret_cast<uint4*>(V.code_eff + (size_t)blk * BV);
-    uint4* cp = reinterpret_cast<uint4*>(V.code_prev + (size_t)blk * BV);
-    uint4* vm = reinterpret_cast<uint4*>(V.vmask + (size_t)blk * BV);
-    uint4* ch = reinterpret_cast<uint4*>(V.chg + (size_t)blk * BV);
-    ce[lane] = make_uint4(0, 0, 0, 0);
-    cp[lane] = make_uint4(0, 0, 0, 0);
-    vm[lane] = make_uint4(0, 0, 0, 0);
-    ch[lane] = make_uint4(0, 0, 0, 0);
+    reinterpret_cast<uint4*>(V.code_eff + (size_t)blk * BV)[lane] = make_uint4(0, 0, 0, 0);
+    reinterpret_cast<uint4*>(V.code_prev + (size_t)blk * BV)[lane] = make_uint4(0, 0, 0, 0);
+    reinterpret_cast<uint4*>(V.vmask + (size_t)blk * BV)[lane] = make_uint4(0, 0, 0, 0);
+    if (lane >= 1 && lane < 16 && lane != 8) {
+      // unlink: the neighbour at this slot's offset forgets this block
+      const int other = V.nbr[blk * 16 + lane];
+      if (other >= 0) V.nbr[other * 16 + (lane ^ 8)] = -1;
+    }
+    __syncwarp();
+    if (lane < 16) V.nbr[blk * 16 + lane] = -1;
     if (lane == 0) {
       V.keys[key.w] = KEY_TOMB;
       V.vals[key.w] = -1;
       V.bkey[blk] = make_int4(0, 0, 0, -1);
       V.bnear[blk] = 0;
       ++freed;
+      pool_push(V, V.blk_free, C_BLK_TOP, V.max_blocks, blk);
     }
-    __syncwarp();
-    if (lane == 0) pool_push(V, V.blk_free, C_BLK_TOP, V.max_blocks, blk);
   }
   if (lane == 0 && freed) {
     atomicSub(&V.ctl->c[C_LIVE_BLOCKS], freed);
@@ -88,68 +150,22 @@ __global__ void __launch_bounds__(256) k_gc_blocks(Vol V, int consumed) {
     atomicAdd(&V.ctl->c[C_ST_FREED_BLOCKS], freed);
   }
   if (last_block(V, C_DONE7)) {
+    __shared__ int need;
+    if (threadIdx.x == 0) {
+      const long long live = V.ctl->c[C_LIVE_BLOCKS], tomb = V.ctl->c[C_TOMBS];
+      need = (live + tomb) * 2 > (long long)V.hmask + 1 && tomb > 0;
+    }
+    __syncthreads();
+    if (need) {
+      rehash_in_cta(V, !consumed);
+      if (threadIdx.x == 0) {
+        V.ctl->c[C_TOMBS] = 0;
+        V.ctl->c[C_ST_REHASHES] += 1;
+      }
+    }
     if (threadIdx.x == 0) {
       if (consumed) V.ctl->c[C_N_UPDATE] = 0;
       V.ctl->c[C_DONE7] = 0;
-    }
-  }
-}
-
-// Rebuild the hash without tombstones when live + dead buckets pass half the table:
-// check (one thread) -> wipe every bucket -> re-insert every live block from the block
-// array (bkey holds its key; the new bucket is written back) -> re-mark the current
-// update set so a block is never listed twice.  Each kernel returns at once when no
-// rebuild is needed, so the sequence can sit in every gc call (and in a CUDA graph).
-__global__ void k_rehash_check(Vol V) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    long long live = __ldcg(&V.ctl->c[C_LIVE_BLOCKS]), tomb = __ldcg(&V.ctl->c[C_TOMBS]);
-    V.ctl->c[C_REHASH] = (live + tomb) * 2 > (long long)V.hmask + 1 && tomb > 0;
-  }
-}
-
-__global__ void __launch_bounds__(256) k_rehash_wipe(Vol V) {
-  if (!__ldcg(&V.ctl->c[C_REHASH])) return;
-  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s <= V.hmask; s += gridDim.x * blockDim.x) {
-    V.keys[s] = KEY_EMPTY;
-    V.vals[s] = -1;
-    V.stamp[s] = 0;
-    V.ustamp[s] = 0;
-  }
-}
-
-__global__ void __launch_bounds__(256) k_rehash_insert(Vol V) {
-  if (!__ldcg(&V.ctl->c[C_REHASH])) return;
-  const int hw = min(__ldcg(&V.ctl->c[C_BLK_BUMP]), V.max_blocks);
-  for (int blk = blockIdx.x * blockDim.x + threadIdx.x; blk < hw; blk += gridDim.x * blockDim.x) {
-    int4 k = V.bkey[blk];
-    if (k.w < 0) continue;
-    uint64_t key = pack_key(k.x, k.y, k.z);
-    uint32_t s = (uint32_t)mix64(key) & V.hmask;
-    for (uint32_t p = 0; p <= V.hmask; ++p) {
-      unsigned long long old = atomicCAS((unsigned long long*)&V.keys[s], (unsigned long long)KEY_EMPTY,
-                                         (unsigned long long)key);
-      if (old == KEY_EMPTY) break;
-      s = (s + 1) & V.hmask;
-    }
-    V.vals[s] = blk;
-    V.bkey[blk].w = (int)s;
-  }
-}
-
-__global__ void __launch_bounds__(256) k_rehash_mark(Vol V) {
-  if (!__ldcg(&V.ctl->c[C_REHASH])) return;
-  const int n = min(__ldcg(&V.ctl->c[C_N_UPDATE]), V.list_cap_update);
-  const uint32_t epoch = (uint32_t)__ldcg(&V.ctl->c[C_EPOCH]);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    int4 k = V.bkey[V.update[i]];
-    if (k.w >= 0) V.ustamp[k.w] = epoch;
-  }
-  if (last_block(V, C_DONE6)) {
-    if (threadIdx.x == 0) {
-      V.ctl->c[C_TOMBS] = 0;
-      V.ctl->c[C_REHASH] = 0;
-      V.ctl->c[C_ST_REHASHES] += 1;
-      V.ctl->c[C_DONE6] = 0;
     }
   }
 }

@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(256) k_fill_insert(Vol V, const int* keys, int
       set_status(V, ST_INVALID);
       continue;
     }
-    int s = hash_insert(V, pack_key(x, y, z), x, y, z);
+    int s = hash_insert(V, pack_key(x, y, z), x, y, z, frame);
     if (s >= 0) touch_bucket(V, s, frame);
   }
   if (last_block(V, C_DONE0)) {
@@ -196,7 +196,8 @@ __global__ void __launch_bounds__(256) k_fill_insert(Vol V, const int* keys, int
   }
 }
 
-// Analytic fill, phase 2 (after k_resolve): copy the voxel values, set the near flag.
+// Analytic fill, phase 2 (after the collected keys were resolved): copy the voxel values
+// and set the near flag.
 __global__ void __launch_bounds__(256) k_fill_copy(Vol V, const int* keys, const float* tsdf, const float* weight,
                                                    int n) {
   for (int j = blockIdx.x; j < n; j += gridDim.x) {
@@ -210,13 +211,6 @@ __global__ void __launch_bounds__(256) k_fill_copy(Vol V, const int* keys, const
     }
     int any = __syncthreads_or(near);
     if (threadIdx.x == 0) V.bnear[blk] = (uint8_t)(any != 0);
-  }
-  if (last_block(V, C_DONE2)) {
-    if (threadIdx.x == 0) {
-      V.ctl->c[C_N_TOUCHED] = 0;
-      V.ctl->c[C_FRAME] += 1;
-      V.ctl->c[C_DONE2] = 0;
-    }
   }
 }
 

@@ -19,13 +19,9 @@ using namespace vmk;
 
 namespace {
 
-enum KernelId {
-  K_SET_FRAME = 0, K_ALLOC, K_RESOLVE, K_INTEGRATE, K_LIST_ALL, K_MESH_TYPES, K_VERTICES, K_TRIANGLES,
-  K_GC_VERTICES, K_GC_BLOCKS, K_REHASH, K_COUNT_
-};
-const char* kKernelNames[K_COUNT_] = {"k_set_frame", "k_alloc",      "k_resolve",     "k_integrate",
-                                      "k_list_all",  "k_mesh_types", "k_vertices",    "k_triangles",
-                                      "k_gc_vertices", "k_gc_blocks", "k_rehash"};
+enum KernelId { K_SET_FRAME = 0, K_ALLOC, K_INTEGRATE, K_LIST_ALL, K_MESH, K_GC_VERTICES, K_GC_BLOCKS, K_COUNT_ };
+const char* kKernelNames[K_COUNT_] = {"k_set_frame", "k_alloc",       "k_integrate", "k_list_all",
+                                      "k_mesh",      "k_gc_vertices", "k_gc_blocks"};
 
 __global__ void k_set_frame(FrameParams* dst, FrameParams fp) { *dst = fp; }
 
@@ -63,7 +59,7 @@ struct vm_volume {
   int* remap = nullptr;
   int cta_cap = 0;
   // timing
-  bool timing = false;
+  unsigned timing_mask = 0;  // kernels (bit = KernelId) timed with events
   bool capturing = false;
   std::vector<TimingRec> recs;
   std::vector<TimingRec> graph_recs;  // event-record nodes of the captured frame graph
@@ -98,7 +94,8 @@ cudaEvent_t get_event(vm_volume* v) {
 template <typename F>
 vm_status launch(vm_volume* v, int kid, F&& f) {
   cudaEvent_t a = nullptr, b = nullptr;
-  if (v->timing) {
+  const bool timed = (v->timing_mask >> kid) & 1;
+  if (timed) {
     a = get_event(v);
     b = get_event(v);
     if (v->capturing) cudaEventRecordWithFlags(a, v->cur, cudaEventRecordExternal);
@@ -107,7 +104,7 @@ vm_status launch(vm_volume* v, int kid, F&& f) {
   (void)cudaGetLastError();  // drop a stale non-sticky error so it is not blamed on this launch
   f();
   cudaError_t e = cudaGetLastError();
-  if (v->timing) {
+  if (timed) {
     if (v->capturing) {
       cudaEventRecordWithFlags(b, v->cur, cudaEventRecordExternal);
       v->graph_recs.push_back({kid, a, b});
@@ -188,9 +185,8 @@ vm_status enqueue_integrate(vm_volume* v, const FrameParams& fp, bool set_frame)
   dim3 g((fp.W + ALLOC_TILE_W - 1) / ALLOC_TILE_W, (fp.H + ALLOC_TILE_H - 1) / ALLOC_TILE_H);
   st = launch(v, K_ALLOC, [&] { k_alloc<<<g, ALLOC_THREADS, 0, v->cur>>>(v->V, &ctl->fp, adv); });
   if (st) return st;
-  st = launch(v, K_RESOLVE, [&] { k_resolve<<<grid_for(v, 4), 256, 0, v->cur>>>(v->V); });
-  if (st) return st;
-  st = launch(v, K_INTEGRATE, [&] { k_integrate<<<grid_for(v, 8), INTEG_THREADS, 0, v->cur>>>(v->V, &ctl->fp); });
+  st = launch(v, K_INTEGRATE,
+              [&] { k_integrate<true><<<grid_for(v, 8), INTEG_THREADS, 0, v->cur>>>(v->V, &ctl->fp); });
   v->advance_pending = false;
   return st;
 }
@@ -202,11 +198,7 @@ vm_status enqueue_list_all(vm_volume* v) {
 }
 
 vm_status enqueue_mesh_pass(vm_volume* v, int mode) {
-  vm_status st = launch(v, K_MESH_TYPES, [&] { k_mesh_types<<<grid_for(v, 8), MESH_THREADS, 0, v->cur>>>(v->V, mode); });
-  if (st) return st;
-  st = launch(v, K_VERTICES, [&] { k_vertices<<<grid_for(v, 4), 256, 0, v->cur>>>(v->V); });
-  if (st) return st;
-  return launch(v, K_TRIANGLES, [&] { k_triangles<<<grid_for(v, 8), MESH_THREADS, 0, v->cur>>>(v->V); });
+  return launch(v, K_MESH, [&] { k_mesh<<<grid_for(v, 7), MESH_THREADS, 0, v->cur>>>(v->V, mode); });
 }
 
 vm_status enqueue_update(vm_volume* v, int flags) {
@@ -222,14 +214,7 @@ vm_status enqueue_gc(vm_volume* v) {
   vm_status st = launch(v, K_GC_VERTICES, [&] { k_gc_vertices<<<grid_for(v, 2), 256, 0, v->cur>>>(v->V); });
   if (st) return st;
   const int consumed = v->advance_pending ? 1 : 0;
-  st = launch(v, K_GC_BLOCKS, [&] { k_gc_blocks<<<grid_for(v, 8), 256, 0, v->cur>>>(v->V, consumed); });
-  if (st) return st;
-  return launch(v, K_REHASH, [&] {
-    k_rehash_check<<<1, 32, 0, v->cur>>>(v->V);
-    k_rehash_wipe<<<grid_for(v, 4), 256, 0, v->cur>>>(v->V);
-    k_rehash_insert<<<grid_for(v, 4), 256, 0, v->cur>>>(v->V);
-    k_rehash_mark<<<grid_for(v, 2), 256, 0, v->cur>>>(v->V);
-  });
+  return launch(v, K_GC_BLOCKS, [&] { k_gc_blocks<<<grid_for(v, 8), 256, 0, v->cur>>>(v->V, consumed); });
 }
 
 vm_status sync_status(vm_volume* v) {
@@ -315,6 +300,9 @@ vm_status vm_create_volume(const vm_params* p, void* cuda_stream, vm_volume** ou
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&v->num_sms, cudaDevAttrMultiProcessorCount, dev);
   if (v->num_sms <= 0) v->num_sms = 148;
+  // the mesh kernel keeps ~32 KB of shared memory per CTA: ask for the largest carveout
+  cudaFuncSetAttribute(k_mesh, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  (void)cudaGetLastError();
   if (cudaMemcpyToSymbol(c_ntri, table.ntri, sizeof(table.ntri)) != cudaSuccess ||
       cudaMemcpyToSymbol(c_tri, table.tri, sizeof(table.tri)) != cudaSuccess ||
       cudaMemcpyToSymbol(c_edgemask, table.edgemask, sizeof(table.edgemask)) != cudaSuccess) {
@@ -334,22 +322,32 @@ vm_status vm_create_volume(const vm_params* p, void* cuda_stream, vm_volume** ou
   for (int L = 1; L <= 5; ++L) V.run_cap[L - 1] = (int)(p->max_triangles / L) + 1;
   V.list_cap_touched = (int)(p->max_blocks < hb ? p->max_blocks : hb);
   V.list_cap_update = (int)p->max_blocks;
-  V.list_cap_newedge = (int)p->max_vertices;
   V.list_cap_dead = (int)((2ull * p->max_vertices) < (1ull << 31) - 1 ? 2ull * p->max_vertices : (1ull << 31) - 1);
+  V.list_cap_deadrun = (int)p->max_triangles;
   const size_t NB = p->max_blocks, NV = p->max_vertices, NT = p->max_triangles;
   bool ok = dalloc(v, &V.keys, hb, 0xFF) && dalloc(v, &V.vals, hb, 0xFF) && dalloc(v, &V.stamp, hb, 0) &&
-            dalloc(v, &V.ustamp, hb, 0) && dalloc(v, &V.bkey, NB, 0xFF) && dalloc(v, &V.bntri, NB, 0) &&
-            dalloc(v, &V.bnvert, NB, 0) && dalloc(v, &V.bnear, NB, 0) && dalloc(v, &V.bepoch, NB, 0) &&
-            dalloc(v, &V.tw, NB * BV, 0) && dalloc(v, &V.code_eff, NB * BV, 0) &&
-            dalloc(v, &V.code_prev, NB * BV, 0) && dalloc(v, &V.vmask, NB * BV, 0) && dalloc(v, &V.chg, NB * BV, 0) &&
-            dalloc(v, &V.edge_vtx, NB * BV * 3, 0xFF) && dalloc(v, &V.tri_base, NB * BV, 0xFF) &&
-            dalloc(v, &V.vpos, NV, 0) && dalloc(v, &V.vnrm, NV, 0) && dalloc(v, &V.vref, NV, 0xFF) &&
-            dalloc(v, &V.vedge, NV, 0xFF) && dalloc(v, &V.tris, NT, 0xFF) && dalloc(v, &V.blk_free, NB, 0) &&
-            dalloc(v, &V.vtx_free, NV, 0) && dalloc(v, &V.touched, (size_t)V.list_cap_touched, 0) &&
-            dalloc(v, &V.touched_blk, (size_t)V.list_cap_touched, 0) && dalloc(v, &V.update, NB, 0) &&
-            dalloc(v, &V.newedge, NV, 0) && dalloc(v, &V.dead, (size_t)V.list_cap_dead, 0) &&
+            dalloc(v, &V.ustamp, hb, 0) && dalloc(v, &V.bkey, NB, 0xFF) && dalloc(v, &V.nbr, NB * 16, 0xFF) &&
+            dalloc(v, &V.bntri, NB, 0) && dalloc(v, &V.bnvert, NB, 0) && dalloc(v, &V.bnear, NB, 0) &&
+            dalloc(v, &V.bepoch, NB, 0) && dalloc(v, &V.bborn, NB, 0) && dalloc(v, &V.tw, NB * BV, 0) &&
+            dalloc(v, &V.code_eff, NB * BV, 0) && dalloc(v, &V.code_prev, NB * BV, 0) &&
+            dalloc(v, &V.vmask, NB * BV, 0) && dalloc(v, &V.edge_vtx, NB * BV * 3, 0xFF) &&
+            dalloc(v, &V.tri_base, NB * BV, 0xFF) && dalloc(v, &V.vpos, NV, 0) && dalloc(v, &V.vnrm, NV, 0) &&
+            dalloc(v, &V.vref, NV, 0xFF) && dalloc(v, &V.vedge, NV, 0xFF) && dalloc(v, &V.tris, NT, 0xFF) &&
+            dalloc(v, &V.blk_free, NB, 0) && dalloc(v, &V.vtx_free, NV, 0) &&
+            dalloc(v, &V.touched, (size_t)V.list_cap_touched, 0) && dalloc(v, &V.update, NB, 0) &&
+            dalloc(v, &V.dead, (size_t)V.list_cap_dead, 0) && dalloc(v, &V.deadrun, (size_t)V.list_cap_deadrun, 0) &&
             dalloc(v, &V.ctl, 1, 0);
   for (int L = 0; L < 5 && ok; ++L) ok = dalloc(v, &V.run_free[L], (size_t)V.run_cap[L], 0);
+  uint4* tt = nullptr;
+  if (ok) ok = dalloc(v, &tt, 256, 0);
+  if (ok) {
+    uint8_t host_table[4096];
+    memcpy(host_table, table.tri, sizeof(table.tri));
+    memcpy(host_table + sizeof(table.tri), table.ntri, sizeof(table.ntri));
+    ok = cudaMemcpyAsync(tt, host_table, sizeof(host_table), cudaMemcpyHostToDevice, v->stream) == cudaSuccess &&
+         cudaStreamSynchronize(v->stream) == cudaSuccess;
+    V.tri_table = tt;
+  }
   if (!ok) {
     free_all(v);
     delete v;
@@ -467,7 +465,7 @@ vm_status vm_step(vm_volume* v, const float* depth, const vm_intrinsics* K, cons
   v->advance_pending = true;
   collect_graph_timing(v);  // a previous replay's node events are about to be re-recorded
   cudaError_t e = cudaGraphLaunch(v->graph_exec, v->stream);
-  v->graph_pending = v->timing && !v->graph_recs.empty();
+  v->graph_pending = v->timing_mask && !v->graph_recs.empty();
   return cuda_status(e);
 }
 
@@ -594,6 +592,9 @@ vm_status vm_get_stats(vm_volume* v, vm_frame_stats* s) {
   s->hash_tombstones = c[C_TOMBS];
   s->block_high_water = c[C_BLK_BUMP] < (int)v->p.max_blocks ? c[C_BLK_BUMP] : (int)v->p.max_blocks;
   s->rehashes = c[C_ST_REHASHES];
+  s->emitted_triangles = c[C_ST_EMITTED];
+  s->released_triangles = c[C_ST_RELEASED];
+  s->refreshed_vertices = c[C_ST_REFRESHED];
   return VM_OK;
 }
 
@@ -650,7 +651,7 @@ vm_status vm_set_blocks(vm_volume* v, const int32_t* keys, int64_t n, const floa
   if (ok) {
     const int adv = v->advance_pending ? 1 : 0;
     k_fill_insert<<<grid_for(v, 2), 256, 0, v->stream>>>(v->V, (const int*)dk, (int)n, adv);
-    k_resolve<<<grid_for(v, 4), 256, 0, v->stream>>>(v->V);
+    k_integrate<false><<<grid_for(v, 8), INTEG_THREADS, 0, v->stream>>>(v->V, &v->V.ctl->fp);
     k_fill_copy<<<grid_for(v, 4), 256, 0, v->stream>>>(v->V, (const int*)dk, (const float*)dt, (const float*)dw,
                                                        (int)n);
     ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(v->stream) == cudaSuccess;
@@ -665,7 +666,8 @@ vm_status vm_set_blocks(vm_volume* v, const int32_t* keys, int64_t n, const floa
 vm_status vm_enable_timing(vm_volume* v, int enable) {
   if (!v) return VM_ERR_INVALID_ARG;
   cudaStreamSynchronize(v->stream);
-  if ((enable != 0) != v->timing) drop_graph(v);  // re-capture with / without event nodes
+  const unsigned mask = (unsigned)enable & ((1u << K_COUNT_) - 1);
+  if (mask != v->timing_mask) drop_graph(v);  // re-capture with the new event nodes
   v->graph_pending = false;
   for (auto& r : v->recs) {
     v->event_pool.push_back(r.a);
@@ -676,7 +678,7 @@ vm_status vm_enable_timing(vm_volume* v, int enable) {
     v->tot_ms[k] = 0;
     v->launches[k] = 0;
   }
-  v->timing = enable != 0;
+  v->timing_mask = mask;
   return VM_OK;
 }
 

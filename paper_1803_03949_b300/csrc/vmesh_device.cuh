@@ -4,19 +4,21 @@
 //   hash      keys u64[B] (packed block key, EMPTY / TOMB), vals i32[B] (block index),
 //             stamp u32[B] (integrate call that last collected the bucket's block),
 //             ustamp u32[B] (mesh epoch in which the block joined the update set)
-//   blocks    bkey int4[NB] (x, y, z, bucket; bucket < 0 = free), bntri/bnvert i32[NB]
-//             (triangles in its cubes / vertices it owns), bnear u8[NB] (some voxel
-//             has W > 0 and d < mu), bepoch u32[NB] (epoch it was last collected in)
+//   blocks    bkey int4[NB] (x, y, z, bucket; bucket < 0 = free), nbr i32[NB][16]
+//             (block indices of the neighbours at offsets (o&1, o>>1&1, o>>2&1), o = 1..7,
+//             in slots 1..7 and of the neighbours at the negated offsets in slots 9..15;
+//             -1 = none), bntri/bnvert i32[NB] (triangles in its cubes / vertices it
+//             owns), bnear u8[NB] (some voxel has W > 0 and d < mu), bepoch u32[NB] (epoch
+//             it was last collected in), bborn u32[NB] (integrate call that created it)
 //   voxels    tw float2[NB*512] (TSDF d, weight W), code_eff/code_prev u8[NB*512],
-//             vmask u8[NB*512] (bits 0-2: owned edge has a vertex; bits 3-5: vertex
-//             requested in the current pass), chg u8[NB*512] (cube awaits triangles),
+//             vmask u8[NB*512] (bits 0-2: the owned edge has a vertex),
 //             edge_vtx i32[NB*512*3] (vertex on owned edge, -1 none), tri_base i32[NB*512]
 //   vertices  vpos float4[NV], vnrm float4[NV], vref i32[NV] (reference count, -1 free),
-//             vedge i32[NV] (owning edge id = block*1536 + voxel*3 + axis)
+//             vedge i32[NV] (owning edge id = block*1536 + voxel*3 + axis; -1 = unattached)
 //   triangles tris int4[NT] (three vertex ids, owning cube id; x < 0 = free)
 //   free lists block / vertex stacks and five triangle-run stacks (run length 1..5)
-//   work lists touched buckets, collected blocks, update set, new-edge requests,
-//             zero-reference vertices, plus a control block (counters, status, frame).
+//   work lists collected buckets, update set, zero-reference vertices, released triangle
+//             runs, plus a control block (counters, status, frame parameters).
 #pragma once
 
 #include <cooperative_groups.h>
@@ -46,8 +48,8 @@ enum Counter {
   C_EPOCH,          // mesh epoch, advanced by the first integrate after a mesh update
   C_N_TOUCHED,      // buckets collected by the current integrate call
   C_N_UPDATE,       // blocks in the update set
-  C_N_NEWEDGE,      // vertex requests of the current mesh pass
   C_N_DEAD,         // zero-reference vertices awaiting gc
+  C_N_DEADRUN,      // released triangle runs awaiting gc
   C_BLK_TOP, C_BLK_BUMP,
   C_VTX_TOP, C_VTX_BUMP,
   C_RUN_TOP0, C_RUN_TOP1, C_RUN_TOP2, C_RUN_TOP3, C_RUN_TOP4,
@@ -56,6 +58,7 @@ enum Counter {
   C_TOMBS,
   C_REHASH,         // 1 while a hash rebuild is under way
   C_ST_FRAME_BLOCKS, C_ST_UPDATE_BLOCKS, C_ST_NEW_BLOCKS, C_ST_CHANGED, C_ST_FREED_BLOCKS, C_ST_FREED_VERTS, C_ST_NEW_VERTS, C_ST_REHASHES,
+  C_ST_EMITTED, C_ST_RELEASED, C_ST_REFRESHED,
   C_DONE0, C_DONE1, C_DONE2, C_DONE3, C_DONE4, C_DONE5, C_DONE6, C_DONE7,
   C_COUNT
 };
@@ -79,7 +82,7 @@ struct Vol {
   uint32_t hmask;
   int max_blocks, max_vertices, max_triangles;
   int run_cap[5];
-  int list_cap_touched, list_cap_update, list_cap_newedge, list_cap_dead;
+  int list_cap_touched, list_cap_update, list_cap_dead, list_cap_deadrun;
 
   uint64_t* keys;
   int* vals;
@@ -87,16 +90,17 @@ struct Vol {
   uint32_t* ustamp;
 
   int4* bkey;
+  int* nbr;
   int* bntri;
   int* bnvert;
   uint8_t* bnear;
   uint32_t* bepoch;
+  uint32_t* bborn;
 
   float2* tw;
   uint8_t* code_eff;
   uint8_t* code_prev;
   uint8_t* vmask;
-  uint8_t* chg;
   int* edge_vtx;
   int* tri_base;
 
@@ -107,15 +111,16 @@ struct Vol {
 
   int4* tris;
 
+  const uint4* tri_table;  // global copy of the triangle table (256 x 15 bytes + 256 counts)
+
   int* blk_free;
   int* vtx_free;
   int* run_free[5];
 
   int* touched;       // buckets collected by this integrate call
-  int* touched_blk;   // their blocks
   int* update;        // update-set blocks
-  int* newedge;       // requested edge ids
   int* dead;          // zero-reference vertex ids
+  int2* deadrun;      // released triangle runs (start, length)
 
   Ctl* ctl;
 };

@@ -41,7 +41,7 @@ class vm_frame_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "frame_blocks", "new_blocks", "update_blocks", "changed_cubes", "live_blocks", "live_vertices",
         "live_triangles", "freed_blocks", "freed_vertices", "created_vertices", "hash_tombstones",
-        "block_high_water", "rehashes")]
+        "block_high_water", "rehashes", "emitted_triangles", "released_triangles", "refreshed_vertices")]
 
 
 _lib = None
@@ -251,8 +251,17 @@ class Volume:
         _check(self._lib.vm_set_blocks(self._h, _ptr(k), k.shape[0], _ptr(t), _ptr(w)), "vm_set_blocks")
 
     # --------------------------------------------------------------- timing
-    def enable_timing(self, on: bool = True):
-        _check(self._lib.vm_enable_timing(self._h, int(bool(on))), "vm_enable_timing")
+    KERNELS = ["k_set_frame", "k_alloc", "k_integrate", "k_list_all", "k_mesh", "k_gc_vertices", "k_gc_blocks"]
+
+    def enable_timing(self, on=True):
+        """on: True (every kernel), False (none) or a list of kernel names to time."""
+        if on is True:
+            mask = -1
+        elif not on:
+            mask = 0
+        else:
+            mask = sum(1 << self.KERNELS.index(k) for k in on)
+        _check(self._lib.vm_enable_timing(self._h, mask), "vm_enable_timing")
 
     def kernel_times(self) -> dict:
         cap = 32
