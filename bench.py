@@ -59,6 +59,11 @@ BYTES_MODEL = {
 }
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu capture
+# summarised in profiles/, for kernels unchanged since that capture; None otherwise.
+TRAFFIC = {}
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -216,40 +221,47 @@ def run_vmesh(args, rank, world, local):
     K = Intrinsics(W, H, scene.fx, scene.fy, scene.cx, scene.cy)
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    graph = not args.no_graph
+    vc = scene.volume
+    if args.small_pools:  # same workload, smaller pool allocations (profiling captures)
+        import dataclasses
 
-    def run(vol, timed_frames, e2e=False, collect=True):
-        """Warm-up then timed frames; returns per-frame ms and per-frame counters."""
-        res_host = torch.empty(2, dtype=torch.int32).pin_memory()
-        # warm-up: every kernel timed on all but the last warm-up frame to find the dominant
-        # kernel; then only that kernel keeps its two event nodes, and the last warm-up frame
-        # re-captures the frame graph outside the timed region
+        vc = dataclasses.replace(vc, max_blocks=1 << 15, max_vertices=1 << 21, max_triangles=1 << 22)
+
+    def warm_up(vol, calibrate=False):
+        """Frames 0..W-1, untimed.  With calibrate, every kernel is timed on frames 0..W-2
+        (a per-kernel breakdown); the last warm-up frame captures the graph without events."""
         calib = {}
-        if collect:
+        if calibrate:
             vol.enable_timing(True)
         for f in range(args.warmup):
-            if collect and f == args.warmup - 1:
+            if calibrate and f == args.warmup - 1:
                 calib = vol.kernel_times()
-                main = {k: v for k, v in calib.items() if k in BYTES_MODEL and v[1] > 0}
-                dom = sorted(main, key=lambda k: -main[k][0])[:2]  # the two largest
-                vol.enable_timing(dom)
-            vol.step(depth_dev[f], K, *poses[f], refine=True, gc=True, graph=not args.no_graph)
+                vol.enable_timing(False)
+            vol.step(depth_dev[f], K, *poses[f], refine=True, gc=True, graph=graph)
         torch.cuda.synchronize()
-        if collect:
-            vol.enable_timing(dom)
+        return calib
+
+    def timed(vol, timing_kernels=(), e2e=False):
+        """Frames W..W+K-1, each bracketed by CUDA events on the volume's stream after a
+        256 MB L2 flush; returns per-frame ms, per-frame work counters and kernel times."""
+        if timing_kernels:
+            vol.enable_timing(list(timing_kernels))
+        res_host = torch.empty(2, dtype=torch.int32).pin_memory()
+        dev_buf = torch.empty((H, W), dtype=torch.float32, device="cuda")
         ms, counters = [], []
         prev = vol.stats()
-        dev_buf = torch.empty((H, W), dtype=torch.float32, device="cuda")
-        for f in timed_frames:
+        for f in range(args.warmup, n):
             flush.fill_(f)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             if e2e:
                 dev_buf.copy_(depth_host[f], non_blocking=True)
-                vol.step(dev_buf, K, *poses[f], refine=True, gc=True, graph=not args.no_graph)
+                vol.step(dev_buf, K, *poses[f], refine=True, gc=True, graph=graph)
                 vol.mesh_size_async(res_host)
             else:
-                vol.step(depth_dev[f], K, *poses[f], refine=True, gc=True, graph=not args.no_graph)
+                vol.step(depth_dev[f], K, *poses[f], refine=True, gc=True, graph=graph)
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
@@ -262,45 +274,50 @@ def run_vmesh(args, rank, world, local):
                                  created=st["created_vertices"] - prev["created_vertices"],
                                  high_water=st["block_high_water"], pixels=W * H))
             prev = st
-        kt = vol.kernel_times() if collect else {}
+        kt = vol.kernel_times() if timing_kernels else {}
         vol.check()
-        return ms, counters, kt, calib
+        return ms, counters, kt
 
-    vc = scene.volume
-    if args.small_pools:  # same workload, smaller pool allocations (profiling captures)
-        import dataclasses
-
-        vc = dataclasses.replace(vc, max_blocks=1 << 15, max_vertices=1 << 21, max_triangles=1 << 22)
+    # pass 1 -- the benchmark value: no event nodes inside the frame graph
     vol = Volume.from_config(vc, stream=stream)
-    torch.cuda.synchronize()
+    calib = warm_up(vol, calibrate=True)
     barrier(world)
     clock_path = os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(
         os.path.join(ROOT, "gpurun_out")) else None
     with ClockSampler(local, clock_path if rank == 0 else None) as cs:
-        ms, counters, kt, calib = run(vol, range(args.warmup, n), collect=not args.no_kernel_timing)
+        ms, counters, _ = timed(vol)
         torch.cuda.synchronize()
     barrier(world)
+    vol.close()
     total_ms = sum(ms)
     max_ms = reduce_max(total_ms, world)
     value = world * args.steps / (max_ms / 1000.0)
     voxels = sum(512 * c["frame_blocks"] for c in counters)
     vps = voxels / (total_ms / 1000.0)
 
-    # roofline of the dominant kernel (largest device time in the timed region)
+    # pass 2 -- kernel durations: the same frames on a fresh volume (identical, deterministic
+    # work), with CUDA-event pairs around the two kernels the calibration ranked highest
     peak, peak_kind = load_peaks()
-    main = {k: v for k, v in kt.items() if k in BYTES_MODEL and v[1] > 0}
-    dom = max(main, key=lambda k: main[k][0]) if main else None
+    ranked = sorted((k for k in calib if k in BYTES_MODEL and calib[k][1] > 0), key=lambda k: -calib[k][0])[:2]
     roof = None
-    if dom:
-        tot_ms_k, launches = kt[dom]
-        bytes_total = sum(BYTES_MODEL[dom](c) for c in counters)
+    if ranked and not args.no_kernel_timing:
+        vol2 = Volume.from_config(vc, stream=stream)
+        warm_up(vol2)
+        ms2, counters2, kt = timed(vol2, timing_kernels=ranked)
+        vol2.close()
+        main = {k: kt[k] for k in ranked if kt.get(k, (0, 0))[1] > 0}
+        dom = max(main, key=lambda k: main[k][0])
+        tot_ms_k, launches = main[dom]
+        bytes_total = sum(BYTES_MODEL[dom](c) for c in counters2)
         achieved = bytes_total / (tot_ms_k / 1000.0) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
-                "bytes_per_launch": bytes_total / max(launches, 1), "avg_launch_us": 1000.0 * tot_ms_k / max(launches, 1)}
-        for k in main:  # the runner-up timed in the same region
+                "frac": achieved / peak, "peak_source": peak_kind, "traffic": TRAFFIC.get(dom),
+                "bytes_per_launch": bytes_total / max(launches, 1),
+                "avg_launch_us": 1000.0 * tot_ms_k / max(launches, 1),
+                "timing": "CUDA events around the kernel, same frames replayed on a fresh volume"}
+        for k in main:
             if k != dom:
-                kb = sum(BYTES_MODEL[k](c) for c in counters)
+                kb = sum(BYTES_MODEL[k](c) for c in counters2)
                 roof["runner_up"] = {"kernel": k, "avg_launch_us": 1000.0 * main[k][0] / max(main[k][1], 1),
                                      "achieved": kb / (main[k][0] / 1000.0) / 1e9}
     # kernels per frame, counted on the calibration frames (every launch timed there)
@@ -308,9 +325,11 @@ def run_vmesh(args, rank, world, local):
     per_frame_launches = round(sum(v[1] for v in calib.values()) / calib_frames) if calib else None
     launches_total = per_frame_launches * args.steps if per_frame_launches else None
 
-    # end to end through the public API: pinned host depth -> device, step, result -> host
-    vol_e2e = Volume.from_config(vc, stream=stream)
-    ms_e2e, _, _, _ = run(vol_e2e, range(args.warmup, n), e2e=True, collect=False)
+    # pass 3 -- end to end through the public API: pinned host depth -> device, step, result -> host
+    vol3 = Volume.from_config(vc, stream=stream)
+    warm_up(vol3)
+    ms_e2e, _, _ = timed(vol3, e2e=True)
+    vol3.close()
     e2e_value = world * args.steps / (reduce_max(sum(ms_e2e), world) / 1000.0)
 
     if rank != 0:
@@ -328,7 +347,7 @@ def run_vmesh(args, rank, world, local):
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "frames": "%d..%d" % (args.warmup, n - 1),
-                   "graph": not args.no_graph, "l2": "flushed before every timed frame (256 MB write)",
+                   "graph": graph, "l2": "flushed before every timed frame (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "voxels_per_s": vps,
         "mean_blocks_per_frame": float(np.mean([c["frame_blocks"] for c in counters])),

@@ -178,6 +178,7 @@ __global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(Vol V, const FrameParam
     int s = hash_insert(V, key, bx, by, bz, frame);
     if (s >= 0) touch_bucket(V, s, frame);
   }
+  allow_dependent_launch();
   if (last_block(V, C_DONE0)) {
     if (threadIdx.x == 0) {
       fold_top(V, C_BLK_TOP);
@@ -233,6 +234,7 @@ constexpr int INTEG_THREADS = 128;  // 4 voxels per thread, one block per CTA it
 // and advances the integrate-call counter.
 template <bool FUSE>
 __global__ void __launch_bounds__(INTEG_THREADS) k_integrate(Vol V, const FrameParams* __restrict__ fpp) {
+  grid_dependency_wait();
   const int n = min(__ldcg(&V.ctl->c[C_N_TOUCHED]), V.list_cap_touched);
   const uint32_t frame = (uint32_t)__ldcg(&V.ctl->c[C_FRAME]);
   const uint32_t epoch = (uint32_t)__ldcg(&V.ctl->c[C_EPOCH]);
@@ -284,6 +286,7 @@ __global__ void __launch_bounds__(INTEG_THREADS) k_integrate(Vol V, const FrameP
     const int any = __syncthreads_or(near);
     if (threadIdx.x == 0) V.bnear[blk] = (uint8_t)(any != 0);
   }
+  allow_dependent_launch();
   if (last_block(V, C_DONE2)) {
     if (threadIdx.x == 0) {
       V.ctl->c[C_ST_FRAME_BLOCKS] = n;

@@ -24,6 +24,7 @@ __device__ __forceinline__ void run_push(const Vol& V, int L, int base) {
 // unreferenced; a vertex still attached to its edge is detached.  Released triangle runs
 // go back to their free stacks.
 __global__ void __launch_bounds__(256) k_gc_vertices(Vol V) {
+  grid_dependency_wait();
   const int n = min(__ldcg(&V.ctl->c[C_N_DEAD]), V.list_cap_dead);
   const int nr = min(__ldcg(&V.ctl->c[C_N_DEADRUN]), V.list_cap_deadrun);
   int freed = 0;
@@ -48,6 +49,7 @@ __global__ void __launch_bounds__(256) k_gc_vertices(Vol V) {
     counter_add(V, C_LIVE_VERTS, -freed);
     counter_add(V, C_ST_FREED_VERTS, freed);
   }
+  allow_dependent_launch();
   if (last_block(V, C_DONE5)) {
     if (threadIdx.x == 0) {
       V.ctl->c[C_N_DEAD] = 0;
@@ -105,6 +107,7 @@ __device__ void rehash_in_cta(const Vol& V, bool mark_update) {
 // update never lists a recycled (and possibly reallocated) block index.  The last CTA
 // rebuilds the hash when live plus dead buckets pass half the table.
 __global__ void __launch_bounds__(256) k_gc_blocks(Vol V, int consumed) {
+  grid_dependency_wait();
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;

@@ -194,6 +194,7 @@ __global__ void __launch_bounds__(MESH_THREADS, 7) k_mesh(Vol V, int mode) {
   const uint8_t* __restrict__ tri = reinterpret_cast<const uint8_t*>(V.tri_table);
   for (int i = threadIdx.x; i < 256 / 16; i += MESH_THREADS)
     reinterpret_cast<uint4*>(S.ntri)[i] = V.tri_table[240 + i];
+  grid_dependency_wait();
   const int n = min(__ldcg(&V.ctl->c[C_N_UPDATE]), V.list_cap_update);
   const float eps = V.eps, l = V.l;
   int changed = 0, created = 0, emitted = 0, released = 0, refreshed = 0;
@@ -400,6 +401,7 @@ __global__ void __launch_bounds__(MESH_THREADS, 7) k_mesh(Vol V, int mode) {
     counter_add(V, C_LIVE_VERTS, created);
     counter_add(V, C_ST_NEW_VERTS, created);
   }
+  allow_dependent_launch();
   if (last_block(V, C_DONE3)) {
     if (threadIdx.x == 0) {
       fold_top(V, C_VTX_TOP);

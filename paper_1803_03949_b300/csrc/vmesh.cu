@@ -175,6 +175,23 @@ bool make_frame(const vm_intrinsics* K, const float* Twc, const float* Tcw, cons
 
 int grid_for(vm_volume* v, int per_sm) { return v->num_sms * per_sm; }
 
+// Launch with programmatic stream serialization: the kernel may be scheduled while the
+// previous kernel in the stream drains; it waits for that kernel's results in-kernel.
+template <typename... Params, typename... Args>
+void launch_dependent(void (*kernel)(Params...), int grid, int block, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // ---- enqueue helpers (no validation)
 vm_status enqueue_integrate(vm_volume* v, const FrameParams& fp, bool set_frame) {
   vm_status st = VM_OK;
@@ -185,8 +202,9 @@ vm_status enqueue_integrate(vm_volume* v, const FrameParams& fp, bool set_frame)
   dim3 g((fp.W + ALLOC_TILE_W - 1) / ALLOC_TILE_W, (fp.H + ALLOC_TILE_H - 1) / ALLOC_TILE_H);
   st = launch(v, K_ALLOC, [&] { k_alloc<<<g, ALLOC_THREADS, 0, v->cur>>>(v->V, &ctl->fp, adv); });
   if (st) return st;
-  st = launch(v, K_INTEGRATE,
-              [&] { k_integrate<true><<<grid_for(v, 8), INTEG_THREADS, 0, v->cur>>>(v->V, &ctl->fp); });
+  st = launch(v, K_INTEGRATE, [&] {
+    launch_dependent(k_integrate<true>, grid_for(v, 8), INTEG_THREADS, v->cur, v->V, (const FrameParams*)&ctl->fp);
+  });
   v->advance_pending = false;
   return st;
 }
@@ -198,7 +216,7 @@ vm_status enqueue_list_all(vm_volume* v) {
 }
 
 vm_status enqueue_mesh_pass(vm_volume* v, int mode) {
-  return launch(v, K_MESH, [&] { k_mesh<<<grid_for(v, 7), MESH_THREADS, 0, v->cur>>>(v->V, mode); });
+  return launch(v, K_MESH, [&] { launch_dependent(k_mesh, grid_for(v, 7), MESH_THREADS, v->cur, v->V, mode); });
 }
 
 vm_status enqueue_update(vm_volume* v, int flags) {
@@ -211,10 +229,11 @@ vm_status enqueue_update(vm_volume* v, int flags) {
 }
 
 vm_status enqueue_gc(vm_volume* v) {
-  vm_status st = launch(v, K_GC_VERTICES, [&] { k_gc_vertices<<<grid_for(v, 2), 256, 0, v->cur>>>(v->V); });
+  vm_status st = launch(v, K_GC_VERTICES, [&] { launch_dependent(k_gc_vertices, grid_for(v, 2), 256, v->cur, v->V); });
   if (st) return st;
   const int consumed = v->advance_pending ? 1 : 0;
-  return launch(v, K_GC_BLOCKS, [&] { k_gc_blocks<<<grid_for(v, 8), 256, 0, v->cur>>>(v->V, consumed); });
+  return launch(v, K_GC_BLOCKS,
+                [&] { launch_dependent(k_gc_blocks, grid_for(v, 8), 256, v->cur, v->V, consumed); });
 }
 
 vm_status sync_status(vm_volume* v) {

@@ -267,6 +267,15 @@ __device__ __forceinline__ bool last_block(const Vol& V, int c_done) {
   return false;
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization
+// may start while the previous kernel drains; it waits here (the hardware grid-dependency
+// wait, which returns once the previous grid has completed and its memory is visible)
+// before reading anything that kernel produced.  Without such a dependency it returns at
+// once.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Let the next kernel in the stream be launched early (it still waits for this grid).
+__device__ __forceinline__ void allow_dependent_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ void fold_top(const Vol& V, int c_top) {
   if (V.ctl->c[c_top] < 0) V.ctl->c[c_top] = 0;
 }
