@@ -36,43 +36,71 @@ constexpr int OWNERS = 9 * 9 * 9;  // owner voxels (local 0..8) of the block's c
 constexpr int EDGE_SLOTS = OWNERS * 3;
 constexpr int EDGE_WORDS = (EDGE_SLOTS + 31) / 32;
 
+// Owner voxel offset and axis of cube edge k (the c_edge_owner table), 5 bits per edge in an
+// immediate: bit 0 x offset, bit 1 y offset, bit 2 z offset, bits 3-4 axis.  Edge ids vary
+// per thread, and divergent reads of a __constant__ table would serialize across the warp.
+constexpr uint64_t EDGE_OWNER_BITS = 0x94e30619a440920ull;
+__device__ __forceinline__ int owner_bits(int k) { return (int)((EDGE_OWNER_BITS >> (5 * k)) & 31); }
+
+// Packed triangle table: per cube type, 15 edge ids of 4 bits (triangle t, corner j at bit
+// 4 * (3 t + j)) and the triangle count in bits 60..63.
+__device__ __forceinline__ int packed_ntri(uint64_t w) { return (int)(w >> 60); }
+__device__ __forceinline__ int packed_edge(uint64_t w, int t, int j) { return (int)((w >> (4 * (3 * t + j))) & 15); }
+
 struct __align__(16) MeshSmem {
   float2 halo[HALO_N];
-  uint8_t ntri[256];
+  uint64_t tri64[256];
   int nb[8];
   int dtri;
   int nchg, nedge, nref;
   uint16_t rlist[BV * 3];  // owned edges whose existing vertex is refreshed (voxel * 3 + axis)
   uint16_t chg_cube[BV];  // changed cubes of the block
   uint8_t chg_new[BV], chg_old[BV];
-  int chg_oldbase[BV];    // run of the released triangles
-  int chg_base[BV];       // run of the new triangles
+  int chg_base[BV];       // run of the released triangles (stages b-c), then of the new ones
   unsigned emark[EDGE_WORDS];
   int ecount[EDGE_WORDS];
   uint16_t elist[EDGE_SLOTS];
   int evid[EDGE_SLOTS];
 };
 
-// Eqs. 3-5: snap a disturbed raw type to the nearest admissible regular type.
-__device__ __forceinline__ int refine_type(int raw, int prev, const float* d, float eps) {
+// Eqs. 3-5: snap a disturbed raw type to the nearest admissible regular type.  `small` has
+// bit k set when |d(c_k)| < eps, so a regular type is admissible iff every corner where it
+// differs from the raw type is in `small`.
+__device__ __forceinline__ int refine_type(int raw, int prev, int small) {
   // an empty or full cube is 4 flips from every regular type: never snapped
   if (raw == 0 || raw == 255 || __popc(raw ^ prev) > 3) return raw;
   int best = -1, bestd = 99;
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
-    int diff = raw ^ (int)c_regular[j];
-    int dh = __popc(diff);
-    if (dh > 3) continue;
-    bool ok = true;
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-      if (((diff >> k) & 1) && !(fabsf(d[k]) < eps)) ok = false;
-    if (ok && dh < bestd) {
-      best = j;
+    // regular types of Sec. V-F in the paper's order: 0xCC 0x33 0x99 0x66 0xF0 0x0F
+    const int rj = (int)((0x0FF0669933CCull >> (8 * j)) & 0xFF);
+    const int diff = raw ^ rj;
+    const int dh = __popc(diff);
+    if (dh <= 3 && (diff & ~small) == 0 && dh < bestd) {
+      best = rj;
       bestd = dh;
     }
   }
-  return best >= 0 ? (int)c_regular[best] : raw;
+  return best >= 0 ? best : raw;
+}
+
+// Bourke corner offsets as bit patterns (folded into shared-memory addresses when k is a
+// compile-time constant): corner k is (x, y, z) = (0x66 >> k & 1, 0xCC >> k & 1, 0xF0 >> k & 1).
+__device__ __forceinline__ constexpr int corner_x(int k) { return (0x66 >> k) & 1; }
+__device__ __forceinline__ constexpr int corner_y(int k) { return (0xCC >> k) & 1; }
+__device__ __forceinline__ constexpr int corner_z(int k) { return (0xF0 >> k) & 1; }
+
+// Loads issued where they are written (volatile asm keeps them ahead of the next barrier),
+// so they travel while the halo is staged.
+__device__ __forceinline__ uint32_t ld_early_u32(const uint8_t* p) {
+  uint32_t v;
+  asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ int4 ld_early_i4(const int* p) {
+  int4 v;
+  asm volatile("ld.global.cg.v4.s32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+  return v;
 }
 
 __device__ __forceinline__ float2 halo_at(const MeshSmem& S, int x, int y, int z) {
@@ -92,9 +120,10 @@ __device__ __forceinline__ void edge_vertex(const MeshSmem& S, float l, int4 key
   float t = d0 == d1 ? 0.5f : d0 / (d0 - d1);
   if (t < -1.0f) t = -1.0f;
   if (t > 2.0f) t = 2.0f;
-  const int g[3] = {key.x * BS + x, key.y * BS + y, key.z * BS + z};
-  float p[3] = {(float)g[0] * l, (float)g[1] * l, (float)g[2] * l};
-  p[a] = (float)g[a] * l + t * l;
+  const int gx = key.x * BS + x, gy = key.y * BS + y, gz = key.z * BS + z;
+  const int ga = a == 0 ? gx : (a == 1 ? gy : gz);
+  const float pa = (float)ga * l + t * l;
+  const float p[3] = {a == 0 ? pa : (float)gx * l, a == 1 ? pa : (float)gy * l, a == 2 ? pa : (float)gz * l};
   float n[3];
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
@@ -182,6 +211,22 @@ __device__ __forceinline__ int vertex_of_edge(const Vol& V, const MeshSmem& S, i
   return mine;
 }
 
+// Reserve `cnt` consecutive slots of a shared counter for every lane of the (full) warp,
+// with one shared atomic per warp; returns this lane's first slot.
+__device__ __forceinline__ int warp_reserve(int* counter, int cnt) {
+  const int lane = threadIdx.x & 31;
+  int x = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  int base = 0;
+  if (lane == 31 && x > 0) base = atomicAdd(counter, x);
+  base = __shfl_sync(0xffffffffu, base, 31);
+  return base + x - cnt;
+}
+
 // Shared-memory slot of the edge owned by the voxel at halo coordinates (x, y, z) along a.
 __device__ __forceinline__ int edge_slot(int x, int y, int z, int a) { return ((z * 9 + y) * 9 + x) * 3 + a; }
 
@@ -190,10 +235,7 @@ __device__ __forceinline__ int edge_slot(int x, int y, int z, int a) { return ((
 // stored t_{i-1}).  The last CTA clamps the vertex and run free-stack tops.
 __global__ void __launch_bounds__(MESH_THREADS, 7) k_mesh(Vol V, int mode) {
   __shared__ MeshSmem S;
-  // triangle table: edge ids read through L1 (tri_table bytes 0..3839), counts in shared
-  const uint8_t* __restrict__ tri = reinterpret_cast<const uint8_t*>(V.tri_table);
-  for (int i = threadIdx.x; i < 256 / 16; i += MESH_THREADS)
-    reinterpret_cast<uint4*>(S.ntri)[i] = V.tri_table[240 + i];
+  for (int i = threadIdx.x; i < 128; i += MESH_THREADS) reinterpret_cast<uint4*>(S.tri64)[i] = V.tri_table[i];
   grid_dependency_wait();
   const int n = min(__ldcg(&V.ctl->c[C_N_UPDATE]), V.list_cap_update);
   const float eps = V.eps, l = V.l;
@@ -215,10 +257,10 @@ __global__ void __launch_bounds__(MESH_THREADS, 7) k_mesh(Vol V, int mode) {
     // now so that they arrive while the halo is staged
     const int c0 = 4 * threadIdx.x;  // MESH_THREADS * 4 == BV
     const size_t ci0 = (size_t)blk * BV + c0;
-    const uint32_t eff_w = __ldcg(reinterpret_cast<const uint32_t*>(V.code_eff + ci0));
-    const uint32_t vm_w = (mode & M_UPDATE) ? __ldcg(reinterpret_cast<const uint32_t*>(V.vmask + ci0)) : 0u;
-    const uint32_t prev_w = (mode & M_UPDATE) ? eff_w : __ldcg(reinterpret_cast<const uint32_t*>(V.code_prev + ci0));
-    const int4 tb4 = __ldcg(reinterpret_cast<const int4*>(V.tri_base + ci0));
+    const uint32_t eff_w = ld_early_u32(V.code_eff + ci0);
+    const uint32_t vm_w = ld_early_u32(V.vmask + ci0);
+    const uint32_t prev_w = (mode & M_UPDATE) ? eff_w : ld_early_u32(V.code_prev + ci0);
+    const int4 tb4 = ld_early_i4(V.tri_base + ci0);
     __syncthreads();
     for (int h = threadIdx.x; h < HALO_N; h += MESH_THREADS) {
       const int x = h % HALO, y = (h / HALO) % HALO, z = h / (HALO * HALO);
@@ -235,9 +277,9 @@ __global__ void __launch_bounds__(MESH_THREADS, 7) k_mesh(Vol V, int mode) {
       if (mode & M_UPDATE) *reinterpret_cast<uint32_t*>(V.code_prev + ci0) = eff_w;
       // existing vertices of the 4 voxels: listed for the refresh in stage d
       const uint32_t live_w = vm_w & 0x07070707u;
-      if (live_w) {
+      {
         const int cnt = __popc(live_w);
-        int r = atomicAdd(&S.nref, cnt);
+        int r = warp_reserve(&S.nref, cnt);
 #pragma unroll
         for (int q = 0; q < 12; ++q)
           if ((live_w >> (8 * (q / 3) + q % 3)) & 1) S.rlist[r++] = (uint16_t)((c0 + q / 3) * 3 + q % 3);
@@ -247,35 +289,34 @@ __global__ void __launch_bounds__(MESH_THREADS, 7) k_mesh(Vol V, int mode) {
       for (int j = 0; j < 4; ++j) {
         const int c = c0 + j;
         const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
-        float d[8];
         bool valid = true;
-        int raw = 0;
+        int raw = 0, small = 0;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-          const float2 hv = halo_at(S, x + c_corner[k][0], y + c_corner[k][1], z + c_corner[k][2]);
-          d[k] = hv.x;
+          const float2 hv = halo_at(S, x + corner_x(k), y + corner_y(k), z + corner_z(k));
           valid &= hv.y > 0.0f;
           raw |= (hv.x < 0.0f) << k;
+          small |= (fabsf(hv.x) < eps) << k;
         }
         const int eff_old = (eff_w >> (8 * j)) & 0xFF;
         const int prev = (prev_w >> (8 * j)) & 0xFF;
         int e = valid ? raw : 0;
-        if (valid && (mode & M_REFINE)) e = refine_type(raw, prev, d, eps);
+        if (valid && (mode & M_REFINE)) e = refine_type(raw, prev, small);
         if (e == eff_old) continue;
         ++changed;
         new_w = (new_w & ~(0xFFu << (8 * j))) | ((uint32_t)e << (8 * j));
-        const int nold = S.ntri[eff_old], nnew = S.ntri[e];
-        const int slot = atomicAdd(&S.nchg, 1);
+        const uint64_t tw64 = S.tri64[e];
+        const int nold = packed_ntri(S.tri64[eff_old]), nnew = packed_ntri(tw64);
+        const int slot = atomicAdd(&S.nchg, 1);  // a few changed cubes per thread at most
         S.chg_cube[slot] = (uint16_t)c;
         S.chg_new[slot] = (uint8_t)e;
         S.chg_old[slot] = (uint8_t)eff_old;
-        S.chg_oldbase[slot] = nold > 0 ? tbs[j] : -1;
+        S.chg_base[slot] = nold > 0 ? tbs[j] : -1;
         dtri += nnew - nold;
         for (int t = 0; t < nnew; ++t)
           for (int jj = 0; jj < 3; ++jj) {
-            const int k = tri[15 * e + 3 * t + jj];
-            const int es = edge_slot(x + c_edge_owner[k][0], y + c_edge_owner[k][1], z + c_edge_owner[k][2],
-                                     c_edge_owner[k][3]);
+            const int ob = owner_bits(packed_edge(tw64, t, jj));
+            const int es = edge_slot(x + (ob & 1), y + ((ob >> 1) & 1), z + ((ob >> 2) & 1), ob >> 3);
             atomicOr(&S.emark[es >> 5], 1u << (es & 31));
           }
       }
@@ -284,38 +325,8 @@ __global__ void __launch_bounds__(MESH_THREADS, 7) k_mesh(Vol V, int mode) {
     if (dtri) atomicAdd(&S.dtri, dtri);
     __syncthreads();
     const int nchg = S.nchg;
-    // ---- c. release old triangles; pop runs for the new ones; compact the needed edges
-    for (int q = threadIdx.x; q < nchg; q += MESH_THREADS) {
-      const int nold = S.ntri[S.chg_old[q]], obase = S.chg_oldbase[q];
-      if (obase >= 0) {
-        int4 tr[5];
-#pragma unroll
-        for (int t = 0; t < 5; ++t) tr[t] = t < nold ? __ldcg(&V.tris[obase + t]) : make_int4(-1, -1, -1, -1);
-        int hit[15];
-#pragma unroll
-        for (int t = 0; t < 5; ++t) {
-          const int vs[3] = {tr[t].x, tr[t].y, tr[t].z};
-#pragma unroll
-          for (int jj = 0; jj < 3; ++jj) hit[3 * t + jj] = vs[jj] >= 0 ? atomicSub(&V.vref[vs[jj]], 1) : 0;
-        }
-#pragma unroll
-        for (int t = 0; t < 5; ++t) {
-          if (t < nold) V.tris[obase + t] = make_int4(-1, -1, -1, -1);
-          const int vs[3] = {tr[t].x, tr[t].y, tr[t].z};
-#pragma unroll
-          for (int jj = 0; jj < 3; ++jj)
-            if (hit[3 * t + jj] == 1) list_push(V, V.dead, C_N_DEAD, V.list_cap_dead, vs[jj]);
-        }
-        deadrun_push(V, obase, nold);
-        released += nold;
-      }
-      const int nt = S.ntri[S.chg_new[q]];
-      const int base = nt > 0 ? run_pop(V, nt) : -1;
-      S.chg_base[q] = base;
-      V.tri_base[(size_t)blk * BV + S.chg_cube[q]] = base;
-      if (base >= 0) emitted += nt;
-    }
-    if (threadIdx.x < 32) {  // one warp: exclusive scan of the bitmap's word popcounts
+    // ---- c. compact the needed edges into a list (warp 0 scans the bitmap's word counts)
+    if (threadIdx.x < 32) {
       int carry = 0;
       for (int w0 = 0; w0 < EDGE_WORDS; w0 += 32) {
         const int w = w0 + threadIdx.x;
@@ -341,16 +352,19 @@ __global__ void __launch_bounds__(MESH_THREADS, 7) k_mesh(Vol V, int mode) {
       }
     }
     __syncthreads();
-    // ---- d. one thread per needed edge (its vertex, created on first use) and per existing
-    //         vertex of the block (position and normal recomputed from the new TSDF)
+    // ---- d. one loop over three independent kinds of work, so the stage lasts as long as the
+    //         longest chain rather than their sum:
+    //         per needed edge: its vertex, created on first use;
+    //         per existing vertex of the block: position and normal from the new TSDF;
+    //         per changed cube: release the old triangles, pop a run for the new ones.
     const int nedge = S.nedge, nref = S.nref;
-    for (int j = threadIdx.x; j < nedge + nref; j += MESH_THREADS) {
+    for (int j = threadIdx.x; j < nedge + nref + nchg; j += MESH_THREADS) {
       if (j < nedge) {
         const int es = S.elist[j];
         const int a = es % 3, o = es / 3;
         const int x = o % 9, y = (o / 9) % 9, z = o / 81;
         S.evid[es] = vertex_of_edge(V, S, key, x, y, z, a, created);
-      } else {
+      } else if (j < nedge + nref) {
         const int r = S.rlist[j - nedge];
         const int c = r / 3, a = r - c * 3;
         const int vid = __ldcg(&V.edge_vtx[((size_t)blk * BV + c) * 3 + a]);
@@ -360,6 +374,36 @@ __global__ void __launch_bounds__(MESH_THREADS, 7) k_mesh(Vol V, int mode) {
         V.vpos[vid] = p;
         V.vnrm[vid] = nn;
         ++refreshed;
+      } else {
+        const int q = j - nedge - nref;
+        const int nold = packed_ntri(S.tri64[S.chg_old[q]]), obase = S.chg_base[q];
+        const int nt = packed_ntri(S.tri64[S.chg_new[q]]);
+        if (obase >= 0) {
+          int4 tr[5];
+#pragma unroll
+          for (int t = 0; t < 5; ++t) tr[t] = t < nold ? __ldcg(&V.tris[obase + t]) : make_int4(-1, -1, -1, -1);
+          int hit[15];
+#pragma unroll
+          for (int t = 0; t < 5; ++t) {
+            const int vs[3] = {tr[t].x, tr[t].y, tr[t].z};
+#pragma unroll
+            for (int jj = 0; jj < 3; ++jj) hit[3 * t + jj] = vs[jj] >= 0 ? atomicSub(&V.vref[vs[jj]], 1) : 0;
+          }
+#pragma unroll
+          for (int t = 0; t < 5; ++t) {
+            if (t < nold) V.tris[obase + t] = make_int4(-1, -1, -1, -1);
+            const int vs[3] = {tr[t].x, tr[t].y, tr[t].z};
+#pragma unroll
+            for (int jj = 0; jj < 3; ++jj)
+              if (hit[3 * t + jj] == 1) list_push(V, V.dead, C_N_DEAD, V.list_cap_dead, vs[jj]);
+          }
+          deadrun_push(V, obase, nold);
+          released += nold;
+        }
+        const int base = nt > 0 ? run_pop(V, nt) : -1;
+        S.chg_base[q] = base;
+        V.tri_base[(size_t)blk * BV + S.chg_cube[q]] = base;
+        if (base >= 0) emitted += nt;
       }
     }
     __syncthreads();
@@ -367,15 +411,15 @@ __global__ void __launch_bounds__(MESH_THREADS, 7) k_mesh(Vol V, int mode) {
     for (int j = threadIdx.x; j < nchg * 5; j += MESH_THREADS) {
       const int q = j / 5, t = j - q * 5;
       const int e = S.chg_new[q], base = S.chg_base[q];
-      if (t >= S.ntri[e] || base < 0) continue;
+      const uint64_t tw64 = S.tri64[e];
+      if (t >= packed_ntri(tw64) || base < 0) continue;
       const int c = S.chg_cube[q];
       const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
       int vs[3];
 #pragma unroll
       for (int jj = 0; jj < 3; ++jj) {
-        const int k = tri[15 * e + 3 * t + jj];
-        vs[jj] = S.evid[edge_slot(x + c_edge_owner[k][0], y + c_edge_owner[k][1], z + c_edge_owner[k][2],
-                                  c_edge_owner[k][3])];
+        const int ob = owner_bits(packed_edge(tw64, t, jj));
+        vs[jj] = S.evid[edge_slot(x + (ob & 1), y + ((ob >> 1) & 1), z + ((ob >> 2) & 1), ob >> 3)];
       }
       const int ci = blk * BV + c;
       if (vs[0] < 0 || vs[1] < 0 || vs[2] < 0) {  // vertex pool exhausted

@@ -358,12 +358,16 @@ vm_status vm_create_volume(const vm_params* p, void* cuda_stream, vm_volume** ou
             dalloc(v, &V.ctl, 1, 0);
   for (int L = 0; L < 5 && ok; ++L) ok = dalloc(v, &V.run_free[L], (size_t)V.run_cap[L], 0);
   uint4* tt = nullptr;
-  if (ok) ok = dalloc(v, &tt, 256, 0);
+  if (ok) ok = dalloc(v, &tt, 128, 0);
   if (ok) {
-    uint8_t host_table[4096];
-    memcpy(host_table, table.tri, sizeof(table.tri));
-    memcpy(host_table + sizeof(table.tri), table.ntri, sizeof(table.ntri));
-    ok = cudaMemcpyAsync(tt, host_table, sizeof(host_table), cudaMemcpyHostToDevice, v->stream) == cudaSuccess &&
+    // packed: 15 edge ids of 4 bits (triangle t, corner j at bit 4 (3 t + j)), count in bits 60..63
+    uint64_t packed[256];
+    for (int c = 0; c < 256; ++c) {
+      uint64_t w = (uint64_t)table.ntri[c] << 60;
+      for (int i = 0; i < 3 * table.ntri[c]; ++i) w |= (uint64_t)(table.tri[c][i] & 15) << (4 * i);
+      packed[c] = w;
+    }
+    ok = cudaMemcpyAsync(tt, packed, sizeof(packed), cudaMemcpyHostToDevice, v->stream) == cudaSuccess &&
          cudaStreamSynchronize(v->stream) == cudaSuccess;
     V.tri_table = tt;
   }

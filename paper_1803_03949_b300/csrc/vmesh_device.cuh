@@ -111,7 +111,7 @@ struct Vol {
 
   int4* tris;
 
-  const uint4* tri_table;  // global copy of the triangle table (256 x 15 bytes + 256 counts)
+  const uint4* tri_table;  // packed triangle table, 256 x 64 bits (edge ids and count)
 
   int* blk_free;
   int* vtx_free;
