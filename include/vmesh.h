@@ -79,7 +79,7 @@ typedef struct {
   int64_t frame_blocks;      /* blocks collected by the last integrate_depth (N_t) */
   int64_t new_blocks;        /* blocks allocated since the volume was created */
   int64_t update_blocks;     /* blocks in the update set of the last mesh pass */
-  int64_t changed_cubes;     /* cubes whose effective type changed in the last mesh pass */
+  int64_t changed_cubes;     /* cubes whose effective type changed, summed over mesh passes */
   int64_t live_blocks;       /* allocated blocks */
   int64_t live_vertices;     /* vertices in the pool (includes zero-reference ones awaiting gc) */
   int64_t live_triangles;    /* triangles in the pool */
@@ -92,6 +92,8 @@ typedef struct {
   int64_t emitted_triangles; /* triangles written by mesh passes so far */
   int64_t released_triangles;/* triangles released by mesh passes so far */
   int64_t refreshed_vertices;/* vertex positions and normals recomputed so far */
+  int64_t collected_blocks;  /* N_t summed over integrate calls (kept modulo 2^32) */
+  int64_t meshed_blocks;     /* update-set sizes summed over mesh passes (kept modulo 2^32) */
 } vm_frame_stats;
 
 /* Flags of vm_update_mesh / vm_step. */

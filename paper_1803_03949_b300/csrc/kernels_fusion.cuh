@@ -10,9 +10,9 @@
 namespace vmk {
 
 // ------------------------------------------------------------------ block collection
-constexpr int ALLOC_TILE_W = 64;     // pixels per tile row (one pixel per thread)
-constexpr int ALLOC_TILE_H = 16;     // tile rows
-constexpr int ALLOC_THREADS = ALLOC_TILE_W * ALLOC_TILE_H;
+constexpr int ALLOC_TILE_W = 64;     // pixels per tile row
+constexpr int ALLOC_TILE_H = 16;     // tile rows; each thread takes two vertically adjacent pixels
+constexpr int ALLOC_THREADS = ALLOC_TILE_W * ALLOC_TILE_H / 2;
 constexpr int ALLOC_SET = 1024;      // CTA-local set of block keys (power of two)
 constexpr int DDA_MAX_CELLS = 1 << 16;
 
@@ -70,8 +70,14 @@ __device__ __forceinline__ void smem_set_insert(unsigned long long* set, const V
                                                 int bz, uint32_t frame) {
   uint32_t h = (uint32_t)(mix64(key) >> 20) & (ALLOC_SET - 1);
   for (int p = 0; p < 32; ++p) {
-    unsigned long long old = atomicCAS(&set[h], (unsigned long long)KEY_EMPTY, (unsigned long long)key);
-    if (old == KEY_EMPTY || old == key) return;
+    // a slot changes once (empty -> key), so a plain read that sees the key settles it;
+    // most pixels of a tile cross the same few cells, and this keeps them off the atomic
+    const unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(&set[h]);
+    if (cur == key) return;
+    if (cur == KEY_EMPTY) {
+      unsigned long long old = atomicCAS(&set[h], (unsigned long long)KEY_EMPTY, (unsigned long long)key);
+      if (old == KEY_EMPTY || old == key) return;
+    }
     h = (h + 1) & (ALLOC_SET - 1);
   }
   // CTA set saturated: insert directly
@@ -152,8 +158,8 @@ __device__ __forceinline__ void collect_pixel(const Vol& V, const FrameParams& f
   }
 }
 
-// One CTA per 64 x 16 pixel tile, one pixel per thread: walk the pixel's segment into a
-// CTA-local key set, then insert the set's unique keys into the global hash and record
+// One CTA per 64 x 16 pixel tile, two vertically adjacent pixels per thread (so a 640 x 480
+// frame fits in one wave of CTAs): walk each pixel's segment into a CTA-local key set, then insert the set's unique keys into the global hash and record
 // them as collected.  The last CTA clamps the block free-stack top and, when
 // `advance_epoch`, starts a new mesh epoch with an empty update set.
 __global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(Vol V, const FrameParams* __restrict__ fpp,
@@ -163,11 +169,14 @@ __global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(Vol V, const FrameParam
   const uint32_t frame = (uint32_t)__ldcg(&V.ctl->c[C_FRAME]);
   for (int i = threadIdx.x; i < ALLOC_SET; i += blockDim.x) set[i] = KEY_EMPTY;
   const int u = blockIdx.x * ALLOC_TILE_W + (threadIdx.x & (ALLOC_TILE_W - 1));
-  const int v = blockIdx.y * ALLOC_TILE_H + threadIdx.x / ALLOC_TILE_W;
-  const float D = (u < fp.W && v < fp.H) ? __ldg(fp.depth + (size_t)v * fp.W + u) : 0.0f;
+  const int v = blockIdx.y * ALLOC_TILE_H + 2 * (threadIdx.x / ALLOC_TILE_W);
+  const bool in0 = u < fp.W && v < fp.H, in1 = u < fp.W && v + 1 < fp.H;
+  const float D0 = in0 ? __ldg(fp.depth + (size_t)v * fp.W + u) : 0.0f;
+  const float D1 = in1 ? __ldg(fp.depth + (size_t)(v + 1) * fp.W + u) : 0.0f;
   __syncthreads();
   uint64_t last = KEY_EMPTY;
-  if (u < fp.W && v < fp.H) collect_pixel(V, fp, u, v, D, set, frame, last);
+  if (in0) collect_pixel(V, fp, u, v, D0, set, frame, last);
+  if (in1) collect_pixel(V, fp, u, v + 1, D1, set, frame, last);
   __syncthreads();
   for (int i = threadIdx.x; i < ALLOC_SET; i += blockDim.x) {
     uint64_t key = set[i];
@@ -290,6 +299,7 @@ __global__ void __launch_bounds__(INTEG_THREADS) k_integrate(Vol V, const FrameP
   if (last_block(V, C_DONE2)) {
     if (threadIdx.x == 0) {
       V.ctl->c[C_ST_FRAME_BLOCKS] = n;
+      reinterpret_cast<unsigned*>(V.ctl->c)[C_ST_COLLECTED] += (unsigned)n;  // wraps modulo 2^32
       V.ctl->c[C_N_TOUCHED] = 0;
       V.ctl->c[C_FRAME] += 1;
       V.ctl->c[C_DONE2] = 0;

@@ -452,6 +452,7 @@ __global__ void __launch_bounds__(MESH_THREADS, 7) k_mesh(Vol V, int mode) {
 #pragma unroll
       for (int L = 0; L < 5; ++L) fold_top(V, C_RUN_TOP0 + L);
       V.ctl->c[C_ST_UPDATE_BLOCKS] = n;
+      reinterpret_cast<unsigned*>(V.ctl->c)[C_ST_MESHED] += (unsigned)n;  // wraps modulo 2^32
       V.ctl->c[C_DONE3] = 0;
     }
   }

@@ -618,6 +618,8 @@ vm_status vm_get_stats(vm_volume* v, vm_frame_stats* s) {
   s->emitted_triangles = c[C_ST_EMITTED];
   s->released_triangles = c[C_ST_RELEASED];
   s->refreshed_vertices = c[C_ST_REFRESHED];
+  s->collected_blocks = (uint32_t)c[C_ST_COLLECTED];
+  s->meshed_blocks = (uint32_t)c[C_ST_MESHED];
   return VM_OK;
 }
 

@@ -57,7 +57,7 @@ enum Counter {
   C_LIVE_BLOCKS, C_LIVE_VERTS, C_LIVE_TRIS,
   C_TOMBS,
   C_REHASH,         // 1 while a hash rebuild is under way
-  C_ST_FRAME_BLOCKS, C_ST_UPDATE_BLOCKS, C_ST_NEW_BLOCKS, C_ST_CHANGED, C_ST_FREED_BLOCKS, C_ST_FREED_VERTS, C_ST_NEW_VERTS, C_ST_REHASHES,
+  C_ST_FRAME_BLOCKS, C_ST_UPDATE_BLOCKS, C_ST_COLLECTED, C_ST_MESHED, C_ST_NEW_BLOCKS, C_ST_CHANGED, C_ST_FREED_BLOCKS, C_ST_FREED_VERTS, C_ST_NEW_VERTS, C_ST_REHASHES,
   C_ST_EMITTED, C_ST_RELEASED, C_ST_REFRESHED,
   C_DONE0, C_DONE1, C_DONE2, C_DONE3, C_DONE4, C_DONE5, C_DONE6, C_DONE7,
   C_COUNT

@@ -41,7 +41,8 @@ class vm_frame_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "frame_blocks", "new_blocks", "update_blocks", "changed_cubes", "live_blocks", "live_vertices",
         "live_triangles", "freed_blocks", "freed_vertices", "created_vertices", "hash_tombstones",
-        "block_high_water", "rehashes", "emitted_triangles", "released_triangles", "refreshed_vertices")]
+        "block_high_water", "rehashes", "emitted_triangles", "released_triangles", "refreshed_vertices",
+        "collected_blocks", "meshed_blocks")]
 
 
 _lib = None
