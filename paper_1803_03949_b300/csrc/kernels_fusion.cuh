@@ -13,17 +13,24 @@ namespace vmk {
 constexpr int ALLOC_TILE_W = 64;     // pixels per tile row
 constexpr int ALLOC_TILE_H = 16;     // tile rows; each thread takes two vertically adjacent pixels
 constexpr int ALLOC_THREADS = ALLOC_TILE_W * ALLOC_TILE_H / 2;
-constexpr int ALLOC_SET = 1024;      // CTA-local set of block keys (power of two)
+constexpr int ALLOC_SET_LOG2 = 10;
+constexpr int ALLOC_SET = 1 << ALLOC_SET_LOG2;  // CTA-local set of block keys
 constexpr int DDA_MAX_CELLS = 1 << 16;
 
 // Insert `key` into the global hash; returns its bucket or -1.  A new key takes a block
 // from the block pool (stamped with the creating integrate call); its index is published
-// in vals[] for later kernels.
-__device__ int hash_insert(const Vol& V, uint64_t key, int bx, int by, int bz, uint32_t frame) {
+// in vals[] for later kernels.  `blk` receives the block index when it is already known
+// here, else -1 (a key another thread inserted in the same launch may not have its index
+// published yet; readers then take it from vals[] after the launch).
+__device__ int hash_insert(const Vol& V, uint64_t key, int bx, int by, int bz, uint32_t frame, int& blk_out) {
   uint32_t s = (uint32_t)mix64(key) & V.hmask;
+  blk_out = -1;
   for (uint32_t p = 0; p <= V.hmask; ++p) {
     uint64_t k = __ldcg(&V.keys[s]);
-    if (k == key) return (int)s;
+    if (k == key) {
+      blk_out = __ldcg(&V.vals[s]);
+      return (int)s;
+    }
     if (k == KEY_EMPTY) {
       unsigned long long old = atomicCAS((unsigned long long*)&V.keys[s], (unsigned long long)KEY_EMPTY,
                                          (unsigned long long)key);
@@ -40,6 +47,7 @@ __device__ int hash_insert(const Vol& V, uint64_t key, int bx, int by, int bz, u
           }
         }
         V.vals[s] = blk;
+        blk_out = blk;
         if (blk >= 0) {
           V.bkey[blk] = make_int4(bx, by, bz, (int)s);
           V.bborn[blk] = frame;
@@ -56,19 +64,18 @@ __device__ int hash_insert(const Vol& V, uint64_t key, int bx, int by, int bz, u
   return -1;
 }
 
-// Record a collected bucket once per integrate call.
-__device__ __forceinline__ void touch_bucket(const Vol& V, int s, uint32_t frame) {
+// Record a collected bucket once per integrate call, as {packed key (low, high word), block
+// index or -1, bucket}: the fusion kernel then needs no hash or key lookups of its own.
+__device__ __forceinline__ void touch_bucket(const Vol& V, int s, uint64_t key, int blk, uint32_t frame) {
   if (__ldcg(&V.stamp[s]) == frame) return;
-  if (atomicExch(&V.stamp[s], frame) != frame) {
-    int i = atomicAdd(&V.ctl->c[C_N_TOUCHED], 1);
-    if (i < V.list_cap_touched) V.touched[i] = s;
-    else set_status(V, ST_POOL_FULL);
-  }
+  if (atomicExch(&V.stamp[s], frame) != frame)
+    list_push(V, V.touched, C_N_TOUCHED, V.list_cap_touched, make_int4((int)(uint32_t)key, (int)(key >> 32), blk, s));
 }
 
 __device__ __forceinline__ void smem_set_insert(unsigned long long* set, const Vol& V, uint64_t key, int bx, int by,
                                                 int bz, uint32_t frame) {
-  uint32_t h = (uint32_t)(mix64(key) >> 20) & (ALLOC_SET - 1);
+  // any spread of the 63 key bits serves here (the set lives for one CTA): fold and multiply
+  uint32_t h = (((uint32_t)key ^ (uint32_t)(key >> 21) ^ (uint32_t)(key >> 42)) * 0x9E3779B1u) >> (32 - ALLOC_SET_LOG2);
   for (int p = 0; p < 32; ++p) {
     // a slot changes once (empty -> key), so a plain read that sees the key settles it;
     // most pixels of a tile cross the same few cells, and this keeps them off the atomic
@@ -81,8 +88,9 @@ __device__ __forceinline__ void smem_set_insert(unsigned long long* set, const V
     h = (h + 1) & (ALLOC_SET - 1);
   }
   // CTA set saturated: insert directly
-  int s = hash_insert(V, key, bx, by, bz, frame);
-  if (s >= 0) touch_bucket(V, s, frame);
+  int blk;
+  int s = hash_insert(V, key, bx, by, bz, frame, blk);
+  if (s >= 0) touch_bucket(V, s, key, blk, frame);
 }
 
 // DDA set-up along one axis: start cell c, remaining steps rem, step direction, the ray
@@ -159,14 +167,17 @@ __device__ __forceinline__ void collect_pixel(const Vol& V, const FrameParams& f
 }
 
 // One CTA per 64 x 16 pixel tile, two vertically adjacent pixels per thread (so a 640 x 480
-// frame fits in one wave of CTAs): walk each pixel's segment into a CTA-local key set, then insert the set's unique keys into the global hash and record
-// them as collected.  The last CTA clamps the block free-stack top and, when
-// `advance_epoch`, starts a new mesh epoch with an empty update set.
-__global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(Vol V, const FrameParams* __restrict__ fpp,
+// frame fits in one wave of CTAs): walk each pixel's segment into a CTA-local key set, then
+// insert the set's unique keys into the global hash and record them as collected.  The
+// frame's parameters arrive as a launch argument; the first CTA
+// stores them in the control block for the kernels that follow.  The last CTA clamps the
+// block free-stack top and, when `advance_epoch`, starts a new mesh epoch with an empty
+// update set.
+__global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(Vol V, const __grid_constant__ FrameParams fp,
                                                          int advance_epoch) {
   __shared__ unsigned long long set[ALLOC_SET];
-  const FrameParams& fp = *fpp;
   const uint32_t frame = (uint32_t)__ldcg(&V.ctl->c[C_FRAME]);
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) V.ctl->fp = fp;  // for the later kernels
   for (int i = threadIdx.x; i < ALLOC_SET; i += blockDim.x) set[i] = KEY_EMPTY;
   const int u = blockIdx.x * ALLOC_TILE_W + (threadIdx.x & (ALLOC_TILE_W - 1));
   const int v = blockIdx.y * ALLOC_TILE_H + 2 * (threadIdx.x / ALLOC_TILE_W);
@@ -184,8 +195,9 @@ __global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(Vol V, const FrameParam
     int bx = (int)((key >> 42) & 0x1FFFFF) - KEY_BIAS;
     int by = (int)((key >> 21) & 0x1FFFFF) - KEY_BIAS;
     int bz = (int)(key & 0x1FFFFF) - KEY_BIAS;
-    int s = hash_insert(V, key, bx, by, bz, frame);
-    if (s >= 0) touch_bucket(V, s, frame);
+    int blk;
+    int s = hash_insert(V, key, bx, by, bz, frame, blk);
+    if (s >= 0) touch_bucket(V, s, key, blk, frame);
   }
   allow_dependent_launch();
   if (last_block(V, C_DONE0)) {
@@ -235,6 +247,7 @@ __device__ __forceinline__ void resolve_block(const Vol& V, int blk, int4 key, u
 
 // ------------------------------------------------------------------ fusion (Eq. 2)
 constexpr int INTEG_THREADS = 128;  // 4 voxels per thread, one block per CTA iteration
+constexpr int INTEG_CTAS_PER_SM = 12;  // ~1.8k blocks (a 640 x 480 frame) in one wave
 
 // Per collected bucket: resolve it (update set, neighbour table), then (FUSE) fuse the frame
 // into every voxel of its block.  Voxels stream as float2 (d, W) pairs, 32 bytes per
@@ -242,7 +255,7 @@ constexpr int INTEG_THREADS = 128;  // 4 voxels per thread, one block per CTA it
 // of the block has W > 0 and d < mu (used by gc).  The last CTA empties the collected list
 // and advances the integrate-call counter.
 template <bool FUSE>
-__global__ void __launch_bounds__(INTEG_THREADS) k_integrate(Vol V, const FrameParams* __restrict__ fpp) {
+__global__ void __launch_bounds__(INTEG_THREADS, INTEG_CTAS_PER_SM) k_integrate(Vol V, const FrameParams* __restrict__ fpp) {
   grid_dependency_wait();
   const int n = min(__ldcg(&V.ctl->c[C_N_TOUCHED]), V.list_cap_touched);
   const uint32_t frame = (uint32_t)__ldcg(&V.ctl->c[C_FRAME]);
@@ -251,9 +264,12 @@ __global__ void __launch_bounds__(INTEG_THREADS) k_integrate(Vol V, const FrameP
   const int v0 = threadIdx.x * 4;
   const int lx = v0 & 7, ly = (v0 >> 3) & 7, lz = v0 >> 6;
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
-    const int blk = __ldcg(&V.vals[V.touched[i]]);
+    const int4 t = __ldcg(&V.touched[i]);
+    const int blk = t.z >= 0 ? t.z : __ldcg(&V.vals[t.w]);
     if (blk < 0) continue;
-    const int4 key = V.bkey[blk];
+    const uint64_t kk = ((uint64_t)(uint32_t)t.y << 32) | (uint32_t)t.x;
+    const int4 key = make_int4((int)((kk >> 42) & 0x1FFFFF) - KEY_BIAS, (int)((kk >> 21) & 0x1FFFFF) - KEY_BIAS,
+                               (int)(kk & 0x1FFFFF) - KEY_BIAS, t.w);
     resolve_block(V, blk, key, frame, epoch);
     if (!FUSE) continue;
     const FrameParams& fp = *fpp;

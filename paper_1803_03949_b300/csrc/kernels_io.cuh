@@ -181,8 +181,10 @@ __global__ void __launch_bounds__(256) k_fill_insert(Vol V, const int* keys, int
       set_status(V, ST_INVALID);
       continue;
     }
-    int s = hash_insert(V, pack_key(x, y, z), x, y, z, frame);
-    if (s >= 0) touch_bucket(V, s, frame);
+    const uint64_t key = pack_key(x, y, z);
+    int blk;
+    int s = hash_insert(V, key, x, y, z, frame, blk);
+    if (s >= 0) touch_bucket(V, s, key, blk, frame);
   }
   if (last_block(V, C_DONE0)) {
     if (threadIdx.x == 0) {

@@ -19,11 +19,8 @@ using namespace vmk;
 
 namespace {
 
-enum KernelId { K_SET_FRAME = 0, K_ALLOC, K_INTEGRATE, K_LIST_ALL, K_MESH, K_GC_VERTICES, K_GC_BLOCKS, K_COUNT_ };
-const char* kKernelNames[K_COUNT_] = {"k_set_frame", "k_alloc",       "k_integrate", "k_list_all",
-                                      "k_mesh",      "k_gc_vertices", "k_gc_blocks"};
-
-__global__ void k_set_frame(FrameParams* dst, FrameParams fp) { *dst = fp; }
+enum KernelId { K_ALLOC = 0, K_INTEGRATE, K_LIST_ALL, K_MESH, K_GC_VERTICES, K_GC_BLOCKS, K_COUNT_ };
+const char* kKernelNames[K_COUNT_] = {"k_alloc", "k_integrate", "k_list_all", "k_mesh", "k_gc_vertices", "k_gc_blocks"};
 
 // Every allocated block joins the update set (full extraction).
 __global__ void __launch_bounds__(256) k_list_all(Vol V) {
@@ -67,7 +64,10 @@ struct vm_volume {
   std::vector<cudaEvent_t> event_pool;
   double tot_ms[K_COUNT_] = {0};
   long long launches[K_COUNT_] = {0};
-  // graph replay of vm_step
+  // graph replay of vm_step; the frame's parameters reach the graph as k_alloc's launch
+  // arguments, replaced in alloc_node before every replay
+  cudaGraph_t graph = nullptr;
+  cudaGraphNode_t alloc_node = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   int graph_flags = -1;
   int graph_W = -1, graph_H = -1;
@@ -193,17 +193,17 @@ void launch_dependent(void (*kernel)(Params...), int grid, int block, cudaStream
 }
 
 // ---- enqueue helpers (no validation)
-vm_status enqueue_integrate(vm_volume* v, const FrameParams& fp, bool set_frame) {
-  vm_status st = VM_OK;
+dim3 alloc_grid(const FrameParams& fp) {
+  return dim3((fp.W + ALLOC_TILE_W - 1) / ALLOC_TILE_W, (fp.H + ALLOC_TILE_H - 1) / ALLOC_TILE_H);
+}
+
+vm_status enqueue_integrate(vm_volume* v, const FrameParams& fp) {
   Ctl* ctl = v->V.ctl;
-  if (set_frame) st = launch(v, K_SET_FRAME, [&] { k_set_frame<<<1, 1, 0, v->cur>>>(&ctl->fp, fp); });
-  if (st) return st;
   const int adv = v->advance_pending ? 1 : 0;
-  dim3 g((fp.W + ALLOC_TILE_W - 1) / ALLOC_TILE_W, (fp.H + ALLOC_TILE_H - 1) / ALLOC_TILE_H);
-  st = launch(v, K_ALLOC, [&] { k_alloc<<<g, ALLOC_THREADS, 0, v->cur>>>(v->V, &ctl->fp, adv); });
+  vm_status st = launch(v, K_ALLOC, [&] { k_alloc<<<alloc_grid(fp), ALLOC_THREADS, 0, v->cur>>>(v->V, fp, adv); });
   if (st) return st;
   st = launch(v, K_INTEGRATE, [&] {
-    launch_dependent(k_integrate<true>, grid_for(v, 8), INTEG_THREADS, v->cur, v->V, (const FrameParams*)&ctl->fp);
+    launch_dependent(k_integrate<true>, grid_for(v, INTEG_CTAS_PER_SM), INTEG_THREADS, v->cur, v->V, (const FrameParams*)&ctl->fp);
   });
   v->advance_pending = false;
   return st;
@@ -247,11 +247,29 @@ int read_counter(vm_volume* v, int c) {
   return x;
 }
 
+// The kernel node of `g` that launches `func`, or null.
+cudaGraphNode_t find_kernel_node(cudaGraph_t g, void* func) {
+  size_t n = 0;
+  if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return nullptr;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return nullptr;
+  for (cudaGraphNode_t node : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(node, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+    cudaKernelNodeParams kp;
+    if (cudaGraphKernelNodeGetParams(node, &kp) == cudaSuccess && kp.func == func) return node;
+  }
+  return nullptr;
+}
+
 void drop_graph(vm_volume* v) {
   if (v->graph_exec) {
     cudaStreamSynchronize(v->stream);
     cudaGraphExecDestroy(v->graph_exec);
   }
+  if (v->graph) cudaGraphDestroy(v->graph);
+  v->graph = nullptr;
+  v->alloc_node = nullptr;
   v->graph_exec = nullptr;
   v->graph_flags = -1;
   v->graph_pending = false;
@@ -408,7 +426,7 @@ vm_status vm_integrate_depth(vm_volume* v, const float* depth, const vm_intrinsi
   if (!v) return VM_ERR_INVALID_ARG;
   FrameParams fp;
   if (!make_frame(K, Twc, Tcw, depth, &fp)) return VM_ERR_INVALID_ARG;
-  return enqueue_integrate(v, fp, true);
+  return enqueue_integrate(v, fp);
 }
 
 vm_status vm_update_mesh(vm_volume* v, int flags) {
@@ -434,10 +452,8 @@ vm_status vm_step(vm_volume* v, const float* depth, const vm_intrinsics* K, cons
   if (!v || (flags & ~(VM_FULL | VM_REFINE | VM_GC))) return VM_ERR_INVALID_ARG;
   FrameParams fp;
   if (!make_frame(K, Twc, Tcw, depth, &fp)) return VM_ERR_INVALID_ARG;
-  vm_status st = launch(v, K_SET_FRAME, [&] { k_set_frame<<<1, 1, 0, v->stream>>>(&v->V.ctl->fp, fp); });
-  if (st) return st;
   auto body = [&]() -> vm_status {
-    vm_status s = enqueue_integrate(v, fp, false);
+    vm_status s = enqueue_integrate(v, fp);
     if (s) return s;
     s = enqueue_update(v, flags & (VM_FULL | VM_REFINE));
     if (s) return s;
@@ -475,10 +491,13 @@ vm_status vm_step(vm_volume* v, const float* depth, const vm_intrinsics* K, cons
       (void)cudaGetLastError();
       return VM_ERR_CUDA;
     }
-    e = cudaGraphInstantiate(&v->graph_exec, g, 0);
-    cudaGraphDestroy(g);
+    v->graph = g;
+    v->alloc_node = find_kernel_node(g, reinterpret_cast<void*>(k_alloc));
+    e = v->alloc_node ? cudaGraphInstantiate(&v->graph_exec, g, 0) : cudaErrorInvalidValue;
     if (e != cudaSuccess) {
+      (void)cudaGetLastError();
       v->graph_exec = nullptr;
+      drop_graph(v);
       return VM_ERR_CUDA;
     }
     v->graph_flags = flags;
@@ -487,7 +506,23 @@ vm_status vm_step(vm_volume* v, const float* depth, const vm_intrinsics* K, cons
   }
   v->advance_pending = true;
   collect_graph_timing(v);  // a previous replay's node events are about to be re-recorded
-  cudaError_t e = cudaGraphLaunch(v->graph_exec, v->stream);
+  // this frame's parameters become k_alloc's arguments (the captured graph advances the
+  // epoch at its start, so advance_epoch is 1)
+  int adv = 1;
+  void* args[3] = {&v->V, &fp, &adv};
+  cudaKernelNodeParams kp = {};
+  kp.func = reinterpret_cast<void*>(k_alloc);
+  kp.gridDim = alloc_grid(fp);
+  kp.blockDim = dim3(ALLOC_THREADS);
+  kp.sharedMemBytes = 0;
+  kp.kernelParams = args;
+  kp.extra = nullptr;
+  cudaError_t e = cudaGraphExecKernelNodeSetParams(v->graph_exec, v->alloc_node, &kp);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return VM_ERR_CUDA;
+  }
+  e = cudaGraphLaunch(v->graph_exec, v->stream);
   v->graph_pending = v->timing_mask && !v->graph_recs.empty();
   return cuda_status(e);
 }
@@ -676,7 +711,7 @@ vm_status vm_set_blocks(vm_volume* v, const int32_t* keys, int64_t n, const floa
   if (ok) {
     const int adv = v->advance_pending ? 1 : 0;
     k_fill_insert<<<grid_for(v, 2), 256, 0, v->stream>>>(v->V, (const int*)dk, (int)n, adv);
-    k_integrate<false><<<grid_for(v, 8), INTEG_THREADS, 0, v->stream>>>(v->V, &v->V.ctl->fp);
+    k_integrate<false><<<grid_for(v, INTEG_CTAS_PER_SM), INTEG_THREADS, 0, v->stream>>>(v->V, &v->V.ctl->fp);
     k_fill_copy<<<grid_for(v, 4), 256, 0, v->stream>>>(v->V, (const int*)dk, (const float*)dt, (const float*)dw,
                                                        (int)n);
     ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(v->stream) == cudaSuccess;

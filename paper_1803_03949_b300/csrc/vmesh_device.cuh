@@ -117,7 +117,7 @@ struct Vol {
   int* vtx_free;
   int* run_free[5];
 
-  int* touched;       // buckets collected by this integrate call
+  int4* touched;      // blocks collected by this integrate call: {key low, key high, block or -1, bucket}
   int* update;        // update-set blocks
   int* dead;          // zero-reference vertex ids
   int2* deadrun;      // released triangle runs (start, length)
@@ -215,7 +215,8 @@ __device__ __forceinline__ void pool_push(const Vol& V, int* stack, int c_top, i
 }
 
 // Append to a work list, aggregated over the calling lanes; false (and POOL_FULL) on overflow.
-__device__ __forceinline__ bool list_push(const Vol& V, int* list, int c_count, int cap, int value) {
+template <typename T>
+__device__ __forceinline__ bool list_push(const Vol& V, T* list, int c_count, int cap, T value) {
   cg::coalesced_group g = cg::coalesced_threads();
   int base = 0;
   if (g.thread_rank() == 0) base = atomicAdd(&V.ctl->c[c_count], (int)g.size());

@@ -252,7 +252,7 @@ class Volume:
         _check(self._lib.vm_set_blocks(self._h, _ptr(k), k.shape[0], _ptr(t), _ptr(w)), "vm_set_blocks")
 
     # --------------------------------------------------------------- timing
-    KERNELS = ["k_set_frame", "k_alloc", "k_integrate", "k_list_all", "k_mesh", "k_gc_vertices", "k_gc_blocks"]
+    KERNELS = ["k_alloc", "k_integrate", "k_list_all", "k_mesh", "k_gc_vertices", "k_gc_blocks"]
 
     def enable_timing(self, on=True):
         """on: True (every kernel), False (none) or a list of kernel names to time."""
