@@ -223,9 +223,12 @@ __global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(Vol V, const __grid_con
 __device__ __forceinline__ void resolve_block(const Vol& V, int blk, int4 key, uint32_t frame, uint32_t epoch) {
   const int t = threadIdx.x;
   if (t >= 16) return;
-  const bool is_new = __ldcg(&V.bborn[blk]) == frame;
   const int o = t & 7;
   const int sgn = t < 8 ? -1 : 1;  // threads 0..7: lower neighbours (and self), 8..15: upper
+  // both loads issued together; the table entry is used only for an old block
+  const uint32_t born = __ldcg(&V.bborn[blk]);
+  const int nb_old = (sgn < 0 && o != 0) ? __ldcg(&V.nbr[blk * 16 + 8 + o]) : -1;
+  const bool is_new = born == frame;
   int nb;
   if (o == 0) {
     nb = blk;
@@ -235,14 +238,12 @@ __device__ __forceinline__ void resolve_block(const Vol& V, int blk, int4 key, u
     V.nbr[blk * 16 + (sgn > 0 ? o : 8 + o)] = nb;
     if (nb >= 0) V.nbr[nb * 16 + (sgn > 0 ? 8 + o : o)] = blk;
   } else {
-    nb = sgn < 0 ? __ldcg(&V.nbr[blk * 16 + 8 + o]) : -1;
+    nb = nb_old;
   }
   if (t == 0) V.bepoch[blk] = epoch;
   if (sgn > 0 || nb < 0) return;
-  const int ns = o == 0 ? key.w : __ldcg(&V.bkey[nb].w);
-  if (ns < 0) return;
-  if (__ldcg(&V.ustamp[ns]) == epoch) return;
-  if (atomicExch(&V.ustamp[ns], epoch) != epoch) list_push(V, V.update, C_N_UPDATE, V.list_cap_update, nb);
+  if (__ldcg(&V.ustamp[nb]) == epoch) return;
+  if (atomicExch(&V.ustamp[nb], epoch) != epoch) list_push(V, V.update, C_N_UPDATE, V.list_cap_update, nb);
 }
 
 // ------------------------------------------------------------------ fusion (Eq. 2)

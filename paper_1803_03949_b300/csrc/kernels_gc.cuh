@@ -59,15 +59,14 @@ __global__ void __launch_bounds__(256) k_gc_vertices(Vol V) {
   }
 }
 
-// Rebuild the hash without tombstones (one CTA): empty every bucket, re-insert every live
-// block from the block array (bkey holds its key; its new bucket is written back), then
-// re-mark the pending update set so no block is listed twice.
-__device__ void rehash_in_cta(const Vol& V, bool mark_update) {
+// Rebuild the hash without tombstones (one CTA): empty every bucket, then re-insert every
+// live block from the block array (bkey holds its key; its new bucket is written back).
+// Block indices, and with them the update-set marks, do not change.
+__device__ void rehash_in_cta(const Vol& V) {
   for (uint32_t s = threadIdx.x; s <= V.hmask; s += blockDim.x) {
     V.keys[s] = KEY_EMPTY;
     V.vals[s] = -1;
     V.stamp[s] = 0;
-    V.ustamp[s] = 0;
   }
   __threadfence();
   __syncthreads();
@@ -88,14 +87,6 @@ __device__ void rehash_in_cta(const Vol& V, bool mark_update) {
   }
   __threadfence();
   __syncthreads();
-  if (mark_update) {
-    const int n = min(__ldcg(&V.ctl->c[C_N_UPDATE]), V.list_cap_update);
-    const uint32_t epoch = (uint32_t)__ldcg(&V.ctl->c[C_EPOCH]);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const int4 k = V.bkey[V.update[i]];
-      if (k.w >= 0) V.ustamp[k.w] = epoch;
-    }
-  }
 }
 
 // Block recycling, one warp per pool slot.  A block is freed when it was not collected in
@@ -117,7 +108,7 @@ __global__ void __launch_bounds__(256) k_gc_blocks(Vol V, int consumed) {
   for (int blk = warp; blk < hw; blk += nwarps) {
     const int4 key = V.bkey[blk];
     const bool cand = key.w >= 0 && V.bepoch[blk] != epoch && V.bntri[blk] == 0 && V.bnvert[blk] == 0 &&
-                      V.bnear[blk] == 0 && (consumed || V.ustamp[key.w] != epoch);
+                      V.bnear[blk] == 0 && (consumed || V.ustamp[blk] != epoch);
     if (!cand) continue;  // warp-uniform
     bool lower_tri = false;
     if (lane >= 1 && lane < 8) {
@@ -160,7 +151,7 @@ __global__ void __launch_bounds__(256) k_gc_blocks(Vol V, int consumed) {
     }
     __syncthreads();
     if (need) {
-      rehash_in_cta(V, !consumed);
+      rehash_in_cta(V);
       if (threadIdx.x == 0) {
         V.ctl->c[C_TOMBS] = 0;
         V.ctl->c[C_ST_REHASHES] += 1;

@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(256) k_list_all(Vol V) {
   for (int blk = blockIdx.x * blockDim.x + threadIdx.x; blk < hw; blk += gridDim.x * blockDim.x) {
     int4 k = V.bkey[blk];
     if (k.w < 0) continue;
-    V.ustamp[k.w] = epoch;
+    V.ustamp[blk] = epoch;
     list_push(V, V.update, C_N_UPDATE, V.list_cap_update, blk);
   }
 }
@@ -363,7 +363,7 @@ vm_status vm_create_volume(const vm_params* p, void* cuda_stream, vm_volume** ou
   V.list_cap_deadrun = (int)p->max_triangles;
   const size_t NB = p->max_blocks, NV = p->max_vertices, NT = p->max_triangles;
   bool ok = dalloc(v, &V.keys, hb, 0xFF) && dalloc(v, &V.vals, hb, 0xFF) && dalloc(v, &V.stamp, hb, 0) &&
-            dalloc(v, &V.ustamp, hb, 0) && dalloc(v, &V.bkey, NB, 0xFF) && dalloc(v, &V.nbr, NB * 16, 0xFF) &&
+            dalloc(v, &V.ustamp, NB, 0) && dalloc(v, &V.bkey, NB, 0xFF) && dalloc(v, &V.nbr, NB * 16, 0xFF) &&
             dalloc(v, &V.bntri, NB, 0) && dalloc(v, &V.bnvert, NB, 0) && dalloc(v, &V.bnear, NB, 0) &&
             dalloc(v, &V.bepoch, NB, 0) && dalloc(v, &V.bborn, NB, 0) && dalloc(v, &V.tw, NB * BV, 0) &&
             dalloc(v, &V.code_eff, NB * BV, 0) && dalloc(v, &V.code_prev, NB * BV, 0) &&

@@ -2,9 +2,9 @@
 //
 // HBM layout of a volume (all arrays owned by the library, cleared at creation):
 //   hash      keys u64[B] (packed block key, EMPTY / TOMB), vals i32[B] (block index),
-//             stamp u32[B] (integrate call that last collected the bucket's block),
-//             ustamp u32[B] (mesh epoch in which the block joined the update set)
-//   blocks    bkey int4[NB] (x, y, z, bucket; bucket < 0 = free), nbr i32[NB][16]
+//             stamp u32[B] (integrate call that last collected the bucket's block)
+//   blocks    ustamp u32[NB] (mesh epoch in which the block joined the update set),
+//             bkey int4[NB] (x, y, z, bucket; bucket < 0 = free), nbr i32[NB][16]
 //             (block indices of the neighbours at offsets (o&1, o>>1&1, o>>2&1), o = 1..7,
 //             in slots 1..7 and of the neighbours at the negated offsets in slots 9..15;
 //             -1 = none), bntri/bnvert i32[NB] (triangles in its cubes / vertices it
