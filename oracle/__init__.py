@@ -64,6 +64,15 @@ def _lib(prec: str):
         lib.or_mesh_build.restype = i64
         lib.or_mesh_build.argtypes = [vp, P(i64)]
         lib.or_mesh_fetch.argtypes = [vp, P(ctypes.c_uint64), P(d), P(d), P(ctypes.c_uint64)]
+        lib.or_diff_begin.argtypes = [vp]
+        lib.or_diff_end.argtypes = [vp]
+        lib.or_diff_frames.restype = i
+        lib.or_diff_frames.argtypes = [vp]
+        lib.or_grad_vertices.argtypes = [vp, i64, P(ctypes.c_uint64), P(d), P(d)]
+        lib.or_grad_export.argtypes = [vp, P(d)]
+        lib.or_grad_depth.argtypes = [vp, i, i, P(d)]
+        lib.or_set_voxel.restype = i
+        lib.or_set_voxel.argtypes = [vp, i, i, i, d]
         _loaded[prec] = lib
     return _loaded[prec]
 
@@ -165,10 +174,41 @@ class Volume:
         return dict(keys=keys, tsdf=tsdf, weight=weight, code_eff=ce, code_prev=cp)
 
     def stats(self):
-        out = np.zeros(5, np.int64)
+        out = np.zeros(6, np.int64)
         self._lib.or_stats(self._h, _ptr(out, ctypes.c_int64))
         return dict(cells=int(out[0]), voxels_integrated=int(out[1]), frame_blocks=int(out[2]),
-                    update_blocks=int(out[3]), epoch=int(out[4]))
+                    update_blocks=int(out[3]), epoch=int(out[4]), truncated=int(out[5]))
+
+    # ------------------------------------------------------------ differentiable path
+    def diff_begin(self) -> None:
+        """Record every integration from now on (and clear dL/dd); no gc until the gradients are taken."""
+        self._lib.or_diff_begin(self._h)
+
+    def diff_end(self) -> None:
+        self._lib.or_diff_end(self._h)
+
+    def grad_vertices(self, keys, gpos, gnrm) -> None:
+        """Add the TSDF gradients of vertices `keys` (edge keys) given dL/dpos, dL/dnrm (n, 3)."""
+        k = np.ascontiguousarray(keys, np.uint64)
+        a = np.ascontiguousarray(gpos, np.float64).reshape(-1, 3)
+        b = np.ascontiguousarray(gnrm, np.float64).reshape(-1, 3)
+        self._lib.or_grad_vertices(self._h, k.shape[0], _ptr(k, ctypes.c_uint64), _ptr(a, ctypes.c_double),
+                                   _ptr(b, ctypes.c_double))
+
+    def grad_tsdf(self) -> np.ndarray:
+        """dL/dd per voxel, (n_blocks, 512), rows in the order of blocks()['keys']."""
+        out = np.zeros((self.num_blocks(), 512), np.float64)
+        self._lib.or_grad_export(self._h, _ptr(out, ctypes.c_double))
+        return out
+
+    def grad_depth(self, W: int, H: int) -> np.ndarray:
+        """dL/dD of every recorded frame, (frames, H, W); consumes dL/dd."""
+        out = np.zeros((self._lib.or_diff_frames(self._h), H, W), np.float64)
+        self._lib.or_grad_depth(self._h, W, H, _ptr(out, ctypes.c_double))
+        return out
+
+    def set_voxel(self, g, d: float) -> bool:
+        return bool(self._lib.or_set_voxel(self._h, int(g[0]), int(g[1]), int(g[2]), float(d)))
 
     def mesh(self):
         """dict(vkeys (nv,) uint64 sorted, pos/nrm (nv,3) float64, tkeys (nt,3) uint64)."""

@@ -61,6 +61,17 @@
  *     recycling is this implementation's addition.  A gc between a frame's
  *     integration and its mesh update keeps the pending update set; a gc after the
  *     mesh update empties the update set (a refinement pass after gc does nothing).
+ *   - Differentiable path (the reading taken for gradients through Secs. V-A and V-C,
+ *     topology held fixed): between or_diff_begin and the gradient calls every
+ *     integration of a voxel is recorded with its frame, pixel, pre-update weight W
+ *     and whether d~ = sdf (sdf < mu; d~ = mu is constant in the depth).  Gradients
+ *     of a loss given by its derivatives at the vertex positions and normals flow
+ *     (or_grad_vertices) into the TSDF values through the edge interpolation and the
+ *     normal above, and (or_grad_depth) from the TSDF values to the depth pixels by
+ *     reverse-mode through d <- (d W + d~) / (W + 1): per recorded integration,
+ *     taken last to first, dL/dd~ = g / (W + 1) reaches the pixel when d~ = sdf, and
+ *     g <- g W / (W + 1).  Decisions (which voxel, pixel, branch) are this build's;
+ *     the derivative arithmetic is float64 in both builds.
  */
 #include <math.h>
 #include <stdint.h>
@@ -214,7 +225,15 @@ typedef struct {
   real weight[BV];
   unsigned char code_eff[BV];
   unsigned char code_prev[BV];
+  double gd[BV]; /* dL/dd of the differentiable path */
 } oblock;
+
+/* one recorded integration of the differentiable path */
+typedef struct {
+  int block, voxel, frame, pixel;
+  double wpre;       /* weight before the update */
+  unsigned char lin; /* d~ = sdf (1) or d~ = mu (0) */
+} orec;
 
 typedef struct {
   real l, mu, eps, wmax;
@@ -228,7 +247,11 @@ typedef struct {
   int *pending, npending, pcap;
   int *last_set, nlast, lcap;
   int *frame_list, nframe, fcap;
-  int64_t stat_cells, stat_voxels_integrated;
+  int64_t stat_cells, stat_voxels_integrated, stat_truncated;
+  /* differentiable path: recording switch, recorded integrate calls, records */
+  int diff_on, diff_frames;
+  orec* recs;
+  int64_t nrec, rcap;
   /* mesh export scratch */
   uint64_t* vkeys;
   double *vpos, *vnrm;
@@ -346,6 +369,7 @@ void or_destroy(void* h) {
   for (int b = 0; b < V->nblocks; ++b) free(V->blocks[b]);
   free(V->blocks); free(V->mkeys); free(V->mvals);
   free(V->pending); free(V->last_set); free(V->frame_list);
+  free(V->recs);
   free_mesh(V);
   free(V);
 }
@@ -430,7 +454,8 @@ static void pixel_segment(const ovol* V, int u, int v, real D, const real* K, co
 static int depth_valid(float D) { return isfinite(D) && D > 0.0f; }
 
 /* ------------------------------------------------------------ fusion (Sec. V-A, Eq. 2) */
-static void integrate_block(ovol* V, oblock* B, const float* depth, int W, int H, const real* K, const real* Tcw) {
+static void integrate_block(ovol* V, int b, const float* depth, int W, int H, const real* K, const real* Tcw) {
+  oblock* B = V->blocks[b];
   for (int z = 0; z < BS; ++z)
     for (int y = 0; y < BS; ++y)
       for (int x = 0; x < BS; ++x) {
@@ -452,6 +477,15 @@ static void integrate_block(ovol* V, oblock* B, const float* depth, int W, int H
         if (sdf < -V->mu) continue;
         real dt = sdf < V->mu ? sdf : V->mu;
         real Wo = B->weight[i];
+        if (!(sdf < V->mu)) V->stat_truncated++;
+        if (V->diff_on) {
+          if (V->nrec == V->rcap) {
+            V->rcap = V->rcap ? 2 * V->rcap : 4096;
+            V->recs = (orec*)realloc(V->recs, sizeof(orec) * (size_t)V->rcap);
+          }
+          orec r = {b, i, V->diff_frames, iv * W + iu, (double)Wo, (unsigned char)(sdf < V->mu)};
+          V->recs[V->nrec++] = r;
+        }
         real num = B->tsdf[i] * Wo + dt;
         real den = Wo + (real)1;
         B->tsdf[i] = num / den;
@@ -504,7 +538,8 @@ int or_integrate(void* h, const float* depth, int W, int H, const double* intr, 
       }
     }
   free(cells);
-  for (int j = 0; j < V->nframe; ++j) integrate_block(V, V->blocks[V->frame_list[j]], depth, W, H, K, Tcw);
+  for (int j = 0; j < V->nframe; ++j) integrate_block(V, V->frame_list[j], depth, W, H, K, Tcw);
+  if (V->diff_on) V->diff_frames++;
   return 0;
 }
 
@@ -759,6 +794,7 @@ void or_stats(void* h, int64_t* out) {
   out[2] = V->nframe;
   out[3] = V->nlast;
   out[4] = V->epoch;
+  out[5] = V->stat_truncated;
 }
 
 /* edge key: voxel coordinates biased by 2^19 (20 bits each) and the axis (2 bits) */
@@ -852,4 +888,150 @@ void or_mesh_fetch(void* h, uint64_t* vkeys, double* pos, double* nrm, uint64_t*
   if (pos) memcpy(pos, V->vpos, sizeof(double) * (size_t)(3 * V->nv));
   if (nrm) memcpy(nrm, V->vnrm, sizeof(double) * (size_t)(3 * V->nv));
   if (tkeys) memcpy(tkeys, V->tkeys, sizeof(uint64_t) * (size_t)(3 * V->nt));
+}
+
+/* ------------------------------------------------------------ differentiable path */
+/* Start recording integrations (and clear dL/dd).  No gc may run until the gradients
+ * have been taken: block indices name the recorded voxels. */
+void or_diff_begin(void* h) {
+  ovol* V = (ovol*)h;
+  V->diff_on = 1;
+  V->diff_frames = 0;
+  V->nrec = 0;
+  for (int b = 0; b < V->nblocks; ++b) memset(V->blocks[b]->gd, 0, sizeof(V->blocks[b]->gd));
+}
+
+void or_diff_end(void* h) {
+  ovol* V = (ovol*)h;
+  V->diff_on = 0;
+}
+
+int or_diff_frames(void* h) { return ((ovol*)h)->diff_frames; }
+
+/* dL/dd of global voxel g, or NULL when its block is not allocated */
+static double* grad_at(ovol* V, int gx, int gy, int gz) {
+  int bx = floordiv8(gx), by = floordiv8(gy), bz = floordiv8(gz);
+  int b = find_block(V, bx, by, bz);
+  if (b < 0) return NULL;
+  return &V->blocks[b]->gd[(gx - 8 * bx) + 8 * (gy - 8 * by) + 64 * (gz - 8 * bz)];
+}
+
+/* Add the TSDF-value gradients of the vertices `keys` (n edge keys) given dL/dp and
+ * dL/dn (n x 3 each) at their positions and normals (Sec. V-C as above):
+ *   p_a = g_a l + t l, t = d0 / (d0 - d1): dt/dd0 = -d1 / (d0 - d1)^2, dt/dd1 = d0 / (d0 - d1)^2
+ *   (0 where t is clamped or d0 = d1);
+ *   n = m / |m|, m_a = d1 - d0, m_b = (1 - t)(e0_b - d0) + t (e1_b - d1) for b != a with
+ *   both corners usable: dL/dm = (dL/dn - n (n . dL/dn)) / |m| (0 when |m| = 0). */
+void or_grad_vertices(void* h, int64_t n, const uint64_t* keys, const double* gpos, const double* gnrm) {
+  ovol* V = (ovol*)h;
+  for (int64_t j = 0; j < n; ++j) {
+    uint64_t key = keys[j];
+    int g[3] = {(int)((key >> 42) & 0xFFFFF) - (1 << 19), (int)((key >> 22) & 0xFFFFF) - (1 << 19),
+                (int)((key >> 2) & 0xFFFFF) - (1 << 19)};
+    int a = (int)(key & 3);
+    int g1[3] = {g[0], g[1], g[2]};
+    g1[a] += 1;
+    double* G0 = grad_at(V, g[0], g[1], g[2]);
+    double* G1 = grad_at(V, g1[0], g1[1], g1[2]);
+    if (!G0 || !G1) continue;
+    real d0r = 0, d1r = 0;
+    voxel_at(V, g[0], g[1], g[2], &d0r, NULL);
+    voxel_at(V, g1[0], g1[1], g1[2], &d1r, NULL);
+    real tr = d0r == d1r ? (real)0.5 : d0r / (d0r - d1r);
+    const int fixed_t = d0r == d1r || tr < (real)-1 || tr > (real)2;
+    if (tr < (real)-1) tr = (real)-1;
+    if (tr > (real)2) tr = (real)2;
+    const double d0 = (double)d0r, d1 = (double)d1r, t = (double)tr;
+    double dt0 = 0, dt1 = 0;
+    if (!fixed_t) {
+      const double q = d0 - d1;
+      dt0 = -d1 / (q * q);
+      dt1 = d0 / (q * q);
+    }
+    double gt = gpos[3 * j + a] * (double)V->l;
+    /* the normal: corner values, usability (decided as in the forward), m in float64 */
+    double m[3], e0v[3] = {0, 0, 0}, e1v[3] = {0, 0, 0};
+    double *GE0[3] = {NULL, NULL, NULL}, *GE1[3] = {NULL, NULL, NULL};
+    real mr[3];
+    int use[3] = {0, 0, 0};
+    for (int b = 0; b < 3; ++b) {
+      if (b == a) {
+        m[b] = d1 - d0;
+        mr[b] = d1r - d0r;
+        continue;
+      }
+      real e0r = 0, e1r = 0;
+      int h0 = voxel_at(V, g[0] + (b == 0), g[1] + (b == 1), g[2] + (b == 2), &e0r, NULL);
+      int h1 = voxel_at(V, g1[0] + (b == 0), g1[1] + (b == 1), g1[2] + (b == 2), &e1r, NULL);
+      use[b] = h0 && h1;
+      if (use[b]) {
+        e0v[b] = (double)e0r;
+        e1v[b] = (double)e1r;
+        GE0[b] = grad_at(V, g[0] + (b == 0), g[1] + (b == 1), g[2] + (b == 2));
+        GE1[b] = grad_at(V, g1[0] + (b == 0), g1[1] + (b == 1), g1[2] + (b == 2));
+        m[b] = (1 - t) * (e0v[b] - d0) + t * (e1v[b] - d1);
+        mr[b] = ((real)1 - tr) * (e0r - d0r) + tr * (e1r - d1r);
+      } else {
+        m[b] = 0;
+        mr[b] = 0;
+      }
+    }
+    double gm[3] = {0, 0, 0};
+    const real lenr = real_sqrt((mr[0] * mr[0] + mr[1] * mr[1]) + mr[2] * mr[2]);
+    const double len = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+    if (lenr > 0 && len > 0) {
+      double nh[3] = {m[0] / len, m[1] / len, m[2] / len};
+      double dot = nh[0] * gnrm[3 * j] + nh[1] * gnrm[3 * j + 1] + nh[2] * gnrm[3 * j + 2];
+      for (int i = 0; i < 3; ++i) gm[i] = (gnrm[3 * j + i] - nh[i] * dot) / len;
+    }
+    double gd0 = -gm[a], gd1 = gm[a];
+    for (int b = 0; b < 3; ++b) {
+      if (b == a || !use[b]) continue;
+      *GE0[b] += gm[b] * (1 - t);
+      *GE1[b] += gm[b] * t;
+      gd0 -= gm[b] * (1 - t);
+      gd1 -= gm[b] * t;
+      gt += gm[b] * ((e1v[b] - d1) - (e0v[b] - d0));
+    }
+    gd0 += gt * dt0;
+    gd1 += gt * dt1;
+    *G0 += gd0;
+    *G1 += gd1;
+  }
+}
+
+/* dL/dd of every allocated block, in the order of or_export_blocks (n_blocks x 512). */
+void or_grad_export(void* h, double* out) {
+  ovol* V = (ovol*)h;
+  int n = 0;
+  for (int b = 0; b < V->nblocks; ++b) {
+    if (!V->blocks[b]->alive) continue;
+    memcpy(out + (size_t)n * BV, V->blocks[b]->gd, sizeof(double) * BV);
+    ++n;
+  }
+}
+
+/* Reverse-mode through the recorded integrations, last to first: dL/dD of every recorded
+ * frame into gdepth (frames x H x W, zeroed here).  Consumes dL/dd (afterwards it holds
+ * the gradient with respect to the values before the first recorded frame). */
+void or_grad_depth(void* h, int W, int H, double* gdepth) {
+  ovol* V = (ovol*)h;
+  memset(gdepth, 0, sizeof(double) * (size_t)V->diff_frames * (size_t)W * (size_t)H);
+  for (int64_t r = V->nrec - 1; r >= 0; --r) {
+    const orec* R = &V->recs[r];
+    double* g = &V->blocks[R->block]->gd[R->voxel];
+    const double gdt = *g / (R->wpre + 1);
+    if (R->lin) gdepth[(size_t)R->frame * (size_t)W * (size_t)H + (size_t)R->pixel] += gdt;
+    *g = *g * R->wpre / (R->wpre + 1);
+  }
+}
+
+/* Overwrite the TSDF value of one allocated voxel (finite-difference tests); 0 if absent. */
+int or_set_voxel(void* h, int gx, int gy, int gz, double d) {
+  ovol* V = (ovol*)h;
+  int bx = floordiv8(gx), by = floordiv8(gy), bz = floordiv8(gz);
+  int b = find_block(V, bx, by, bz);
+  if (b < 0) return 0;
+  V->blocks[b]->tsdf[(gx - 8 * bx) + 8 * (gy - 8 * by) + 64 * (gz - 8 * bz)] = (real)d;
+  return 1;
 }
