@@ -225,6 +225,48 @@ vm_status vm_enable_timing(vm_volume* vol, int enable);
 vm_status vm_kernel_times(vm_volume* vol, const char** names, double* total_ms, int64_t* launches, int cap,
                           int* n);
 
+/* ---------------------------------------------------------------- differentiable path
+ * Gradients of a loss on the mesh vertex positions and normals, taken to the TSDF values
+ * through the edge interpolation and normal of Sec. V-C (recomputed from the TSDF, not
+ * stored) and on to the depth pixels by reverse mode through the running average of
+ * Sec. V-A, Eq. 2 (d <- (d W + d~) / (W + 1), d~ = min(sdf, mu)).  Topology, block
+ * collection, pixel choice and branches are held fixed: d~ = mu (sdf >= mu) passes no
+ * gradient, a t clamped to [-1, 2] is constant.  Sequence: vm_diff_begin, the recorded
+ * vm_integrate_depth calls, a mesh update, vm_grad_vertices (any number of calls, they
+ * add), optionally vm_export_grad (dL/dd of the final TSDF), then vm_grad_depth for the
+ * recorded calls last to first, then vm_diff_end. */
+
+/* Checkpoints every voxel weight, clears dL/dd and records the next max_frames
+ * (1..65535) vm_integrate_depth calls (the blocks each collects and, per voxel, whether it
+ * integrated it).  Buffers: 10 B per voxel of the block pool plus 4 B per collected-list
+ * entry per recorded call, owned by the volume and kept for the next begin; VM_ERR_OOM
+ * when they cannot be allocated.  While recording, vm_gc and vm_step return
+ * VM_ERR_INVALID_ARG (recycling blocks would rename recorded voxels), as does an integrate
+ * call beyond max_frames or after the first vm_grad_depth. */
+vm_status vm_diff_begin(vm_volume* vol, int max_frames);
+
+/* Ends recording (the buffers stay allocated until vm_destroy_volume). */
+vm_status vm_diff_end(vm_volume* vol);
+
+/* Adds dL/dd given dL/dp and dL/dn of n vertices: edge_keys (n uint64, the vm_download_mesh
+ * key of each vertex), grad_pos and grad_nrm (n x 3 float32), all DEVICE pointers owned by
+ * the caller.  A vertex whose owner voxels are not allocated is skipped.  Enqueues only. */
+vm_status vm_grad_vertices(vm_volume* vol, int64_t n, const uint64_t* edge_keys, const float* grad_pos,
+                           const float* grad_nrm);
+
+/* Reverse step of recorded call `frame` (0-based; the last recorded call first, then each
+ * earlier one): writes dL/dD of that call's depth pixels into grad_depth (DEVICE, H x W
+ * float32, overwritten) and moves dL/dd to before the call.  depth, *K, T_wc and T_cw
+ * must be the recorded call's inputs (a voxel the call did not integrate sets the sticky
+ * status VM_ERR_INVALID_ARG).  A frame out of order is VM_ERR_INVALID_ARG. */
+vm_status vm_grad_depth(vm_volume* vol, int frame, const float* depth, const vm_intrinsics* K, const float T_wc[16],
+                        const float T_cw[16], float* grad_depth);
+
+/* Synchronises; copies dL/dd of every allocated block to host buffers sized from
+ * vm_num_blocks (any order): keys n x 3 int32, grad n x 512 float32 (voxel x + 8 y + 64 z).
+ * VM_ERR_INVALID_ARG before the first vm_diff_begin. */
+vm_status vm_export_grad(vm_volume* vol, int32_t* keys, float* grad);
+
 #ifdef __cplusplus
 }
 #endif

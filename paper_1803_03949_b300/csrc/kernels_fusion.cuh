@@ -247,6 +247,25 @@ __device__ __forceinline__ void resolve_block(const Vol& V, int blk, int4 key, u
 }
 
 // ------------------------------------------------------------------ fusion (Eq. 2)
+// Eq. 2's inputs for the voxel at world point (px, py, pz): false when the frame does not
+// integrate it (behind the camera, outside the image, invalid depth, sdf < -mu); else its
+// nearest pixel and sdf = D - z_c.  The fusion and its gradient share this definition.
+__device__ __forceinline__ bool project_voxel(const FrameParams& fp, float mu, float px, float py, float pz, int& pix,
+                                              float& sdf) {
+  const float xc = ((fp.Tcw[0] * px + fp.Tcw[1] * py) + fp.Tcw[2] * pz) + fp.Tcw[3];
+  const float yc = ((fp.Tcw[4] * px + fp.Tcw[5] * py) + fp.Tcw[6] * pz) + fp.Tcw[7];
+  const float zc = ((fp.Tcw[8] * px + fp.Tcw[9] * py) + fp.Tcw[10] * pz) + fp.Tcw[11];
+  if (!(zc > 0.0f)) return false;
+  const float us = ((fp.fx * xc) / zc + fp.cx) + 0.5f;
+  const float vs = ((fp.fy * yc) / zc + fp.cy) + 0.5f;
+  if (!(us >= 0.0f && us < (float)fp.W && vs >= 0.0f && vs < (float)fp.H)) return false;
+  pix = (int)floorf(vs) * fp.W + (int)floorf(us);
+  const float D = __ldg(fp.depth + pix);
+  if (!(D > 0.0f) || !isfinite(D)) return false;
+  sdf = D - zc;
+  return !(sdf < -mu);
+}
+
 constexpr int INTEG_THREADS = 128;  // 4 voxels per thread, one block per CTA iteration
 constexpr int INTEG_CTAS_PER_SM = 12;  // ~1.8k blocks (a 640 x 480 frame) in one wave
 
@@ -283,18 +302,9 @@ __global__ void __launch_bounds__(INTEG_THREADS, INTEG_CTAS_PER_SM) k_integrate(
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const float px = (float)(key.x * BS + lx + j) * l;
-      const float xc = ((fp.Tcw[0] * px + fp.Tcw[1] * py) + fp.Tcw[2] * pz) + fp.Tcw[3];
-      const float yc = ((fp.Tcw[4] * px + fp.Tcw[5] * py) + fp.Tcw[6] * pz) + fp.Tcw[7];
-      const float zc = ((fp.Tcw[8] * px + fp.Tcw[9] * py) + fp.Tcw[10] * pz) + fp.Tcw[11];
-      if (!(zc > 0.0f)) continue;
-      const float us = ((fp.fx * xc) / zc + fp.cx) + 0.5f;
-      const float vs = ((fp.fy * yc) / zc + fp.cy) + 0.5f;
-      if (!(us >= 0.0f && us < (float)fp.W && vs >= 0.0f && vs < (float)fp.H)) continue;
-      const int iu = (int)floorf(us), iv = (int)floorf(vs);
-      const float D = __ldg(fp.depth + (size_t)iv * fp.W + iu);
-      if (!(D > 0.0f) || !isfinite(D)) continue;
-      const float sdf = D - zc;
-      if (sdf < -mu) continue;
+      int pix;
+      float sdf;
+      if (!project_voxel(fp, mu, px, py, pz, pix, sdf)) continue;
       const float dt = sdf < mu ? sdf : mu;
       const float num = dd[j] * ww[j] + dt;
       const float den = ww[j] + 1.0f;

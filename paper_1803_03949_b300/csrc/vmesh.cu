@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "vmesh.h"
+#include "kernels_diff.cuh"
 #include "kernels_fusion.cuh"
 #include "kernels_gc.cuh"
 #include "kernels_io.cuh"
@@ -64,6 +65,13 @@ struct vm_volume {
   std::vector<cudaEvent_t> event_pool;
   double tot_ms[K_COUNT_] = {0};
   long long launches[K_COUNT_] = {0};
+  // differentiable path: recording state and its buffers (owned here, freed in free_all)
+  bool diff_on = false;     // integrate calls are being recorded
+  int diff_max = 0;         // recorded calls the buffers hold
+  int diff_frames = 0;      // recorded calls so far
+  int grad_next = -1;       // next recorded call vm_grad_depth takes (-1: gradients not started)
+  int diff_rec_cap = 0;     // ints in V.drec
+  std::vector<void*> diff_allocs;
   // graph replay of vm_step; the frame's parameters reach the graph as k_alloc's launch
   // arguments, replaced in alloc_node before every replay
   cudaGraph_t graph = nullptr;
@@ -289,6 +297,8 @@ void free_all(vm_volume* v) {
   for (auto e : v->event_pool) cudaEventDestroy(e);
   for (void* p : v->allocs) cudaFree(p);
   v->allocs.clear();
+  for (void* p : v->diff_allocs) cudaFree(p);
+  v->diff_allocs.clear();
   if (v->cap_stream) cudaStreamDestroy(v->cap_stream);
   v->cap_stream = nullptr;
 }
@@ -426,7 +436,13 @@ vm_status vm_integrate_depth(vm_volume* v, const float* depth, const vm_intrinsi
   if (!v) return VM_ERR_INVALID_ARG;
   FrameParams fp;
   if (!make_frame(K, Twc, Tcw, depth, &fp)) return VM_ERR_INVALID_ARG;
-  return enqueue_integrate(v, fp);
+  if (v->diff_on && (v->diff_frames >= v->diff_max || v->grad_next >= 0)) return VM_ERR_INVALID_ARG;
+  vm_status st = enqueue_integrate(v, fp);
+  if (st || !v->diff_on) return st;
+  (void)cudaGetLastError();
+  k_diff_record<<<grid_for(v, INTEG_CTAS_PER_SM), INTEG_THREADS, 0, v->stream>>>(v->V, v->diff_frames);
+  ++v->diff_frames;
+  return cuda_status(cudaGetLastError());
 }
 
 vm_status vm_update_mesh(vm_volume* v, int flags) {
@@ -443,13 +459,13 @@ vm_status vm_refine_mesh(vm_volume* v, int full) {
 }
 
 vm_status vm_gc(vm_volume* v) {
-  if (!v) return VM_ERR_INVALID_ARG;
+  if (!v || v->diff_on) return VM_ERR_INVALID_ARG;  // recycling would rename recorded voxels
   return enqueue_gc(v);
 }
 
 vm_status vm_step(vm_volume* v, const float* depth, const vm_intrinsics* K, const float Twc[16], const float Tcw[16],
                   int flags, int use_graph) {
-  if (!v || (flags & ~(VM_FULL | VM_REFINE | VM_GC))) return VM_ERR_INVALID_ARG;
+  if (!v || (flags & ~(VM_FULL | VM_REFINE | VM_GC)) || v->diff_on) return VM_ERR_INVALID_ARG;
   FrameParams fp;
   if (!make_frame(K, Twc, Tcw, depth, &fp)) return VM_ERR_INVALID_ARG;
   auto body = [&]() -> vm_status {
@@ -692,6 +708,111 @@ vm_status vm_export_blocks(vm_volume* v, int32_t* keys, float* tsdf, float* weig
   cudaFree(dw);
   cudaFree(dce);
   cudaFree(dcp);
+  cudaFree(cnt);
+  return ok ? VM_OK : VM_ERR_CUDA;
+}
+
+// ---- differentiable path
+vm_status vm_diff_begin(vm_volume* v, int max_frames) {
+  if (!v || max_frames < 1 || max_frames > 65535) return VM_ERR_INVALID_ARG;
+  const size_t nvox = (size_t)v->p.max_blocks * BV;
+  const size_t rec = (size_t)max_frames * (size_t)v->V.list_cap_touched;
+  if (!v->V.dgrad || (size_t)v->diff_rec_cap < rec) {
+    if (sync_status(v)) return VM_ERR_CUDA;
+    for (void* p : v->diff_allocs) cudaFree(p);
+    v->diff_allocs.clear();
+    v->V.dcnt = nullptr;
+    v->V.dwck = v->V.dgrad = nullptr;
+    v->V.drec = v->V.drec_off = nullptr;
+    v->diff_rec_cap = 0;
+    void *a = nullptr, *b = nullptr, *c = nullptr, *d = nullptr, *e = nullptr;
+    const bool ok = cudaMalloc(&a, nvox * sizeof(uint16_t)) == cudaSuccess &&
+                    cudaMalloc(&b, nvox * sizeof(float)) == cudaSuccess &&
+                    cudaMalloc(&c, nvox * sizeof(float)) == cudaSuccess &&
+                    cudaMalloc(&d, rec * sizeof(int)) == cudaSuccess &&
+                    cudaMalloc(&e, (size_t)(max_frames + 1) * sizeof(int)) == cudaSuccess;
+    for (void* p : {a, b, c, d, e})
+      if (p) v->diff_allocs.push_back(p);
+    if (!ok) {
+      (void)cudaGetLastError();
+      for (void* p : v->diff_allocs) cudaFree(p);
+      v->diff_allocs.clear();
+      return VM_ERR_OOM;
+    }
+    v->V.dcnt = static_cast<uint16_t*>(a);
+    v->V.dwck = static_cast<float*>(b);
+    v->V.dgrad = static_cast<float*>(c);
+    v->V.drec = static_cast<int*>(d);
+    v->V.drec_off = static_cast<int*>(e);
+    v->diff_rec_cap = (int)(rec < (size_t)INT32_MAX ? rec : (size_t)INT32_MAX);
+  }
+  drop_graph(v);  // frame graphs captured the volume view without the record buffers
+  (void)cudaGetLastError();
+  cudaMemsetAsync(v->V.dcnt, 0, nvox * sizeof(uint16_t), v->stream);
+  cudaMemsetAsync(v->V.dwck, 0, nvox * sizeof(float), v->stream);
+  cudaMemsetAsync(v->V.dgrad, 0, nvox * sizeof(float), v->stream);
+  cudaMemsetAsync(v->V.drec_off, 0, sizeof(int), v->stream);
+  k_diff_checkpoint<<<grid_for(v, 8), 256, 0, v->stream>>>(v->V);
+  v->diff_on = true;
+  v->diff_max = max_frames;
+  v->diff_frames = 0;
+  v->grad_next = -1;
+  return cuda_status(cudaGetLastError());
+}
+
+vm_status vm_diff_end(vm_volume* v) {
+  if (!v) return VM_ERR_INVALID_ARG;
+  v->diff_on = false;
+  v->grad_next = -1;
+  return VM_OK;
+}
+
+vm_status vm_grad_vertices(vm_volume* v, int64_t n, const uint64_t* edge_keys, const float* grad_pos,
+                           const float* grad_nrm) {
+  if (!v || !v->diff_on || n < 0 || n > INT32_MAX || (n > 0 && (!edge_keys || !grad_pos || !grad_nrm)))
+    return VM_ERR_INVALID_ARG;
+  if (n == 0) return VM_OK;
+  (void)cudaGetLastError();
+  k_grad_vertices<<<grid_for(v, 8), 256, 0, v->stream>>>(v->V, (int)n,
+                                                          reinterpret_cast<const unsigned long long*>(edge_keys),
+                                                          grad_pos, grad_nrm);
+  return cuda_status(cudaGetLastError());
+}
+
+vm_status vm_grad_depth(vm_volume* v, int frame, const float* depth, const vm_intrinsics* K, const float Twc[16],
+                        const float Tcw[16], float* grad_depth) {
+  if (!v || !v->diff_on || !grad_depth) return VM_ERR_INVALID_ARG;
+  const int expect = v->grad_next >= 0 ? v->grad_next : v->diff_frames - 1;
+  if (frame != expect || frame < 0) return VM_ERR_INVALID_ARG;
+  FrameParams fp;
+  if (!make_frame(K, Twc, Tcw, depth, &fp)) return VM_ERR_INVALID_ARG;
+  (void)cudaGetLastError();
+  if (cudaMemsetAsync(grad_depth, 0, (size_t)fp.W * fp.H * sizeof(float), v->stream) != cudaSuccess)
+    return VM_ERR_CUDA;
+  k_grad_depth<<<grid_for(v, INTEG_CTAS_PER_SM), INTEG_THREADS, 0, v->stream>>>(v->V, frame, fp, grad_depth);
+  v->grad_next = frame - 1;
+  return cuda_status(cudaGetLastError());
+}
+
+vm_status vm_export_grad(vm_volume* v, int32_t* keys, float* grad) {
+  if (!v || !v->V.dgrad || !keys || !grad) return VM_ERR_INVALID_ARG;
+  if (sync_status(v)) return VM_ERR_CUDA;
+  const int n = read_counter(v, C_LIVE_BLOCKS);
+  void *dk = nullptr, *dg = nullptr, *cnt = nullptr;
+  const size_t nn = n > 0 ? (size_t)n : 1;
+  bool ok = cudaMalloc(&dk, nn * 12) == cudaSuccess && cudaMalloc(&dg, nn * BV * 4) == cudaSuccess &&
+            cudaMalloc(&cnt, 4) == cudaSuccess;
+  if (ok) {
+    cudaMemsetAsync(cnt, 0, 4, v->stream);
+    k_export_grad<<<grid_for(v, 8), 256, 0, v->stream>>>(v->V, (int*)cnt, (int*)dk, (float*)dg);
+    ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(v->stream) == cudaSuccess;
+    if (ok && n > 0)
+      ok = cudaMemcpy(keys, dk, (size_t)n * 12, cudaMemcpyDeviceToHost) == cudaSuccess &&
+           cudaMemcpy(grad, dg, (size_t)n * BV * 4, cudaMemcpyDeviceToHost) == cudaSuccess;
+  }
+  (void)cudaGetLastError();
+  cudaFree(dk);
+  cudaFree(dg);
   cudaFree(cnt);
   return ok ? VM_OK : VM_ERR_CUDA;
 }

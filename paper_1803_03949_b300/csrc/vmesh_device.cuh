@@ -122,6 +122,15 @@ struct Vol {
   int* dead;          // zero-reference vertex ids
   int2* deadrun;      // released triangle runs (start, length)
 
+  // differentiable path (null unless allocated): per voxel the integrations since the
+  // checkpoint, the checkpoint weight and dL/dd; the blocks each recorded call collected
+  // (drec[drec_off[f] .. drec_off[f + 1]) for recorded call f)
+  uint16_t* dcnt;
+  float* dwck;
+  float* dgrad;
+  int* drec;
+  int* drec_off;
+
   Ctl* ctl;
 };
 

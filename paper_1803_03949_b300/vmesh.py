@@ -50,7 +50,8 @@ _lib = None
 EXPORTS = ["vm_create_volume", "vm_destroy_volume", "vm_set_stream", "vm_integrate_depth", "vm_update_mesh",
            "vm_refine_mesh", "vm_gc", "vm_step", "vm_mesh_counts", "vm_download_mesh", "vm_get_stats",
            "vm_last_error", "vm_num_blocks", "vm_export_blocks", "vm_set_blocks", "vm_enable_timing",
-           "vm_kernel_times", "vm_mesh_size_async", "vm_download_mesh_noalloc"]
+           "vm_kernel_times", "vm_mesh_size_async", "vm_download_mesh_noalloc", "vm_diff_begin", "vm_diff_end",
+           "vm_grad_vertices", "vm_grad_depth", "vm_export_grad"]
 
 
 def load_library(path: str = LIB_PATH):
@@ -84,6 +85,11 @@ def load_library(path: str = LIB_PATH):
         "vm_kernel_times": [vp, P(ctypes.c_char_p), P(ctypes.c_double), P(i64), i, P(i)],
         "vm_mesh_size_async": [vp, vp, i],
         "vm_download_mesh_noalloc": [vp, vp, vp, vp, vp, vp, i64, i64, P(i64), P(i64)],
+        "vm_diff_begin": [vp, i],
+        "vm_diff_end": [vp],
+        "vm_grad_vertices": [vp, i64, vp, vp, vp],
+        "vm_grad_depth": [vp, i, vp, P(vm_intrinsics), F16, F16, vp],
+        "vm_export_grad": [vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -101,6 +107,12 @@ def _check(code: int, where: str):
 def _f16(T) -> ctypes.Array:
     a = np.ascontiguousarray(np.asarray(T, np.float32).reshape(16))
     return (ctypes.c_float * 16)(*a.tolist())
+
+
+def _contig_cuda(*ts):
+    for t in ts:
+        if not (t.is_cuda and t.is_contiguous()):
+            raise ValueError("expected contiguous CUDA tensors")
 
 
 def _ptr(x) -> int:
@@ -251,6 +263,35 @@ class Volume:
         w = np.ascontiguousarray(weight, np.float32).reshape(-1, 512)
         _check(self._lib.vm_set_blocks(self._h, _ptr(k), k.shape[0], _ptr(t), _ptr(w)), "vm_set_blocks")
 
+    # --------------------------------------------------------------- differentiable path
+    def diff_begin(self, max_frames: int):
+        """Checkpoint the weights and record the next `max_frames` integrate calls."""
+        _check(self._lib.vm_diff_begin(self._h, int(max_frames)), "vm_diff_begin")
+
+    def diff_end(self):
+        _check(self._lib.vm_diff_end(self._h), "vm_diff_end")
+
+    def grad_vertices(self, keys, grad_pos, grad_nrm):
+        """Add dL/dd from dL/dpos, dL/dnrm: CUDA tensors keys (n,) int64 (edge keys),
+        grad_pos, grad_nrm (n, 3) float32."""
+        _contig_cuda(keys, grad_pos, grad_nrm)
+        _check(self._lib.vm_grad_vertices(self._h, int(keys.shape[0]), _ptr(keys), _ptr(grad_pos), _ptr(grad_nrm)),
+               "vm_grad_vertices")
+
+    def grad_depth(self, frame: int, depth, intr: Intrinsics, T_wc, T_cw, out):
+        """dL/dD of recorded call `frame` (last first) into `out` (CUDA float32, like depth)."""
+        _contig_cuda(depth, out)
+        _check(self._lib.vm_grad_depth(self._h, int(frame), _ptr(depth), ctypes.byref(intr.c()), _f16(T_wc),
+                                       _f16(T_cw), _ptr(out)), "vm_grad_depth")
+
+    def export_grad(self) -> dict:
+        """dL/dd of every allocated block: keys (n,3) i32, grad (n,512) f32."""
+        n = self.num_blocks()
+        keys = np.empty((n, 3), np.int32)
+        grad = np.empty((n, 512), np.float32)
+        _check(self._lib.vm_export_grad(self._h, _ptr(keys), _ptr(grad)), "vm_export_grad")
+        return dict(keys=keys, grad=grad)
+
     # --------------------------------------------------------------- timing
     KERNELS = ["k_alloc", "k_integrate", "k_list_all", "k_mesh", "k_gc_vertices", "k_gc_blocks"]
 
@@ -272,3 +313,54 @@ class Volume:
         n = ctypes.c_int()
         _check(self._lib.vm_kernel_times(self._h, names, ms, cnt, cap, ctypes.byref(n)), "vm_kernel_times")
         return {names[i].decode(): (ms[i], cnt[i]) for i in range(n.value)}
+
+
+def _diff_mesh_function():
+    import torch
+
+    class DiffMesh(torch.autograd.Function):
+        """Differentiable fusion and meshing: integrates the leaf depth frames (recording
+        them), extracts the full mesh (refined when `refine`), and returns vertex positions
+        and normals (differentiable), triangles and edge keys.  The backward runs the
+        library's gradient kernels: vertices -> TSDF values -> depth pixels, topology fixed."""
+
+        @staticmethod
+        def forward(ctx, vol, intr, poses, refine, *depths):
+            vol.diff_begin(len(depths))
+            for d, (T_wc, T_cw) in zip(depths, poses):
+                vol.integrate(d, intr, T_wc, T_cw)
+            vol.update_mesh(full=True, refine=refine)
+            m = vol.download(device=True)
+            ctx.vol, ctx.intr, ctx.poses = vol, intr, poses
+            ctx.save_for_backward(m["keys"], *depths)
+            ctx.mark_non_differentiable(m["tris"], m["keys"])
+            return m["pos"], m["nrm"], m["tris"], m["keys"]
+
+        @staticmethod
+        def backward(ctx, g_pos, g_nrm, _g_tris, _g_keys):
+            keys, *depths = ctx.saved_tensors
+            vol = ctx.vol
+            n = keys.shape[0]
+            g_pos = torch.zeros((n, 3), dtype=torch.float32, device=keys.device) if g_pos is None else g_pos.contiguous()
+            g_nrm = torch.zeros((n, 3), dtype=torch.float32, device=keys.device) if g_nrm is None else g_nrm.contiguous()
+            vol.grad_vertices(keys, g_pos, g_nrm)
+            grads = [None] * len(depths)
+            for k in reversed(range(len(depths))):
+                grads[k] = torch.empty_like(depths[k])
+                vol.grad_depth(k, depths[k], ctx.intr, *ctx.poses[k], grads[k])
+            vol.diff_end()
+            return (None, None, None, None, *grads)
+
+    return DiffMesh
+
+
+_DIFF = None
+
+
+def diff_mesh(vol: Volume, intr: Intrinsics, poses, depths, refine: bool = True):
+    """(pos, nrm, tris, keys) of the mesh after integrating `depths` (CUDA float32 (H, W)
+    tensors; gradients flow to those that require them) at `poses` ((T_wc, T_cw) pairs)."""
+    global _DIFF
+    if _DIFF is None:
+        _DIFF = _diff_mesh_function()
+    return _DIFF.apply(vol, intr, list(poses), bool(refine), *[d.contiguous() for d in depths])
