@@ -267,6 +267,46 @@ vm_status vm_grad_depth(vm_volume* vol, int frame, const float* depth, const vm_
  * VM_ERR_INVALID_ARG before the first vm_diff_begin. */
 vm_status vm_export_grad(vm_volume* vol, int32_t* keys, float* grad);
 
+/* ---------------------------------------------------------------- batched step
+ * Many independent volumes (scenes of uneven sizes, each created with its own parameters),
+ * stepped one frame each per tick by five launches in total: every per-frame kernel runs
+ * once over the concatenation of all scenes' work (tiles, collected blocks, update sets,
+ * gc lists), optionally replayed from one CUDA graph per tick.  Results per scene are those
+ * of vm_step on that scene alone.  Kernel schedules (pixels per thread of the block
+ * collection; CTAs per SM of the persistent fusion, mesh and gc grids) come from an
+ * autotuner that times the candidate options on live ticks. */
+typedef struct vm_batch vm_batch;
+
+/* A batch of n (1..64) distinct volumes on the current device.  It enqueues on the first
+ * volume's stream; while it steps them, work on the volumes' own streams must be ordered
+ * with that stream by the caller.  The volumes stay owned by the caller and must outlive
+ * the batch.  VM_ERR_OOM when its small buffers cannot be allocated. */
+vm_status vm_batch_create(vm_volume* const* vols, int n, vm_batch** out);
+vm_status vm_batch_destroy(vm_batch* batch);
+
+/* One tick: for scene i, depth depths[i] (DEVICE, K[i].height x K[i].width float32),
+ * intrinsics K[i], poses T_wc + 16 i, T_cw + 16 i (host, row-major), as vm_step with
+ * `flags` (VM_REFINE, VM_GC; VM_FULL is not available).  use_graph != 0 replays the
+ * tick's five launches from a CUDA graph (captured on first use, re-captured when the
+ * flags, the largest image or the schedule change).  Any invalid frame, or a volume that
+ * is recording for the differentiable path, gives VM_ERR_INVALID_ARG before anything is
+ * enqueued.  Enqueues only. */
+vm_status vm_batch_step(vm_batch* batch, const float* const* depths, const vm_intrinsics* K, const float* T_wc,
+                        const float* T_cw, int flags, int use_graph);
+
+/* Autotune on the next 3 * rounds ticks (1..100 rounds): each tick runs every kernel on one
+ * of its three candidate options (eagerly, with CUDA events around each kernel); after the
+ * last, each kernel keeps its fastest option (the tuning ticks are real steps). */
+vm_status vm_batch_tune(vm_batch* batch, int rounds);
+
+/* The schedule in use, 5 ints: k_alloc pixels per thread (1, 2, 4), CTAs per SM of the
+ * fusion (4, 8, 12), mesh (3, 5, 7), vertex-gc (1, 2, 4) and block-gc (2, 4, 8) kernels;
+ * tuned_ms (optional, 15 doubles) receives the mean time of each option from the last
+ * tuning (-1 where untimed).  vm_batch_set_schedule installs a schedule from those options
+ * (VM_ERR_INVALID_ARG otherwise). */
+vm_status vm_batch_schedule(vm_batch* batch, int* sched, double* tuned_ms);
+vm_status vm_batch_set_schedule(vm_batch* batch, const int* sched);
+
 #ifdef __cplusplus
 }
 #endif

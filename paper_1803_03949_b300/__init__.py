@@ -7,4 +7,4 @@ distance (Sec. V-F) and recycle dead vertices, triangles and blocks (Sec. V-E).
 
 The C ABI is ``include/vmesh.h``; :mod:`paper_1803_03949_b300.vmesh` is its binding.
 """
-from .vmesh import Intrinsics, Volume, VmeshError, diff_mesh, load_library  # noqa: F401
+from .vmesh import Intrinsics, Scenes, Volume, VmeshError, diff_mesh, load_library  # noqa: F401

@@ -1,0 +1,190 @@
+// Batched step: one frame of each of up to MAX_SCENES independent volumes per launch of
+// each per-frame kernel.  Every kernel is the single-volume kernel's per-item body (one
+// tile, one collected block, one update-set block, one pool slot...) run over the
+// concatenation of all scenes' work, so a tick costs five launches whatever the number of
+// scenes, and the GPU is filled by the sum of the scenes' work rather than by one scene.
+// Work is handed out so that a CTA (tiles, blocks) or a warp (gc items) never mixes scenes:
+// the warp-aggregated appends and counters assume one volume per group of lanes.
+#pragma once
+
+#include "kernels_fusion.cuh"
+#include "kernels_gc.cuh"
+#include "kernels_mesh.cuh"
+
+namespace vmk {
+
+constexpr int MAX_SCENES = 64;
+
+// Launch argument of the batched block collection (replaced before every graph replay).
+struct BatchFrames {
+  FrameParams fp[MAX_SCENES];
+  int advance[MAX_SCENES];  // start a new mesh epoch for this scene (as k_alloc's argument)
+};
+
+// Batch control: last-CTA tickets of the five batched kernels.
+enum BatchDone { BD_ALLOC = 0, BD_INTEGRATE, BD_MESH, BD_GC_VERTICES, BD_GC_BLOCKS, BD_COUNT };
+
+// pre[s] = sum of count(t) over scenes t < s, pre[n] = total (shared memory, whole CTA).
+template <typename F>
+__device__ __forceinline__ void scene_prefix(int n, int* pre, F count) {
+  __shared__ int cnt[MAX_SCENES];
+  if (threadIdx.x < n) cnt[threadIdx.x] = count(threadIdx.x);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int t = 0; t < n; ++t) {
+      pre[t] = acc;
+      acc += cnt[t];
+    }
+    pre[n] = acc;
+  }
+  __syncthreads();
+}
+
+// The scene whose range [pre[s], pre[s + 1]) holds global item g (pre ascending, g < pre[n]).
+__device__ __forceinline__ int scene_of(const int* pre, int n, int g) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Block collection: grid (tiles across, tiles down, scenes); a CTA whose tile lies outside
+// its scene's image only takes its ticket.  The last CTA finishes every scene.
+template <int PPT>
+__global__ void __launch_bounds__(ALLOC_TILE_W * ALLOC_TILE_H / PPT)
+    kb_alloc(const Vol* __restrict__ vols, int nscenes, const __grid_constant__ BatchFrames bf, int* bdone) {
+  __shared__ unsigned long long set[ALLOC_SET];
+  const int s = blockIdx.z;
+  const Vol& V = vols[s];
+  const FrameParams& fp = bf.fp[s];
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) V.ctl->fp = fp;  // for the later kernels
+  if ((int)blockIdx.x * ALLOC_TILE_W < fp.W && (int)blockIdx.y * ALLOC_TILE_H < fp.H)
+    alloc_tile<PPT>(V, fp, blockIdx.x, blockIdx.y, set);
+  allow_dependent_launch();
+  if (last_block_at(bdone + BD_ALLOC)) {
+    for (int t = threadIdx.x; t < nscenes; t += blockDim.x) alloc_finish(vols[t], bf.advance[t]);
+    if (threadIdx.x == 0) bdone[BD_ALLOC] = 0;
+  }
+}
+
+// Fusion: every scene's collected blocks, one per CTA iteration.
+__global__ void __launch_bounds__(INTEG_THREADS) kb_integrate(const Vol* __restrict__ vols, int nscenes, int* bdone) {
+  grid_dependency_wait();
+  __shared__ int pre[MAX_SCENES + 1];
+  __shared__ uint32_t sframe[MAX_SCENES], sepoch[MAX_SCENES];
+  if (threadIdx.x < nscenes) {
+    sframe[threadIdx.x] = (uint32_t)__ldcg(&vols[threadIdx.x].ctl->c[C_FRAME]);
+    sepoch[threadIdx.x] = (uint32_t)__ldcg(&vols[threadIdx.x].ctl->c[C_EPOCH]);
+  }
+  scene_prefix(nscenes, pre, [&](int t) { return min(__ldcg(&vols[t].ctl->c[C_N_TOUCHED]), vols[t].list_cap_touched); });
+  const int total = pre[nscenes];
+  for (int g = blockIdx.x; g < total; g += gridDim.x) {
+    const int s = scene_of(pre, nscenes, g);
+    const Vol& V = vols[s];
+    integrate_block<true>(V, V.ctl->fp, __ldcg(&V.touched[g - pre[s]]), sframe[s], sepoch[s]);
+  }
+  allow_dependent_launch();
+  if (last_block_at(bdone + BD_INTEGRATE)) {
+    for (int t = threadIdx.x; t < nscenes; t += blockDim.x) integrate_finish(vols[t], pre[t + 1] - pre[t]);
+    if (threadIdx.x == 0) bdone[BD_INTEGRATE] = 0;
+  }
+}
+
+// Mesh pass: every scene's update set, one block per CTA iteration.
+__global__ void __launch_bounds__(MESH_THREADS, 7) kb_mesh(const Vol* __restrict__ vols, int nscenes, int mode,
+                                                           int* bdone) {
+  __shared__ MeshSmem S;
+  __shared__ int pre[MAX_SCENES + 1];
+  for (int i = threadIdx.x; i < 128; i += MESH_THREADS) reinterpret_cast<uint4*>(S.tri64)[i] = vols[0].tri_table[i];
+  grid_dependency_wait();
+  scene_prefix(nscenes, pre, [&](int t) { return min(__ldcg(&vols[t].ctl->c[C_N_UPDATE]), vols[t].list_cap_update); });
+  const int total = pre[nscenes];
+  MeshCounts cnt;
+  int cur = -1;
+  for (int g = blockIdx.x; g < total; g += gridDim.x) {
+    const int s = scene_of(pre, nscenes, g);
+    if (s != cur) {
+      if (cur >= 0) mesh_flush(vols[cur], cnt);
+      cur = s;
+    }
+    const Vol& V = vols[s];
+    mesh_block(V, S, V.update[g - pre[s]], mode, cnt);
+  }
+  if (cur >= 0) mesh_flush(vols[cur], cnt);
+  allow_dependent_launch();
+  if (last_block_at(bdone + BD_MESH)) {
+    for (int t = threadIdx.x; t < nscenes; t += blockDim.x) mesh_finish(vols[t], pre[t + 1] - pre[t]);
+    if (threadIdx.x == 0) bdone[BD_MESH] = 0;
+  }
+}
+
+// Zero-reference vertices and released runs of every scene, in chunks of 32 list entries
+// (one warp per chunk, so the lanes of a warp share a scene).
+__global__ void __launch_bounds__(256) kb_gc_vertices(const Vol* __restrict__ vols, int nscenes, int* bdone) {
+  grid_dependency_wait();
+  __shared__ int pre_d[MAX_SCENES + 1], pre_r[MAX_SCENES + 1];
+  scene_prefix(nscenes, pre_d, [&](int t) { return (min(__ldcg(&vols[t].ctl->c[C_N_DEAD]), vols[t].list_cap_dead) + 31) >> 5; });
+  scene_prefix(nscenes, pre_r,
+               [&](int t) { return (min(__ldcg(&vols[t].ctl->c[C_N_DEADRUN]), vols[t].list_cap_deadrun) + 31) >> 5; });
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int u = warp; u < pre_d[nscenes]; u += nwarps) {
+    const int s = scene_of(pre_d, nscenes, u);
+    const Vol& V = vols[s];
+    const int n = min(__ldcg(&V.ctl->c[C_N_DEAD]), V.list_cap_dead);
+    const int i = ((u - pre_d[s]) << 5) + lane;
+    int freed = 0;
+    if (i < n) freed = gc_vertex(V, V.dead[i]);
+    gc_flush_vertices(V, freed);
+  }
+  for (int u = warp; u < pre_r[nscenes]; u += nwarps) {
+    const int s = scene_of(pre_r, nscenes, u);
+    const Vol& V = vols[s];
+    const int n = min(__ldcg(&V.ctl->c[C_N_DEADRUN]), V.list_cap_deadrun);
+    const int i = ((u - pre_r[s]) << 5) + lane;
+    if (i < n) {
+      const int2 r = V.deadrun[i];
+      if (r.y >= 1 && r.y <= 5) run_push(V, r.y, r.x);
+    }
+  }
+  allow_dependent_launch();
+  if (last_block_at(bdone + BD_GC_VERTICES)) {
+    for (int t = threadIdx.x; t < nscenes; t += blockDim.x) gc_vertices_finish(vols[t]);
+    if (threadIdx.x == 0) bdone[BD_GC_VERTICES] = 0;
+  }
+}
+
+// Block recycling of every scene, one warp per pool slot in use.  The last CTA finishes the
+// scenes one after another (a hash rebuild takes the whole CTA).
+__global__ void __launch_bounds__(256) kb_gc_blocks(const Vol* __restrict__ vols, int nscenes, int consumed,
+                                                    int* bdone) {
+  grid_dependency_wait();
+  __shared__ int pre[MAX_SCENES + 1];
+  __shared__ uint32_t sepoch[MAX_SCENES];
+  if (threadIdx.x < nscenes) sepoch[threadIdx.x] = (uint32_t)__ldcg(&vols[threadIdx.x].ctl->c[C_EPOCH]);
+  scene_prefix(nscenes, pre, [&](int t) { return min(__ldcg(&vols[t].ctl->c[C_BLK_BUMP]), vols[t].max_blocks); });
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  int freed = 0, cur = -1;
+  for (int g = warp; g < pre[nscenes]; g += nwarps) {
+    const int s = scene_of(pre, nscenes, g);
+    if (s != cur) {
+      if (cur >= 0) gc_flush_blocks(vols[cur], freed);
+      cur = s;
+    }
+    const Vol& V = vols[s];
+    freed += gc_block(V, g - pre[s], sepoch[s], consumed);
+  }
+  if (cur >= 0) gc_flush_blocks(vols[cur], freed);
+  if (last_block_at(bdone + BD_GC_BLOCKS)) {
+    for (int t = 0; t < nscenes; ++t) gc_blocks_finish(vols[t], consumed);
+    if (threadIdx.x == 0) bdone[BD_GC_BLOCKS] = 0;
+  }
+}
+
+}  // namespace vmk

@@ -11,8 +11,9 @@ namespace vmk {
 
 // ------------------------------------------------------------------ block collection
 constexpr int ALLOC_TILE_W = 64;     // pixels per tile row
-constexpr int ALLOC_TILE_H = 16;     // tile rows; each thread takes two vertically adjacent pixels
-constexpr int ALLOC_THREADS = ALLOC_TILE_W * ALLOC_TILE_H / 2;
+constexpr int ALLOC_TILE_H = 16;     // tile rows
+constexpr int ALLOC_PPT = 2;         // vertically adjacent pixels per thread (k_alloc)
+constexpr int ALLOC_THREADS = ALLOC_TILE_W * ALLOC_TILE_H / ALLOC_PPT;
 constexpr int ALLOC_SET_LOG2 = 10;
 constexpr int ALLOC_SET = 1 << ALLOC_SET_LOG2;  // CTA-local set of block keys
 constexpr int DDA_MAX_CELLS = 1 << 16;
@@ -166,28 +167,25 @@ __device__ __forceinline__ void collect_pixel(const Vol& V, const FrameParams& f
   }
 }
 
-// One CTA per 64 x 16 pixel tile, two vertically adjacent pixels per thread (so a 640 x 480
-// frame fits in one wave of CTAs): walk each pixel's segment into a CTA-local key set, then
-// insert the set's unique keys into the global hash and record them as collected.  The
-// frame's parameters arrive as a launch argument; the first CTA
-// stores them in the control block for the kernels that follow.  The last CTA clamps the
-// block free-stack top and, when `advance_epoch`, starts a new mesh epoch with an empty
-// update set.
-__global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(Vol V, const __grid_constant__ FrameParams fp,
-                                                         int advance_epoch) {
-  __shared__ unsigned long long set[ALLOC_SET];
+// One 64 x 16 pixel tile (tile column tx, row ty) walked by the calling CTA of
+// 1024 / PPT threads, PPT vertically adjacent pixels per thread: each pixel's segment goes
+// into the CTA-local key set `set`, then the set's unique keys are inserted into the global
+// hash and recorded as collected.
+template <int PPT>
+__device__ __forceinline__ void alloc_tile(const Vol& V, const FrameParams& fp, int tx, int ty,
+                                           unsigned long long* set) {
   const uint32_t frame = (uint32_t)__ldcg(&V.ctl->c[C_FRAME]);
-  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) V.ctl->fp = fp;  // for the later kernels
   for (int i = threadIdx.x; i < ALLOC_SET; i += blockDim.x) set[i] = KEY_EMPTY;
-  const int u = blockIdx.x * ALLOC_TILE_W + (threadIdx.x & (ALLOC_TILE_W - 1));
-  const int v = blockIdx.y * ALLOC_TILE_H + 2 * (threadIdx.x / ALLOC_TILE_W);
-  const bool in0 = u < fp.W && v < fp.H, in1 = u < fp.W && v + 1 < fp.H;
-  const float D0 = in0 ? __ldg(fp.depth + (size_t)v * fp.W + u) : 0.0f;
-  const float D1 = in1 ? __ldg(fp.depth + (size_t)(v + 1) * fp.W + u) : 0.0f;
+  const int u = tx * ALLOC_TILE_W + (threadIdx.x & (ALLOC_TILE_W - 1));
+  const int v = ty * ALLOC_TILE_H + PPT * (threadIdx.x / ALLOC_TILE_W);
+  float D[PPT];
+#pragma unroll
+  for (int r = 0; r < PPT; ++r) D[r] = (u < fp.W && v + r < fp.H) ? __ldg(fp.depth + (size_t)(v + r) * fp.W + u) : 0.0f;
   __syncthreads();
   uint64_t last = KEY_EMPTY;
-  if (in0) collect_pixel(V, fp, u, v, D0, set, frame, last);
-  if (in1) collect_pixel(V, fp, u, v + 1, D1, set, frame, last);
+#pragma unroll
+  for (int r = 0; r < PPT; ++r)
+    if (u < fp.W && v + r < fp.H) collect_pixel(V, fp, u, v + r, D[r], set, frame, last);
   __syncthreads();
   for (int i = threadIdx.x; i < ALLOC_SET; i += blockDim.x) {
     uint64_t key = set[i];
@@ -199,14 +197,30 @@ __global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(Vol V, const __grid_con
     int s = hash_insert(V, key, bx, by, bz, frame, blk);
     if (s >= 0) touch_bucket(V, s, key, blk, frame);
   }
+}
+
+// After the last tile of a frame (one thread): clamp the block free-stack top and, when
+// `advance_epoch`, start a new mesh epoch with an empty update set.
+__device__ __forceinline__ void alloc_finish(const Vol& V, int advance_epoch) {
+  fold_top(V, C_BLK_TOP);
+  if (advance_epoch) {
+    V.ctl->c[C_EPOCH] += 1;
+    V.ctl->c[C_N_UPDATE] = 0;
+  }
+}
+
+// One CTA per 64 x 16 pixel tile, two vertically adjacent pixels per thread (so a 640 x 480
+// frame fits in one wave of CTAs).  The frame's parameters arrive as a launch argument; the
+// first CTA stores them in the control block for the kernels that follow.
+__global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(Vol V, const __grid_constant__ FrameParams fp,
+                                                         int advance_epoch) {
+  __shared__ unsigned long long set[ALLOC_SET];
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) V.ctl->fp = fp;  // for the later kernels
+  alloc_tile<ALLOC_PPT>(V, fp, blockIdx.x, blockIdx.y, set);
   allow_dependent_launch();
   if (last_block(V, C_DONE0)) {
     if (threadIdx.x == 0) {
-      fold_top(V, C_BLK_TOP);
-      if (advance_epoch) {
-        V.ctl->c[C_EPOCH] += 1;
-        V.ctl->c[C_N_UPDATE] = 0;
-      }
+      alloc_finish(V, advance_epoch);
       V.ctl->c[C_DONE0] = 0;
     }
   }
@@ -269,66 +283,76 @@ __device__ __forceinline__ bool project_voxel(const FrameParams& fp, float mu, f
 constexpr int INTEG_THREADS = 128;  // 4 voxels per thread, one block per CTA iteration
 constexpr int INTEG_CTAS_PER_SM = 12;  // ~1.8k blocks (a 640 x 480 frame) in one wave
 
-// Per collected bucket: resolve it (update set, neighbour table), then (FUSE) fuse the frame
-// into every voxel of its block.  Voxels stream as float2 (d, W) pairs, 32 bytes per
-// thread; depth is gathered through the read-only path.  Also records whether any voxel
-// of the block has W > 0 and d < mu (used by gc).  The last CTA empties the collected list
-// and advances the integrate-call counter.
+// One collected block (entry `t` of the collected list), the calling CTA of INTEG_THREADS:
+// resolve it (update set, neighbour table), then (FUSE) fuse the frame into its 512 voxels.
+// Voxels stream as float2 (d, W) pairs, 32 bytes per thread; depth is gathered through the
+// read-only path.  Also records whether any voxel of the block has W > 0 and d < mu (used
+// by gc).
+template <bool FUSE>
+__device__ __forceinline__ void integrate_block(const Vol& V, const FrameParams& fp, int4 t, uint32_t frame,
+                                                uint32_t epoch) {
+  const float mu = V.mu, l = V.l, wmax = V.wmax;
+  const int v0 = threadIdx.x * 4;
+  const int lx = v0 & 7, ly = (v0 >> 3) & 7, lz = v0 >> 6;
+  const int blk = t.z >= 0 ? t.z : __ldcg(&V.vals[t.w]);
+  if (blk < 0) return;  // uniform over the CTA
+  const uint64_t kk = ((uint64_t)(uint32_t)t.y << 32) | (uint32_t)t.x;
+  const int4 key = make_int4((int)((kk >> 42) & 0x1FFFFF) - KEY_BIAS, (int)((kk >> 21) & 0x1FFFFF) - KEY_BIAS,
+                             (int)(kk & 0x1FFFFF) - KEY_BIAS, t.w);
+  resolve_block(V, blk, key, frame, epoch);
+  if (!FUSE) return;
+  float4* p = reinterpret_cast<float4*>(V.tw + (size_t)blk * BV + v0);
+  float4 q0 = __ldcg(p), q1 = __ldcg(p + 1);
+  float dd[4] = {q0.x, q0.z, q1.x, q1.z};
+  float ww[4] = {q0.y, q0.w, q1.y, q1.w};
+  bool changed = false;
+  const float py = (float)(key.y * BS + ly) * l, pz = (float)(key.z * BS + lz) * l;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float px = (float)(key.x * BS + lx + j) * l;
+    int pix;
+    float sdf;
+    if (!project_voxel(fp, mu, px, py, pz, pix, sdf)) continue;
+    const float dt = sdf < mu ? sdf : mu;
+    const float num = dd[j] * ww[j] + dt;
+    const float den = ww[j] + 1.0f;
+    dd[j] = num / den;
+    ww[j] = den < wmax ? den : wmax;
+    changed = true;
+  }
+  if (changed) {
+    p[0] = make_float4(dd[0], ww[0], dd[1], ww[1]);
+    p[1] = make_float4(dd[2], ww[2], dd[3], ww[3]);
+  }
+  bool near = false;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) near |= (ww[j] > 0.0f && dd[j] < mu);
+  const int any = __syncthreads_or(near);
+  if (threadIdx.x == 0) V.bnear[blk] = (uint8_t)(any != 0);
+}
+
+// After the last collected block of an integrate call (one thread): statistics, an empty
+// collected list, the next integrate call's number.
+__device__ __forceinline__ void integrate_finish(const Vol& V, int n) {
+  V.ctl->c[C_ST_FRAME_BLOCKS] = n;
+  reinterpret_cast<unsigned*>(V.ctl->c)[C_ST_COLLECTED] += (unsigned)n;  // wraps modulo 2^32
+  V.ctl->c[C_N_TOUCHED] = 0;
+  V.ctl->c[C_FRAME] += 1;
+}
+
+// Every collected block, one per CTA iteration (FUSE = false: resolve only, for analytic
+// fills).  The last CTA empties the collected list and advances the integrate-call counter.
 template <bool FUSE>
 __global__ void __launch_bounds__(INTEG_THREADS, INTEG_CTAS_PER_SM) k_integrate(Vol V, const FrameParams* __restrict__ fpp) {
   grid_dependency_wait();
   const int n = min(__ldcg(&V.ctl->c[C_N_TOUCHED]), V.list_cap_touched);
   const uint32_t frame = (uint32_t)__ldcg(&V.ctl->c[C_FRAME]);
   const uint32_t epoch = (uint32_t)__ldcg(&V.ctl->c[C_EPOCH]);
-  const float mu = V.mu, l = V.l, wmax = V.wmax;
-  const int v0 = threadIdx.x * 4;
-  const int lx = v0 & 7, ly = (v0 >> 3) & 7, lz = v0 >> 6;
-  for (int i = blockIdx.x; i < n; i += gridDim.x) {
-    const int4 t = __ldcg(&V.touched[i]);
-    const int blk = t.z >= 0 ? t.z : __ldcg(&V.vals[t.w]);
-    if (blk < 0) continue;
-    const uint64_t kk = ((uint64_t)(uint32_t)t.y << 32) | (uint32_t)t.x;
-    const int4 key = make_int4((int)((kk >> 42) & 0x1FFFFF) - KEY_BIAS, (int)((kk >> 21) & 0x1FFFFF) - KEY_BIAS,
-                               (int)(kk & 0x1FFFFF) - KEY_BIAS, t.w);
-    resolve_block(V, blk, key, frame, epoch);
-    if (!FUSE) continue;
-    const FrameParams& fp = *fpp;
-    float4* p = reinterpret_cast<float4*>(V.tw + (size_t)blk * BV + v0);
-    float4 q0 = __ldcg(p), q1 = __ldcg(p + 1);
-    float dd[4] = {q0.x, q0.z, q1.x, q1.z};
-    float ww[4] = {q0.y, q0.w, q1.y, q1.w};
-    bool changed = false;
-    const float py = (float)(key.y * BS + ly) * l, pz = (float)(key.z * BS + lz) * l;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float px = (float)(key.x * BS + lx + j) * l;
-      int pix;
-      float sdf;
-      if (!project_voxel(fp, mu, px, py, pz, pix, sdf)) continue;
-      const float dt = sdf < mu ? sdf : mu;
-      const float num = dd[j] * ww[j] + dt;
-      const float den = ww[j] + 1.0f;
-      dd[j] = num / den;
-      ww[j] = den < wmax ? den : wmax;
-      changed = true;
-    }
-    if (changed) {
-      p[0] = make_float4(dd[0], ww[0], dd[1], ww[1]);
-      p[1] = make_float4(dd[2], ww[2], dd[3], ww[3]);
-    }
-    bool near = false;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) near |= (ww[j] > 0.0f && dd[j] < mu);
-    const int any = __syncthreads_or(near);
-    if (threadIdx.x == 0) V.bnear[blk] = (uint8_t)(any != 0);
-  }
+  for (int i = blockIdx.x; i < n; i += gridDim.x) integrate_block<FUSE>(V, *fpp, __ldcg(&V.touched[i]), frame, epoch);
   allow_dependent_launch();
   if (last_block(V, C_DONE2)) {
     if (threadIdx.x == 0) {
-      V.ctl->c[C_ST_FRAME_BLOCKS] = n;
-      reinterpret_cast<unsigned*>(V.ctl->c)[C_ST_COLLECTED] += (unsigned)n;  // wraps modulo 2^32
-      V.ctl->c[C_N_TOUCHED] = 0;
-      V.ctl->c[C_FRAME] += 1;
+      integrate_finish(V, n);
       V.ctl->c[C_DONE2] = 0;
     }
   }

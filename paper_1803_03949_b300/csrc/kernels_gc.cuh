@@ -19,41 +19,55 @@ __device__ __forceinline__ void run_push(const Vol& V, int L, int base) {
   else set_status(V, ST_POOL_FULL);
 }
 
-// Zero-reference vertices: claim with CAS(0 -> -1), so a vertex listed twice, or one that
-// regained a reference after it was listed, is freed at most once and only when
-// unreferenced; a vertex still attached to its edge is detached.  Released triangle runs
-// go back to their free stacks.
+// Zero-reference vertex `vid` (listed by a mesh pass): claim with CAS(0 -> -1), so a vertex
+// listed twice, or one that regained a reference after it was listed, is freed at most once
+// and only when unreferenced; a vertex still attached to its edge is detached.  Returns
+// whether a detached vertex was freed.
+__device__ __forceinline__ bool gc_vertex(const Vol& V, int vid) {
+  if (atomicCAS(&V.vref[vid], 0, -1) != 0) return false;
+  const int e = V.vedge[vid];
+  bool detached = false;
+  if (e >= 0) {
+    const int ob = e / EPB, r = e - ob * EPB, ov = r / 3, a = r - ov * 3;
+    V.edge_vtx[e] = -1;
+    atomic_and_u8(V.vmask + (size_t)ob * BV + ov, (uint8_t)~(1 << a));
+    atomicSub(&V.bnvert[ob], 1);
+    detached = true;
+  }
+  pool_push(V, V.vtx_free, C_VTX_TOP, V.max_vertices, vid);
+  return detached;
+}
+
+__device__ __forceinline__ void gc_flush_vertices(const Vol& V, int& freed) {
+  if (freed) {
+    counter_add(V, C_LIVE_VERTS, -freed);
+    counter_add(V, C_ST_FREED_VERTS, freed);
+  }
+  freed = 0;
+}
+
+// After the last CTA (one thread): empty the two lists.
+__device__ __forceinline__ void gc_vertices_finish(const Vol& V) {
+  V.ctl->c[C_N_DEAD] = 0;
+  V.ctl->c[C_N_DEADRUN] = 0;
+}
+
+// Zero-reference vertices and released triangle runs back to their free stacks.
 __global__ void __launch_bounds__(256) k_gc_vertices(Vol V) {
   grid_dependency_wait();
   const int n = min(__ldcg(&V.ctl->c[C_N_DEAD]), V.list_cap_dead);
   const int nr = min(__ldcg(&V.ctl->c[C_N_DEADRUN]), V.list_cap_deadrun);
   int freed = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int vid = V.dead[i];
-    if (atomicCAS(&V.vref[vid], 0, -1) != 0) continue;
-    const int e = V.vedge[vid];
-    if (e >= 0) {
-      const int ob = e / EPB, r = e - ob * EPB, ov = r / 3, a = r - ov * 3;
-      V.edge_vtx[e] = -1;
-      atomic_and_u8(V.vmask + (size_t)ob * BV + ov, (uint8_t)~(1 << a));
-      atomicSub(&V.bnvert[ob], 1);
-      ++freed;
-    }
-    pool_push(V, V.vtx_free, C_VTX_TOP, V.max_vertices, vid);
-  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) freed += gc_vertex(V, V.dead[i]);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
     const int2 r = V.deadrun[i];
     if (r.y >= 1 && r.y <= 5) run_push(V, r.y, r.x);
   }
-  if (freed) {
-    counter_add(V, C_LIVE_VERTS, -freed);
-    counter_add(V, C_ST_FREED_VERTS, freed);
-  }
+  gc_flush_vertices(V, freed);
   allow_dependent_launch();
   if (last_block(V, C_DONE5)) {
     if (threadIdx.x == 0) {
-      V.ctl->c[C_N_DEAD] = 0;
-      V.ctl->c[C_N_DEADRUN] = 0;
+      gc_vertices_finish(V);
       V.ctl->c[C_DONE5] = 0;
     }
   }
@@ -89,78 +103,89 @@ __device__ void rehash_in_cta(const Vol& V) {
   __syncthreads();
 }
 
-// Block recycling, one warp per pool slot.  A block is freed when it was not collected in
-// the current epoch, has no triangles and owns no vertex, all of its voxels have W = 0 or
-// d >= mu, and none of its 7 lower neighbours (whose cubes reach into it) has triangles.
-// Its bucket becomes a tombstone, its voxels are cleared, its neighbours forget it, its
-// index returns to the pool.  `consumed` says the update set has been meshed since it was
-// collected: then it is emptied here; otherwise its blocks are kept so that the pending
-// update never lists a recycled (and possibly reallocated) block index.  The last CTA
-// rebuilds the hash when live plus dead buckets pass half the table.
+// Block slot `blk` (the calling warp): freed when it was not collected in the current
+// epoch, has no triangles and owns no vertex, all of its voxels have W = 0 or d >= mu, and
+// none of its 7 lower neighbours (whose cubes reach into it) has triangles.  Its bucket
+// becomes a tombstone, its voxels are cleared, its neighbours forget it, its index returns
+// to the pool.  `consumed`: the update set has been meshed since it was collected (else its
+// blocks are kept, so that the pending update never lists a recycled block index).
+// Returns (in lane 0) whether the block was freed.
+__device__ __forceinline__ bool gc_block(const Vol& V, int blk, uint32_t epoch, int consumed) {
+  const int lane = threadIdx.x & 31;
+  const int4 key = V.bkey[blk];
+  const bool cand = key.w >= 0 && V.bepoch[blk] != epoch && V.bntri[blk] == 0 && V.bnvert[blk] == 0 &&
+                    V.bnear[blk] == 0 && (consumed || V.ustamp[blk] != epoch);
+  if (!cand) return false;  // warp-uniform
+  bool lower_tri = false;
+  if (lane >= 1 && lane < 8) {
+    const int nbk = V.nbr[blk * 16 + 8 + lane];
+    lower_tri = nbk >= 0 && V.bntri[nbk] != 0;
+  }
+  if (__any_sync(0xffffffffu, lower_tri)) return false;
+  float4* tw = reinterpret_cast<float4*>(V.tw + (size_t)blk * BV);
+  for (int j = lane; j < BV / 2; j += 32) tw[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+  reinterpret_cast<uint4*>(V.code_eff + (size_t)blk * BV)[lane] = make_uint4(0, 0, 0, 0);
+  reinterpret_cast<uint4*>(V.code_prev + (size_t)blk * BV)[lane] = make_uint4(0, 0, 0, 0);
+  reinterpret_cast<uint4*>(V.vmask + (size_t)blk * BV)[lane] = make_uint4(0, 0, 0, 0);
+  if (lane >= 1 && lane < 16 && lane != 8) {
+    // unlink: the neighbour at this slot's offset forgets this block
+    const int other = V.nbr[blk * 16 + lane];
+    if (other >= 0) V.nbr[other * 16 + (lane ^ 8)] = -1;
+  }
+  __syncwarp();
+  if (lane < 16) V.nbr[blk * 16 + lane] = -1;
+  if (lane == 0) {
+    V.keys[key.w] = KEY_TOMB;
+    V.vals[key.w] = -1;
+    V.bkey[blk] = make_int4(0, 0, 0, -1);
+    V.bnear[blk] = 0;
+    pool_push(V, V.blk_free, C_BLK_TOP, V.max_blocks, blk);
+  }
+  return true;
+}
+
+__device__ __forceinline__ void gc_flush_blocks(const Vol& V, int& freed) {
+  if ((threadIdx.x & 31) == 0 && freed) {
+    atomicSub(&V.ctl->c[C_LIVE_BLOCKS], freed);
+    atomicAdd(&V.ctl->c[C_TOMBS], freed);
+    atomicAdd(&V.ctl->c[C_ST_FREED_BLOCKS], freed);
+  }
+  freed = 0;
+}
+
+// After the last CTA (the whole CTA): rebuild the hash when live plus dead buckets pass
+// half the table; with `consumed`, empty the update set.
+__device__ __forceinline__ void gc_blocks_finish(const Vol& V, int consumed) {
+  __shared__ int need;
+  if (threadIdx.x == 0) {
+    const long long live = V.ctl->c[C_LIVE_BLOCKS], tomb = V.ctl->c[C_TOMBS];
+    need = (live + tomb) * 2 > (long long)V.hmask + 1 && tomb > 0;
+  }
+  __syncthreads();
+  if (need) {
+    rehash_in_cta(V);
+    if (threadIdx.x == 0) {
+      V.ctl->c[C_TOMBS] = 0;
+      V.ctl->c[C_ST_REHASHES] += 1;
+    }
+  }
+  if (threadIdx.x == 0 && consumed) V.ctl->c[C_N_UPDATE] = 0;
+  __syncthreads();
+}
+
+// Block recycling, one warp per pool slot.  The last CTA finishes the pass.
 __global__ void __launch_bounds__(256) k_gc_blocks(Vol V, int consumed) {
   grid_dependency_wait();
-  const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int hw = min(__ldcg(&V.ctl->c[C_BLK_BUMP]), V.max_blocks);
   const uint32_t epoch = (uint32_t)__ldcg(&V.ctl->c[C_EPOCH]);
   int freed = 0;
-  for (int blk = warp; blk < hw; blk += nwarps) {
-    const int4 key = V.bkey[blk];
-    const bool cand = key.w >= 0 && V.bepoch[blk] != epoch && V.bntri[blk] == 0 && V.bnvert[blk] == 0 &&
-                      V.bnear[blk] == 0 && (consumed || V.ustamp[blk] != epoch);
-    if (!cand) continue;  // warp-uniform
-    bool lower_tri = false;
-    if (lane >= 1 && lane < 8) {
-      const int nbk = V.nbr[blk * 16 + 8 + lane];
-      lower_tri = nbk >= 0 && V.bntri[nbk] != 0;
-    }
-    if (__any_sync(0xffffffffu, lower_tri)) continue;
-    // free it
-    float4* tw = reinterpret_cast<float4*>(V.tw + (size_t)blk * BV);
-    for (int j = lane; j < BV / 2; j += 32) tw[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-    reinterpret_cast<uint4*>(V.code_eff + (size_t)blk * BV)[lane] = make_uint4(0, 0, 0, 0);
-    reinterpret_cast<uint4*>(V.code_prev + (size_t)blk * BV)[lane] = make_uint4(0, 0, 0, 0);
-    reinterpret_cast<uint4*>(V.vmask + (size_t)blk * BV)[lane] = make_uint4(0, 0, 0, 0);
-    if (lane >= 1 && lane < 16 && lane != 8) {
-      // unlink: the neighbour at this slot's offset forgets this block
-      const int other = V.nbr[blk * 16 + lane];
-      if (other >= 0) V.nbr[other * 16 + (lane ^ 8)] = -1;
-    }
-    __syncwarp();
-    if (lane < 16) V.nbr[blk * 16 + lane] = -1;
-    if (lane == 0) {
-      V.keys[key.w] = KEY_TOMB;
-      V.vals[key.w] = -1;
-      V.bkey[blk] = make_int4(0, 0, 0, -1);
-      V.bnear[blk] = 0;
-      ++freed;
-      pool_push(V, V.blk_free, C_BLK_TOP, V.max_blocks, blk);
-    }
-  }
-  if (lane == 0 && freed) {
-    atomicSub(&V.ctl->c[C_LIVE_BLOCKS], freed);
-    atomicAdd(&V.ctl->c[C_TOMBS], freed);
-    atomicAdd(&V.ctl->c[C_ST_FREED_BLOCKS], freed);
-  }
+  for (int blk = warp; blk < hw; blk += nwarps) freed += gc_block(V, blk, epoch, consumed);
+  gc_flush_blocks(V, freed);
   if (last_block(V, C_DONE7)) {
-    __shared__ int need;
-    if (threadIdx.x == 0) {
-      const long long live = V.ctl->c[C_LIVE_BLOCKS], tomb = V.ctl->c[C_TOMBS];
-      need = (live + tomb) * 2 > (long long)V.hmask + 1 && tomb > 0;
-    }
-    __syncthreads();
-    if (need) {
-      rehash_in_cta(V);
-      if (threadIdx.x == 0) {
-        V.ctl->c[C_TOMBS] = 0;
-        V.ctl->c[C_ST_REHASHES] += 1;
-      }
-    }
-    if (threadIdx.x == 0) {
-      if (consumed) V.ctl->c[C_N_UPDATE] = 0;
-      V.ctl->c[C_DONE7] = 0;
-    }
+    gc_blocks_finish(V, consumed);
+    if (threadIdx.x == 0) V.ctl->c[C_DONE7] = 0;
   }
 }
 

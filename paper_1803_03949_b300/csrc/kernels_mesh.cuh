@@ -230,6 +230,240 @@ __device__ __forceinline__ int warp_reserve(int* counter, int cnt) {
 // Shared-memory slot of the edge owned by the voxel at halo coordinates (x, y, z) along a.
 __device__ __forceinline__ int edge_slot(int x, int y, int z, int a) { return ((z * 9 + y) * 9 + x) * 3 + a; }
 
+// Counters a mesh pass accumulates per CTA.
+struct MeshCounts {
+  int changed = 0, created = 0, emitted = 0, released = 0, refreshed = 0;
+};
+
+// One update-set block `blk` through stages a-e, the calling CTA of MESH_THREADS with its
+// shared staging area S (S.tri64 already holds the triangle table).
+__device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, int mode, MeshCounts& cnt) {
+  const float eps = V.eps, l = V.l;
+  int& changed = cnt.changed;
+  int& created = cnt.created;
+  int& emitted = cnt.emitted;
+  int& released = cnt.released;
+  int& refreshed = cnt.refreshed;
+  const int4 key = V.bkey[blk];
+  if (key.w < 0) return;  // freed since it joined the set (uniform over the CTA)
+  // ---- a. neighbours and halo
+  if (threadIdx.x < 8) S.nb[threadIdx.x] = threadIdx.x == 0 ? blk : __ldcg(&V.nbr[blk * 16 + threadIdx.x]);
+  if (threadIdx.x == 0) {
+    S.dtri = 0;
+    S.nchg = 0;
+    S.nedge = 0;
+    S.nref = 0;
+  }
+  for (int w = threadIdx.x; w < EDGE_WORDS; w += MESH_THREADS) S.emark[w] = 0;
+  // this thread's 4 cubes: type, previous-type and vertex-flag bytes and run slots, loaded
+  // now so that they arrive while the halo is staged
+  const int c0 = 4 * threadIdx.x;  // MESH_THREADS * 4 == BV
+  const size_t ci0 = (size_t)blk * BV + c0;
+  const uint32_t eff_w = ld_early_u32(V.code_eff + ci0);
+  const uint32_t vm_w = ld_early_u32(V.vmask + ci0);
+  const uint32_t prev_w = (mode & M_UPDATE) ? eff_w : ld_early_u32(V.code_prev + ci0);
+  const int4 tb4 = ld_early_i4(V.tri_base + ci0);
+  __syncthreads();
+  for (int h = threadIdx.x; h < HALO_N; h += MESH_THREADS) {
+    const int x = h % HALO, y = (h / HALO) % HALO, z = h / (HALO * HALO);
+    const int b = S.nb[(x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2)];
+    S.halo[h] = b >= 0 ? __ldcg(&V.tw[(size_t)b * BV + (x & 7) + 8 * (y & 7) + 64 * (z & 7)])
+                       : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  // ---- b. cube types, vertex refresh, changed-cube list, needed edges (4 consecutive cubes
+  //         per thread: the type, previous-type and vertex-flag bytes move as 32-bit words)
+  int dtri = 0;
+  {
+    const int tbs[4] = {tb4.x, tb4.y, tb4.z, tb4.w};
+    if (mode & M_UPDATE) *reinterpret_cast<uint32_t*>(V.code_prev + ci0) = eff_w;
+    // existing vertices of the 4 voxels: listed for the refresh in stage d
+    const uint32_t live_w = vm_w & 0x07070707u;
+    {
+      const int cnt = __popc(live_w);
+      int r = warp_reserve(&S.nref, cnt);
+#pragma unroll
+      for (int q = 0; q < 12; ++q)
+        if ((live_w >> (8 * (q / 3) + q % 3)) & 1) S.rlist[r++] = (uint16_t)((c0 + q / 3) * 3 + q % 3);
+    }
+    uint32_t new_w = eff_w;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = c0 + j;
+      const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
+      bool valid = true;
+      int raw = 0, small = 0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float2 hv = halo_at(S, x + corner_x(k), y + corner_y(k), z + corner_z(k));
+        valid &= hv.y > 0.0f;
+        raw |= (hv.x < 0.0f) << k;
+        small |= (fabsf(hv.x) < eps) << k;
+      }
+      const int eff_old = (eff_w >> (8 * j)) & 0xFF;
+      const int prev = (prev_w >> (8 * j)) & 0xFF;
+      int e = valid ? raw : 0;
+      if (valid && (mode & M_REFINE)) e = refine_type(raw, prev, small);
+      if (e == eff_old) continue;
+      ++changed;
+      new_w = (new_w & ~(0xFFu << (8 * j))) | ((uint32_t)e << (8 * j));
+      const uint64_t tw64 = S.tri64[e];
+      const int nold = packed_ntri(S.tri64[eff_old]), nnew = packed_ntri(tw64);
+      const int slot = atomicAdd(&S.nchg, 1);  // a few changed cubes per thread at most
+      S.chg_cube[slot] = (uint16_t)c;
+      S.chg_new[slot] = (uint8_t)e;
+      S.chg_old[slot] = (uint8_t)eff_old;
+      S.chg_base[slot] = nold > 0 ? tbs[j] : -1;
+      dtri += nnew - nold;
+      for (int t = 0; t < nnew; ++t)
+        for (int jj = 0; jj < 3; ++jj) {
+          const int ob = owner_bits(packed_edge(tw64, t, jj));
+          const int es = edge_slot(x + (ob & 1), y + ((ob >> 1) & 1), z + ((ob >> 2) & 1), ob >> 3);
+          atomicOr(&S.emark[es >> 5], 1u << (es & 31));
+        }
+    }
+    if (new_w != eff_w) *reinterpret_cast<uint32_t*>(V.code_eff + ci0) = new_w;
+  }
+  if (dtri) atomicAdd(&S.dtri, dtri);
+  __syncthreads();
+  const int nchg = S.nchg;
+  // ---- c. compact the needed edges into a list (warp 0 scans the bitmap's word counts)
+  if (threadIdx.x < 32) {
+    int carry = 0;
+    for (int w0 = 0; w0 < EDGE_WORDS; w0 += 32) {
+      const int w = w0 + threadIdx.x;
+      const int cnt = w < EDGE_WORDS ? __popc(S.emark[w]) : 0;
+      int x = cnt;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if ((int)threadIdx.x >= o) x += y;
+      }
+      if (w < EDGE_WORDS) S.ecount[w] = carry + x - cnt;
+      carry += __shfl_sync(0xffffffffu, x, 31);
+    }
+    if (threadIdx.x == 0) S.nedge = carry;
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < EDGE_WORDS; w += MESH_THREADS) {
+    unsigned mbits = S.emark[w];
+    int r = S.ecount[w];
+    while (mbits) {
+      const int b = __ffs(mbits) - 1;
+      mbits &= mbits - 1;
+      S.elist[r++] = (uint16_t)(w * 32 + b);
+    }
+  }
+  __syncthreads();
+  // ---- d. one loop over three independent kinds of work, so the stage lasts as long as the
+  //         longest chain rather than their sum:
+  //         per needed edge: its vertex, created on first use;
+  //         per existing vertex of the block: position and normal from the new TSDF;
+  //         per changed cube: release the old triangles, pop a run for the new ones.
+  const int nedge = S.nedge, nref = S.nref;
+  for (int j = threadIdx.x; j < nedge + nref + nchg; j += MESH_THREADS) {
+    if (j < nedge) {
+      const int es = S.elist[j];
+      const int a = es % 3, o = es / 3;
+      const int x = o % 9, y = (o / 9) % 9, z = o / 81;
+      S.evid[es] = vertex_of_edge(V, S, key, x, y, z, a, created);
+    } else if (j < nedge + nref) {
+      const int r = S.rlist[j - nedge];
+      const int c = r / 3, a = r - c * 3;
+      const int vid = __ldcg(&V.edge_vtx[((size_t)blk * BV + c) * 3 + a]);
+      if (vid < 0) continue;
+      float4 p, nn;
+      edge_vertex(S, l, key, c & 7, (c >> 3) & 7, c >> 6, a, &p, &nn);
+      V.vpos[vid] = p;
+      V.vnrm[vid] = nn;
+      ++refreshed;
+    } else {
+      const int q = j - nedge - nref;
+      const int nold = packed_ntri(S.tri64[S.chg_old[q]]), obase = S.chg_base[q];
+      const int nt = packed_ntri(S.tri64[S.chg_new[q]]);
+      if (obase >= 0) {
+        int4 tr[5];
+#pragma unroll
+        for (int t = 0; t < 5; ++t) tr[t] = t < nold ? __ldcg(&V.tris[obase + t]) : make_int4(-1, -1, -1, -1);
+        int hit[15];
+#pragma unroll
+        for (int t = 0; t < 5; ++t) {
+          const int vs[3] = {tr[t].x, tr[t].y, tr[t].z};
+#pragma unroll
+          for (int jj = 0; jj < 3; ++jj) hit[3 * t + jj] = vs[jj] >= 0 ? atomicSub(&V.vref[vs[jj]], 1) : 0;
+        }
+#pragma unroll
+        for (int t = 0; t < 5; ++t) {
+          if (t < nold) V.tris[obase + t] = make_int4(-1, -1, -1, -1);
+          const int vs[3] = {tr[t].x, tr[t].y, tr[t].z};
+#pragma unroll
+          for (int jj = 0; jj < 3; ++jj)
+            if (hit[3 * t + jj] == 1) list_push(V, V.dead, C_N_DEAD, V.list_cap_dead, vs[jj]);
+        }
+        deadrun_push(V, obase, nold);
+        released += nold;
+      }
+      const int base = nt > 0 ? run_pop(V, nt) : -1;
+      S.chg_base[q] = base;
+      V.tri_base[(size_t)blk * BV + S.chg_cube[q]] = base;
+      if (base >= 0) emitted += nt;
+    }
+  }
+  __syncthreads();
+  // ---- e. one thread per new triangle
+  for (int j = threadIdx.x; j < nchg * 5; j += MESH_THREADS) {
+    const int q = j / 5, t = j - q * 5;
+    const int e = S.chg_new[q], base = S.chg_base[q];
+    const uint64_t tw64 = S.tri64[e];
+    if (t >= packed_ntri(tw64) || base < 0) continue;
+    const int c = S.chg_cube[q];
+    const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
+    int vs[3];
+#pragma unroll
+    for (int jj = 0; jj < 3; ++jj) {
+      const int ob = owner_bits(packed_edge(tw64, t, jj));
+      vs[jj] = S.evid[edge_slot(x + (ob & 1), y + ((ob >> 1) & 1), z + ((ob >> 2) & 1), ob >> 3)];
+    }
+    const int ci = blk * BV + c;
+    if (vs[0] < 0 || vs[1] < 0 || vs[2] < 0) {  // vertex pool exhausted
+      set_status(V, ST_POOL_FULL);
+      V.tris[base + t] = make_int4(-1, -1, -1, ci);
+      continue;
+    }
+#pragma unroll
+    for (int jj = 0; jj < 3; ++jj) atomicAdd(&V.vref[vs[jj]], 1);
+    V.tris[base + t] = make_int4(vs[0], vs[1], vs[2], ci);
+  }
+  if (threadIdx.x == 0 && S.dtri) {
+    atomicAdd(&V.bntri[blk], S.dtri);
+    atomicAdd(&V.ctl->c[C_LIVE_TRIS], S.dtri);
+  }
+  __syncthreads();
+}
+
+// Flush a CTA's counters into the volume's statistics.
+__device__ __forceinline__ void mesh_flush(const Vol& V, MeshCounts& c) {
+  if (c.changed) counter_add(V, C_ST_CHANGED, c.changed);
+  if (c.emitted) counter_add(V, C_ST_EMITTED, c.emitted);
+  if (c.released) counter_add(V, C_ST_RELEASED, c.released);
+  if (c.refreshed) counter_add(V, C_ST_REFRESHED, c.refreshed);
+  if (c.created) {
+    counter_add(V, C_LIVE_VERTS, c.created);
+    counter_add(V, C_ST_NEW_VERTS, c.created);
+  }
+  c = MeshCounts();
+}
+
+// After the last block of a mesh pass over n update-set blocks (one thread): clamp the
+// vertex and run free-stack tops, statistics.
+__device__ __forceinline__ void mesh_finish(const Vol& V, int n) {
+  fold_top(V, C_VTX_TOP);
+#pragma unroll
+  for (int L = 0; L < 5; ++L) fold_top(V, C_RUN_TOP0 + L);
+  V.ctl->c[C_ST_UPDATE_BLOCKS] = n;
+  reinterpret_cast<unsigned*>(V.ctl->c)[C_ST_MESHED] += (unsigned)n;  // wraps modulo 2^32
+}
+
+// Every update-set block, one per CTA iteration.
 // mode: M_UPDATE (types from the current TSDF; t_{i-1} := previous effective type; refresh
 // the positions and normals of the block's existing vertices), M_REFINE (Eqs. 3-5 with the
 // stored t_{i-1}).  The last CTA clamps the vertex and run free-stack tops.
@@ -238,221 +472,13 @@ __global__ void __launch_bounds__(MESH_THREADS, 7) k_mesh(Vol V, int mode) {
   for (int i = threadIdx.x; i < 128; i += MESH_THREADS) reinterpret_cast<uint4*>(S.tri64)[i] = V.tri_table[i];
   grid_dependency_wait();
   const int n = min(__ldcg(&V.ctl->c[C_N_UPDATE]), V.list_cap_update);
-  const float eps = V.eps, l = V.l;
-  int changed = 0, created = 0, emitted = 0, released = 0, refreshed = 0;
-  for (int i = blockIdx.x; i < n; i += gridDim.x) {
-    const int blk = V.update[i];
-    const int4 key = V.bkey[blk];
-    if (key.w < 0) continue;  // freed since it joined the set
-    // ---- a. neighbours and halo
-    if (threadIdx.x < 8) S.nb[threadIdx.x] = threadIdx.x == 0 ? blk : __ldcg(&V.nbr[blk * 16 + threadIdx.x]);
-    if (threadIdx.x == 0) {
-      S.dtri = 0;
-      S.nchg = 0;
-      S.nedge = 0;
-      S.nref = 0;
-    }
-    for (int w = threadIdx.x; w < EDGE_WORDS; w += MESH_THREADS) S.emark[w] = 0;
-    // this thread's 4 cubes: type, previous-type and vertex-flag bytes and run slots, loaded
-    // now so that they arrive while the halo is staged
-    const int c0 = 4 * threadIdx.x;  // MESH_THREADS * 4 == BV
-    const size_t ci0 = (size_t)blk * BV + c0;
-    const uint32_t eff_w = ld_early_u32(V.code_eff + ci0);
-    const uint32_t vm_w = ld_early_u32(V.vmask + ci0);
-    const uint32_t prev_w = (mode & M_UPDATE) ? eff_w : ld_early_u32(V.code_prev + ci0);
-    const int4 tb4 = ld_early_i4(V.tri_base + ci0);
-    __syncthreads();
-    for (int h = threadIdx.x; h < HALO_N; h += MESH_THREADS) {
-      const int x = h % HALO, y = (h / HALO) % HALO, z = h / (HALO * HALO);
-      const int b = S.nb[(x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2)];
-      S.halo[h] = b >= 0 ? __ldcg(&V.tw[(size_t)b * BV + (x & 7) + 8 * (y & 7) + 64 * (z & 7)])
-                         : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    // ---- b. cube types, vertex refresh, changed-cube list, needed edges (4 consecutive cubes
-    //         per thread: the type, previous-type and vertex-flag bytes move as 32-bit words)
-    int dtri = 0;
-    {
-      const int tbs[4] = {tb4.x, tb4.y, tb4.z, tb4.w};
-      if (mode & M_UPDATE) *reinterpret_cast<uint32_t*>(V.code_prev + ci0) = eff_w;
-      // existing vertices of the 4 voxels: listed for the refresh in stage d
-      const uint32_t live_w = vm_w & 0x07070707u;
-      {
-        const int cnt = __popc(live_w);
-        int r = warp_reserve(&S.nref, cnt);
-#pragma unroll
-        for (int q = 0; q < 12; ++q)
-          if ((live_w >> (8 * (q / 3) + q % 3)) & 1) S.rlist[r++] = (uint16_t)((c0 + q / 3) * 3 + q % 3);
-      }
-      uint32_t new_w = eff_w;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c = c0 + j;
-        const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
-        bool valid = true;
-        int raw = 0, small = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const float2 hv = halo_at(S, x + corner_x(k), y + corner_y(k), z + corner_z(k));
-          valid &= hv.y > 0.0f;
-          raw |= (hv.x < 0.0f) << k;
-          small |= (fabsf(hv.x) < eps) << k;
-        }
-        const int eff_old = (eff_w >> (8 * j)) & 0xFF;
-        const int prev = (prev_w >> (8 * j)) & 0xFF;
-        int e = valid ? raw : 0;
-        if (valid && (mode & M_REFINE)) e = refine_type(raw, prev, small);
-        if (e == eff_old) continue;
-        ++changed;
-        new_w = (new_w & ~(0xFFu << (8 * j))) | ((uint32_t)e << (8 * j));
-        const uint64_t tw64 = S.tri64[e];
-        const int nold = packed_ntri(S.tri64[eff_old]), nnew = packed_ntri(tw64);
-        const int slot = atomicAdd(&S.nchg, 1);  // a few changed cubes per thread at most
-        S.chg_cube[slot] = (uint16_t)c;
-        S.chg_new[slot] = (uint8_t)e;
-        S.chg_old[slot] = (uint8_t)eff_old;
-        S.chg_base[slot] = nold > 0 ? tbs[j] : -1;
-        dtri += nnew - nold;
-        for (int t = 0; t < nnew; ++t)
-          for (int jj = 0; jj < 3; ++jj) {
-            const int ob = owner_bits(packed_edge(tw64, t, jj));
-            const int es = edge_slot(x + (ob & 1), y + ((ob >> 1) & 1), z + ((ob >> 2) & 1), ob >> 3);
-            atomicOr(&S.emark[es >> 5], 1u << (es & 31));
-          }
-      }
-      if (new_w != eff_w) *reinterpret_cast<uint32_t*>(V.code_eff + ci0) = new_w;
-    }
-    if (dtri) atomicAdd(&S.dtri, dtri);
-    __syncthreads();
-    const int nchg = S.nchg;
-    // ---- c. compact the needed edges into a list (warp 0 scans the bitmap's word counts)
-    if (threadIdx.x < 32) {
-      int carry = 0;
-      for (int w0 = 0; w0 < EDGE_WORDS; w0 += 32) {
-        const int w = w0 + threadIdx.x;
-        const int cnt = w < EDGE_WORDS ? __popc(S.emark[w]) : 0;
-        int x = cnt;
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(0xffffffffu, x, o);
-          if ((int)threadIdx.x >= o) x += y;
-        }
-        if (w < EDGE_WORDS) S.ecount[w] = carry + x - cnt;
-        carry += __shfl_sync(0xffffffffu, x, 31);
-      }
-      if (threadIdx.x == 0) S.nedge = carry;
-    }
-    __syncthreads();
-    for (int w = threadIdx.x; w < EDGE_WORDS; w += MESH_THREADS) {
-      unsigned mbits = S.emark[w];
-      int r = S.ecount[w];
-      while (mbits) {
-        const int b = __ffs(mbits) - 1;
-        mbits &= mbits - 1;
-        S.elist[r++] = (uint16_t)(w * 32 + b);
-      }
-    }
-    __syncthreads();
-    // ---- d. one loop over three independent kinds of work, so the stage lasts as long as the
-    //         longest chain rather than their sum:
-    //         per needed edge: its vertex, created on first use;
-    //         per existing vertex of the block: position and normal from the new TSDF;
-    //         per changed cube: release the old triangles, pop a run for the new ones.
-    const int nedge = S.nedge, nref = S.nref;
-    for (int j = threadIdx.x; j < nedge + nref + nchg; j += MESH_THREADS) {
-      if (j < nedge) {
-        const int es = S.elist[j];
-        const int a = es % 3, o = es / 3;
-        const int x = o % 9, y = (o / 9) % 9, z = o / 81;
-        S.evid[es] = vertex_of_edge(V, S, key, x, y, z, a, created);
-      } else if (j < nedge + nref) {
-        const int r = S.rlist[j - nedge];
-        const int c = r / 3, a = r - c * 3;
-        const int vid = __ldcg(&V.edge_vtx[((size_t)blk * BV + c) * 3 + a]);
-        if (vid < 0) continue;
-        float4 p, nn;
-        edge_vertex(S, l, key, c & 7, (c >> 3) & 7, c >> 6, a, &p, &nn);
-        V.vpos[vid] = p;
-        V.vnrm[vid] = nn;
-        ++refreshed;
-      } else {
-        const int q = j - nedge - nref;
-        const int nold = packed_ntri(S.tri64[S.chg_old[q]]), obase = S.chg_base[q];
-        const int nt = packed_ntri(S.tri64[S.chg_new[q]]);
-        if (obase >= 0) {
-          int4 tr[5];
-#pragma unroll
-          for (int t = 0; t < 5; ++t) tr[t] = t < nold ? __ldcg(&V.tris[obase + t]) : make_int4(-1, -1, -1, -1);
-          int hit[15];
-#pragma unroll
-          for (int t = 0; t < 5; ++t) {
-            const int vs[3] = {tr[t].x, tr[t].y, tr[t].z};
-#pragma unroll
-            for (int jj = 0; jj < 3; ++jj) hit[3 * t + jj] = vs[jj] >= 0 ? atomicSub(&V.vref[vs[jj]], 1) : 0;
-          }
-#pragma unroll
-          for (int t = 0; t < 5; ++t) {
-            if (t < nold) V.tris[obase + t] = make_int4(-1, -1, -1, -1);
-            const int vs[3] = {tr[t].x, tr[t].y, tr[t].z};
-#pragma unroll
-            for (int jj = 0; jj < 3; ++jj)
-              if (hit[3 * t + jj] == 1) list_push(V, V.dead, C_N_DEAD, V.list_cap_dead, vs[jj]);
-          }
-          deadrun_push(V, obase, nold);
-          released += nold;
-        }
-        const int base = nt > 0 ? run_pop(V, nt) : -1;
-        S.chg_base[q] = base;
-        V.tri_base[(size_t)blk * BV + S.chg_cube[q]] = base;
-        if (base >= 0) emitted += nt;
-      }
-    }
-    __syncthreads();
-    // ---- e. one thread per new triangle
-    for (int j = threadIdx.x; j < nchg * 5; j += MESH_THREADS) {
-      const int q = j / 5, t = j - q * 5;
-      const int e = S.chg_new[q], base = S.chg_base[q];
-      const uint64_t tw64 = S.tri64[e];
-      if (t >= packed_ntri(tw64) || base < 0) continue;
-      const int c = S.chg_cube[q];
-      const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
-      int vs[3];
-#pragma unroll
-      for (int jj = 0; jj < 3; ++jj) {
-        const int ob = owner_bits(packed_edge(tw64, t, jj));
-        vs[jj] = S.evid[edge_slot(x + (ob & 1), y + ((ob >> 1) & 1), z + ((ob >> 2) & 1), ob >> 3)];
-      }
-      const int ci = blk * BV + c;
-      if (vs[0] < 0 || vs[1] < 0 || vs[2] < 0) {  // vertex pool exhausted
-        set_status(V, ST_POOL_FULL);
-        V.tris[base + t] = make_int4(-1, -1, -1, ci);
-        continue;
-      }
-#pragma unroll
-      for (int jj = 0; jj < 3; ++jj) atomicAdd(&V.vref[vs[jj]], 1);
-      V.tris[base + t] = make_int4(vs[0], vs[1], vs[2], ci);
-    }
-    if (threadIdx.x == 0 && S.dtri) {
-      atomicAdd(&V.bntri[blk], S.dtri);
-      atomicAdd(&V.ctl->c[C_LIVE_TRIS], S.dtri);
-    }
-    __syncthreads();
-  }
-  if (changed) counter_add(V, C_ST_CHANGED, changed);
-  if (emitted) counter_add(V, C_ST_EMITTED, emitted);
-  if (released) counter_add(V, C_ST_RELEASED, released);
-  if (refreshed) counter_add(V, C_ST_REFRESHED, refreshed);
-  if (created) {
-    counter_add(V, C_LIVE_VERTS, created);
-    counter_add(V, C_ST_NEW_VERTS, created);
-  }
+  MeshCounts cnt;
+  for (int i = blockIdx.x; i < n; i += gridDim.x) mesh_block(V, S, V.update[i], mode, cnt);
+  mesh_flush(V, cnt);
   allow_dependent_launch();
   if (last_block(V, C_DONE3)) {
     if (threadIdx.x == 0) {
-      fold_top(V, C_VTX_TOP);
-#pragma unroll
-      for (int L = 0; L < 5; ++L) fold_top(V, C_RUN_TOP0 + L);
-      V.ctl->c[C_ST_UPDATE_BLOCKS] = n;
-      reinterpret_cast<unsigned*>(V.ctl->c)[C_ST_MESHED] += (unsigned)n;  // wraps modulo 2^32
+      mesh_finish(V, n);
       V.ctl->c[C_DONE3] = 0;
     }
   }

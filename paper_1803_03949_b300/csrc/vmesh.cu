@@ -1,6 +1,7 @@
 // C ABI of the vmesh library (declared in include/vmesh.h): volume lifetime, the
 // per-frame calls, CUDA-graph replay of a whole frame, per-kernel timing and the
 // download / export paths.  All device work is the kernels in this directory.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -8,6 +9,7 @@
 #include <vector>
 
 #include "vmesh.h"
+#include "kernels_batch.cuh"
 #include "kernels_diff.cuh"
 #include "kernels_fusion.cuh"
 #include "kernels_gc.cuh"
@@ -1057,3 +1059,288 @@ extern "C" vm_status vm_download_mesh_noalloc(vm_volume* v, float* pos, float* n
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return VM_ERR_CUDA;
   return VM_OK;
 }
+
+// ====================================================================== batched step
+namespace {
+
+// Schedule options the autotuner picks from, per kernel (index = schedule slot):
+//   0 k_alloc pixels per thread (CTA of 1024 / ppt threads per 64 x 16 tile), 1-4 CTAs per SM
+//   of the fusion, mesh, vertex-gc and block-gc kernels (persistent grids).
+constexpr int SCHED_SLOTS = 5;
+constexpr int SCHED_OPTS = 3;
+const int kSchedOptions[SCHED_SLOTS][SCHED_OPTS] = {{1, 2, 4}, {4, 8, 12}, {3, 5, 7}, {1, 2, 4}, {2, 4, 8}};
+const int kSchedDefault[SCHED_SLOTS] = {2, 12, 7, 2, 8};
+
+struct TuneRec {
+  int opt;
+  cudaEvent_t ev[SCHED_SLOTS + 1];
+};
+
+}  // namespace
+
+struct vm_batch {
+  std::vector<vm_volume*> vols;
+  int n = 0;
+  Vol* d_vols = nullptr;
+  int* d_done = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  int num_sms = 148;
+  int sched[SCHED_SLOTS];
+  // graph of one tick; the frame table reaches it as kb_alloc's launch argument
+  cudaGraph_t graph = nullptr;
+  cudaGraphNode_t alloc_node = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int graph_flags = -1, graph_tx = -1, graph_ty = -1;
+  // autotuning: ticks still to time, the timed ticks, per-option totals
+  int tune_left = 0;
+  std::vector<TuneRec> tune_recs;
+  double tune_ms[SCHED_SLOTS][SCHED_OPTS] = {};
+  int tune_cnt[SCHED_SLOTS][SCHED_OPTS] = {};
+  BatchFrames* frames = nullptr;  // host staging of the launch argument (8.5 KB)
+};
+
+namespace {
+
+void batch_drop_graph(vm_batch* b) {
+  if (b->exec) {
+    cudaStreamSynchronize(b->stream);
+    cudaGraphExecDestroy(b->exec);
+  }
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  b->alloc_node = nullptr;
+  b->graph_flags = -1;
+}
+
+void* batch_alloc_kernel(int ppt) {
+  switch (ppt) {
+    case 1: return reinterpret_cast<void*>(kb_alloc<1>);
+    case 4: return reinterpret_cast<void*>(kb_alloc<4>);
+    default: return reinterpret_cast<void*>(kb_alloc<2>);
+  }
+}
+
+// Enqueue one tick's five launches with schedule `sc`; with `rec`, event pairs around each.
+vm_status batch_enqueue(vm_batch* b, cudaStream_t st, const int* sc, int flags, int tx, int ty, TuneRec* rec) {
+  const int mode = M_UPDATE | ((flags & VM_REFINE) ? M_REFINE : 0);
+  (void)cudaGetLastError();
+  if (rec) cudaEventRecord(rec->ev[0], st);
+  const dim3 grid(tx, ty, b->n);
+  const int threads = ALLOC_TILE_W * ALLOC_TILE_H / sc[0];
+  switch (sc[0]) {
+    case 1: kb_alloc<1><<<grid, threads, 0, st>>>(b->d_vols, b->n, *b->frames, b->d_done); break;
+    case 4: kb_alloc<4><<<grid, threads, 0, st>>>(b->d_vols, b->n, *b->frames, b->d_done); break;
+    default: kb_alloc<2><<<grid, threads, 0, st>>>(b->d_vols, b->n, *b->frames, b->d_done); break;
+  }
+  if (rec) cudaEventRecord(rec->ev[1], st);
+  launch_dependent(kb_integrate, b->num_sms * sc[1], INTEG_THREADS, st, (const Vol*)b->d_vols, b->n, b->d_done);
+  if (rec) cudaEventRecord(rec->ev[2], st);
+  launch_dependent(kb_mesh, b->num_sms * sc[2], MESH_THREADS, st, (const Vol*)b->d_vols, b->n, mode, b->d_done);
+  if (rec) cudaEventRecord(rec->ev[3], st);
+  if (flags & VM_GC) {
+    launch_dependent(kb_gc_vertices, b->num_sms * sc[3], 256, st, (const Vol*)b->d_vols, b->n, b->d_done);
+    if (rec) cudaEventRecord(rec->ev[4], st);
+    launch_dependent(kb_gc_blocks, b->num_sms * sc[4], 256, st, (const Vol*)b->d_vols, b->n, 1, b->d_done);
+  } else if (rec) {
+    cudaEventRecord(rec->ev[4], st);
+  }
+  if (rec) cudaEventRecord(rec->ev[5], st);
+  return cuda_status(cudaGetLastError());
+}
+
+// Fold the timed ticks into the per-option totals and pick each kernel's fastest option.
+vm_status batch_finish_tuning(vm_batch* b) {
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return VM_ERR_CUDA;
+  for (auto& r : b->tune_recs) {
+    for (int k = 0; k < SCHED_SLOTS; ++k) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, r.ev[k], r.ev[k + 1]) == cudaSuccess) {
+        b->tune_ms[k][r.opt] += ms;
+        b->tune_cnt[k][r.opt] += 1;
+      }
+    }
+    for (auto e : r.ev) cudaEventDestroy(e);
+  }
+  b->tune_recs.clear();
+  for (int k = 0; k < SCHED_SLOTS; ++k) {
+    int best = -1;
+    double best_ms = 0;
+    for (int o = 0; o < SCHED_OPTS; ++o) {
+      if (!b->tune_cnt[k][o]) continue;
+      const double m = b->tune_ms[k][o] / b->tune_cnt[k][o];
+      if (best < 0 || m < best_ms) best = o, best_ms = m;
+    }
+    if (best >= 0) b->sched[k] = kSchedOptions[k][best];
+  }
+  batch_drop_graph(b);
+  return VM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vm_status vm_batch_create(vm_volume* const* vols, int n, vm_batch** out) {
+  if (!vols || !out || n < 1 || n > MAX_SCENES) return VM_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (!vols[i]) return VM_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (vols[j] == vols[i]) return VM_ERR_INVALID_ARG;
+  }
+  vm_batch* b = new vm_batch();
+  b->vols.assign(vols, vols + n);
+  b->n = n;
+  b->stream = vols[0]->stream;
+  b->num_sms = vols[0]->num_sms;
+  for (int k = 0; k < SCHED_SLOTS; ++k) b->sched[k] = kSchedDefault[k];
+  std::vector<Vol> host(n);
+  for (int i = 0; i < n; ++i) host[i] = vols[i]->V;
+  (void)cudaGetLastError();
+  bool ok = cudaMalloc(&b->d_vols, sizeof(Vol) * n) == cudaSuccess &&
+            cudaMalloc(&b->d_done, sizeof(int) * BD_COUNT) == cudaSuccess &&
+            cudaMallocHost(&b->frames, sizeof(BatchFrames)) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(b->d_vols, host.data(), sizeof(Vol) * n, cudaMemcpyHostToDevice, b->stream) == cudaSuccess &&
+       cudaMemsetAsync(b->d_done, 0, sizeof(int) * BD_COUNT, b->stream) == cudaSuccess &&
+       cudaStreamSynchronize(b->stream) == cudaSuccess;
+  if (!ok) {
+    (void)cudaGetLastError();
+    cudaFree(b->d_vols);
+    cudaFree(b->d_done);
+    if (b->frames) cudaFreeHost(b->frames);
+    delete b;
+    return VM_ERR_OOM;
+  }
+  memset(b->frames, 0, sizeof(BatchFrames));
+  *out = b;
+  return VM_OK;
+}
+
+vm_status vm_batch_destroy(vm_batch* b) {
+  if (!b) return VM_ERR_INVALID_ARG;
+  cudaStreamSynchronize(b->stream);
+  batch_drop_graph(b);
+  for (auto& r : b->tune_recs)
+    for (auto e : r.ev) cudaEventDestroy(e);
+  cudaFree(b->d_vols);
+  cudaFree(b->d_done);
+  cudaFreeHost(b->frames);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  delete b;
+  return VM_OK;
+}
+
+vm_status vm_batch_step(vm_batch* b, const float* const* depths, const vm_intrinsics* K, const float* T_wc,
+                        const float* T_cw, int flags, int use_graph) {
+  if (!b || !depths || !K || !T_wc || !T_cw || (flags & ~(VM_REFINE | VM_GC))) return VM_ERR_INVALID_ARG;
+  int tx = 1, ty = 1;
+  BatchFrames& bf = *b->frames;
+  for (int i = 0; i < b->n; ++i) {
+    if (b->vols[i]->diff_on) return VM_ERR_INVALID_ARG;
+    if (!make_frame(&K[i], T_wc + 16 * i, T_cw + 16 * i, depths[i], &bf.fp[i])) return VM_ERR_INVALID_ARG;
+    tx = std::max(tx, (bf.fp[i].W + ALLOC_TILE_W - 1) / ALLOC_TILE_W);
+    ty = std::max(ty, (bf.fp[i].H + ALLOC_TILE_H - 1) / ALLOC_TILE_H);
+  }
+  for (int i = 0; i < b->n; ++i) bf.advance[i] = b->vols[i]->advance_pending ? 1 : 0;
+  vm_status st = VM_OK;
+  if (b->tune_left > 0) {
+    // autotuning tick: eager launches, every kernel on its option (tick index mod 3)
+    TuneRec r;
+    r.opt = (int)(b->tune_recs.size() % SCHED_OPTS);
+    for (auto& e : r.ev) cudaEventCreate(&e);
+    int sc[SCHED_SLOTS];
+    for (int k = 0; k < SCHED_SLOTS; ++k) sc[k] = kSchedOptions[k][r.opt];
+    st = batch_enqueue(b, b->stream, sc, flags, tx, ty, &r);
+    b->tune_recs.push_back(r);
+    if (--b->tune_left == 0 && !st) st = batch_finish_tuning(b);
+  } else if (!use_graph) {
+    st = batch_enqueue(b, b->stream, b->sched, flags, tx, ty, nullptr);
+  } else {
+    if (!b->exec || b->graph_flags != flags || b->graph_tx != tx || b->graph_ty != ty) {
+      batch_drop_graph(b);
+      if (!b->cap_stream && cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        (void)cudaGetLastError();
+        b->cap_stream = nullptr;
+        return VM_ERR_CUDA;
+      }
+      if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return VM_ERR_CUDA;
+      }
+      vm_status s = batch_enqueue(b, b->cap_stream, b->sched, flags, tx, ty, nullptr);
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+      if (s || e != cudaSuccess) {
+        (void)cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        return s ? s : VM_ERR_CUDA;
+      }
+      b->graph = g;
+      b->alloc_node = find_kernel_node(g, batch_alloc_kernel(b->sched[0]));
+      e = b->alloc_node ? cudaGraphInstantiate(&b->exec, g, 0) : cudaErrorInvalidValue;
+      if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        b->exec = nullptr;
+        batch_drop_graph(b);
+        return VM_ERR_CUDA;
+      }
+      b->graph_flags = flags;
+      b->graph_tx = tx;
+      b->graph_ty = ty;
+    }
+    const Vol* dv = b->d_vols;
+    int n = b->n;
+    int* dd = b->d_done;
+    void* args[4] = {&dv, &n, b->frames, &dd};
+    cudaKernelNodeParams kp = {};
+    kp.func = batch_alloc_kernel(b->sched[0]);
+    kp.gridDim = dim3(tx, ty, b->n);
+    kp.blockDim = dim3(ALLOC_TILE_W * ALLOC_TILE_H / b->sched[0]);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    cudaError_t e = cudaGraphExecKernelNodeSetParams(b->exec, b->alloc_node, &kp);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->stream);
+    if (e != cudaSuccess) (void)cudaGetLastError();
+    st = cuda_status(e);
+  }
+  if (!st)
+    for (auto* v : b->vols) v->advance_pending = true;
+  return st;
+}
+
+vm_status vm_batch_tune(vm_batch* b, int rounds) {
+  if (!b || rounds < 1 || rounds > 100) return VM_ERR_INVALID_ARG;
+  for (auto& r : b->tune_recs)
+    for (auto e : r.ev) cudaEventDestroy(e);
+  b->tune_recs.clear();
+  memset(b->tune_ms, 0, sizeof(b->tune_ms));
+  memset(b->tune_cnt, 0, sizeof(b->tune_cnt));
+  b->tune_left = rounds * SCHED_OPTS;
+  return VM_OK;
+}
+
+vm_status vm_batch_schedule(vm_batch* b, int* sched, double* tuned_ms) {
+  if (!b || !sched) return VM_ERR_INVALID_ARG;
+  for (int k = 0; k < SCHED_SLOTS; ++k) sched[k] = b->sched[k];
+  if (tuned_ms)
+    for (int k = 0; k < SCHED_SLOTS; ++k)
+      for (int o = 0; o < SCHED_OPTS; ++o)
+        tuned_ms[k * SCHED_OPTS + o] = b->tune_cnt[k][o] ? b->tune_ms[k][o] / b->tune_cnt[k][o] : -1.0;
+  return VM_OK;
+}
+
+vm_status vm_batch_set_schedule(vm_batch* b, const int* sched) {
+  if (!b || !sched) return VM_ERR_INVALID_ARG;
+  for (int k = 0; k < SCHED_SLOTS; ++k) {
+    bool ok = false;
+    for (int o = 0; o < SCHED_OPTS; ++o) ok |= sched[k] == kSchedOptions[k][o];
+    if (!ok) return VM_ERR_INVALID_ARG;
+  }
+  for (int k = 0; k < SCHED_SLOTS; ++k) b->sched[k] = sched[k];
+  batch_drop_graph(b);
+  return VM_OK;
+}
+
+}  // extern "C"

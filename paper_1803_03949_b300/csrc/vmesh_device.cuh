@@ -261,12 +261,12 @@ __device__ __forceinline__ uint8_t atomic_and_u8(uint8_t* p, uint8_t bits) {
 
 // Last-block-done ticket: returns true in exactly one CTA of the grid, after every
 // other CTA has finished its work (threadfence reduction pattern; no waiting).
-__device__ __forceinline__ bool last_block(const Vol& V, int c_done) {
+__device__ __forceinline__ bool last_block_at(int* done) {
   __shared__ bool s_last;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
-    int t = atomicAdd(&V.ctl->c[c_done], 1);
+    int t = atomicAdd(done, 1);
     s_last = (t == (int)(gridDim.x * gridDim.y * gridDim.z) - 1);
   }
   __syncthreads();
@@ -276,6 +276,7 @@ __device__ __forceinline__ bool last_block(const Vol& V, int c_done) {
   }
   return false;
 }
+__device__ __forceinline__ bool last_block(const Vol& V, int c_done) { return last_block_at(&V.ctl->c[c_done]); }
 
 // Programmatic dependent launch: a kernel launched with programmatic stream serialization
 // may start while the previous kernel drains; it waits here (the hardware grid-dependency

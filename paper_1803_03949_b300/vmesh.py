@@ -51,7 +51,8 @@ EXPORTS = ["vm_create_volume", "vm_destroy_volume", "vm_set_stream", "vm_integra
            "vm_refine_mesh", "vm_gc", "vm_step", "vm_mesh_counts", "vm_download_mesh", "vm_get_stats",
            "vm_last_error", "vm_num_blocks", "vm_export_blocks", "vm_set_blocks", "vm_enable_timing",
            "vm_kernel_times", "vm_mesh_size_async", "vm_download_mesh_noalloc", "vm_diff_begin", "vm_diff_end",
-           "vm_grad_vertices", "vm_grad_depth", "vm_export_grad"]
+           "vm_grad_vertices", "vm_grad_depth", "vm_export_grad", "vm_batch_create", "vm_batch_destroy",
+           "vm_batch_step", "vm_batch_tune", "vm_batch_schedule", "vm_batch_set_schedule"]
 
 
 def load_library(path: str = LIB_PATH):
@@ -90,6 +91,12 @@ def load_library(path: str = LIB_PATH):
         "vm_grad_vertices": [vp, i64, vp, vp, vp],
         "vm_grad_depth": [vp, i, vp, P(vm_intrinsics), F16, F16, vp],
         "vm_export_grad": [vp, vp, vp],
+        "vm_batch_create": [P(vp), i, P(vp)],
+        "vm_batch_destroy": [vp],
+        "vm_batch_step": [vp, P(vp), P(vm_intrinsics), P(f), P(f), i, i],
+        "vm_batch_tune": [vp, i],
+        "vm_batch_schedule": [vp, P(i), P(ctypes.c_double)],
+        "vm_batch_set_schedule": [vp, P(i)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -313,6 +320,61 @@ class Volume:
         n = ctypes.c_int()
         _check(self._lib.vm_kernel_times(self._h, names, ms, cnt, cap, ctypes.byref(n)), "vm_kernel_times")
         return {names[i].decode(): (ms[i], cnt[i]) for i in range(n.value)}
+
+
+class Scenes:
+    """Independent volumes stepped together: one frame of every scene per tick, five launches
+    in total (optionally replayed from one CUDA graph), schedules picked by an autotuner."""
+
+    SLOTS = ["alloc_pixels_per_thread", "integrate_ctas_per_sm", "mesh_ctas_per_sm", "gc_vertices_ctas_per_sm",
+             "gc_blocks_ctas_per_sm"]
+
+    def __init__(self, volumes):
+        self._lib = load_library()
+        self.volumes = list(volumes)
+        n = len(self.volumes)
+        arr = (ctypes.c_void_p * n)(*[v._h.value for v in self.volumes])
+        h = ctypes.c_void_p()
+        _check(self._lib.vm_batch_create(arr, n, ctypes.byref(h)), "vm_batch_create")
+        self._h = h
+
+    def close(self):
+        h, self._h = getattr(self, "_h", None), None
+        if h is not None and h.value:
+            self._lib.vm_batch_destroy(h)
+
+    def __del__(self):
+        self.close()
+
+    def step_all(self, depths, intrinsics, poses, refine=True, gc=True, graph=True):
+        """depths: CUDA float32 (H, W) tensors, one per scene; intrinsics: Intrinsics per scene;
+        poses: (T_wc, T_cw) per scene (host 4x4, rounded to float32)."""
+        n = len(self.volumes)
+        assert len(depths) == len(intrinsics) == len(poses) == n
+        _contig_cuda(*depths)
+        dp = (ctypes.c_void_p * n)(*[_ptr(d) for d in depths])
+        ks = (vm_intrinsics * n)(*[k.c() for k in intrinsics])
+        twc = np.ascontiguousarray(np.stack([np.asarray(p[0], np.float32).reshape(16) for p in poses]))
+        tcw = np.ascontiguousarray(np.stack([np.asarray(p[1], np.float32).reshape(16) for p in poses]))
+        flags = (VM_REFINE if refine else 0) | (VM_GC if gc else 0)
+        fp = ctypes.POINTER(ctypes.c_float)
+        _check(self._lib.vm_batch_step(self._h, dp, ks, twc.ctypes.data_as(fp), tcw.ctypes.data_as(fp), flags,
+                                       int(bool(graph))), "vm_batch_step")
+
+    def tune(self, rounds: int = 2):
+        """Autotune on the next 3 * rounds ticks."""
+        _check(self._lib.vm_batch_tune(self._h, int(rounds)), "vm_batch_tune")
+
+    def schedule(self) -> dict:
+        sc = (ctypes.c_int * 5)()
+        ms = (ctypes.c_double * 15)()
+        _check(self._lib.vm_batch_schedule(self._h, sc, ms), "vm_batch_schedule")
+        return dict(schedule=dict(zip(self.SLOTS, list(sc))),
+                    tuned_ms={k: [ms[3 * i + o] for o in range(3)] for i, k in enumerate(self.SLOTS)})
+
+    def set_schedule(self, sched):
+        sc = (ctypes.c_int * 5)(*[int(x) for x in sched])
+        _check(self._lib.vm_batch_set_schedule(self._h, sc), "vm_batch_set_schedule")
 
 
 def _diff_mesh_function():
