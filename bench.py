@@ -9,6 +9,12 @@ integrate_depth + update_mesh(refine) + gc, replayed from a CUDA graph, depth al
 resident in HBM.  L2 is flushed (256 MB write) before every timed frame; each frame is
 timed with CUDA events on the volume's stream.
 
+The same JSON line also reports the two forms the method grows into, measured on the same
+GPU: "batched" (32 independent scenes of uneven sizes, one frame each per tick, five
+launches per tick from one CUDA graph, autotuned schedules, against the same scenes stepped
+one after another) and "differentiable" (forward and backward of the 60-frame sphere orbit
+with 50 leaf depth frames, against the plain path on the same frames).
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl vmesh|reference]
 With N > 1 (torchrun, one rank per GPU) every rank runs an independent replica on its own
 seeded scene (no data-path collective); value = frames of all ranks / max rank time.
@@ -205,6 +211,202 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def mesh_bytes(c):
+    return BYTES_MODEL["k_mesh"](c)
+
+
+def run_batched(args, stream, flush, peak):
+    """The batched form (BASELINE config 5 reading): `--batch-scenes` independent room scenes of
+    uneven sizes (floor plan scaled 1-3.5x, voxel 5-10 mm), one 640x480 frame of each per tick,
+    five launches per tick replayed from one CUDA graph, schedules autotuned on the first 6
+    warm-up ticks.  Against it: the same scenes and frames stepped one scene after another
+    through vm_step (one graph per scene) on fresh volumes.  L2 flushed before every tick."""
+    import torch
+
+    from paper_1803_03949_b300 import Intrinsics, Scenes, Volume
+
+    S, T, Wm, P = args.batch_scenes, args.batch_ticks, max(args.batch_warmup, 8), 5
+    n = Wm + T + P
+    scenes = synth.batch_scenes(S, n)
+    dev = [torch.from_numpy(np.stack([sc.depth(k) for k in range(n)])).cuda() for sc in scenes]
+    Ks = [Intrinsics(sc.W, sc.H, sc.fx, sc.fy, sc.cx, sc.cy) for sc in scenes]
+    poses = []
+    for sc in scenes:
+        pp = []
+        for k in range(n):
+            T4 = sc.pose(k)
+            pp.append((T4.astype(np.float32), synth.pose_inverse_f64(T4).astype(np.float32)))
+        poses.append(pp)
+
+    def tick_args(k):
+        return [d[k] for d in dev], Ks, [pp[k] for pp in poses]
+
+    def stat_sum(vols, key):
+        return sum(v.stats()[key] for v in vols)
+
+    def timed_ticks(step_tick, k0, k1):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k1 - k0)]
+        for i, k in enumerate(range(k0, k1)):
+            flush.fill_(k)
+            evs[i][0].record(stream)
+            step_tick(k)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in evs]
+
+    # batched
+    vols = [Volume.from_config(sc.volume, stream=stream) for sc in scenes]
+    batch = Scenes(vols)
+    batch.tune(2)
+    for k in range(Wm):
+        batch.step_all(*tick_args(k), graph=True)
+    torch.cuda.synchronize()
+    c0, u0 = stat_sum(vols, "collected_blocks"), stat_sum(vols, "meshed_blocks")
+    ms = timed_ticks(lambda k: batch.step_all(*tick_args(k), graph=True), Wm, Wm + T)
+    c1, u1 = stat_sum(vols, "collected_blocks"), stat_sum(vols, "meshed_blocks")
+    # per-kernel times on P more ticks (eager launches with events) and their work counters
+    before = [v.stats() for v in vols]
+    batch.profile(P)
+    for k in range(Wm + T, n):
+        flush.fill_(k)
+        batch.step_all(*tick_args(k), graph=True)
+    kms = batch.kernel_ms()
+    after = [v.stats() for v in vols]
+    work = dict(update_blocks=0, frame_blocks=0, changed=0, emitted=0, released=0, refreshed=0, created=0)
+    for a0, a1 in zip(before, after):
+        work["update_blocks"] += (a1["meshed_blocks"] - a0["meshed_blocks"]) % (1 << 32)
+        work["frame_blocks"] += (a1["collected_blocks"] - a0["collected_blocks"]) % (1 << 32)
+        work["changed"] += a1["changed_cubes"] - a0["changed_cubes"]
+        work["emitted"] += a1["emitted_triangles"] - a0["emitted_triangles"]
+        work["released"] += a1["released_triangles"] - a0["released_triangles"]
+        work["refreshed"] += a1["refreshed_vertices"] - a0["refreshed_vertices"]
+        work["created"] += a1["created_vertices"] - a0["created_vertices"]
+    roof = {}
+    for name, model in (("kb_mesh", mesh_bytes), ("kb_integrate", BYTES_MODEL["k_integrate"])):
+        t_ms = kms[name] * kms["ticks"]
+        if t_ms > 0:
+            gbs = model(work) / (t_ms / 1000.0) / 1e9
+            roof[name] = {"avg_launch_us": 1000.0 * kms[name], "achieved": gbs, "peak": peak, "unit": "GB/s",
+                          "frac": gbs / peak, "bytes_per_launch": model(work) / kms["ticks"]}
+    sched = batch.schedule()
+    active = sorted(v.stats()["live_blocks"] for v in vols)
+    for v in vols:
+        v.check()
+    batch.close()
+    for v in vols:
+        v.close()
+    del vols
+    torch.cuda.empty_cache()
+
+    # the same scenes one after another through vm_step
+    vols = [Volume.from_config(sc.volume, stream=stream) for sc in scenes]
+
+    def seq_tick(k):
+        for v, d, K, pp in zip(vols, dev, Ks, poses):
+            v.step(d[k], K, *pp[k], refine=True, gc=True, graph=True)
+
+    for k in range(Wm):
+        seq_tick(k)
+    torch.cuda.synchronize()
+    ms_seq = timed_ticks(seq_tick, Wm, Wm + T)
+    for v in vols:
+        v.check()
+        v.close()
+    del vols, dev
+    torch.cuda.empty_cache()
+    tot, tot_seq = sum(ms) / 1000.0, sum(ms_seq) / 1000.0
+    return {
+        "workload": "%d room scenes (floor plan 6x4 m scaled 1-3.5x log-uniform, 3 m high, 20 primitives, "
+                    "voxel 5-10 mm, trunc 4 voxels), 640x480 float32 depth, one frame of each per tick; "
+                    "integrate + incremental mesh + refine + gc" % S,
+        "scenes": S, "ticks": T, "warmup_ticks": Wm, "value": S * T / tot, "unit": "scene-frames/s",
+        "ms_per_tick": 1000.0 * tot / T, "voxels_per_s": 512 * ((c1 - c0) % (1 << 32)) / tot,
+        "mean_blocks_per_tick": ((c1 - c0) % (1 << 32)) / T, "mean_update_blocks_per_tick": ((u1 - u0) % (1 << 32)) / T,
+        "launches_per_tick": 5, "graph": True, "l2": "flushed before every tick (256 MB write)",
+        "sequential": {"value": S * T / tot_seq, "unit": "scene-frames/s", "ms_per_tick": 1000.0 * tot_seq / T,
+                       "how": "the same frames through vm_step, one CUDA graph per scene, scenes one after another"},
+        "speedup_vs_sequential": tot_seq / tot,
+        "schedule": sched["schedule"], "tuned_ms_per_option": sched["tuned_ms"],
+        "kernel_ms_per_tick": {k: v for k, v in kms.items() if k != "ticks"}, "profiled_ticks": kms["ticks"],
+        "roofline": roof,
+        "active_blocks": {"min": active[0], "median": active[len(active) // 2], "max": active[-1]},
+    }
+
+
+def run_differentiable(args, stream):
+    """The differentiable form (BASELINE config 4 reading): the sphere orbit extended to 60
+    frames, frames 0-9 integrated as constants, frames 10-59 leaf tensors; forward = the 50
+    recorded integrations + one full refined mesh + download, backward = loss.backward()
+    (vertex -> TSDF -> depth kernels, 50 reverse steps).  Against it: the plain path on the
+    same frames (50 integrations + full refined mesh + download).  CUDA events; median of 5."""
+    import torch
+
+    from paper_1803_03949_b300 import Intrinsics, Volume, diff_mesh
+
+    sc = synth.sphere_scene(num_frames=60)
+    K = Intrinsics(sc.W, sc.H, sc.fx, sc.fy, sc.cx, sc.cy)
+    dev = [torch.from_numpy(sc.depth(k)).cuda() for k in range(60)]
+    poses = []
+    for k in range(60):
+        T4 = sc.pose(k)
+        poses.append((T4.astype(np.float32), synth.pose_inverse_f64(T4).astype(np.float32)))
+    c = torch.tensor([0.0, 0.0, 0.3], device="cuda")
+
+    def loss_fn(pos, nrm):
+        r = pos - c
+        dist = torch.linalg.norm(r, dim=1)
+        sph = dist - 0.3 <= pos[:, 2]
+        sdf = torch.where(sph, dist - 0.3, pos[:, 2])
+        up = torch.zeros_like(pos)
+        up[:, 2] = 1.0
+        u = torch.where(sph[:, None], r / dist[:, None], up)
+        return (sdf ** 2).mean() + 0.1 * (1.0 - (nrm * u).sum(1)).mean()
+
+    plain, fwd, bwd, nverts = [], [], [], 0
+    for rep in range(5):
+        v = Volume.from_config(sc.volume, stream=stream)
+        for k in range(10):
+            v.integrate(dev[k], K, *poses[k])
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record(stream)
+        for k in range(10, 60):
+            v.integrate(dev[k], K, *poses[k])
+        v.update_mesh(full=True, refine=True)
+        m = v.download(device=True)
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        plain.append(e[0].elapsed_time(e[1]))
+        v.close()
+        v = Volume.from_config(sc.volume, stream=stream)
+        for k in range(10):
+            v.integrate(dev[k], K, *poses[k])
+        leaves = [d.clone().requires_grad_(True) for d in dev[10:]]
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        pos, nrm, tris, keys = diff_mesh(v, K, poses[10:], leaves, refine=True)
+        e[1].record(stream)
+        loss = loss_fn(pos, nrm)
+        e[2].record(stream)
+        loss.backward()
+        e[3].record(stream)
+        torch.cuda.synchronize()
+        fwd.append(e[0].elapsed_time(e[1]))
+        bwd.append(e[2].elapsed_time(e[3]))
+        nverts = int(pos.shape[0])
+        v.check()
+        v.close()
+    med = statistics.median
+    return {
+        "workload": "sphere orbit 320x240, 60 frames (0-9 constant, 10-59 leaf depth tensors), voxel 1 cm; "
+                    "loss = mean sdf^2 + 0.1 mean(1 - n . grad sdf / |grad sdf|)",
+        "plain_forward_ms": med(plain), "diff_forward_ms": med(fwd), "backward_ms": med(bwd),
+        "forward_overhead": med(fwd) / med(plain), "backward_over_forward": med(bwd) / med(fwd),
+        "vertices": nverts, "leaf_pixels": 50 * sc.W * sc.H,
+        "timing": "CUDA events on the volume's stream, median of 5 runs, caches warm",
+    }
+
+
 def run_vmesh(args, rank, world, local):
     import torch
 
@@ -385,6 +587,9 @@ def run_vmesh(args, rank, world, local):
         "gpu_launches": launches_total,
         "clocks": cs.summary(),
     }
+    if not args.skip_forms:
+        line["batched"] = run_batched(args, stream, flush, peak)
+        line["differentiable"] = run_differentiable(args, stream)
     print(json.dumps(line), flush=True)
 
 
@@ -400,6 +605,10 @@ def main():
     ap.add_argument("--no-kernel-timing", action="store_true",
                     help="time frames without per-kernel event nodes (no roofline)")
     ap.add_argument("--cpu-frames", type=int, default=200)
+    ap.add_argument("--skip-forms", action="store_true", help="skip the batched and differentiable forms")
+    ap.add_argument("--batch-scenes", type=int, default=32)
+    ap.add_argument("--batch-ticks", type=int, default=60)
+    ap.add_argument("--batch-warmup", type=int, default=10)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

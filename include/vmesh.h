@@ -307,6 +307,14 @@ vm_status vm_batch_tune(vm_batch* batch, int rounds);
 vm_status vm_batch_schedule(vm_batch* batch, int* sched, double* tuned_ms);
 vm_status vm_batch_set_schedule(vm_batch* batch, const int* sched);
 
+/* Profile the next `ticks` (1..100000) steps: they run eagerly with the current schedule and
+ * CUDA events around each of the five kernels (event-record work adds device time).
+ * vm_batch_kernel_ms synchronises and writes the mean milliseconds per profiled tick of
+ * each kernel (block collection, fusion, mesh, vertex gc, block gc; -1 when none was
+ * profiled) and the number of profiled ticks (optional). */
+vm_status vm_batch_profile(vm_batch* batch, int ticks);
+vm_status vm_batch_kernel_ms(vm_batch* batch, double* ms, int* ticks);
+
 #ifdef __cplusplus
 }
 #endif

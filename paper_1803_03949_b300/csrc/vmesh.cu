@@ -1097,6 +1097,11 @@ struct vm_batch {
   std::vector<TuneRec> tune_recs;
   double tune_ms[SCHED_SLOTS][SCHED_OPTS] = {};
   int tune_cnt[SCHED_SLOTS][SCHED_OPTS] = {};
+  // profiling: ticks still to time with the current schedule, their records, totals
+  int prof_left = 0;
+  std::vector<TuneRec> prof_recs;
+  double prof_ms[SCHED_SLOTS] = {};
+  int prof_cnt = 0;
   BatchFrames* frames = nullptr;  // host staging of the launch argument (8.5 KB)
 };
 
@@ -1223,6 +1228,8 @@ vm_status vm_batch_destroy(vm_batch* b) {
   batch_drop_graph(b);
   for (auto& r : b->tune_recs)
     for (auto e : r.ev) cudaEventDestroy(e);
+  for (auto& r : b->prof_recs)
+    for (auto e : r.ev) cudaEventDestroy(e);
   cudaFree(b->d_vols);
   cudaFree(b->d_done);
   cudaFreeHost(b->frames);
@@ -1254,6 +1261,13 @@ vm_status vm_batch_step(vm_batch* b, const float* const* depths, const vm_intrin
     st = batch_enqueue(b, b->stream, sc, flags, tx, ty, &r);
     b->tune_recs.push_back(r);
     if (--b->tune_left == 0 && !st) st = batch_finish_tuning(b);
+  } else if (b->prof_left > 0) {
+    TuneRec r;
+    r.opt = -1;
+    for (auto& e : r.ev) cudaEventCreate(&e);
+    st = batch_enqueue(b, b->stream, b->sched, flags, tx, ty, &r);
+    b->prof_recs.push_back(r);
+    --b->prof_left;
   } else if (!use_graph) {
     st = batch_enqueue(b, b->stream, b->sched, flags, tx, ty, nullptr);
   } else {
@@ -1328,6 +1342,34 @@ vm_status vm_batch_schedule(vm_batch* b, int* sched, double* tuned_ms) {
     for (int k = 0; k < SCHED_SLOTS; ++k)
       for (int o = 0; o < SCHED_OPTS; ++o)
         tuned_ms[k * SCHED_OPTS + o] = b->tune_cnt[k][o] ? b->tune_ms[k][o] / b->tune_cnt[k][o] : -1.0;
+  return VM_OK;
+}
+
+vm_status vm_batch_profile(vm_batch* b, int ticks) {
+  if (!b || ticks < 1 || ticks > 100000) return VM_ERR_INVALID_ARG;
+  for (auto& r : b->prof_recs)
+    for (auto e : r.ev) cudaEventDestroy(e);
+  b->prof_recs.clear();
+  memset(b->prof_ms, 0, sizeof(b->prof_ms));
+  b->prof_cnt = 0;
+  b->prof_left = ticks;
+  return VM_OK;
+}
+
+vm_status vm_batch_kernel_ms(vm_batch* b, double* ms, int* ticks) {
+  if (!b || !ms) return VM_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return VM_ERR_CUDA;
+  for (auto& r : b->prof_recs) {
+    for (int k = 0; k < SCHED_SLOTS; ++k) {
+      float t = 0;
+      if (cudaEventElapsedTime(&t, r.ev[k], r.ev[k + 1]) == cudaSuccess) b->prof_ms[k] += t;
+    }
+    ++b->prof_cnt;
+    for (auto e : r.ev) cudaEventDestroy(e);
+  }
+  b->prof_recs.clear();
+  for (int k = 0; k < SCHED_SLOTS; ++k) ms[k] = b->prof_cnt ? b->prof_ms[k] / b->prof_cnt : -1.0;
+  if (ticks) *ticks = b->prof_cnt;
   return VM_OK;
 }
 

@@ -52,7 +52,8 @@ EXPORTS = ["vm_create_volume", "vm_destroy_volume", "vm_set_stream", "vm_integra
            "vm_last_error", "vm_num_blocks", "vm_export_blocks", "vm_set_blocks", "vm_enable_timing",
            "vm_kernel_times", "vm_mesh_size_async", "vm_download_mesh_noalloc", "vm_diff_begin", "vm_diff_end",
            "vm_grad_vertices", "vm_grad_depth", "vm_export_grad", "vm_batch_create", "vm_batch_destroy",
-           "vm_batch_step", "vm_batch_tune", "vm_batch_schedule", "vm_batch_set_schedule"]
+           "vm_batch_step", "vm_batch_tune", "vm_batch_schedule", "vm_batch_set_schedule", "vm_batch_profile",
+           "vm_batch_kernel_ms"]
 
 
 def load_library(path: str = LIB_PATH):
@@ -97,6 +98,8 @@ def load_library(path: str = LIB_PATH):
         "vm_batch_tune": [vp, i],
         "vm_batch_schedule": [vp, P(i), P(ctypes.c_double)],
         "vm_batch_set_schedule": [vp, P(i)],
+        "vm_batch_profile": [vp, i],
+        "vm_batch_kernel_ms": [vp, P(ctypes.c_double), P(i)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -371,6 +374,18 @@ class Scenes:
         _check(self._lib.vm_batch_schedule(self._h, sc, ms), "vm_batch_schedule")
         return dict(schedule=dict(zip(self.SLOTS, list(sc))),
                     tuned_ms={k: [ms[3 * i + o] for o in range(3)] for i, k in enumerate(self.SLOTS)})
+
+    KERNELS = ["kb_alloc", "kb_integrate", "kb_mesh", "kb_gc_vertices", "kb_gc_blocks"]
+
+    def profile(self, ticks: int):
+        """Time each kernel (CUDA events, eager launches) over the next `ticks` steps."""
+        _check(self._lib.vm_batch_profile(self._h, int(ticks)), "vm_batch_profile")
+
+    def kernel_ms(self) -> dict:
+        ms = (ctypes.c_double * 5)()
+        n = ctypes.c_int()
+        _check(self._lib.vm_batch_kernel_ms(self._h, ms, ctypes.byref(n)), "vm_batch_kernel_ms")
+        return dict(zip(self.KERNELS, list(ms)), ticks=n.value)
 
     def set_schedule(self, sched):
         sc = (ctypes.c_int * 5)(*[int(x) for x in sched])

@@ -93,6 +93,7 @@ class Scene:
         self.W, self.H = W.value, H.value
         self.fx, self.fy, self.cx, self.cy = list(intr)
         self.num_frames = lib.synth_num_frames(handle)
+        self.max_range = None  # depth beyond this (metres) reads as invalid, like a sensor's range
 
     def __del__(self):
         h, self._h = getattr(self, "_h", None), None
@@ -120,6 +121,8 @@ class Scene:
         out = np.zeros((self.H, self.W), np.float32)
         if self._lib.synth_render(self._h, int(k), out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))) != 0:
             raise IndexError(k)
+        if self.max_range is not None:
+            out[out > self.max_range] = 0.0
         return out
 
     def sdf(self, pts: np.ndarray, with_grad: bool = False):
@@ -175,6 +178,31 @@ def floor_scene(num_frames: int = 2000, seed: int = SEED_BASE + 3) -> Scene:
     vol = VolumeConfig(voxel_size=0.005, trunc=0.02, hash_buckets=1 << 23, max_blocks=1 << 21,
                        max_vertices=1 << 25, max_triangles=1 << 26)
     return Scene(h, lib, "floor_20x20x4_640x480_l5mm", vol)
+
+
+def batch_scenes(num_scenes: int = 32, num_frames: int = 100, seed: int = SEED_BASE + 5) -> list:
+    """Independent scenes of uneven sizes for the batched workload: the room recipe with its
+    6 x 4 m floor plan scaled by a log-uniform factor in [1, 3.5] (height 3 m, 20 primitives),
+    voxel l drawn from {5, 6, ..., 10} mm, truncation 4 l,
+    640 x 480 depth with the room noise model and a 4.5 m sensor range (farther depth reads as
+    invalid, as on a structured-light camera); each scene has its own seed and trajectory."""
+    lib = _load()
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(num_scenes):
+        scale = float(np.exp(rng.uniform(0.0, np.log(3.5))))
+        l = int(rng.integers(5, 11)) * 1e-3
+        sx, sy = 6.0 * scale, 4.0 * scale
+        nprims = 20
+        h = lib.synth_create_room(seed + 1000 * (i + 1), num_frames, 640, 480, 525.0, 525.0, 319.5, 239.5, sx, sy, 3.0,
+                                  nprims, 0.0012, 0.02)
+        mb = 1 << 18 if l <= 0.006 else (1 << 17 if l <= 0.008 else 1 << 16)
+        vol = VolumeConfig(voxel_size=l, trunc=4 * l, hash_buckets=4 * mb, max_blocks=mb, max_vertices=64 * mb,
+                           max_triangles=128 * mb)
+        sc = Scene(h, lib, "room_%.1fx%.1fx3_640x480_l%dmm" % (sx, sy, round(l * 1000)), vol)
+        sc.max_range = 4.5
+        out.append(sc)
+    return out
 
 
 def small_room_scene(num_frames: int = 8, seed: int = SEED_BASE + 12, W: int = 96, H: int = 72) -> Scene:
