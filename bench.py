@@ -514,6 +514,7 @@ def run_vmesh(args, rank, world, local):
         ms, collected, meshed = streamed(vol)
         torch.cuda.synchronize()
     barrier(world)
+    mem = vol.mesh_memory()
     vol.close()
     total_ms = sum(ms)
     max_ms = reduce_max(total_ms, world)
@@ -586,6 +587,15 @@ def run_vmesh(args, rank, world, local):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * W * H, "d2h_bytes_per_step": 8},
         "gpu_launches": launches_total,
         "clocks": cs.summary(),
+        "mesh_memory": {
+            "after_frames": n, "vertices": mem["vertices"], "triangles": mem["triangles"],
+            "per_block_extraction_vertices": mem["block_vertices"], "loose_triangle_vertices": mem["loose_vertices"],
+            "per_block_over_ours": mem["block_vertices"] / max(mem["vertices"], 1),
+            "loose_over_ours": mem["loose_vertices"] / max(mem["vertices"], 1),
+            "blocks": mem["blocks"], "cube_bytes": mem["cube_bytes"], "paper_cube_bytes": 56,
+            "paper_compact_cube_bytes": 24, "bytes_in_use": mem["bytes_in_use"],
+            "bytes_allocated": mem["bytes_allocated"],
+        },
     }
     if not args.skip_forms:
         line["batched"] = run_batched(args, stream, flush, peak)

@@ -172,6 +172,25 @@ vm_status vm_download_mesh(vm_volume* vol, float* pos, float* nrm, int32_t* tris
  * next gc will recycle. */
 vm_status vm_mesh_size_async(vm_volume* vol, int32_t* dst, int on_device);
 
+/* Mesh memory (Sec. VI-B "Memory"; the paper compares vertex counts with a mesher whose
+ * blocks share no vertices, and states 56 bytes per cube for its own structure). */
+typedef struct {
+  int64_t vertices;        /* referenced vertices of the edge-owned mesh (each stored once) */
+  int64_t triangles;       /* triangles */
+  int64_t block_vertices;  /* vertices a per-block extraction stores: shared by the cubes of
+                              one block, copied in every block whose cubes use them */
+  int64_t loose_vertices;  /* 3 per triangle: every triangle with its own corners */
+  int64_t blocks;          /* allocated blocks */
+  int64_t cube_bytes;      /* bytes per cube (voxel) of this layout: (d, W) 8, two types 2,
+                              vertex flags 1, vertex ids of the 3 owned edges 12, triangle run 4 */
+  int64_t bytes_in_use;    /* blocks x (512 cubes + block record) + vertices x 40 +
+                              triangles x 16 + hash buckets x 16 */
+  int64_t bytes_allocated; /* device memory the volume holds (pool capacities) */
+} vm_mesh_memory;
+
+/* Synchronises and fills *m (runs a counting kernel over the allocated blocks). */
+vm_status vm_mesh_memory_stats(vm_volume* vol, vm_mesh_memory* m);
+
 /* Synchronises and fills *stats. */
 vm_status vm_get_stats(vm_volume* vol, vm_frame_stats* stats);
 

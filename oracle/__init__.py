@@ -71,6 +71,7 @@ def _lib(prec: str):
         lib.or_grad_vertices.argtypes = [vp, i64, P(ctypes.c_uint64), P(d), P(d)]
         lib.or_grad_export.argtypes = [vp, P(d)]
         lib.or_grad_depth.argtypes = [vp, i, i, P(d)]
+        lib.or_mesh_memory.argtypes = [vp, P(i64)]
         lib.or_set_voxel.restype = i
         lib.or_set_voxel.argtypes = [vp, i, i, i, d]
         _loaded[prec] = lib
@@ -178,6 +179,13 @@ class Volume:
         self._lib.or_stats(self._h, _ptr(out, ctypes.c_int64))
         return dict(cells=int(out[0]), voxels_integrated=int(out[1]), frame_blocks=int(out[2]),
                     update_blocks=int(out[3]), epoch=int(out[4]), truncated=int(out[5]))
+
+    def mesh_memory(self) -> dict:
+        """dict(vertices, block_vertices, loose_vertices, triangles) of the current mesh."""
+        out = np.zeros(4, np.int64)
+        self._lib.or_mesh_memory(self._h, _ptr(out, ctypes.c_int64))
+        return dict(vertices=int(out[0]), block_vertices=int(out[1]), loose_vertices=int(out[2]),
+                    triangles=int(out[3]))
 
     # ------------------------------------------------------------ differentiable path
     def diff_begin(self) -> None:

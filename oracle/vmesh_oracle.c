@@ -1035,3 +1035,51 @@ int or_set_voxel(void* h, int gx, int gy, int gz, double d) {
   V->blocks[b]->tsdf[(gx - 8 * bx) + 8 * (gy - 8 * by) + 64 * (gz - 8 * bz)] = (real)d;
   return 1;
 }
+
+/* ------------------------------------------------------------ mesh memory (Sec. VI-B) */
+/* Vertex counts of meshes that share fewer vertices, from the effective types: out[0] the
+ * distinct edges used over all blocks (this mesh), out[1] the sum over blocks of the
+ * distinct edges used by each block's own cubes (a per-block extraction), out[2] three per
+ * triangle (loose triangles), out[3] the triangles. */
+void or_mesh_memory(void* h, int64_t* out) {
+  ovol* V = (ovol*)h;
+  int64_t total = 0, per_block = 0, ntri = 0;
+  uint64_t* all = NULL;
+  int64_t nall = 0, call = 0;
+  uint64_t* loc = (uint64_t*)malloc(sizeof(uint64_t) * BV * 15);
+  for (int b = 0; b < V->nblocks; ++b) {
+    const oblock* B = V->blocks[b];
+    if (!B->alive) continue;
+    int64_t nloc = 0;
+    for (int i = 0; i < BV; ++i) {
+      int e = B->code_eff[i];
+      int cg[3] = {B->key[0] * BS + i % 8, B->key[1] * BS + (i / 8) % 8, B->key[2] * BS + i / 64};
+      ntri += tri_n[e];
+      for (int t = 0; t < tri_n[e]; ++t)
+        for (int j = 0; j < 3; ++j) {
+          int ek = tri_e[e][t][j];
+          const int* off = CORNER[EDGE[ek][0]];
+          loc[nloc++] = edge_key(cg[0] + off[0], cg[1] + off[1], cg[2] + off[2], edge_axis(ek));
+        }
+    }
+    qsort(loc, (size_t)nloc, sizeof(uint64_t), cmp_u64);
+    for (int64_t j = 0; j < nloc; ++j) {
+      if (j > 0 && loc[j] == loc[j - 1]) continue;
+      ++per_block;
+      if (nall == call) {
+        call = call ? 2 * call : 4096;
+        all = (uint64_t*)realloc(all, sizeof(uint64_t) * (size_t)call);
+      }
+      all[nall++] = loc[j];
+    }
+  }
+  if (nall) qsort(all, (size_t)nall, sizeof(uint64_t), cmp_u64);
+  for (int64_t j = 0; j < nall; ++j)
+    if (j == 0 || all[j] != all[j - 1]) ++total;
+  free(all);
+  free(loc);
+  out[0] = total;
+  out[1] = per_block;
+  out[2] = 3 * ntri;
+  out[3] = ntri;
+}

@@ -14,6 +14,7 @@
 #include "kernels_fusion.cuh"
 #include "kernels_gc.cuh"
 #include "kernels_io.cuh"
+#include "kernels_memory.cuh"
 #include "kernels_mesh.cuh"
 #include "mc_table.h"
 #include "vmesh_device.cuh"
@@ -53,6 +54,7 @@ struct vm_volume {
   int num_sms = 148;
   bool advance_pending = false;
   std::vector<void*> allocs;
+  size_t bytes_allocated = 0;  // device memory held through allocs
   // download scratch
   int* cta_counts = nullptr;
   int* scan_total = nullptr;
@@ -147,6 +149,7 @@ bool dalloc(vm_volume* v, T** p, size_t count, int fill_byte) {
   if (bytes == 0) bytes = sizeof(T);
   if (cudaMalloc(&q, bytes) != cudaSuccess) return false;
   v->allocs.push_back(q);
+  v->bytes_allocated += bytes;
   if (cudaMemsetAsync(q, fill_byte, bytes, v->cur) != cudaSuccess) return false;
   *p = static_cast<T*>(q);
   return true;
@@ -571,6 +574,46 @@ vm_status vm_mesh_counts(vm_volume* v, int64_t* nv, int64_t* nt) {
   if ((st = count_live(v, true, &b))) return st;
   *nv = a;
   *nt = b;
+  return VM_OK;
+}
+
+vm_status vm_mesh_memory_stats(vm_volume* v, vm_mesh_memory* m) {
+  if (!v || !m) return VM_ERR_INVALID_ARG;
+  int64_t nv = 0, nt = 0;
+  vm_status st = vm_mesh_counts(v, &nv, &nt);
+  if (st) return st;
+  unsigned long long* d = nullptr;
+  unsigned long long bv = 0;
+  (void)cudaGetLastError();
+  bool ok = cudaMalloc(&d, sizeof(*d)) == cudaSuccess && cudaMemsetAsync(d, 0, sizeof(*d), v->stream) == cudaSuccess;
+  if (ok) {
+    k_block_vertices<<<grid_for(v, 8), 128, 0, v->stream>>>(v->V, d);
+    ok = cudaGetLastError() == cudaSuccess &&
+         cudaMemcpyAsync(&bv, d, sizeof(bv), cudaMemcpyDeviceToHost, v->stream) == cudaSuccess &&
+         cudaStreamSynchronize(v->stream) == cudaSuccess;
+  }
+  cudaFree(d);
+  if (!ok) {
+    (void)cudaGetLastError();
+    return VM_ERR_CUDA;
+  }
+  const int64_t blocks = read_counter(v, C_LIVE_BLOCKS);
+  // per voxel (cube): (d, W) 8, current and previous type 2, vertex flags 1, vertex ids of
+  // the 3 owned edges 12, triangle-run start 4
+  const int64_t cube = 8 + 2 + 1 + 12 + 4;
+  // per block: key + bucket 16, neighbour table 64, triangle/vertex counts 8, near flag 1,
+  // three stamps 12; per vertex: position 16, normal 16, reference count 4, owning edge 4;
+  // per triangle: 16; per hash bucket: key 8, block index 4, stamp 4
+  const int64_t per_block = 16 + 64 + 8 + 1 + 12, per_vertex = 40, per_tri = 16, per_bucket = 16;
+  m->vertices = nv;
+  m->triangles = nt;
+  m->block_vertices = (int64_t)bv;
+  m->loose_vertices = 3 * nt;
+  m->blocks = blocks;
+  m->cube_bytes = cube;
+  m->bytes_in_use = blocks * (BV * cube + per_block) + nv * per_vertex + nt * per_tri +
+                    (int64_t)(v->V.hmask + 1) * per_bucket;
+  m->bytes_allocated = (int64_t)v->bytes_allocated;
   return VM_OK;
 }
 

@@ -45,6 +45,12 @@ class vm_frame_stats(ctypes.Structure):
         "collected_blocks", "meshed_blocks")]
 
 
+class vm_mesh_memory(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "vertices", "triangles", "block_vertices", "loose_vertices", "blocks", "cube_bytes", "bytes_in_use",
+        "bytes_allocated")]
+
+
 _lib = None
 
 EXPORTS = ["vm_create_volume", "vm_destroy_volume", "vm_set_stream", "vm_integrate_depth", "vm_update_mesh",
@@ -53,7 +59,7 @@ EXPORTS = ["vm_create_volume", "vm_destroy_volume", "vm_set_stream", "vm_integra
            "vm_kernel_times", "vm_mesh_size_async", "vm_download_mesh_noalloc", "vm_diff_begin", "vm_diff_end",
            "vm_grad_vertices", "vm_grad_depth", "vm_export_grad", "vm_batch_create", "vm_batch_destroy",
            "vm_batch_step", "vm_batch_tune", "vm_batch_schedule", "vm_batch_set_schedule", "vm_batch_profile",
-           "vm_batch_kernel_ms"]
+           "vm_batch_kernel_ms", "vm_mesh_memory_stats"]
 
 
 def load_library(path: str = LIB_PATH):
@@ -99,6 +105,7 @@ def load_library(path: str = LIB_PATH):
         "vm_batch_schedule": [vp, P(i), P(ctypes.c_double)],
         "vm_batch_set_schedule": [vp, P(i)],
         "vm_batch_profile": [vp, i],
+        "vm_mesh_memory_stats": [vp, P(vm_mesh_memory)],
         "vm_batch_kernel_ms": [vp, P(ctypes.c_double), P(i)],
     }
     for name, args in sig.items():
@@ -212,6 +219,12 @@ class Volume:
         s = vm_frame_stats()
         _check(self._lib.vm_get_stats(self._h, ctypes.byref(s)), "vm_get_stats")
         return {n: getattr(s, n) for n, _ in vm_frame_stats._fields_}
+
+    def mesh_memory(self) -> dict:
+        """Vertex counts of this mesh against per-block and loose-triangle meshes, and bytes."""
+        m = vm_mesh_memory()
+        _check(self._lib.vm_mesh_memory_stats(self._h, ctypes.byref(m)), "vm_mesh_memory_stats")
+        return {n: getattr(m, n) for n, _ in vm_mesh_memory._fields_}
 
     def num_blocks(self) -> int:
         n = ctypes.c_int64()
