@@ -9,8 +9,8 @@ integrate_depth + update_mesh(refine) + gc, replayed from a CUDA graph, depth al
 resident in HBM.  L2 is flushed (256 MB write) before every timed frame; each frame is
 timed with CUDA events on the volume's stream.
 
-The same JSON line also reports the two forms the method grows into, measured on the same
-GPU: "batched" (32 independent scenes of uneven sizes, one frame each per tick, five
+The same JSON line also reports the large workload ("large": the 20x20x4 m floor at 5 mm)
+and the two forms the method grows into, measured on the same GPU: "batched" (32 independent scenes of uneven sizes, one frame each per tick, five
 launches per tick from one CUDA graph, autotuned schedules, against the same scenes stepped
 one after another) and "differentiable" (forward and backward of the 60-frame sphere orbit
 with 50 leaf depth frames, against the plain path on the same frames).
@@ -333,6 +333,85 @@ def run_batched(args, stream, flush, peak):
     }
 
 
+def run_large(args, stream, flush, peak):
+    """The large workload (BASELINE config 3): the 20x20x4 m floor of 4x4 rooms, 640x480,
+    voxel 5 mm, truncation 2 cm, 2^23 buckets; the first `--large-frames` frames after 10
+    warm-up frames of the configuration's 2000-frame trajectory (the default keeps the
+    benchmark within minutes; `--large-frames 1990` runs all of it), each
+    frame integrate + update(refine) + gc from the frame graph, enqueued back to back, L2
+    flushed before every frame.  A second pass on a fresh volume times k_mesh and
+    k_integrate with event nodes for their roofline."""
+    import torch
+
+    from paper_1803_03949_b300 import Intrinsics, Volume
+
+    T, Wm = args.large_frames, 10
+    n = Wm + T
+    sc = synth.floor_scene()  # the configuration's 2000-frame trajectory, its first n frames
+    dev = torch.from_numpy(np.stack([sc.depth(k) for k in range(n)])).cuda()
+    K = Intrinsics(sc.W, sc.H, sc.fx, sc.fy, sc.cx, sc.cy)
+    poses = []
+    for k in range(n):
+        T4 = sc.pose(k)
+        poses.append((T4.astype(np.float32), synth.pose_inverse_f64(T4).astype(np.float32)))
+
+    def run(timing):
+        v = Volume.from_config(sc.volume, stream=stream)
+        for k in range(Wm):
+            v.step(dev[k], K, *poses[k], refine=True, gc=True, graph=True)
+        if timing:
+            v.enable_timing(["k_mesh", "k_integrate"])
+        torch.cuda.synchronize()
+        s0 = v.stats()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(T)]
+        work = dict(update_blocks=0, frame_blocks=0, changed=0, emitted=0, released=0, refreshed=0, created=0)
+        prev = s0
+        for i, k in enumerate(range(Wm, n)):
+            flush.fill_(k)
+            evs[i][0].record(stream)
+            v.step(dev[k], K, *poses[k], refine=True, gc=True, graph=True)
+            evs[i][1].record(stream)
+            if timing:  # per-frame work counters for the byte model
+                st = v.stats()
+                work["update_blocks"] += st["update_blocks"]
+                work["frame_blocks"] += st["frame_blocks"]
+                work["changed"] += st["changed_cubes"] - prev["changed_cubes"]
+                work["emitted"] += st["emitted_triangles"] - prev["emitted_triangles"]
+                work["released"] += st["released_triangles"] - prev["released_triangles"]
+                work["refreshed"] += st["refreshed_vertices"] - prev["refreshed_vertices"]
+                work["created"] += st["created_vertices"] - prev["created_vertices"]
+                prev = st
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        s1 = v.stats()
+        kt = v.kernel_times() if timing else {}
+        v.check()
+        v.close()
+        return ms, s0, s1, kt, work
+
+    ms, s0, s1, _, _ = run(False)
+    _, _, _, kt, work = run(True)
+    del dev
+    torch.cuda.empty_cache()
+    tot = sum(ms) / 1000.0
+    collected = (s1["collected_blocks"] - s0["collected_blocks"]) % (1 << 32)
+    roof = {}
+    for name, model in (("k_mesh", mesh_bytes), ("k_integrate", BYTES_MODEL["k_integrate"])):
+        t_ms, cnt = kt.get(name, (0.0, 0))
+        if t_ms > 0:
+            gbs = model(work) / (t_ms / 1000.0) / 1e9
+            roof[name] = {"avg_launch_us": 1000.0 * t_ms / cnt, "achieved": gbs, "peak": peak, "unit": "GB/s",
+                          "frac": gbs / peak, "bytes_per_launch": model(work) / max(cnt, 1)}
+    return {
+        "workload": "floor 20x20x4 m (4x4 rooms with doorways, 8 primitives each), 640x480 float32 depth, voxel 5 mm, "
+                    "trunc 2 cm, 2^23 buckets; per frame integrate + incremental mesh + refine + gc",
+        "frames": T, "warmup": Wm, "value": T / tot, "unit": "frames/s", "ms_per_step": 1000.0 * tot / T,
+        "voxels_per_s": 512 * collected / tot, "mean_blocks_per_frame": collected / T,
+        "live_blocks_at_end": s1["live_blocks"], "l2": "flushed before every frame (256 MB write)",
+        "roofline": roof,
+    }
+
+
 def run_differentiable(args, stream):
     """The differentiable form (BASELINE config 4 reading): the sphere orbit extended to 60
     frames, frames 0-9 integrated as constants, frames 10-59 leaf tensors; forward = the 50
@@ -598,6 +677,7 @@ def run_vmesh(args, rank, world, local):
         },
     }
     if not args.skip_forms:
+        line["large"] = run_large(args, stream, flush, peak)
         line["batched"] = run_batched(args, stream, flush, peak)
         line["differentiable"] = run_differentiable(args, stream)
     print(json.dumps(line), flush=True)
@@ -616,6 +696,7 @@ def main():
                     help="time frames without per-kernel event nodes (no roofline)")
     ap.add_argument("--cpu-frames", type=int, default=200)
     ap.add_argument("--skip-forms", action="store_true", help="skip the batched and differentiable forms")
+    ap.add_argument("--large-frames", type=int, default=300)
     ap.add_argument("--batch-scenes", type=int, default=32)
     ap.add_argument("--batch-ticks", type=int, default=60)
     ap.add_argument("--batch-warmup", type=int, default=10)

@@ -63,7 +63,7 @@ typedef struct {
   float eps_refine;       /* epsilon of Eq. 5 in metres (proportional to l; 0.2 l is typical), >= 0 */
   float w_max;            /* cap of the fusion weight, >= 1 */
   uint32_t hash_buckets;  /* power of two, 2^4 .. 2^30 */
-  uint32_t max_blocks;    /* block pool size, 1 .. 2^20 */
+  uint32_t max_blocks;    /* block pool size, 1 .. 2^21 */
   uint32_t max_vertices;  /* vertex pool size, 1 .. 2^30 */
   uint32_t max_triangles; /* triangle pool size, 1 .. 2^30 */
 } vm_params;
@@ -73,6 +73,24 @@ typedef struct {
   float fx, fy, cx, cy;  /* pinhole intrinsics in pixels, fx, fy > 0; every pixel ray's
                             slope |(u - cx) / fx|, |(v - cy) / fy| must be <= 64 */
 } vm_intrinsics;
+
+/* Capacities a sticky VM_ERR_POOL_FULL or VM_ERR_HASH_FULL status can name (vm_frame_stats
+ * full_pool): the block pool (max_blocks), vertex pool (max_vertices), triangle pool
+ * (max_triangles), the per-frame collected-block list (min(max_blocks, hash_buckets)), the
+ * update-set list (max_blocks), the zero-reference vertex list (2 max_vertices), the
+ * released-run list (max_triangles), a free stack, the hash table. */
+typedef enum {
+  VM_POOL_NONE = 0,
+  VM_POOL_BLOCKS,
+  VM_POOL_VERTICES,
+  VM_POOL_TRIANGLES,
+  VM_POOL_COLLECTED_LIST,
+  VM_POOL_UPDATE_LIST,
+  VM_POOL_DEAD_VERTEX_LIST,
+  VM_POOL_DEAD_RUN_LIST,
+  VM_POOL_FREE_STACK,
+  VM_POOL_HASH
+} vm_pool;
 
 /* Per-call counters, filled by vm_get_stats (which synchronises). */
 typedef struct {
@@ -94,6 +112,8 @@ typedef struct {
   int64_t refreshed_vertices;/* vertex positions and normals recomputed so far */
   int64_t collected_blocks;  /* N_t summed over integrate calls (kept modulo 2^32) */
   int64_t meshed_blocks;     /* update-set sizes summed over mesh passes (kept modulo 2^32) */
+  int64_t full_pool;         /* vm_pool: the capacity a VM_ERR_POOL_FULL / HASH_FULL status ran
+                                out of first (VM_POOL_NONE while the status is clear) */
 } vm_frame_stats;
 
 /* Flags of vm_update_mesh / vm_step. */

@@ -43,7 +43,7 @@ __device__ int hash_insert(const Vol& V, uint64_t key, int bx, int by, int bz, u
         } else {
           blk = atomicAdd(&V.ctl->c[C_BLK_BUMP], 1);
           if (blk >= V.max_blocks) {
-            set_status(V, ST_POOL_FULL);
+            set_status(V, ST_POOL_FULL, P_BLOCKS);
             blk = -1;
           }
         }
@@ -61,7 +61,7 @@ __device__ int hash_insert(const Vol& V, uint64_t key, int bx, int by, int bz, u
     }
     s = (s + 1) & V.hmask;
   }
-  set_status(V, ST_HASH_FULL);
+  set_status(V, ST_HASH_FULL, P_HASH);
   return -1;
 }
 

@@ -16,7 +16,7 @@ __device__ __forceinline__ void run_push(const Vol& V, int L, int base) {
   if (g.thread_rank() == 0) slot = atomicAdd(&V.ctl->c[C_RUN_TOP0 + L - 1], (int)g.size());
   slot = g.shfl(slot, 0) + (int)g.thread_rank();
   if (slot < V.run_cap[L - 1]) V.run_free[L - 1][slot] = base;
-  else set_status(V, ST_POOL_FULL);
+  else set_status(V, ST_POOL_FULL, P_FREE_STACK);
 }
 
 // Zero-reference vertex `vid` (listed by a mesh pass): claim with CAS(0 -> -1), so a vertex
@@ -25,10 +25,10 @@ __device__ __forceinline__ void run_push(const Vol& V, int L, int base) {
 // whether a detached vertex was freed.
 __device__ __forceinline__ bool gc_vertex(const Vol& V, int vid) {
   if (atomicCAS(&V.vref[vid], 0, -1) != 0) return false;
-  const int e = V.vedge[vid];
+  const uint32_t e = V.vedge[vid];
   bool detached = false;
-  if (e >= 0) {
-    const int ob = e / EPB, r = e - ob * EPB, ov = r / 3, a = r - ov * 3;
+  if (e != NO_EDGE) {
+    const int ob = (int)(e / EPB), r = (int)(e - (uint32_t)ob * EPB), ov = r / 3, a = r - ov * 3;
     V.edge_vtx[e] = -1;
     atomic_and_u8(V.vmask + (size_t)ob * BV + ov, (uint8_t)~(1 << a));
     atomicSub(&V.bnvert[ob], 1);

@@ -65,8 +65,8 @@ __global__ void __launch_bounds__(1024) k_scan_counts(int* cta_counts, int n, in
   if (threadIdx.x == 0) *total = carry;
 }
 
-__device__ __forceinline__ uint64_t edge_key_of(const Vol& V, int e) {
-  const int ob = e / EPB, r = e - ob * EPB, ov = r / 3, a = r - ov * 3;
+__device__ __forceinline__ uint64_t edge_key_of(const Vol& V, uint32_t e) {
+  const int ob = (int)(e / EPB), r = (int)(e - (uint32_t)ob * EPB), ov = r / 3, a = r - ov * 3;
   int4 k = V.bkey[ob];
   int gx = k.x * BS + (ov & 7), gy = k.y * BS + ((ov >> 3) & 7), gz = k.z * BS + (ov >> 6);
   return ((uint64_t)(uint32_t)(gx + (1 << 19)) << 42) | ((uint64_t)(uint32_t)(gy + (1 << 19)) << 22) |

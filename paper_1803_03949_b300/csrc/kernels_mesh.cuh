@@ -159,7 +159,7 @@ __device__ __forceinline__ int run_pop(const Vol& V, int L) {
   if (rank < from_stack) return __ldcg(&V.run_free[L - 1][old - 1 - rank]);
   const long long b = (long long)bump0 + (long long)(rank - from_stack) * L;
   if (b + L > V.max_triangles) {
-    set_status(V, ST_POOL_FULL);
+    set_status(V, ST_POOL_FULL, P_TRIANGLES);
     return -1;
   }
   return (int)b;
@@ -172,7 +172,7 @@ __device__ __forceinline__ void deadrun_push(const Vol& V, int base, int L) {
   if (g.thread_rank() == 0) slot = atomicAdd(&V.ctl->c[C_N_DEADRUN], (int)g.size());
   slot = g.shfl(slot, 0) + (int)g.thread_rank();
   if (slot < V.list_cap_deadrun) V.deadrun[slot] = make_int2(base, L);
-  else set_status(V, ST_POOL_FULL);
+  else set_status(V, ST_POOL_FULL, P_DEAD_RUN_LIST);
 }
 
 // Id of the vertex on the edge owned by the voxel at halo coordinates (x, y, z) (0..8) along
@@ -187,7 +187,7 @@ __device__ __forceinline__ int vertex_of_edge(const Vol& V, const MeshSmem& S, i
   const int ob = S.nb[(x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2)];
   if (ob < 0) return -1;  // cannot happen for a valid cube
   const int ov = (x & 7) + 8 * (y & 7) + 64 * (z & 7);
-  const int e = ob * EPB + ov * 3 + a;
+  const uint32_t e = (uint32_t)ob * EPB + ov * 3 + a;
   const int vid = __ldcg(&V.edge_vtx[e]);
   if (vid >= 0) return vid;
   const int mine = pool_pop(V, V.vtx_free, C_VTX_TOP, C_VTX_BUMP, V.max_vertices);
@@ -195,7 +195,7 @@ __device__ __forceinline__ int vertex_of_edge(const Vol& V, const MeshSmem& S, i
   const int old = atomicCAS(&V.edge_vtx[e], -1, mine);
   if (old >= 0) {  // another thread claimed the edge first
     V.vref[mine] = 0;
-    V.vedge[mine] = -1;
+    V.vedge[mine] = NO_EDGE;
     list_push(V, V.dead, C_N_DEAD, V.list_cap_dead, mine);
     return old;
   }
@@ -425,7 +425,7 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
     }
     const int ci = blk * BV + c;
     if (vs[0] < 0 || vs[1] < 0 || vs[2] < 0) {  // vertex pool exhausted
-      set_status(V, ST_POOL_FULL);
+      set_status(V, ST_POOL_FULL, P_VERTICES);
       V.tris[base + t] = make_int4(-1, -1, -1, ci);
       continue;
     }

@@ -333,7 +333,7 @@ vm_status vm_create_volume(const vm_params* p, void* cuda_stream, vm_volume** ou
   if (!(p->voxel_size >= 1e-4f) || !std::isfinite(p->voxel_size) || !(p->trunc > 0) ||
       !(p->trunc <= 32.0f * p->voxel_size) || !(p->eps_refine >= 0) || !std::isfinite(p->eps_refine) ||
       !(p->w_max >= 1) || !std::isfinite(p->w_max) || hb < 16 || hb > (1u << 30) || (hb & (hb - 1)) ||
-      p->max_blocks < 1 || p->max_blocks > (1u << 20) || p->max_vertices < 1 || p->max_vertices > (1u << 30) ||
+      p->max_blocks < 1 || p->max_blocks > (1u << 21) || p->max_vertices < 1 || p->max_vertices > (1u << 30) ||
       p->max_triangles < 1 || p->max_triangles > (1u << 30))
     return VM_ERR_INVALID_ARG;
   static vmk_host::McTable table;
@@ -409,7 +409,9 @@ vm_status vm_create_volume(const vm_params* p, void* cuda_stream, vm_volume** ou
     delete v;
     return VM_ERR_OOM;
   }
-  int init[3] = {0, 1, 1};  // status, frame, epoch
+  int init[C_EPOCH + 1] = {};
+  init[C_FRAME] = 1;
+  init[C_EPOCH] = 1;
   if (cudaMemcpyAsync(V.ctl->c, init, sizeof(init), cudaMemcpyHostToDevice, v->stream) != cudaSuccess ||
       cudaStreamSynchronize(v->stream) != cudaSuccess) {
     free_all(v);
@@ -716,6 +718,7 @@ vm_status vm_get_stats(vm_volume* v, vm_frame_stats* s) {
   s->refreshed_vertices = c[C_ST_REFRESHED];
   s->collected_blocks = (uint32_t)c[C_ST_COLLECTED];
   s->meshed_blocks = (uint32_t)c[C_ST_MESHED];
+  s->full_pool = c[C_STATUS_POOL];
   return VM_OK;
 }
 

@@ -14,7 +14,8 @@
 //             vmask u8[NB*512] (bits 0-2: the owned edge has a vertex),
 //             edge_vtx i32[NB*512*3] (vertex on owned edge, -1 none), tri_base i32[NB*512]
 //   vertices  vpos float4[NV], vnrm float4[NV], vref i32[NV] (reference count, -1 free),
-//             vedge i32[NV] (owning edge id = block*1536 + voxel*3 + axis; -1 = unattached)
+//             vedge u32[NV] (owning edge id = block*1536 + voxel*3 + axis, below 2^32 for up
+//             to 2^21 blocks; NO_EDGE = unattached)
 //   triangles tris int4[NT] (three vertex ids, owning cube id; x < 0 = free)
 //   free lists block / vertex stacks and five triangle-run stacks (run length 1..5)
 //   work lists collected buckets, update set, zero-reference vertices, released triangle
@@ -33,6 +34,7 @@ namespace cg = cooperative_groups;
 constexpr int BS = 8;       // block side in voxels (Sec. VI: 8^3 in all configurations)
 constexpr int BV = 512;     // voxels per block
 constexpr int EPB = 1536;   // owned edges per block
+constexpr uint32_t NO_EDGE = 0xFFFFFFFFu;  // vedge of a vertex attached to no edge
 constexpr uint64_t KEY_EMPTY = ~0ull;
 constexpr uint64_t KEY_TOMB = ~0ull - 1ull;
 constexpr int KEY_BIAS = 1 << 20;
@@ -44,6 +46,7 @@ enum Status { ST_OK = 0, ST_INVALID = 1, ST_HASH_FULL = 2, ST_POOL_FULL = 3 };
 // counters of the control block (int slots of Ctl::c)
 enum Counter {
   C_STATUS = 0,
+  C_STATUS_POOL,    // which capacity set the status (PoolCode)
   C_FRAME,          // integrate calls so far + 1
   C_EPOCH,          // mesh epoch, advanced by the first integrate after a mesh update
   C_N_TOUCHED,      // buckets collected by the current integrate call
@@ -107,7 +110,7 @@ struct Vol {
   float4* vpos;
   float4* vnrm;
   int* vref;
-  int* vedge;
+  uint32_t* vedge;
 
   int4* tris;
 
@@ -162,7 +165,17 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {  // murmur3 finaliser
   return z ^ (z >> 33);
 }
 
-__device__ __forceinline__ void set_status(const Vol& V, int st) { atomicCAS(&V.ctl->c[C_STATUS], 0, st); }
+// Which capacity ran out (the first one, kept beside the status; values of the C ABI's
+// vm_pool enum).
+enum PoolCode { P_NONE = 0, P_BLOCKS, P_VERTICES, P_TRIANGLES, P_COLLECTED_LIST, P_UPDATE_LIST, P_DEAD_VERTEX_LIST,
+                P_DEAD_RUN_LIST, P_FREE_STACK, P_HASH };
+__device__ __forceinline__ void set_status(const Vol& V, int st, int pool = P_NONE) {
+  atomicCAS(&V.ctl->c[C_STATUS], 0, st);
+  if (pool != P_NONE) atomicCAS(&V.ctl->c[C_STATUS_POOL], 0, pool);
+}
+__device__ __forceinline__ int list_pool_code(int c_count) {
+  return c_count == C_N_TOUCHED ? P_COLLECTED_LIST : (c_count == C_N_UPDATE ? P_UPDATE_LIST : P_DEAD_VERTEX_LIST);
+}
 
 // Hash lookup: bucket holding `key`, or -1.  Linear probing, at most hmask+1 probes.
 __device__ __forceinline__ int hash_find(const Vol& V, uint64_t key) {
@@ -204,7 +217,7 @@ __device__ __forceinline__ int pool_pop(const Vol& V, int* stack, int c_top, int
   } else {
     long long b = (long long)bump0 + (long long)(rank - from_stack) * stride;
     if (b + stride > cap) {
-      set_status(V, ST_POOL_FULL);
+      set_status(V, ST_POOL_FULL, P_VERTICES);
       id = -1;
     } else {
       id = (int)b;
@@ -220,7 +233,7 @@ __device__ __forceinline__ void pool_push(const Vol& V, int* stack, int c_top, i
   if (g.thread_rank() == 0) base = atomicAdd(&V.ctl->c[c_top], (int)g.size());
   base = g.shfl(base, 0) + (int)g.thread_rank();
   if (base < cap) stack[base] = id;
-  else set_status(V, ST_POOL_FULL);
+  else set_status(V, ST_POOL_FULL, P_FREE_STACK);
 }
 
 // Append to a work list, aggregated over the calling lanes; false (and POOL_FULL) on overflow.
@@ -234,7 +247,7 @@ __device__ __forceinline__ bool list_push(const Vol& V, T* list, int c_count, in
     list[base] = value;
     return true;
   }
-  set_status(V, ST_POOL_FULL);
+  set_status(V, ST_POOL_FULL, list_pool_code(c_count));
   return false;
 }
 

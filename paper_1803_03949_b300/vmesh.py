@@ -42,7 +42,10 @@ class vm_frame_stats(ctypes.Structure):
         "frame_blocks", "new_blocks", "update_blocks", "changed_cubes", "live_blocks", "live_vertices",
         "live_triangles", "freed_blocks", "freed_vertices", "created_vertices", "hash_tombstones",
         "block_high_water", "rehashes", "emitted_triangles", "released_triangles", "refreshed_vertices",
-        "collected_blocks", "meshed_blocks")]
+        "collected_blocks", "meshed_blocks", "full_pool")]
+
+POOLS = ["none", "blocks", "vertices", "triangles", "collected_list", "update_list", "dead_vertex_list", "dead_run_list",
+         "free_stack", "hash"]
 
 
 class vm_mesh_memory(ctypes.Structure):
@@ -213,7 +216,10 @@ class Volume:
         return self._lib.vm_last_error(self._h)
 
     def check(self):
-        _check(self.last_error(), "device status")
+        code = self.last_error()
+        if code != 0:
+            pool = self.stats()["full_pool"]
+            _check(code, "device status" + (" (%s exhausted)" % POOLS[pool] if 0 < pool < len(POOLS) else ""))
 
     def stats(self) -> dict:
         s = vm_frame_stats()

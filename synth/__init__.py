@@ -171,13 +171,18 @@ def room_scene(num_frames: int = 300, seed: int = SEED_BASE + 2, W: int = 640, H
 
 
 def floor_scene(num_frames: int = 2000, seed: int = SEED_BASE + 3) -> Scene:
-    """20x20x4 m floor of 4x4 rooms with doorways and 8 primitives per room, 640x480,
-    same noise model; voxel 5 mm, truncation 2 cm, 2^23 buckets."""
+    """20x20x4 m floor of 4x4 rooms with doorways and 8 primitives per room, 640x480, a
+    serpentine path through the doorways that covers the floor in `num_frames` frames,
+    same noise model with a 4.5 m sensor range (farther depth reads as invalid: at the noise
+    model's sigma = 0.0012 z^2 a 10 m reading is off by 12 cm, six truncation widths);
+    voxel 5 mm, truncation 2 cm, 2^23 buckets."""
     lib = _load()
     h = lib.synth_create_floor(seed, num_frames, 640, 480, 525.0, 525.0, 319.5, 239.5, 8, 0.0012, 0.02, 8.0)
     vol = VolumeConfig(voxel_size=0.005, trunc=0.02, hash_buckets=1 << 23, max_blocks=1 << 21,
-                       max_vertices=1 << 25, max_triangles=1 << 26)
-    return Scene(h, lib, "floor_20x20x4_640x480_l5mm", vol)
+                       max_vertices=1 << 26, max_triangles=1 << 27)
+    sc = Scene(h, lib, "floor_20x20x4_640x480_l5mm", vol)
+    sc.max_range = 4.5
+    return sc
 
 
 def batch_scenes(num_scenes: int = 32, num_frames: int = 100, seed: int = SEED_BASE + 5) -> list:

@@ -63,7 +63,7 @@ def test_bad_arguments_are_refused():
 
 
 @pytest.mark.parametrize("field,value", [("voxel_size", 0.0), ("trunc", -1.0), ("trunc", 1.0), ("hash_buckets", 1000),
-                                         ("hash_buckets", 8), ("max_blocks", 0), ("max_blocks", (1 << 20) + 1),
+                                         ("hash_buckets", 8), ("max_blocks", 0), ("max_blocks", (1 << 21) + 1),
                                          ("w_max", 0.5)])
 def test_bad_params_are_refused(field, value):
     lib = load_library()
