@@ -339,7 +339,7 @@ vm_status vm_batch_step(vm_batch* batch, const float* const* depths, const vm_in
 vm_status vm_batch_tune(vm_batch* batch, int rounds);
 
 /* The schedule in use, 5 ints: k_alloc pixels per thread (1, 2, 4), CTAs per SM of the
- * fusion (4, 8, 12), mesh (3, 5, 7), vertex-gc (1, 2, 4) and block-gc (2, 4, 8) kernels;
+ * fusion (4, 8, 12), mesh (4, 6, 8), vertex-gc (1, 2, 4) and block-gc (2, 4, 8) kernels;
  * tuned_ms (optional, 15 doubles) receives the mean time of each option from the last
  * tuning (-1 where untimed).  vm_batch_set_schedule installs a schedule from those options
  * (VM_ERR_INVALID_ARG otherwise). */

@@ -6,18 +6,19 @@
 // every stage is wide (one thread per cube, per triangle or per edge) and no thread walks
 // a long chain of dependent memory operations:
 //   a. stage the 10^3 voxel halo (the block, local 0..7, plus the +x/+y/+z neighbours'
-//      voxels at local 8..9) in shared memory; every cube type, and every vertex an edge of
-//      these cubes can need, is computed from it;
-//   b. per cube: type (and refinement), previous type, refresh of the vertices the voxel
-//      owns; cubes whose effective type changes go to a shared list and mark the edges
-//      their new triangles use in a shared bitmap;
-//   c. per (changed cube, old triangle): release it (reference counts down; the run is
-//      queued for recycling); per changed cube: pop a run for the new triangles; compact
-//      the marked edges into a list;
-//   d. per marked edge: its vertex id, creating the vertex on first use -- the first
-//      thread to claim the edge pops an id and publishes it with atomicCAS on the owner's
-//      edge slot; a thread that loses the race takes the winner's id and returns its own
-//      through the recycling list, so nobody waits and every vertex exists once;
+//      voxels at local 8..9) in shared memory as d, NaN where W = 0; every cube type, and
+//      every vertex an edge of these cubes can need, is computed from it;
+//   b. per cube: type (and refinement), previous type; the block's existing vertices go to
+//      a refresh list; cubes whose effective type changes go to a shared list and mark the
+//      edges their new triangles use in a shared bitmap;
+//   c. compact the marked edges into a list;
+//   d. one loop over three kinds of independent work: per marked edge its vertex id,
+//      creating the vertex on first use -- the first thread to claim the edge pops an id
+//      and publishes it with atomicCAS on the owner's edge slot; a thread that loses the
+//      race takes the winner's id and returns its own through the recycling list, so
+//      nobody waits and every vertex exists once; per listed vertex a refresh of its
+//      position and normal; per changed cube the release of its old triangles (reference
+//      counts down, the run queued for recycling) and a run for its new ones;
 //   e. per (changed cube, new triangle): write it and count its three references.
 // The paper resolves concurrent vertex creation with an atomic first-claimer lock or with
 // grouped serial launches (Sec. V-C); publishing the id with the claim replaces both.
@@ -47,8 +48,10 @@ __device__ __forceinline__ int owner_bits(int k) { return (int)((EDGE_OWNER_BITS
 __device__ __forceinline__ int packed_ntri(uint64_t w) { return (int)(w >> 60); }
 __device__ __forceinline__ int packed_edge(uint64_t w, int t, int j) { return (int)((w >> (4 * (3 * t + j))) & 15); }
 
+constexpr int MESH_CTAS_PER_SM = 8;  // bounded by registers (64) and shared memory (27 KB)
+
 struct __align__(16) MeshSmem {
-  float2 halo[HALO_N];
+  float halo[HALO_N];  // d of the voxel, NaN where W = 0 or its block is absent
   uint64_t tri64[256];
   int nb[8];
   int dtri;
@@ -103,7 +106,7 @@ __device__ __forceinline__ int4 ld_early_i4(const int* p) {
   return v;
 }
 
-__device__ __forceinline__ float2 halo_at(const MeshSmem& S, int x, int y, int z) {
+__device__ __forceinline__ float halo_at(const MeshSmem& S, int x, int y, int z) {
   return S.halo[x + HALO * y + HALO * HALO * z];
 }
 
@@ -115,8 +118,8 @@ __device__ __forceinline__ float2 halo_at(const MeshSmem& S, int x, int y, int z
 __device__ __forceinline__ void edge_vertex(const MeshSmem& S, float l, int4 key, int x, int y, int z, int a,
                                             float4* pos, float4* nrm) {
   const int ax = a == 0, ay = a == 1, az = a == 2;
-  const float d0 = halo_at(S, x, y, z).x;
-  const float d1 = halo_at(S, x + ax, y + ay, z + az).x;
+  const float d0 = halo_at(S, x, y, z);
+  const float d1 = halo_at(S, x + ax, y + ay, z + az);
   float t = d0 == d1 ? 0.5f : d0 / (d0 - d1);
   if (t < -1.0f) t = -1.0f;
   if (t > 2.0f) t = 2.0f;
@@ -132,9 +135,9 @@ __device__ __forceinline__ void edge_vertex(const MeshSmem& S, float l, int4 key
       continue;
     }
     const int bx = b == 0, by = b == 1, bz = b == 2;
-    const float2 q0 = halo_at(S, x + bx, y + by, z + bz);
-    const float2 q1 = halo_at(S, x + ax + bx, y + ay + by, z + az + bz);
-    n[b] = (q0.y > 0.0f && q1.y > 0.0f) ? (1.0f - t) * (q0.x - d0) + t * (q1.x - d1) : 0.0f;
+    const float q0 = halo_at(S, x + bx, y + by, z + bz);
+    const float q1 = halo_at(S, x + ax + bx, y + ay + by, z + az + bz);
+    n[b] = (!isnan(q0) && !isnan(q1)) ? (1.0f - t) * (q0 - d0) + t * (q1 - d1) : 0.0f;
   }
   const float len = sqrtf((n[0] * n[0] + n[1] * n[1]) + n[2] * n[2]);
   *pos = make_float4(p[0], p[1], p[2], 0.0f);
@@ -182,8 +185,9 @@ __device__ __forceinline__ void deadrun_push(const Vol& V, int base, int L) {
 // additions commute, so the count is exact when the pass ends, and no fence is needed.
 // A thread that loses the claim resets its spare id to an unattached zero-reference vertex
 // and hands it to gc.
-__device__ __forceinline__ int vertex_of_edge(const Vol& V, const MeshSmem& S, int4 key, int x, int y, int z,
-                                              int a, int& created) {
+__device__ __forceinline__ int vertex_of_edge(const Vol& V, const MeshSmem& S, int x, int y, int z, int a,
+                                              bool& claimed) {
+  claimed = false;
   const int ob = S.nb[(x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2)];
   if (ob < 0) return -1;  // cannot happen for a valid cube
   const int ov = (x & 7) + 8 * (y & 7) + 64 * (z & 7);
@@ -201,13 +205,9 @@ __device__ __forceinline__ int vertex_of_edge(const Vol& V, const MeshSmem& S, i
   }
   atomicAdd(&V.vref[mine], 1);  // -1 (free) -> 0, plus the references added by others
   V.vedge[mine] = e;
-  float4 p, n;
-  edge_vertex(S, V.l, key, x, y, z, a, &p, &n);
-  V.vpos[mine] = p;
-  V.vnrm[mine] = n;
   atomic_or_u8(V.vmask + (size_t)ob * BV + ov, (uint8_t)(1 << a));
   atomicAdd(&V.bnvert[ob], 1);
-  ++created;
+  claimed = true;  // the caller writes its position and normal
   return mine;
 }
 
@@ -267,15 +267,15 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
   for (int h = threadIdx.x; h < HALO_N; h += MESH_THREADS) {
     const int x = h % HALO, y = (h / HALO) % HALO, z = h / (HALO * HALO);
     const int b = S.nb[(x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2)];
-    S.halo[h] = b >= 0 ? __ldcg(&V.tw[(size_t)b * BV + (x & 7) + 8 * (y & 7) + 64 * (z & 7)])
-                       : make_float2(0.f, 0.f);
+    const float2 q = b >= 0 ? __ldcg(&V.tw[(size_t)b * BV + (x & 7) + 8 * (y & 7) + 64 * (z & 7)])
+                            : make_float2(0.f, 0.f);
+    S.halo[h] = q.y > 0.0f ? q.x : __int_as_float(0x7fc00000);
   }
   __syncthreads();
   // ---- b. cube types, vertex refresh, changed-cube list, needed edges (4 consecutive cubes
   //         per thread: the type, previous-type and vertex-flag bytes move as 32-bit words)
   int dtri = 0;
   {
-    const int tbs[4] = {tb4.x, tb4.y, tb4.z, tb4.w};
     if (mode & M_UPDATE) *reinterpret_cast<uint32_t*>(V.code_prev + ci0) = eff_w;
     // existing vertices of the 4 voxels: listed for the refresh in stage d
     const uint32_t live_w = vm_w & 0x07070707u;
@@ -287,18 +287,18 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
         if ((live_w >> (8 * (q / 3) + q % 3)) & 1) S.rlist[r++] = (uint16_t)((c0 + q / 3) * 3 + q % 3);
     }
     uint32_t new_w = eff_w;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
+#pragma unroll 1
+    for (int j = 0; j < 4; ++j) {  // rolled: the kernel's code must stay small (instruction cache)
       const int c = c0 + j;
       const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
       bool valid = true;
       int raw = 0, small = 0;
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
-        const float2 hv = halo_at(S, x + corner_x(k), y + corner_y(k), z + corner_z(k));
-        valid &= hv.y > 0.0f;
-        raw |= (hv.x < 0.0f) << k;
-        small |= (fabsf(hv.x) < eps) << k;
+        const float hv = halo_at(S, x + corner_x(k), y + corner_y(k), z + corner_z(k));
+        valid &= !isnan(hv);
+        raw |= (hv < 0.0f) << k;
+        small |= (fabsf(hv) < eps) << k;
       }
       const int eff_old = (eff_w >> (8 * j)) & 0xFF;
       const int prev = (prev_w >> (8 * j)) & 0xFF;
@@ -313,7 +313,7 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
       S.chg_cube[slot] = (uint16_t)c;
       S.chg_new[slot] = (uint8_t)e;
       S.chg_old[slot] = (uint8_t)eff_old;
-      S.chg_base[slot] = nold > 0 ? tbs[j] : -1;
+      S.chg_base[slot] = nold > 0 ? (j == 0 ? tb4.x : (j == 1 ? tb4.y : (j == 2 ? tb4.z : tb4.w))) : -1;
       dtri += nnew - nold;
       for (int t = 0; t < nnew; ++t)
         for (int jj = 0; jj < 3; ++jj) {
@@ -361,21 +361,32 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
   //         per changed cube: release the old triangles, pop a run for the new ones.
   const int nedge = S.nedge, nref = S.nref;
   for (int j = threadIdx.x; j < nedge + nref + nchg; j += MESH_THREADS) {
-    if (j < nedge) {
-      const int es = S.elist[j];
-      const int a = es % 3, o = es / 3;
-      const int x = o % 9, y = (o / 9) % 9, z = o / 81;
-      S.evid[es] = vertex_of_edge(V, S, key, x, y, z, a, created);
-    } else if (j < nedge + nref) {
-      const int r = S.rlist[j - nedge];
-      const int c = r / 3, a = r - c * 3;
-      const int vid = __ldcg(&V.edge_vtx[((size_t)blk * BV + c) * 3 + a]);
-      if (vid < 0) continue;
+    if (j < nedge + nref) {
+      // a vertex to (re)compute: a needed edge's new vertex, or an existing vertex
+      int x, y, z, a, vid;
+      bool fresh;
+      if (j < nedge) {
+        const int es = S.elist[j];
+        const int o = es / 3;
+        a = es - 3 * o;
+        x = o % 9, y = (o / 9) % 9, z = o / 81;
+        vid = vertex_of_edge(V, S, x, y, z, a, fresh);
+        S.evid[es] = vid;
+        created += fresh;
+      } else {
+        const int r = S.rlist[j - nedge];
+        const int c = r / 3;
+        a = r - c * 3;
+        x = c & 7, y = (c >> 3) & 7, z = c >> 6;
+        vid = __ldcg(&V.edge_vtx[((size_t)blk * BV + c) * 3 + a]);
+        fresh = vid >= 0;
+        refreshed += fresh;
+      }
+      if (!fresh) continue;
       float4 p, nn;
-      edge_vertex(S, l, key, c & 7, (c >> 3) & 7, c >> 6, a, &p, &nn);
+      edge_vertex(S, l, key, x, y, z, a, &p, &nn);
       V.vpos[vid] = p;
       V.vnrm[vid] = nn;
-      ++refreshed;
     } else {
       const int q = j - nedge - nref;
       const int nold = packed_ntri(S.tri64[S.chg_old[q]]), obase = S.chg_base[q];
@@ -384,20 +395,24 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
         int4 tr[5];
 #pragma unroll
         for (int t = 0; t < 5; ++t) tr[t] = t < nold ? __ldcg(&V.tris[obase + t]) : make_int4(-1, -1, -1, -1);
-        int hit[15];
+        // all 15 reference drops in flight together; the vertices they leave unreferenced
+        // go to the recycling list through one (rolled) loop
+        unsigned zero = 0;
 #pragma unroll
         for (int t = 0; t < 5; ++t) {
-          const int vs[3] = {tr[t].x, tr[t].y, tr[t].z};
-#pragma unroll
-          for (int jj = 0; jj < 3; ++jj) hit[3 * t + jj] = vs[jj] >= 0 ? atomicSub(&V.vref[vs[jj]], 1) : 0;
-        }
-#pragma unroll
-        for (int t = 0; t < 5; ++t) {
-          if (t < nold) V.tris[obase + t] = make_int4(-1, -1, -1, -1);
           const int vs[3] = {tr[t].x, tr[t].y, tr[t].z};
 #pragma unroll
           for (int jj = 0; jj < 3; ++jj)
-            if (hit[3 * t + jj] == 1) list_push(V, V.dead, C_N_DEAD, V.list_cap_dead, vs[jj]);
+            if (vs[jj] >= 0 && atomicSub(&V.vref[vs[jj]], 1) == 1) zero |= 1u << (3 * t + jj);
+        }
+        for (int t = 0; t < nold; ++t) V.tris[obase + t] = make_int4(-1, -1, -1, -1);
+        while (zero) {
+          const int b = __ffs(zero) - 1;
+          zero &= zero - 1;
+          const int4 tb = tr[0];
+          int4 tt = b < 3 ? tb : (b < 6 ? tr[1] : (b < 9 ? tr[2] : (b < 12 ? tr[3] : tr[4])));
+          const int k = b % 3;
+          list_push(V, V.dead, C_N_DEAD, V.list_cap_dead, k == 0 ? tt.x : (k == 1 ? tt.y : tt.z));
         }
         deadrun_push(V, obase, nold);
         released += nold;
@@ -467,7 +482,7 @@ __device__ __forceinline__ void mesh_finish(const Vol& V, int n) {
 // mode: M_UPDATE (types from the current TSDF; t_{i-1} := previous effective type; refresh
 // the positions and normals of the block's existing vertices), M_REFINE (Eqs. 3-5 with the
 // stored t_{i-1}).  The last CTA clamps the vertex and run free-stack tops.
-__global__ void __launch_bounds__(MESH_THREADS, 7) k_mesh(Vol V, int mode) {
+__global__ void __launch_bounds__(MESH_THREADS, MESH_CTAS_PER_SM) k_mesh(Vol V, int mode) {
   __shared__ MeshSmem S;
   for (int i = threadIdx.x; i < 128; i += MESH_THREADS) reinterpret_cast<uint4*>(S.tri64)[i] = V.tri_table[i];
   grid_dependency_wait();

@@ -229,7 +229,7 @@ vm_status enqueue_list_all(vm_volume* v) {
 }
 
 vm_status enqueue_mesh_pass(vm_volume* v, int mode) {
-  return launch(v, K_MESH, [&] { launch_dependent(k_mesh, grid_for(v, 7), MESH_THREADS, v->cur, v->V, mode); });
+  return launch(v, K_MESH, [&] { launch_dependent(k_mesh, grid_for(v, MESH_CTAS_PER_SM), MESH_THREADS, v->cur, v->V, mode); });
 }
 
 vm_status enqueue_update(vm_volume* v, int flags) {
@@ -354,6 +354,7 @@ vm_status vm_create_volume(const vm_params* p, void* cuda_stream, vm_volume** ou
   if (v->num_sms <= 0) v->num_sms = 148;
   // the mesh kernel keeps ~32 KB of shared memory per CTA: ask for the largest carveout
   cudaFuncSetAttribute(k_mesh, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  cudaFuncSetAttribute(kb_mesh, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   (void)cudaGetLastError();
   if (cudaMemcpyToSymbol(c_ntri, table.ntri, sizeof(table.ntri)) != cudaSuccess ||
       cudaMemcpyToSymbol(c_tri, table.tri, sizeof(table.tri)) != cudaSuccess ||
@@ -1114,8 +1115,8 @@ namespace {
 //   of the fusion, mesh, vertex-gc and block-gc kernels (persistent grids).
 constexpr int SCHED_SLOTS = 5;
 constexpr int SCHED_OPTS = 3;
-const int kSchedOptions[SCHED_SLOTS][SCHED_OPTS] = {{1, 2, 4}, {4, 8, 12}, {3, 5, 7}, {1, 2, 4}, {2, 4, 8}};
-const int kSchedDefault[SCHED_SLOTS] = {2, 12, 7, 2, 8};
+const int kSchedOptions[SCHED_SLOTS][SCHED_OPTS] = {{1, 2, 4}, {4, 8, 12}, {4, 6, 8}, {1, 2, 4}, {2, 4, 8}};
+const int kSchedDefault[SCHED_SLOTS] = {2, 12, 8, 2, 8};
 
 struct TuneRec {
   int opt;

@@ -106,7 +106,7 @@ def test_batch_with_autotuning_and_every_schedule_option(graph):
     singles = [_run_single(s, frames) for s in scenes]
     for v, s1 in zip(vols, singles):
         _same_state(v, s1)
-    for sched in ([1, 4, 3, 1, 2], [4, 12, 7, 4, 8]):
+    for sched in ([1, 4, 4, 1, 2], [4, 12, 8, 4, 8]):
         b2, vols2 = _run_batch(scenes, frames, graph=graph, schedule=sched)
         for v, s1 in zip(vols2, singles):
             _same_state(v, s1)
