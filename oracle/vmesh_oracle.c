@@ -23,7 +23,8 @@
  *     > 0) the ray segment between camera depths max(D - mu, 0.05) and D + mu is
  *     walked with a 3D DDA over block cells (all cells from the start cell to the
  *     end cell, ties x before y before z); every cell visited is collected and
- *     allocated if new.
+ *     allocated if new.  Each division is a product with a reciprocal (of fx, fy,
+ *     the block side 8 l, and of each axis direction of the segment).
  *   - Fusion (Sec. V-A, Eq. 2, averaging as in Newcombe et al. 2011): every
  *     voxel of the blocks collected by this frame is projected (pinhole,
  *     nearest pixel = floor(u + 0.5)); sdf = D - z_c; skipped when z_c <= 0,
@@ -400,11 +401,11 @@ static int dda(const real* A, const real* B, int* out, int cap) {
     if (dir > 0) {
       step[i] = 1;
       tdel[i] = (real)1 / dir;
-      tmax[i] = (((real)c[i] + (real)1) - A[i]) / dir;
+      tmax[i] = (((real)c[i] + (real)1) - A[i]) * tdel[i];
     } else if (dir < 0) {
       step[i] = -1;
       tdel[i] = (real)1 / (-dir);
-      tmax[i] = (A[i] - (real)c[i]) / (-dir);
+      tmax[i] = (A[i] - (real)c[i]) * tdel[i];
     } else {
       step[i] = 0;
       tdel[i] = (real)INFINITY;
@@ -433,21 +434,22 @@ int or_dda(const double* A, const double* B, int* out, int cap) {
 }
 
 /* The block-grid segment of pixel (u, v) with depth D: endpoints at camera depths
- * max(D - mu, ZMIN) and D + mu on the pixel ray, mapped to world by T_wc and divided
- * by the block side 8 l.  A, B receive the endpoints in block units. */
+ * max(D - mu, ZMIN) and D + mu on the pixel ray, mapped to world by T_wc and scaled by
+ * the reciprocal of the block side 8 l.  A, B receive the endpoints in block units.
+ * Divisions are taken once as reciprocals (of fx, fy, the block side) and multiplied. */
 static void pixel_segment(const ovol* V, int u, int v, real D, const real* K, const real* Twc, real* A, real* B) {
-  real xn = ((real)u - K[2]) / K[0];
-  real yn = ((real)v - K[3]) / K[1];
+  real xn = ((real)u - K[2]) * ((real)1 / K[0]);
+  real yn = ((real)v - K[3]) * ((real)1 / K[1]);
   real z0 = D - V->mu;
   if (z0 < ZMIN) z0 = ZMIN;
   real z1 = D + V->mu;
   real pa[3] = {xn * z0, yn * z0, z0}, pb[3] = {xn * z1, yn * z1, z1};
-  real bs = V->l * (real)BS;
+  real ibs = (real)1 / (V->l * (real)BS);
   for (int i = 0; i < 3; ++i) {
     real wa = ((Twc[4 * i] * pa[0] + Twc[4 * i + 1] * pa[1]) + Twc[4 * i + 2] * pa[2]) + Twc[4 * i + 3];
     real wb = ((Twc[4 * i] * pb[0] + Twc[4 * i + 1] * pb[1]) + Twc[4 * i + 2] * pb[2]) + Twc[4 * i + 3];
-    A[i] = wa / bs;
-    B[i] = wb / bs;
+    A[i] = wa * ibs;
+    B[i] = wb * ibs;
   }
 }
 

@@ -103,11 +103,11 @@ __device__ __forceinline__ void dda_axis(float a, float b, int& c, int& rem, int
   if (dir > 0.0f) {
     step = 1;
     tdel = 1.0f / dir;
-    tmax = (((float)c + 1.0f) - a) / dir;
+    tmax = (((float)c + 1.0f) - a) * tdel;
   } else if (dir < 0.0f) {
     step = -1;
     tdel = 1.0f / (-dir);
-    tmax = (a - (float)c) / (-dir);
+    tmax = (a - (float)c) * tdel;
   } else {
     step = 0;
     tdel = __int_as_float(0x7f800000);
@@ -121,21 +121,22 @@ __device__ __forceinline__ void dda_axis(float a, float b, int& c, int& rem, int
 __device__ __forceinline__ void collect_pixel(const Vol& V, const FrameParams& fp, int u, int v, float D,
                                               unsigned long long* set, uint32_t frame, uint64_t& last) {
   if (!(D > 0.0f) || !isfinite(D)) return;
-  const float xn = ((float)u - fp.cx) / fp.fx;
-  const float yn = ((float)v - fp.cy) / fp.fy;
+  // divisions as products with reciprocals (of fx, fy, the block side)
+  const float xn = ((float)u - fp.cx) * (1.0f / fp.fx);
+  const float yn = ((float)v - fp.cy) * (1.0f / fp.fy);
   float z0 = D - V.mu;
   if (z0 < Z_NEAR) z0 = Z_NEAR;
   const float z1 = D + V.mu;
   const float pa0 = xn * z0, pa1 = yn * z0, pa2 = z0;
   const float pb0 = xn * z1, pb1 = yn * z1, pb2 = z1;
-  const float bs = V.l * (float)BS;
+  const float ibs = 1.0f / (V.l * (float)BS);
   float A[3], B[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     float wa = ((fp.Twc[4 * i] * pa0 + fp.Twc[4 * i + 1] * pa1) + fp.Twc[4 * i + 2] * pa2) + fp.Twc[4 * i + 3];
     float wb = ((fp.Twc[4 * i] * pb0 + fp.Twc[4 * i + 1] * pb1) + fp.Twc[4 * i + 2] * pb2) + fp.Twc[4 * i + 3];
-    A[i] = wa / bs;
-    B[i] = wb / bs;
+    A[i] = wa * ibs;
+    B[i] = wb * ibs;
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i)
