@@ -66,7 +66,16 @@ typedef struct {
   uint32_t max_blocks;    /* block pool size, 1 .. 2^21 */
   uint32_t max_vertices;  /* vertex pool size, 1 .. 2^30 */
   uint32_t max_triangles; /* triangle pool size, 1 .. 2^30 */
+  uint32_t flags;         /* 0, or VM_PARAM_COMPACT_EDGES */
 } vm_params;
+
+/* vm_params.flags: the compact cube record (Sec. IV proposes one heap reference each for a
+ * cube's edges and triangles): 19 B per cube -- (d, W) 8, two types 2, vertex flags 1, an
+ * edge-record index 4, a triangle-run start 4 -- plus a 12 B record (3 vertex ids) per voxel
+ * that owns a vertex, instead of 27 B per cube with the 3 vertex ids in place.  Same results;
+ * the record claims and their recycling cost mesh-pass time (about 5 % on a 640x480 room
+ * frame, 14 % on the 5 mm floor). */
+#define VM_PARAM_COMPACT_EDGES 1u
 
 typedef struct {
   int32_t width, height; /* pixels, 1 .. 16384 each */
@@ -78,7 +87,8 @@ typedef struct {
  * full_pool): the block pool (max_blocks), vertex pool (max_vertices), triangle pool
  * (max_triangles), the per-frame collected-block list (min(max_blocks, hash_buckets)), the
  * update-set list (max_blocks), the zero-reference vertex list (2 max_vertices), the
- * released-run list (max_triangles), a free stack, the hash table. */
+ * released-run list (max_triangles), a free stack, the hash table, the edge-record pool
+ * (max_vertices records, one per voxel that owns a vertex). */
 typedef enum {
   VM_POOL_NONE = 0,
   VM_POOL_BLOCKS,
@@ -89,7 +99,8 @@ typedef enum {
   VM_POOL_DEAD_VERTEX_LIST,
   VM_POOL_DEAD_RUN_LIST,
   VM_POOL_FREE_STACK,
-  VM_POOL_HASH
+  VM_POOL_HASH,
+  VM_POOL_EDGE_RECORDS
 } vm_pool;
 
 /* Per-call counters, filled by vm_get_stats (which synchronises). */
@@ -202,9 +213,12 @@ typedef struct {
   int64_t loose_vertices;  /* 3 per triangle: every triangle with its own corners */
   int64_t blocks;          /* allocated blocks */
   int64_t cube_bytes;      /* bytes per cube (voxel) of this layout: (d, W) 8, two types 2,
-                              vertex flags 1, vertex ids of the 3 owned edges 12, triangle run 4 */
-  int64_t bytes_in_use;    /* blocks x (512 cubes + block record) + vertices x 40 +
-                              triangles x 16 + hash buckets x 16 */
+                              vertex flags 1, edge-record index 4, triangle-run start 4 (Sec. IV:
+                              one heap reference each for the edges and the triangles) */
+  int64_t edge_records;    /* edge records in use: one per voxel that owns a vertex, 12 B each
+                              (the vertex ids of its 3 owned edges) */
+  int64_t bytes_in_use;    /* blocks x (512 cubes + block record) + edge records x 12 +
+                              vertices x 40 + triangles x 16 + hash buckets x 16 */
   int64_t bytes_allocated; /* device memory the volume holds (pool capacities) */
 } vm_mesh_memory;
 
@@ -316,7 +330,8 @@ vm_status vm_export_grad(vm_volume* vol, int32_t* keys, float* grad);
  * autotuner that times the candidate options on live ticks. */
 typedef struct vm_batch vm_batch;
 
-/* A batch of n (1..64) distinct volumes on the current device.  It enqueues on the first
+/* A batch of n (1..64) distinct volumes on the current device, all with the same cube layout
+ * (VM_PARAM_COMPACT_EDGES set on all or none).  It enqueues on the first
  * volume's stream; while it steps them, work on the volumes' own streams must be ordered
  * with that stream by the caller.  The volumes stay owned by the caller and must outlive
  * the batch.  VM_ERR_OOM when its small buffers cannot be allocated. */

@@ -95,6 +95,7 @@ __global__ void __launch_bounds__(INTEG_THREADS) kb_integrate(const Vol* __restr
 }
 
 // Mesh pass: every scene's update set, one block per CTA iteration.
+template <bool CE>
 __global__ void __launch_bounds__(MESH_THREADS, MESH_CTAS_PER_SM) kb_mesh(const Vol* __restrict__ vols, int nscenes, int mode,
                                                            int* bdone) {
   __shared__ MeshSmem S;
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(MESH_THREADS, MESH_CTAS_PER_SM) kb_mesh(const 
       cur = s;
     }
     const Vol& V = vols[s];
-    mesh_block(V, S, V.update[g - pre[s]], mode, cnt);
+    mesh_block<CE>(V, S, V.update[g - pre[s]], mode, cnt);
   }
   if (cur >= 0) mesh_flush(vols[cur], cnt);
   allow_dependent_launch();
@@ -124,12 +125,15 @@ __global__ void __launch_bounds__(MESH_THREADS, MESH_CTAS_PER_SM) kb_mesh(const 
 
 // Zero-reference vertices and released runs of every scene, in chunks of 32 list entries
 // (one warp per chunk, so the lanes of a warp share a scene).
+template <bool CE>
 __global__ void __launch_bounds__(256) kb_gc_vertices(const Vol* __restrict__ vols, int nscenes, int* bdone) {
   grid_dependency_wait();
-  __shared__ int pre_d[MAX_SCENES + 1], pre_r[MAX_SCENES + 1];
+  __shared__ int pre_d[MAX_SCENES + 1], pre_r[MAX_SCENES + 1], pre_e[MAX_SCENES + 1];
   scene_prefix(nscenes, pre_d, [&](int t) { return (min(__ldcg(&vols[t].ctl->c[C_N_DEAD]), vols[t].list_cap_dead) + 31) >> 5; });
   scene_prefix(nscenes, pre_r,
                [&](int t) { return (min(__ldcg(&vols[t].ctl->c[C_N_DEADRUN]), vols[t].list_cap_deadrun) + 31) >> 5; });
+  scene_prefix(nscenes, pre_e,
+               [&](int t) { return (min(__ldcg(&vols[t].ctl->c[C_N_DEADREC]), vols[t].max_vertices) + 31) >> 5; });
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -139,7 +143,7 @@ __global__ void __launch_bounds__(256) kb_gc_vertices(const Vol* __restrict__ vo
     const int n = min(__ldcg(&V.ctl->c[C_N_DEAD]), V.list_cap_dead);
     const int i = ((u - pre_d[s]) << 5) + lane;
     int freed = 0;
-    if (i < n) freed = gc_vertex(V, V.dead[i]);
+    if (i < n) freed = gc_vertex<CE>(V, V.dead[i]);
     gc_flush_vertices(V, freed);
   }
   for (int u = warp; u < pre_r[nscenes]; u += nwarps) {
@@ -151,6 +155,13 @@ __global__ void __launch_bounds__(256) kb_gc_vertices(const Vol* __restrict__ vo
       const int2 r = V.deadrun[i];
       if (r.y >= 1 && r.y <= 5) run_push(V, r.y, r.x);
     }
+  }
+  for (int u = warp; CE && u < pre_e[nscenes]; u += nwarps) {
+    const int s = scene_of(pre_e, nscenes, u);
+    const Vol& V = vols[s];
+    const int n = min(__ldcg(&V.ctl->c[C_N_DEADREC]), V.max_vertices);
+    const int i = ((u - pre_e[s]) << 5) + lane;
+    if (i < n) gc_record(V, V.dead_rec[i]);
   }
   allow_dependent_launch();
   if (last_block_at(bdone + BD_GC_VERTICES)) {

@@ -23,14 +23,27 @@ __device__ __forceinline__ void run_push(const Vol& V, int L, int base) {
 // listed twice, or one that regained a reference after it was listed, is freed at most once
 // and only when unreferenced; a vertex still attached to its edge is detached.  Returns
 // whether a detached vertex was freed.
+template <bool CE>
 __device__ __forceinline__ bool gc_vertex(const Vol& V, int vid) {
   if (atomicCAS(&V.vref[vid], 0, -1) != 0) return false;
   const uint32_t e = V.vedge[vid];
   bool detached = false;
   if (e != NO_EDGE) {
     const int ob = (int)(e / EPB), r = (int)(e - (uint32_t)ob * EPB), ov = r / 3, a = r - ov * 3;
-    V.edge_vtx[e] = -1;
-    atomic_and_u8(V.vmask + (size_t)ob * BV + ov, (uint8_t)~(1 << a));
+    const size_t vox = (size_t)ob * BV + ov;
+    if constexpr (CE) {
+      const int rec = V.edge_rec[vox];  // exists while the voxel owns a vertex
+      if (rec >= 0) V.erec[(size_t)rec * 3 + a] = -1;
+      // the thread that clears the voxel's last vertex bit frees its edge record (all -1 now)
+      const uint8_t old = atomic_and_u8(V.vmask + vox, (uint8_t)~(1 << a));
+      if (((old & 7) & ~(1 << a)) == 0 && rec >= 0) {
+        V.edge_rec[vox] = -1;
+        pool_push(V, V.rec_free, C_REC_TOP, V.max_vertices, rec);
+      }
+    } else {
+      V.edge_vtx[e] = -1;
+      atomic_and_u8(V.vmask + vox, (uint8_t)~(1 << a));
+    }
     atomicSub(&V.bnvert[ob], 1);
     detached = true;
   }
@@ -46,22 +59,32 @@ __device__ __forceinline__ void gc_flush_vertices(const Vol& V, int& freed) {
   freed = 0;
 }
 
-// After the last CTA (one thread): empty the two lists.
+// After the last CTA (one thread): empty the three lists.
 __device__ __forceinline__ void gc_vertices_finish(const Vol& V) {
   V.ctl->c[C_N_DEAD] = 0;
   V.ctl->c[C_N_DEADRUN] = 0;
+  V.ctl->c[C_N_DEADREC] = 0;
 }
 
-// Zero-reference vertices and released triangle runs back to their free stacks.
+// A spare edge record of a lost claim back to its free stack.
+__device__ __forceinline__ void gc_record(const Vol& V, int rec) { pool_push(V, V.rec_free, C_REC_TOP, V.max_vertices, rec); }
+
+// Zero-reference vertices and released triangle runs (and, CE, spare edge records) back to
+// their free stacks.
+template <bool CE>
 __global__ void __launch_bounds__(256) k_gc_vertices(Vol V) {
   grid_dependency_wait();
   const int n = min(__ldcg(&V.ctl->c[C_N_DEAD]), V.list_cap_dead);
   const int nr = min(__ldcg(&V.ctl->c[C_N_DEADRUN]), V.list_cap_deadrun);
   int freed = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) freed += gc_vertex(V, V.dead[i]);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) freed += gc_vertex<CE>(V, V.dead[i]);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
     const int2 r = V.deadrun[i];
     if (r.y >= 1 && r.y <= 5) run_push(V, r.y, r.x);
+  }
+  if (CE) {
+    const int nrec = min(__ldcg(&V.ctl->c[C_N_DEADREC]), V.max_vertices);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nrec; i += gridDim.x * blockDim.x) gc_record(V, V.dead_rec[i]);
   }
   gc_flush_vertices(V, freed);
   allow_dependent_launch();

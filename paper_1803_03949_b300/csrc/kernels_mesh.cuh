@@ -11,7 +11,7 @@
 //   b. per cube: type (and refinement), previous type; the block's existing vertices go to
 //      a refresh list; cubes whose effective type changes go to a shared list and mark the
 //      edges their new triangles use in a shared bitmap;
-//   c. compact the marked edges into a list;
+//   c. count the marked edges per bitmap word (stage d locates the j-th from the counts);
 //   d. one loop over three kinds of independent work: per marked edge its vertex id,
 //      creating the vertex on first use -- the first thread to claim the edge pops an id
 //      and publishes it with atomicCAS on the owner's edge slot; a thread that loses the
@@ -61,8 +61,8 @@ struct __align__(16) MeshSmem {
   uint8_t chg_new[BV], chg_old[BV];
   int chg_base[BV];       // run of the released triangles (stages b-c), then of the new ones
   unsigned emark[EDGE_WORDS];
-  int ecount[EDGE_WORDS];
-  uint16_t elist[EDGE_SLOTS];
+  int ecount[EDGE_WORDS];  // exclusive prefix of the marked edges over the bitmap's words
+  alignas(16) int rec[BV];  // the block's edge records (voxel -> record, -1 none), written as int4
   int evid[EDGE_SLOTS];
 };
 
@@ -185,6 +185,8 @@ __device__ __forceinline__ void deadrun_push(const Vol& V, int base, int L) {
 // additions commute, so the count is exact when the pass ends, and no fence is needed.
 // A thread that loses the claim resets its spare id to an unattached zero-reference vertex
 // and hands it to gc.
+// CE: the compact layout (edge records) rather than three vertex ids per voxel.
+template <bool CE>
 __device__ __forceinline__ int vertex_of_edge(const Vol& V, const MeshSmem& S, int x, int y, int z, int a,
                                               bool& claimed) {
   claimed = false;
@@ -192,11 +194,30 @@ __device__ __forceinline__ int vertex_of_edge(const Vol& V, const MeshSmem& S, i
   if (ob < 0) return -1;  // cannot happen for a valid cube
   const int ov = (x & 7) + 8 * (y & 7) + 64 * (z & 7);
   const uint32_t e = (uint32_t)ob * EPB + ov * 3 + a;
-  const int vid = __ldcg(&V.edge_vtx[e]);
+  const size_t vox = (size_t)ob * BV + ov;
+  int* slot;
+  if constexpr (CE) {
+    // the owner voxel's edge record (claimed like a vertex: first claimer publishes a record
+    // from the pool, whose three slots are -1 there; a loser's spare record goes to gc);
+    // voxels of the block itself have theirs staged in shared memory
+    int rec = (x | y | z) < 8 ? S.rec[ov] : -1;
+    if (rec < 0) rec = __ldcg(&V.edge_rec[vox]);
+    if (rec < 0) {
+      const int spare = pool_pop(V, V.rec_free, C_REC_TOP, C_REC_BUMP, V.max_vertices, 1, P_EDGE_RECORDS);
+      if (spare < 0) return -1;
+      rec = atomicCAS(&V.edge_rec[vox], -1, spare);
+      if (rec >= 0) list_push(V, V.dead_rec, C_N_DEADREC, V.max_vertices, spare);
+      else rec = spare;
+    }
+    slot = V.erec + (size_t)rec * 3 + a;
+  } else {
+    slot = V.edge_vtx + (size_t)e;
+  }
+  const int vid = __ldcg(slot);
   if (vid >= 0) return vid;
   const int mine = pool_pop(V, V.vtx_free, C_VTX_TOP, C_VTX_BUMP, V.max_vertices);
   if (mine < 0) return -1;
-  const int old = atomicCAS(&V.edge_vtx[e], -1, mine);
+  const int old = atomicCAS(slot, -1, mine);
   if (old >= 0) {  // another thread claimed the edge first
     V.vref[mine] = 0;
     V.vedge[mine] = NO_EDGE;
@@ -205,7 +226,7 @@ __device__ __forceinline__ int vertex_of_edge(const Vol& V, const MeshSmem& S, i
   }
   atomicAdd(&V.vref[mine], 1);  // -1 (free) -> 0, plus the references added by others
   V.vedge[mine] = e;
-  atomic_or_u8(V.vmask + (size_t)ob * BV + ov, (uint8_t)(1 << a));
+  atomic_or_u8(V.vmask + vox, (uint8_t)(1 << a));
   atomicAdd(&V.bnvert[ob], 1);
   claimed = true;  // the caller writes its position and normal
   return mine;
@@ -237,6 +258,7 @@ struct MeshCounts {
 
 // One update-set block `blk` through stages a-e, the calling CTA of MESH_THREADS with its
 // shared staging area S (S.tri64 already holds the triangle table).
+template <bool CE>
 __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, int mode, MeshCounts& cnt) {
   const float eps = V.eps, l = V.l;
   int& changed = cnt.changed;
@@ -263,6 +285,7 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
   const uint32_t vm_w = ld_early_u32(V.vmask + ci0);
   const uint32_t prev_w = (mode & M_UPDATE) ? eff_w : ld_early_u32(V.code_prev + ci0);
   const int4 tb4 = ld_early_i4(V.tri_base + ci0);
+  const int4 rec4 = CE ? ld_early_i4(V.edge_rec + ci0) : make_int4(-1, -1, -1, -1);
   __syncthreads();
   for (int h = threadIdx.x; h < HALO_N; h += MESH_THREADS) {
     const int x = h % HALO, y = (h / HALO) % HALO, z = h / (HALO * HALO);
@@ -272,6 +295,7 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
     S.halo[h] = q.y > 0.0f ? q.x : __int_as_float(0x7fc00000);
   }
   __syncthreads();
+  if (CE) reinterpret_cast<int4*>(S.rec)[threadIdx.x] = rec4;  // read from stage d on
   // ---- b. cube types, vertex refresh, changed-cube list, needed edges (4 consecutive cubes
   //         per thread: the type, previous-type and vertex-flag bytes move as 32-bit words)
   int dtri = 0;
@@ -327,7 +351,8 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
   if (dtri) atomicAdd(&S.dtri, dtri);
   __syncthreads();
   const int nchg = S.nchg;
-  // ---- c. compact the needed edges into a list (warp 0 scans the bitmap's word counts)
+  // ---- c. count the needed edges (warp 0 scans the bitmap's word counts; stage d finds the
+  //         j-th marked edge from these prefixes)
   if (threadIdx.x < 32) {
     int carry = 0;
     for (int w0 = 0; w0 < EDGE_WORDS; w0 += 32) {
@@ -344,16 +369,6 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
     if (threadIdx.x == 0) S.nedge = carry;
   }
   __syncthreads();
-  for (int w = threadIdx.x; w < EDGE_WORDS; w += MESH_THREADS) {
-    unsigned mbits = S.emark[w];
-    int r = S.ecount[w];
-    while (mbits) {
-      const int b = __ffs(mbits) - 1;
-      mbits &= mbits - 1;
-      S.elist[r++] = (uint16_t)(w * 32 + b);
-    }
-  }
-  __syncthreads();
   // ---- d. one loop over three independent kinds of work, so the stage lasts as long as the
   //         longest chain rather than their sum:
   //         per needed edge: its vertex, created on first use;
@@ -366,11 +381,17 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
       int x, y, z, a, vid;
       bool fresh;
       if (j < nedge) {
-        const int es = S.elist[j];
+        int lo = 0, hi = EDGE_WORDS - 1;  // the word holding marked edge j
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (S.ecount[mid] <= j) lo = mid;
+          else hi = mid - 1;
+        }
+        const int es = lo * 32 + (int)__fns(S.emark[lo], 0, j - S.ecount[lo] + 1);
         const int o = es / 3;
         a = es - 3 * o;
         x = o % 9, y = (o / 9) % 9, z = o / 81;
-        vid = vertex_of_edge(V, S, x, y, z, a, fresh);
+        vid = vertex_of_edge<CE>(V, S, x, y, z, a, fresh);
         S.evid[es] = vid;
         created += fresh;
       } else {
@@ -378,7 +399,12 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
         const int c = r / 3;
         a = r - c * 3;
         x = c & 7, y = (c >> 3) & 7, z = c >> 6;
-        vid = __ldcg(&V.edge_vtx[((size_t)blk * BV + c) * 3 + a]);
+        if constexpr (CE) {
+          const int rec = S.rec[c];
+          vid = rec >= 0 ? __ldcg(&V.erec[(size_t)rec * 3 + a]) : -1;
+        } else {
+          vid = __ldcg(&V.edge_vtx[((size_t)blk * BV + c) * 3 + a]);
+        }
         fresh = vid >= 0;
         refreshed += fresh;
       }
@@ -472,6 +498,7 @@ __device__ __forceinline__ void mesh_flush(const Vol& V, MeshCounts& c) {
 // vertex and run free-stack tops, statistics.
 __device__ __forceinline__ void mesh_finish(const Vol& V, int n) {
   fold_top(V, C_VTX_TOP);
+  fold_top(V, C_REC_TOP);
 #pragma unroll
   for (int L = 0; L < 5; ++L) fold_top(V, C_RUN_TOP0 + L);
   V.ctl->c[C_ST_UPDATE_BLOCKS] = n;
@@ -482,13 +509,14 @@ __device__ __forceinline__ void mesh_finish(const Vol& V, int n) {
 // mode: M_UPDATE (types from the current TSDF; t_{i-1} := previous effective type; refresh
 // the positions and normals of the block's existing vertices), M_REFINE (Eqs. 3-5 with the
 // stored t_{i-1}).  The last CTA clamps the vertex and run free-stack tops.
+template <bool CE>
 __global__ void __launch_bounds__(MESH_THREADS, MESH_CTAS_PER_SM) k_mesh(Vol V, int mode) {
   __shared__ MeshSmem S;
   for (int i = threadIdx.x; i < 128; i += MESH_THREADS) reinterpret_cast<uint4*>(S.tri64)[i] = V.tri_table[i];
   grid_dependency_wait();
   const int n = min(__ldcg(&V.ctl->c[C_N_UPDATE]), V.list_cap_update);
   MeshCounts cnt;
-  for (int i = blockIdx.x; i < n; i += gridDim.x) mesh_block(V, S, V.update[i], mode, cnt);
+  for (int i = blockIdx.x; i < n; i += gridDim.x) mesh_block<CE>(V, S, V.update[i], mode, cnt);
   mesh_flush(V, cnt);
   allow_dependent_launch();
   if (last_block(V, C_DONE3)) {

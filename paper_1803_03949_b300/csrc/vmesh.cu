@@ -229,7 +229,11 @@ vm_status enqueue_list_all(vm_volume* v) {
 }
 
 vm_status enqueue_mesh_pass(vm_volume* v, int mode) {
-  return launch(v, K_MESH, [&] { launch_dependent(k_mesh, grid_for(v, MESH_CTAS_PER_SM), MESH_THREADS, v->cur, v->V, mode); });
+  const bool ce = (v->p.flags & VM_PARAM_COMPACT_EDGES) != 0;
+  return launch(v, K_MESH, [&] {
+    launch_dependent(ce ? k_mesh<true> : k_mesh<false>, grid_for(v, MESH_CTAS_PER_SM), MESH_THREADS, v->cur, v->V,
+                     mode);
+  });
 }
 
 vm_status enqueue_update(vm_volume* v, int flags) {
@@ -242,7 +246,10 @@ vm_status enqueue_update(vm_volume* v, int flags) {
 }
 
 vm_status enqueue_gc(vm_volume* v) {
-  vm_status st = launch(v, K_GC_VERTICES, [&] { launch_dependent(k_gc_vertices, grid_for(v, 2), 256, v->cur, v->V); });
+  const bool ce = (v->p.flags & VM_PARAM_COMPACT_EDGES) != 0;
+  vm_status st = launch(v, K_GC_VERTICES, [&] {
+    launch_dependent(ce ? k_gc_vertices<true> : k_gc_vertices<false>, grid_for(v, 2), 256, v->cur, v->V);
+  });
   if (st) return st;
   const int consumed = v->advance_pending ? 1 : 0;
   return launch(v, K_GC_BLOCKS,
@@ -334,7 +341,7 @@ vm_status vm_create_volume(const vm_params* p, void* cuda_stream, vm_volume** ou
       !(p->trunc <= 32.0f * p->voxel_size) || !(p->eps_refine >= 0) || !std::isfinite(p->eps_refine) ||
       !(p->w_max >= 1) || !std::isfinite(p->w_max) || hb < 16 || hb > (1u << 30) || (hb & (hb - 1)) ||
       p->max_blocks < 1 || p->max_blocks > (1u << 21) || p->max_vertices < 1 || p->max_vertices > (1u << 30) ||
-      p->max_triangles < 1 || p->max_triangles > (1u << 30))
+      p->max_triangles < 1 || p->max_triangles > (1u << 30) || (p->flags & ~VM_PARAM_COMPACT_EDGES))
     return VM_ERR_INVALID_ARG;
   static vmk_host::McTable table;
   static bool table_built = false;
@@ -353,8 +360,10 @@ vm_status vm_create_volume(const vm_params* p, void* cuda_stream, vm_volume** ou
   cudaDeviceGetAttribute(&v->num_sms, cudaDevAttrMultiProcessorCount, dev);
   if (v->num_sms <= 0) v->num_sms = 148;
   // the mesh kernel keeps ~32 KB of shared memory per CTA: ask for the largest carveout
-  cudaFuncSetAttribute(k_mesh, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-  cudaFuncSetAttribute(kb_mesh, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  cudaFuncSetAttribute(k_mesh<false>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  cudaFuncSetAttribute(k_mesh<true>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  cudaFuncSetAttribute(kb_mesh<false>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  cudaFuncSetAttribute(kb_mesh<true>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   (void)cudaGetLastError();
   if (cudaMemcpyToSymbol(c_ntri, table.ntri, sizeof(table.ntri)) != cudaSuccess ||
       cudaMemcpyToSymbol(c_tri, table.tri, sizeof(table.tri)) != cudaSuccess ||
@@ -378,12 +387,16 @@ vm_status vm_create_volume(const vm_params* p, void* cuda_stream, vm_volume** ou
   V.list_cap_dead = (int)((2ull * p->max_vertices) < (1ull << 31) - 1 ? 2ull * p->max_vertices : (1ull << 31) - 1);
   V.list_cap_deadrun = (int)p->max_triangles;
   const size_t NB = p->max_blocks, NV = p->max_vertices, NT = p->max_triangles;
+  const bool compact = (p->flags & VM_PARAM_COMPACT_EDGES) != 0;
   bool ok = dalloc(v, &V.keys, hb, 0xFF) && dalloc(v, &V.vals, hb, 0xFF) && dalloc(v, &V.stamp, hb, 0) &&
             dalloc(v, &V.ustamp, NB, 0) && dalloc(v, &V.bkey, NB, 0xFF) && dalloc(v, &V.nbr, NB * 16, 0xFF) &&
             dalloc(v, &V.bntri, NB, 0) && dalloc(v, &V.bnvert, NB, 0) && dalloc(v, &V.bnear, NB, 0) &&
             dalloc(v, &V.bepoch, NB, 0) && dalloc(v, &V.bborn, NB, 0) && dalloc(v, &V.tw, NB * BV, 0) &&
             dalloc(v, &V.code_eff, NB * BV, 0) && dalloc(v, &V.code_prev, NB * BV, 0) &&
-            dalloc(v, &V.vmask, NB * BV, 0) && dalloc(v, &V.edge_vtx, NB * BV * 3, 0xFF) &&
+            dalloc(v, &V.vmask, NB * BV, 0) &&
+            (compact ? dalloc(v, &V.edge_rec, NB * BV, 0xFF) && dalloc(v, &V.erec, NV * 3, 0xFF) &&
+                           dalloc(v, &V.rec_free, NV, 0) && dalloc(v, &V.dead_rec, NV, 0)
+                     : dalloc(v, &V.edge_vtx, NB * BV * 3, 0xFF)) &&
             dalloc(v, &V.tri_base, NB * BV, 0xFF) && dalloc(v, &V.vpos, NV, 0) && dalloc(v, &V.vnrm, NV, 0) &&
             dalloc(v, &V.vref, NV, 0xFF) && dalloc(v, &V.vedge, NV, 0xFF) && dalloc(v, &V.tris, NT, 0xFF) &&
             dalloc(v, &V.blk_free, NB, 0) && dalloc(v, &V.vtx_free, NV, 0) &&
@@ -601,9 +614,15 @@ vm_status vm_mesh_memory_stats(vm_volume* v, vm_mesh_memory* m) {
     return VM_ERR_CUDA;
   }
   const int64_t blocks = read_counter(v, C_LIVE_BLOCKS);
-  // per voxel (cube): (d, W) 8, current and previous type 2, vertex flags 1, vertex ids of
-  // the 3 owned edges 12, triangle-run start 4
-  const int64_t cube = 8 + 2 + 1 + 12 + 4;
+  const bool ce = (v->p.flags & VM_PARAM_COMPACT_EDGES) != 0;
+  const int64_t records =
+      !ce ? 0
+          : std::max<int64_t>(0, (int64_t)std::min(read_counter(v, C_REC_BUMP), (int)v->p.max_vertices) -
+                                     std::max(read_counter(v, C_REC_TOP), 0));
+  // per voxel (cube): (d, W) 8, current and previous type 2, vertex flags 1, then either the
+  // vertex ids of its 3 owned edges 12 or (compact) an edge-record index 4 with a 12 B record
+  // per voxel that owns a vertex; triangle-run start 4
+  const int64_t cube = 8 + 2 + 1 + (ce ? 4 : 12) + 4;
   // per block: key + bucket 16, neighbour table 64, triangle/vertex counts 8, near flag 1,
   // three stamps 12; per vertex: position 16, normal 16, reference count 4, owning edge 4;
   // per triangle: 16; per hash bucket: key 8, block index 4, stamp 4
@@ -614,7 +633,8 @@ vm_status vm_mesh_memory_stats(vm_volume* v, vm_mesh_memory* m) {
   m->loose_vertices = 3 * nt;
   m->blocks = blocks;
   m->cube_bytes = cube;
-  m->bytes_in_use = blocks * (BV * cube + per_block) + nv * per_vertex + nt * per_tri +
+  m->edge_records = records;
+  m->bytes_in_use = blocks * (BV * cube + per_block) + records * 12 + nv * per_vertex + nt * per_tri +
                     (int64_t)(v->V.hmask + 1) * per_bucket;
   m->bytes_allocated = (int64_t)v->bytes_allocated;
   return VM_OK;
@@ -1128,6 +1148,7 @@ struct TuneRec {
 struct vm_batch {
   std::vector<vm_volume*> vols;
   int n = 0;
+  bool compact = false;  // every volume of a batch has the same cube layout
   Vol* d_vols = nullptr;
   int* d_done = nullptr;
   cudaStream_t stream = nullptr;
@@ -1189,10 +1210,12 @@ vm_status batch_enqueue(vm_batch* b, cudaStream_t st, const int* sc, int flags, 
   if (rec) cudaEventRecord(rec->ev[1], st);
   launch_dependent(kb_integrate, b->num_sms * sc[1], INTEG_THREADS, st, (const Vol*)b->d_vols, b->n, b->d_done);
   if (rec) cudaEventRecord(rec->ev[2], st);
-  launch_dependent(kb_mesh, b->num_sms * sc[2], MESH_THREADS, st, (const Vol*)b->d_vols, b->n, mode, b->d_done);
+  launch_dependent(b->compact ? kb_mesh<true> : kb_mesh<false>, b->num_sms * sc[2], MESH_THREADS, st,
+                   (const Vol*)b->d_vols, b->n, mode, b->d_done);
   if (rec) cudaEventRecord(rec->ev[3], st);
   if (flags & VM_GC) {
-    launch_dependent(kb_gc_vertices, b->num_sms * sc[3], 256, st, (const Vol*)b->d_vols, b->n, b->d_done);
+    launch_dependent(b->compact ? kb_gc_vertices<true> : kb_gc_vertices<false>, b->num_sms * sc[3], 256, st,
+                     (const Vol*)b->d_vols, b->n, b->d_done);
     if (rec) cudaEventRecord(rec->ev[4], st);
     launch_dependent(kb_gc_blocks, b->num_sms * sc[4], 256, st, (const Vol*)b->d_vols, b->n, 1, b->d_done);
   } else if (rec) {
@@ -1238,12 +1261,14 @@ vm_status vm_batch_create(vm_volume* const* vols, int n, vm_batch** out) {
   if (!vols || !out || n < 1 || n > MAX_SCENES) return VM_ERR_INVALID_ARG;
   for (int i = 0; i < n; ++i) {
     if (!vols[i]) return VM_ERR_INVALID_ARG;
+    if ((vols[i]->p.flags ^ vols[0]->p.flags) & VM_PARAM_COMPACT_EDGES) return VM_ERR_INVALID_ARG;
     for (int j = 0; j < i; ++j)
       if (vols[j] == vols[i]) return VM_ERR_INVALID_ARG;
   }
   vm_batch* b = new vm_batch();
   b->vols.assign(vols, vols + n);
   b->n = n;
+  b->compact = (vols[0]->p.flags & VM_PARAM_COMPACT_EDGES) != 0;
   b->stream = vols[0]->stream;
   b->num_sms = vols[0]->num_sms;
   for (int k = 0; k < SCHED_SLOTS; ++k) b->sched[k] = kSchedDefault[k];

@@ -11,8 +11,12 @@
 //             owns), bnear u8[NB] (some voxel has W > 0 and d < mu), bepoch u32[NB] (epoch
 //             it was last collected in), bborn u32[NB] (integrate call that created it)
 //   voxels    tw float2[NB*512] (TSDF d, weight W), code_eff/code_prev u8[NB*512],
-//             vmask u8[NB*512] (bits 0-2: the owned edge has a vertex),
-//             edge_vtx i32[NB*512*3] (vertex on owned edge, -1 none), tri_base i32[NB*512]
+//             vmask u8[NB*512] (bits 0-2: the owned edge has a vertex), tri_base i32[NB*512],
+//             and the vertex ids of the voxel's 3 owned edges (-1 none), either
+//             edge_vtx i32[NB*512*3] (wide layout, 27 B per cube) or, with the compact layout
+//             (19 B per cube), edge_rec i32[NB*512] (the voxel's edge record, -1 none) into
+//             erec i32[NV*3], one record per voxel that owns a vertex, from a pool with its
+//             own free stack
 //   vertices  vpos float4[NV], vnrm float4[NV], vref i32[NV] (reference count, -1 free),
 //             vedge u32[NV] (owning edge id = block*1536 + voxel*3 + axis, below 2^32 for up
 //             to 2^21 blocks; NO_EDGE = unattached)
@@ -53,6 +57,8 @@ enum Counter {
   C_N_UPDATE,       // blocks in the update set
   C_N_DEAD,         // zero-reference vertices awaiting gc
   C_N_DEADRUN,      // released triangle runs awaiting gc
+  C_N_DEADREC,      // spare edge records of lost record claims, awaiting gc
+  C_REC_TOP, C_REC_BUMP,
   C_BLK_TOP, C_BLK_BUMP,
   C_VTX_TOP, C_VTX_BUMP,
   C_RUN_TOP0, C_RUN_TOP1, C_RUN_TOP2, C_RUN_TOP3, C_RUN_TOP4,
@@ -104,7 +110,11 @@ struct Vol {
   uint8_t* code_eff;
   uint8_t* code_prev;
   uint8_t* vmask;
-  int* edge_vtx;
+  int* edge_vtx;  // wide layout: per voxel the vertex ids of its 3 owned edges
+  int* edge_rec;  // compact layout: per voxel the index of its edge record, -1 none
+  int* erec;      // edge records: 3 vertex ids each (-1 none)
+  int* rec_free;  // free stack of edge records
+  int* dead_rec;  // spare records of lost claims (recycled by gc)
   int* tri_base;
 
   float4* vpos;
@@ -168,13 +178,15 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {  // murmur3 finaliser
 // Which capacity ran out (the first one, kept beside the status; values of the C ABI's
 // vm_pool enum).
 enum PoolCode { P_NONE = 0, P_BLOCKS, P_VERTICES, P_TRIANGLES, P_COLLECTED_LIST, P_UPDATE_LIST, P_DEAD_VERTEX_LIST,
-                P_DEAD_RUN_LIST, P_FREE_STACK, P_HASH };
+                P_DEAD_RUN_LIST, P_FREE_STACK, P_HASH, P_EDGE_RECORDS };
 __device__ __forceinline__ void set_status(const Vol& V, int st, int pool = P_NONE) {
   atomicCAS(&V.ctl->c[C_STATUS], 0, st);
   if (pool != P_NONE) atomicCAS(&V.ctl->c[C_STATUS_POOL], 0, pool);
 }
 __device__ __forceinline__ int list_pool_code(int c_count) {
-  return c_count == C_N_TOUCHED ? P_COLLECTED_LIST : (c_count == C_N_UPDATE ? P_UPDATE_LIST : P_DEAD_VERTEX_LIST);
+  return c_count == C_N_TOUCHED ? P_COLLECTED_LIST
+                                : (c_count == C_N_UPDATE ? P_UPDATE_LIST
+                                                         : (c_count == C_N_DEADREC ? P_EDGE_RECORDS : P_DEAD_VERTEX_LIST));
 }
 
 // Hash lookup: bucket holding `key`, or -1.  Linear probing, at most hmask+1 probes.
@@ -199,7 +211,8 @@ __device__ __forceinline__ int find_block(const Vol& V, int x, int y, int z) {
 // by a bump range, aggregated over the lanes that call it together.  Pops and pushes of
 // one stack never share a kernel; the popping kernel clamps the stack top at 0 when it
 // ends (fold_top).  Returns -1 (and sets POOL_FULL) when the pool is exhausted.
-__device__ __forceinline__ int pool_pop(const Vol& V, int* stack, int c_top, int c_bump, int cap, int stride = 1) {
+__device__ __forceinline__ int pool_pop(const Vol& V, int* stack, int c_top, int c_bump, int cap, int stride = 1,
+                                        int pool = P_VERTICES) {
   cg::coalesced_group g = cg::coalesced_threads();
   int n = (int)g.size(), rank = (int)g.thread_rank();
   int old = 0, bump0 = 0, from_stack = 0;
@@ -217,7 +230,7 @@ __device__ __forceinline__ int pool_pop(const Vol& V, int* stack, int c_top, int
   } else {
     long long b = (long long)bump0 + (long long)(rank - from_stack) * stride;
     if (b + stride > cap) {
-      set_status(V, ST_POOL_FULL, P_VERTICES);
+      set_status(V, ST_POOL_FULL, pool);
       id = -1;
     } else {
       id = (int)b;

@@ -16,6 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libvmesh.so")
 
 VM_FULL, VM_REFINE, VM_GC = 1, 2, 4
+VM_PARAM_COMPACT_EDGES = 1
 STATUS = {0: "VM_OK", 1: "VM_ERR_INVALID_ARG", 2: "VM_ERR_HASH_FULL", 3: "VM_ERR_POOL_FULL", 4: "VM_ERR_CUDA",
           5: "VM_ERR_OOM"}
 
@@ -29,7 +30,7 @@ class VmeshError(RuntimeError):
 class vm_params(ctypes.Structure):
     _fields_ = [("voxel_size", ctypes.c_float), ("trunc", ctypes.c_float), ("eps_refine", ctypes.c_float),
                 ("w_max", ctypes.c_float), ("hash_buckets", ctypes.c_uint32), ("max_blocks", ctypes.c_uint32),
-                ("max_vertices", ctypes.c_uint32), ("max_triangles", ctypes.c_uint32)]
+                ("max_vertices", ctypes.c_uint32), ("max_triangles", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
 
 
 class vm_intrinsics(ctypes.Structure):
@@ -45,13 +46,13 @@ class vm_frame_stats(ctypes.Structure):
         "collected_blocks", "meshed_blocks", "full_pool")]
 
 POOLS = ["none", "blocks", "vertices", "triangles", "collected_list", "update_list", "dead_vertex_list", "dead_run_list",
-         "free_stack", "hash"]
+         "free_stack", "hash", "edge_records"]
 
 
 class vm_mesh_memory(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
-        "vertices", "triangles", "block_vertices", "loose_vertices", "blocks", "cube_bytes", "bytes_in_use",
-        "bytes_allocated")]
+        "vertices", "triangles", "block_vertices", "loose_vertices", "blocks", "cube_bytes", "edge_records",
+        "bytes_in_use", "bytes_allocated")]
 
 
 _lib = None
@@ -161,7 +162,7 @@ class Volume:
     """A spatially hashed TSDF volume with its incrementally maintained mesh (one GPU)."""
 
     def __init__(self, voxel_size, trunc, hash_buckets, max_blocks, max_vertices, max_triangles,
-                 eps_refine=None, w_max=255.0, stream=None):
+                 eps_refine=None, w_max=255.0, stream=None, compact_edges=False):
         import torch
 
         if not torch.cuda.is_available():
@@ -170,7 +171,7 @@ class Volume:
         if eps_refine is None:
             eps_refine = 0.2 * voxel_size
         self.params = vm_params(voxel_size, trunc, eps_refine, w_max, hash_buckets, max_blocks, max_vertices,
-                                max_triangles)
+                                max_triangles, VM_PARAM_COMPACT_EDGES if compact_edges else 0)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = ctypes.c_void_p()
         _check(self._lib.vm_create_volume(ctypes.byref(self.params), ctypes.c_void_p(self.stream.cuda_stream),
@@ -179,6 +180,7 @@ class Volume:
 
     @classmethod
     def from_config(cls, vc, **kw):
+        kw.setdefault("compact_edges", getattr(vc, "compact_edges", False))
         return cls(vc.voxel_size, vc.trunc, vc.hash_buckets, vc.max_blocks, vc.max_vertices, vc.max_triangles,
                    eps_refine=vc.eps_refine, w_max=vc.w_max, **kw)
 

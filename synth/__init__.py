@@ -73,6 +73,7 @@ class VolumeConfig:
     max_triangles: int
     eps_refine_frac: float = 0.2  # epsilon of Eq. 5 as a fraction of l
     w_max: float = 255.0
+    compact_edges: bool = False  # the compact cube record (one edge-record index per voxel)
 
     @property
     def eps_refine(self) -> float:

@@ -64,7 +64,7 @@ def test_bad_arguments_are_refused():
 
 @pytest.mark.parametrize("field,value", [("voxel_size", 0.0), ("trunc", -1.0), ("trunc", 1.0), ("hash_buckets", 1000),
                                          ("hash_buckets", 8), ("max_blocks", 0), ("max_blocks", (1 << 21) + 1),
-                                         ("w_max", 0.5)])
+                                         ("w_max", 0.5), ("flags", 2)])
 def test_bad_params_are_refused(field, value):
     lib = load_library()
     p = vm_params(0.01, 0.04, 0.002, 255.0, 1 << 14, 1 << 10, 1 << 16, 1 << 16)

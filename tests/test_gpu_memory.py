@@ -1,5 +1,7 @@
 """Mesh memory counts on the GPU (Sec. VI-B): edge-owned vertices against a per-block
 extraction and loose triangles, equal to the oracle's counts."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -11,11 +13,18 @@ from tests.meshutil import field_fill
 pytestmark = pytest.mark.gpu
 
 
-def _check_counts(g, o):
+def _check_counts(g, o, after_gc):
     gm, om = g.mesh_memory(), o.mesh_memory()
     for k in ("vertices", "block_vertices", "loose_vertices", "triangles"):
         assert gm[k] == om[k], (k, gm[k], om[k])
-    assert gm["cube_bytes"] == 27
+    if g.params.flags:  # the compact cube record
+        assert gm["cube_bytes"] == 19
+        # one edge record per voxel owning a vertex: exactly the live vertices' owners after a gc
+        # (before it, also voxels whose vertices await recycling and spares of lost claims)
+        owners = len(np.unique(np.asarray(g.download()["keys"], np.uint64) >> np.uint64(2)))
+        assert gm["edge_records"] == owners if after_gc else gm["edge_records"] >= owners, (gm["edge_records"], owners)
+    else:
+        assert gm["cube_bytes"] == 27 and gm["edge_records"] == 0
     assert 0 < gm["bytes_in_use"] < gm["bytes_allocated"]
     return gm
 
@@ -39,13 +48,14 @@ def test_sphere_workload_counts_match_oracle():
     run_frames(s, range(10), gpu=g, orc=o, refine=False, gc=False)
     g.update_mesh(full=True, refine=True)
     o.update_mesh(full=True, refine=True)
-    m = _check_counts(g, o)
+    m = _check_counts(g, o, after_gc=False)
     assert m["block_vertices"] > m["vertices"] and m["loose_vertices"] > 4 * m["vertices"]
 
 
-def test_room_incremental_counts_match_oracle():
+@pytest.mark.parametrize("compact", [False, True])
+def test_room_incremental_counts_match_oracle(compact):
     s = synth.room_scene(num_frames=12, W=320, H=240)
-    g = gpu_volume(s.volume)
+    g = gpu_volume(dataclasses.replace(s.volume, compact_edges=compact))
     o = oracle.Volume.from_config(s.volume, prec="f32")
     run_frames(s, range(12), gpu=g, orc=o, refine=True, gc=True, mode="graph")
-    _check_counts(g, o)
+    _check_counts(g, o, after_gc=True)
