@@ -614,6 +614,18 @@ def run_vmesh(args, rank, world, local):
     value = world * args.steps / (max_ms / 1000.0)
     vps = 512 * collected / (total_ms / 1000.0)
 
+    # the compact cube record on the same frames (value pass only): speed and memory
+    import dataclasses
+
+    volc = Volume.from_config(dataclasses.replace(vc, compact_edges=True), stream=stream)
+    warm_up(volc)
+    ms_c, _, _ = streamed(volc)
+    mem_c = volc.mesh_memory()
+    volc.close()
+    compact = {"value": args.steps / (sum(ms_c) / 1000.0), "unit": UNIT, "cube_bytes": mem_c["cube_bytes"],
+               "edge_records": mem_c["edge_records"], "bytes_in_use": mem_c["bytes_in_use"],
+               "bytes_allocated": mem_c["bytes_allocated"]}
+
     # pass 2 -- kernel durations: the same frames on a fresh volume (identical, deterministic
     # work), with CUDA-event pairs around the two kernels the calibration ranked highest
     peak, peak_kind = load_peaks()
@@ -685,9 +697,11 @@ def run_vmesh(args, rank, world, local):
             "per_block_extraction_vertices": mem["block_vertices"], "loose_triangle_vertices": mem["loose_vertices"],
             "per_block_over_ours": mem["block_vertices"] / max(mem["vertices"], 1),
             "loose_over_ours": mem["loose_vertices"] / max(mem["vertices"], 1),
-            "blocks": mem["blocks"], "cube_bytes": mem["cube_bytes"], "paper_cube_bytes": 56,
+            "blocks": mem["blocks"], "cube_bytes": mem["cube_bytes"], "edge_records": mem["edge_records"],
+            "paper_cube_bytes": 56,
             "paper_compact_cube_bytes": 24, "bytes_in_use": mem["bytes_in_use"],
             "bytes_allocated": mem["bytes_allocated"],
+            "compact_layout": compact,
         },
     }
     if not args.skip_forms:
