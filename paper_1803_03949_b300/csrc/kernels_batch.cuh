@@ -53,7 +53,7 @@ __device__ __forceinline__ int scene_of(const int* pre, int n, int g) {
 }
 
 // Block collection: grid (tiles across, tiles down, scenes); a CTA whose tile lies outside
-// its scene's image only takes its ticket.  The last CTA finishes every scene.
+// its scene's image does nothing; each scene's first CTA starts its epoch.
 template <int PPT>
 __global__ void __launch_bounds__(ALLOC_TILE_W * ALLOC_TILE_H / PPT)
     kb_alloc(const Vol* __restrict__ vols, int nscenes, const __grid_constant__ BatchFrames bf, int* bdone) {
@@ -61,14 +61,13 @@ __global__ void __launch_bounds__(ALLOC_TILE_W * ALLOC_TILE_H / PPT)
   const int s = blockIdx.z;
   const Vol& V = vols[s];
   const FrameParams& fp = bf.fp[s];
-  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) V.ctl->fp = fp;  // for the later kernels
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    V.ctl->fp = fp;  // for the later kernels
+    alloc_begin(V, bf.advance[s]);
+  }
   if ((int)blockIdx.x * ALLOC_TILE_W < fp.W && (int)blockIdx.y * ALLOC_TILE_H < fp.H)
     alloc_tile<PPT>(V, fp, blockIdx.x, blockIdx.y, set);
   allow_dependent_launch();
-  if (last_block_at(bdone + BD_ALLOC)) {
-    for (int t = threadIdx.x; t < nscenes; t += blockDim.x) alloc_finish(vols[t], bf.advance[t]);
-    if (threadIdx.x == 0) bdone[BD_ALLOC] = 0;
-  }
 }
 
 // Fusion: every scene's collected blocks, one per CTA iteration.
@@ -104,6 +103,8 @@ __global__ void __launch_bounds__(MESH_THREADS, MESH_CTAS_PER_SM) kb_mesh(const 
   grid_dependency_wait();
   scene_prefix(nscenes, pre, [&](int t) { return min(__ldcg(&vols[t].ctl->c[C_N_UPDATE]), vols[t].list_cap_update); });
   const int total = pre[nscenes];
+  if (blockIdx.x == 0)
+    for (int t = threadIdx.x; t < nscenes; t += blockDim.x) mesh_begin(vols[t], pre[t + 1] - pre[t]);
   MeshCounts cnt;
   int cur = -1;
   for (int g = blockIdx.x; g < total; g += gridDim.x) {
@@ -117,10 +118,6 @@ __global__ void __launch_bounds__(MESH_THREADS, MESH_CTAS_PER_SM) kb_mesh(const 
   }
   if (cur >= 0) mesh_flush(vols[cur], cnt);
   allow_dependent_launch();
-  if (last_block_at(bdone + BD_MESH)) {
-    for (int t = threadIdx.x; t < nscenes; t += blockDim.x) mesh_finish(vols[t], pre[t + 1] - pre[t]);
-    if (threadIdx.x == 0) bdone[BD_MESH] = 0;
-  }
 }
 
 // Zero-reference vertices and released runs of every scene, in chunks of 32 list entries
@@ -164,10 +161,6 @@ __global__ void __launch_bounds__(256) kb_gc_vertices(const Vol* __restrict__ vo
     if (i < n) gc_record(V, V.dead_rec[i]);
   }
   allow_dependent_launch();
-  if (last_block_at(bdone + BD_GC_VERTICES)) {
-    for (int t = threadIdx.x; t < nscenes; t += blockDim.x) gc_vertices_finish(vols[t]);
-    if (threadIdx.x == 0) bdone[BD_GC_VERTICES] = 0;
-  }
 }
 
 // Block recycling of every scene, one warp per pool slot in use.  The last CTA finishes the
@@ -175,6 +168,8 @@ __global__ void __launch_bounds__(256) kb_gc_vertices(const Vol* __restrict__ vo
 __global__ void __launch_bounds__(256) kb_gc_blocks(const Vol* __restrict__ vols, int nscenes, int consumed,
                                                     int* bdone) {
   grid_dependency_wait();
+  if (blockIdx.x == 0)
+    for (int t = threadIdx.x; t < nscenes; t += blockDim.x) gc_lists_reset(vols[t]);
   __shared__ int pre[MAX_SCENES + 1];
   __shared__ uint32_t sepoch[MAX_SCENES];
   if (threadIdx.x < nscenes) sepoch[threadIdx.x] = (uint32_t)__ldcg(&vols[threadIdx.x].ctl->c[C_EPOCH]);

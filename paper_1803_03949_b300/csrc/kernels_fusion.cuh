@@ -41,6 +41,7 @@ __device__ int hash_insert(const Vol& V, uint64_t key, int bx, int by, int bz, u
         if (old_top > 0) {
           blk = __ldcg(&V.blk_free[old_top - 1]);
         } else {
+          atomicAdd(&V.ctl->c[C_BLK_TOP], 1);  // the empty stack's top back to >= 0
           blk = atomicAdd(&V.ctl->c[C_BLK_BUMP], 1);
           if (blk >= V.max_blocks) {
             set_status(V, ST_POOL_FULL, P_BLOCKS);
@@ -200,10 +201,10 @@ __device__ __forceinline__ void alloc_tile(const Vol& V, const FrameParams& fp, 
   }
 }
 
-// After the last tile of a frame (one thread): clamp the block free-stack top and, when
-// `advance_epoch`, start a new mesh epoch with an empty update set.
-__device__ __forceinline__ void alloc_finish(const Vol& V, int advance_epoch) {
-  fold_top(V, C_BLK_TOP);
+// At the start of a frame's collection (one thread of the first CTA; nothing in the
+// collection reads the epoch or the update set): with `advance_epoch`, a new mesh epoch
+// with an empty update set.
+__device__ __forceinline__ void alloc_begin(const Vol& V, int advance_epoch) {
   if (advance_epoch) {
     V.ctl->c[C_EPOCH] += 1;
     V.ctl->c[C_N_UPDATE] = 0;
@@ -212,19 +213,17 @@ __device__ __forceinline__ void alloc_finish(const Vol& V, int advance_epoch) {
 
 // One CTA per 64 x 16 pixel tile, two vertically adjacent pixels per thread (so a 640 x 480
 // frame fits in one wave of CTAs).  The frame's parameters arrive as a launch argument; the
-// first CTA stores them in the control block for the kernels that follow.
+// first CTA stores them in the control block for the kernels that follow and starts the
+// epoch.  No CTA waits for the others: the kernel ends with its last tile.
 __global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(Vol V, const __grid_constant__ FrameParams fp,
                                                          int advance_epoch) {
   __shared__ unsigned long long set[ALLOC_SET];
-  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) V.ctl->fp = fp;  // for the later kernels
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    V.ctl->fp = fp;  // for the later kernels
+    alloc_begin(V, advance_epoch);
+  }
   alloc_tile<ALLOC_PPT>(V, fp, blockIdx.x, blockIdx.y, set);
   allow_dependent_launch();
-  if (last_block(V, C_DONE0)) {
-    if (threadIdx.x == 0) {
-      alloc_finish(V, advance_epoch);
-      V.ctl->c[C_DONE0] = 0;
-    }
-  }
 }
 
 // Resolve one collected bucket (threads 0..15 of the calling CTA):

@@ -59,8 +59,9 @@ __device__ __forceinline__ void gc_flush_vertices(const Vol& V, int& freed) {
   freed = 0;
 }
 
-// After the last CTA (one thread): empty the three lists.
-__device__ __forceinline__ void gc_vertices_finish(const Vol& V) {
+// Empty the three lists the vertex gc consumed (one thread; the block gc does it at its
+// start, after the vertex gc has ended).
+__device__ __forceinline__ void gc_lists_reset(const Vol& V) {
   V.ctl->c[C_N_DEAD] = 0;
   V.ctl->c[C_N_DEADRUN] = 0;
   V.ctl->c[C_N_DEADREC] = 0;
@@ -88,12 +89,6 @@ __global__ void __launch_bounds__(256) k_gc_vertices(Vol V) {
   }
   gc_flush_vertices(V, freed);
   allow_dependent_launch();
-  if (last_block(V, C_DONE5)) {
-    if (threadIdx.x == 0) {
-      gc_vertices_finish(V);
-      V.ctl->c[C_DONE5] = 0;
-    }
-  }
 }
 
 // Rebuild the hash without tombstones (one CTA): empty every bucket, then re-insert every
@@ -199,6 +194,7 @@ __device__ __forceinline__ void gc_blocks_finish(const Vol& V, int consumed) {
 // Block recycling, one warp per pool slot.  The last CTA finishes the pass.
 __global__ void __launch_bounds__(256) k_gc_blocks(Vol V, int consumed) {
   grid_dependency_wait();
+  if (blockIdx.x == 0 && threadIdx.x == 0) gc_lists_reset(V);
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int hw = min(__ldcg(&V.ctl->c[C_BLK_BUMP]), V.max_blocks);

@@ -188,7 +188,6 @@ __global__ void __launch_bounds__(256) k_fill_insert(Vol V, const int* keys, int
   }
   if (last_block(V, C_DONE0)) {
     if (threadIdx.x == 0) {
-      fold_top(V, C_BLK_TOP);
       if (advance_epoch) {
         V.ctl->c[C_EPOCH] += 1;
         V.ctl->c[C_N_UPDATE] = 0;

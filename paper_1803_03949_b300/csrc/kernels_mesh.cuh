@@ -154,7 +154,10 @@ __device__ __forceinline__ int run_pop(const Vol& V, int L) {
   if (rank == 0) {
     old = atomicSub(&V.ctl->c[C_RUN_TOP0 + L - 1], n);
     from_stack = old <= 0 ? 0 : (old < n ? old : n);
-    if (from_stack < n) bump0 = atomicAdd(&V.ctl->c[C_TRI_BUMP], (n - from_stack) * L);
+    if (from_stack < n) {
+      bump0 = atomicAdd(&V.ctl->c[C_TRI_BUMP], (n - from_stack) * L);
+      atomicAdd(&V.ctl->c[C_RUN_TOP0 + L - 1], n - from_stack);  // top back to >= 0 (see pool_pop)
+    }
   }
   old = g.shfl(old, 0);
   from_stack = g.shfl(from_stack, 0);
@@ -494,13 +497,8 @@ __device__ __forceinline__ void mesh_flush(const Vol& V, MeshCounts& c) {
   c = MeshCounts();
 }
 
-// After the last block of a mesh pass over n update-set blocks (one thread): clamp the
-// vertex and run free-stack tops, statistics.
-__device__ __forceinline__ void mesh_finish(const Vol& V, int n) {
-  fold_top(V, C_VTX_TOP);
-  fold_top(V, C_REC_TOP);
-#pragma unroll
-  for (int L = 0; L < 5; ++L) fold_top(V, C_RUN_TOP0 + L);
+// Statistics of a mesh pass over n update-set blocks (one thread, at the start).
+__device__ __forceinline__ void mesh_begin(const Vol& V, int n) {
   V.ctl->c[C_ST_UPDATE_BLOCKS] = n;
   reinterpret_cast<unsigned*>(V.ctl->c)[C_ST_MESHED] += (unsigned)n;  // wraps modulo 2^32
 }
@@ -508,23 +506,18 @@ __device__ __forceinline__ void mesh_finish(const Vol& V, int n) {
 // Every update-set block, one per CTA iteration.
 // mode: M_UPDATE (types from the current TSDF; t_{i-1} := previous effective type; refresh
 // the positions and normals of the block's existing vertices), M_REFINE (Eqs. 3-5 with the
-// stored t_{i-1}).  The last CTA clamps the vertex and run free-stack tops.
+// stored t_{i-1}).
 template <bool CE>
 __global__ void __launch_bounds__(MESH_THREADS, MESH_CTAS_PER_SM) k_mesh(Vol V, int mode) {
   __shared__ MeshSmem S;
   for (int i = threadIdx.x; i < 128; i += MESH_THREADS) reinterpret_cast<uint4*>(S.tri64)[i] = V.tri_table[i];
   grid_dependency_wait();
   const int n = min(__ldcg(&V.ctl->c[C_N_UPDATE]), V.list_cap_update);
+  if (blockIdx.x == 0 && threadIdx.x == 0) mesh_begin(V, n);
   MeshCounts cnt;
   for (int i = blockIdx.x; i < n; i += gridDim.x) mesh_block<CE>(V, S, V.update[i], mode, cnt);
   mesh_flush(V, cnt);
   allow_dependent_launch();
-  if (last_block(V, C_DONE3)) {
-    if (threadIdx.x == 0) {
-      mesh_finish(V, n);
-      V.ctl->c[C_DONE3] = 0;
-    }
-  }
 }
 
 }  // namespace vmk

@@ -209,8 +209,9 @@ __device__ __forceinline__ int find_block(const Vol& V, int x, int y, int z) {
 
 // Pop of `stride` consecutive ids per calling lane from a free stack of run starts backed
 // by a bump range, aggregated over the lanes that call it together.  Pops and pushes of
-// one stack never share a kernel; the popping kernel clamps the stack top at 0 when it
-// ends (fold_top).  Returns -1 (and sets POOL_FULL) when the pool is exhausted.
+// one stack never share a kernel.  The part of a pop the stack cannot supply is added back
+// to the top at once, so the top returns to >= 0 when the pops end and no kernel has to
+// clamp it.  Returns -1 (and sets POOL_FULL) when the pool is exhausted.
 __device__ __forceinline__ int pool_pop(const Vol& V, int* stack, int c_top, int c_bump, int cap, int stride = 1,
                                         int pool = P_VERTICES) {
   cg::coalesced_group g = cg::coalesced_threads();
@@ -219,7 +220,10 @@ __device__ __forceinline__ int pool_pop(const Vol& V, int* stack, int c_top, int
   if (rank == 0) {
     old = atomicSub(&V.ctl->c[c_top], n);
     from_stack = old <= 0 ? 0 : (old < n ? old : n);
-    if (from_stack < n) bump0 = atomicAdd(&V.ctl->c[c_bump], (n - from_stack) * stride);
+    if (from_stack < n) {
+      bump0 = atomicAdd(&V.ctl->c[c_bump], (n - from_stack) * stride);
+      atomicAdd(&V.ctl->c[c_top], n - from_stack);
+    }
   }
   old = g.shfl(old, 0);
   from_stack = g.shfl(from_stack, 0);
@@ -313,8 +317,5 @@ __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepco
 // Let the next kernel in the stream be launched early (it still waits for this grid).
 __device__ __forceinline__ void allow_dependent_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-__device__ __forceinline__ void fold_top(const Vol& V, int c_top) {
-  if (V.ctl->c[c_top] < 0) V.ctl->c[c_top] = 0;
-}
 
 }  // namespace vmk
