@@ -13,7 +13,7 @@ __device__ __forceinline__ void run_push(const Vol& V, int L, int base) {
   cg::coalesced_group g0 = cg::coalesced_threads();
   cg::coalesced_group g = cg::labeled_partition(g0, L);
   int slot = 0;
-  if (g.thread_rank() == 0) slot = atomicAdd(&V.ctl->c[C_RUN_TOP0 + L - 1], (int)g.size());
+  if (g.thread_rank() == 0) slot = atomicAdd(&V.ctl->c[run_top(L)], (int)g.size());
   slot = g.shfl(slot, 0) + (int)g.thread_rank();
   if (slot < V.run_cap[L - 1]) V.run_free[L - 1][slot] = base;
   else set_status(V, ST_POOL_FULL, P_FREE_STACK);

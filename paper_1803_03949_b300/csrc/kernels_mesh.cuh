@@ -3,23 +3,28 @@
 // reference counts that drive recycling (Sec. V-E), in one pass over the update set.
 //
 // One CTA per update-set block (persistent loop), in stages separated by barriers so that
-// every stage is wide (one thread per cube, per triangle or per edge) and no thread walks
-// a long chain of dependent memory operations:
+// every stage is wide (one thread per cube, per edge or per changed cube) and no thread
+// walks a long chain of dependent memory operations:
 //   a. stage the 10^3 voxel halo (the block, local 0..7, plus the +x/+y/+z neighbours'
-//      voxels at local 8..9) in shared memory as d, NaN where W = 0; every cube type, and
-//      every vertex an edge of these cubes can need, is computed from it;
-//   b. per cube: type (and refinement), previous type; the block's existing vertices go to
-//      a refresh list; cubes whose effective type changes go to a shared list and mark the
-//      edges their new triangles use in a shared bitmap;
+//      voxels at local 8..9) in shared memory as d, NaN where W = 0, with 16-byte loads;
+//      every cube type, and every vertex an edge of these cubes can need, is computed from
+//      it.  The block's own cube bytes, run slots and edge slots are loaded first, so they
+//      travel with the halo; the edge slots (vertex ids) go to shared memory;
+//   b. per cube: type (and refinement), previous type; the block's edges that carry a
+//      vertex are marked for a refresh; cubes whose effective type changes go to a shared
+//      list, take a rank among the block's new runs of their length and among its released
+//      runs, and mark the edges their new triangles use;
 //   c. count the marked edges per bitmap word (stage d locates the j-th from the counts);
-//   d. one loop over three kinds of independent work: per marked edge its vertex id,
-//      creating the vertex on first use -- the first thread to claim the edge pops an id
-//      and publishes it with atomicCAS on the owner's edge slot; a thread that loses the
-//      race takes the winner's id and returns its own through the recycling list, so
-//      nobody waits and every vertex exists once; per listed vertex a refresh of its
-//      position and normal; per changed cube the release of its old triangles (reference
-//      counts down, the run queued for recycling) and a run for its new ones;
-//   e. per (changed cube, new triangle): write it and count its three references.
+//   d. one loop over independent work: per marked edge its vertex -- refreshed (position
+//      and normal from the new TSDF) if the block owns it, created on first use if a new
+//      triangle needs it: the first thread to claim the edge pops an id and publishes it
+//      with atomicCAS on the owner's edge slot; a thread that loses the race takes the
+//      winner's id and returns its own through the recycling list, so nobody waits and
+//      every vertex exists once; per changed cube the release of its old triangles
+//      (reference counts down); per run length one pop of all the block's new runs, and
+//      one reservation of recycling-list slots for the released runs;
+//   e. per changed cube: its new run (from the pop and its rank), the released run queued
+//      for recycling, the new triangles written and their references counted.
 // The paper resolves concurrent vertex creation with an atomic first-claimer lock or with
 // grouped serial launches (Sec. V-C); publishing the id with the claim replaces both.
 #pragma once
@@ -48,22 +53,28 @@ __device__ __forceinline__ int owner_bits(int k) { return (int)((EDGE_OWNER_BITS
 __device__ __forceinline__ int packed_ntri(uint64_t w) { return (int)(w >> 60); }
 __device__ __forceinline__ int packed_edge(uint64_t w, int t, int j) { return (int)((w >> (4 * (3 * t + j))) & 15); }
 
-constexpr int MESH_CTAS_PER_SM = 8;  // bounded by registers (64) and shared memory (27 KB)
+constexpr int MESH_CTAS_PER_SM = 8;  // bounded by registers (64) and shared memory (24 KB)
+constexpr int HALO_PAIRS = 244;      // 16-byte pairs of neighbour voxels in the halo (488 voxels)
 
 struct __align__(16) MeshSmem {
   float halo[HALO_N];  // d of the voxel, NaN where W = 0 or its block is absent
   uint64_t tri64[256];
   int nb[8];
   int dtri;
-  int nchg, nedge, nref;
-  uint16_t rlist[BV * 3];  // owned edges whose existing vertex is refreshed (voxel * 3 + axis)
-  uint16_t chg_cube[BV];  // changed cubes of the block
+  int nchg, nedge, ndr;  // changed cubes, visited edges, released runs
+  int nrun[5];           // new runs per length L = 1..5 (stage b), then their pop (stage d):
+  int run_old[5], run_fs[5], run_bump[5];  // stack top seen, entries taken from it, first bump slot
+  int dr_base;                             // first recycling-list slot of the released runs
+  uint16_t chg_cube[BV];                   // changed cubes of the block
   uint8_t chg_new[BV], chg_old[BV];
-  int chg_base[BV];       // run of the released triangles (stages b-c), then of the new ones
-  unsigned emark[EDGE_WORDS];
-  int ecount[EDGE_WORDS];  // exclusive prefix of the marked edges over the bitmap's words
-  alignas(16) int rec[BV];  // the block's edge records (voxel -> record, -1 none), written as int4
-  int evid[EDGE_SLOTS];
+  uint16_t chg_rrank[BV], chg_drank[BV];  // rank among the new runs of its length / the released runs
+  int chg_base[BV];                        // run of the released triangles, -1 none
+  unsigned nmark[EDGE_WORDS];              // edges the new triangles use
+  unsigned lmark[EDGE_WORDS];              // the block's own edges that carry a vertex
+  unsigned emark[EDGE_WORDS];              // their union: the edges stage d visits
+  int ecount[EDGE_WORDS];                  // exclusive prefix of emark's bits over its words
+  alignas(16) int rec[BV];                 // the block's edge records (voxel -> record, -1 none)
+  int evid[EDGE_SLOTS];                    // vertex id per edge slot (own slots from stage a)
 };
 
 // Eqs. 3-5: snap a disturbed raw type to the nearest admissible regular type.  `small` has
@@ -105,6 +116,19 @@ __device__ __forceinline__ int4 ld_early_i4(const int* p) {
   asm volatile("ld.global.cg.v4.s32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
   return v;
 }
+__device__ __forceinline__ int ld_early_s32(const int* p) {
+  int v;
+  asm volatile("ld.global.cg.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float4 ld_early_f4(const float2* p) {
+  float4 v;
+  asm volatile("ld.global.cg.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+  return v;
+}
+
+// Halo entry of a voxel (d, W): d, or NaN where W = 0.
+__device__ __forceinline__ float halo_value(float d, float w) { return w > 0.0f ? d : __int_as_float(0x7fc00000); }
 
 __device__ __forceinline__ float halo_at(const MeshSmem& S, int x, int y, int z) {
   return S.halo[x + HALO * y + HALO * HALO * z];
@@ -145,44 +169,11 @@ __device__ __forceinline__ void edge_vertex(const MeshSmem& S, float l, int4 key
   else *nrm = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 }
 
-// Pop one run of L consecutive triangle slots, aggregated over the lanes popping the same L.
-__device__ __forceinline__ int run_pop(const Vol& V, int L) {
-  cg::coalesced_group g0 = cg::coalesced_threads();
-  cg::coalesced_group g = cg::labeled_partition(g0, L);
-  const int n = (int)g.size(), rank = (int)g.thread_rank();
-  int old = 0, from_stack = 0, bump0 = 0;
-  if (rank == 0) {
-    old = atomicSub(&V.ctl->c[C_RUN_TOP0 + L - 1], n);
-    from_stack = old <= 0 ? 0 : (old < n ? old : n);
-    if (from_stack < n) {
-      bump0 = atomicAdd(&V.ctl->c[C_TRI_BUMP], (n - from_stack) * L);
-      atomicAdd(&V.ctl->c[C_RUN_TOP0 + L - 1], n - from_stack);  // top back to >= 0 (see pool_pop)
-    }
-  }
-  old = g.shfl(old, 0);
-  from_stack = g.shfl(from_stack, 0);
-  bump0 = g.shfl(bump0, 0);
-  if (rank < from_stack) return __ldcg(&V.run_free[L - 1][old - 1 - rank]);
-  const long long b = (long long)bump0 + (long long)(rank - from_stack) * L;
-  if (b + L > V.max_triangles) {
-    set_status(V, ST_POOL_FULL, P_TRIANGLES);
-    return -1;
-  }
-  return (int)b;
-}
-
-// Append a released triangle run to the recycling list.
-__device__ __forceinline__ void deadrun_push(const Vol& V, int base, int L) {
-  cg::coalesced_group g = cg::coalesced_threads();
-  int slot = 0;
-  if (g.thread_rank() == 0) slot = atomicAdd(&V.ctl->c[C_N_DEADRUN], (int)g.size());
-  slot = g.shfl(slot, 0) + (int)g.thread_rank();
-  if (slot < V.list_cap_deadrun) V.deadrun[slot] = make_int2(base, L);
-  else set_status(V, ST_POOL_FULL, P_DEAD_RUN_LIST);
-}
-
 // Id of the vertex on the edge owned by the voxel at halo coordinates (x, y, z) (0..8) along
 // axis a, creating it on first use.  Returns -1 when the vertex pool is exhausted.
+// `own`: the voxel is the block's own and its slot, loaded in stage a, held no vertex, so
+// the claim starts at once (a vertex another block's pass made since makes the claim fail
+// and is taken like any winner's).
 // A free vertex carries the reference count -1.  The claimer publishes the popped id with
 // atomicCAS and then adds 1, while threads that found the id add their references: the
 // additions commute, so the count is exact when the pass ends, and no fence is needed.
@@ -191,7 +182,7 @@ __device__ __forceinline__ void deadrun_push(const Vol& V, int base, int L) {
 // CE: the compact layout (edge records) rather than three vertex ids per voxel.
 template <bool CE>
 __device__ __forceinline__ int vertex_of_edge(const Vol& V, const MeshSmem& S, int x, int y, int z, int a,
-                                              bool& claimed) {
+                                              bool own, bool& claimed) {
   claimed = false;
   const int ob = S.nb[(x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2)];
   if (ob < 0) return -1;  // cannot happen for a valid cube
@@ -203,8 +194,7 @@ __device__ __forceinline__ int vertex_of_edge(const Vol& V, const MeshSmem& S, i
     // the owner voxel's edge record (claimed like a vertex: first claimer publishes a record
     // from the pool, whose three slots are -1 there; a loser's spare record goes to gc);
     // voxels of the block itself have theirs staged in shared memory
-    int rec = (x | y | z) < 8 ? S.rec[ov] : -1;
-    if (rec < 0) rec = __ldcg(&V.edge_rec[vox]);
+    int rec = own ? S.rec[ov] : __ldcg(&V.edge_rec[vox]);
     if (rec < 0) {
       const int spare = pool_pop(V, V.rec_free, C_REC_TOP, C_REC_BUMP, V.max_vertices, 1, P_EDGE_RECORDS);
       if (spare < 0) return -1;
@@ -216,8 +206,10 @@ __device__ __forceinline__ int vertex_of_edge(const Vol& V, const MeshSmem& S, i
   } else {
     slot = V.edge_vtx + (size_t)e;
   }
-  const int vid = __ldcg(slot);
-  if (vid >= 0) return vid;
+  if (!own) {
+    const int vid = __ldcg(slot);
+    if (vid >= 0) return vid;
+  }
   const int mine = pool_pop(V, V.vtx_free, C_VTX_TOP, C_VTX_BUMP, V.max_vertices);
   if (mine < 0) return -1;
   const int old = atomicCAS(slot, -1, mine);
@@ -235,28 +227,12 @@ __device__ __forceinline__ int vertex_of_edge(const Vol& V, const MeshSmem& S, i
   return mine;
 }
 
-// Reserve `cnt` consecutive slots of a shared counter for every lane of the (full) warp,
-// with one shared atomic per warp; returns this lane's first slot.
-__device__ __forceinline__ int warp_reserve(int* counter, int cnt) {
-  const int lane = threadIdx.x & 31;
-  int x = cnt;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  int base = 0;
-  if (lane == 31 && x > 0) base = atomicAdd(counter, x);
-  base = __shfl_sync(0xffffffffu, base, 31);
-  return base + x - cnt;
-}
-
 // Shared-memory slot of the edge owned by the voxel at halo coordinates (x, y, z) along a.
 __device__ __forceinline__ int edge_slot(int x, int y, int z, int a) { return ((z * 9 + y) * 9 + x) * 3 + a; }
 
 // Counters a mesh pass accumulates per CTA.
 struct MeshCounts {
-  int changed = 0, created = 0, emitted = 0, released = 0, refreshed = 0;
+  int changed = 0, created = 0, emitted = 0, released = 0, refreshed = 0, dtri = 0;
 };
 
 // One update-set block `blk` through stages a-e, the calling CTA of MESH_THREADS with its
@@ -264,60 +240,117 @@ struct MeshCounts {
 template <bool CE>
 __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, int mode, MeshCounts& cnt) {
   const float eps = V.eps, l = V.l;
-  int& changed = cnt.changed;
-  int& created = cnt.created;
-  int& emitted = cnt.emitted;
-  int& released = cnt.released;
-  int& refreshed = cnt.refreshed;
-  const int4 key = V.bkey[blk];
-  if (key.w < 0) return;  // freed since it joined the set (uniform over the CTA)
-  // ---- a. neighbours and halo
-  if (threadIdx.x < 8) S.nb[threadIdx.x] = threadIdx.x == 0 ? blk : __ldcg(&V.nbr[blk * 16 + threadIdx.x]);
-  if (threadIdx.x == 0) {
-    S.dtri = 0;
-    S.nchg = 0;
-    S.nedge = 0;
-    S.nref = 0;
-  }
-  for (int w = threadIdx.x; w < EDGE_WORDS; w += MESH_THREADS) S.emark[w] = 0;
-  // this thread's 4 cubes: type, previous-type and vertex-flag bytes and run slots, loaded
-  // now so that they arrive while the halo is staged
+  // ---- a. this thread's 4 cubes (c0..c0+3, consecutive along x): their voxels, type,
+  //         previous-type and vertex-flag bytes, run slots and edge slots (or edge records),
+  //         all loaded before anything waits; the addresses are valid for a freed block too
   const int c0 = 4 * threadIdx.x;  // MESH_THREADS * 4 == BV
   const size_t ci0 = (size_t)blk * BV + c0;
+  const int nbv = (threadIdx.x >= 1 && threadIdx.x < 8) ? ld_early_s32(&V.nbr[blk * 16 + threadIdx.x]) : blk;
+  const float4 h01 = ld_early_f4(V.tw + ci0), h23 = ld_early_f4(V.tw + ci0 + 2);
   const uint32_t eff_w = ld_early_u32(V.code_eff + ci0);
   const uint32_t vm_w = ld_early_u32(V.vmask + ci0);
   const uint32_t prev_w = (mode & M_UPDATE) ? eff_w : ld_early_u32(V.code_prev + ci0);
   const int4 tb4 = ld_early_i4(V.tri_base + ci0);
-  const int4 rec4 = CE ? ld_early_i4(V.edge_rec + ci0) : make_int4(-1, -1, -1, -1);
-  __syncthreads();
-  for (int h = threadIdx.x; h < HALO_N; h += MESH_THREADS) {
-    const int x = h % HALO, y = (h / HALO) % HALO, z = h / (HALO * HALO);
-    const int b = S.nb[(x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2)];
-    const float2 q = b >= 0 ? __ldcg(&V.tw[(size_t)b * BV + (x & 7) + 8 * (y & 7) + 64 * (z & 7)])
-                            : make_float2(0.f, 0.f);
-    S.halo[h] = q.y > 0.0f ? q.x : __int_as_float(0x7fc00000);
+  int4 ev0, ev1, ev2;  // wide layout: the 12 edge slots of the 4 voxels
+  if constexpr (CE) {
+    ev0 = ld_early_i4(V.edge_rec + ci0);  // compact layout: the 4 voxels' edge records
+  } else {
+    ev0 = ld_early_i4(V.edge_vtx + ci0 * 3);
+    ev1 = ld_early_i4(V.edge_vtx + ci0 * 3 + 4);
+    ev2 = ld_early_i4(V.edge_vtx + ci0 * 3 + 8);
+  }
+  const int4 key = V.bkey[blk];
+  if (key.w < 0) return;  // freed since it joined the set (uniform over the CTA)
+  if (threadIdx.x < 8) S.nb[threadIdx.x] = nbv;
+  if (threadIdx.x == 0) {
+    S.dtri = 0;
+    S.nchg = 0;
+    S.ndr = 0;
+  }
+  if (threadIdx.x < 5) S.nrun[threadIdx.x] = 0;
+  for (int w = threadIdx.x; w < EDGE_WORDS; w += MESH_THREADS) {
+    S.nmark[w] = 0;
+    S.lmark[w] = 0;
   }
   __syncthreads();
-  if (CE) reinterpret_cast<int4*>(S.rec)[threadIdx.x] = rec4;  // read from stage d on
-  // ---- b. cube types, vertex refresh, changed-cube list, needed edges (4 consecutive cubes
-  //         per thread: the type, previous-type and vertex-flag bytes move as 32-bit words)
+  // the neighbours' 488 halo voxels as 244 pairs adjacent along x (16 bytes each): rows
+  // y, z < 8 take x = 8..9 from the +x neighbour; the 36 rows with y or z at 8..9 take
+  // x = 0..9 in five pairs
+  float4 qn[2];
+  int qh[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int i = threadIdx.x + k * MESH_THREADS;
+    qh[k] = -1;
+    qn[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < HALO_PAIRS) {
+      int X, Y, Z;
+      if (i < 64) {
+        X = 8, Y = i & 7, Z = i >> 3;
+      } else {
+        const int r = (i - 64) / 5;
+        X = 2 * (i - 64 - 5 * r);
+        if (r < 16) Y = 8 + (r & 1), Z = r >> 1;
+        else Y = (r - 16) % 10, Z = 8 + (r - 16) / 10;
+      }
+      const int b = S.nb[(X >> 3) | ((Y >> 3) << 1) | ((Z >> 3) << 2)];
+      qh[k] = X + HALO * Y + HALO * HALO * Z;
+      if (b >= 0)
+        qn[k] = __ldcg(reinterpret_cast<const float4*>(V.tw + (size_t)b * BV + (X & 7) + 8 * (Y & 7) + 64 * (Z & 7)));
+    }
+  }
+  int ev[12];
+  if constexpr (CE) {
+    const int rv[4] = {ev0.x, ev0.y, ev0.z, ev0.w};
+#pragma unroll
+    for (int q = 0; q < 12; ++q) ev[q] = rv[q / 3] >= 0 ? __ldcg(&V.erec[(size_t)rv[q / 3] * 3 + q % 3]) : -1;
+    reinterpret_cast<int4*>(S.rec)[threadIdx.x] = ev0;  // read from stage d on
+  } else {
+    const int4 e4[3] = {ev0, ev1, ev2};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      ev[4 * q] = e4[q].x, ev[4 * q + 1] = e4[q].y;
+      ev[4 * q + 2] = e4[q].z, ev[4 * q + 3] = e4[q].w;
+    }
+  }
+  const int cx = c0 & 7, cy = (c0 >> 3) & 7, cz = c0 >> 6;
+  {
+    float* h = S.halo + cx + HALO * cy + HALO * HALO * cz;
+    h[0] = halo_value(h01.x, h01.y);
+    h[1] = halo_value(h01.z, h01.w);
+    h[2] = halo_value(h23.x, h23.y);
+    h[3] = halo_value(h23.z, h23.w);
+    // the 4 voxels' 12 edge slots are consecutive in the shared slot array
+    int* es = S.evid + edge_slot(cx, cy, cz, 0);
+#pragma unroll
+    for (int q = 0; q < 12; ++q) es[q] = ev[q];
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+    if (qh[k] >= 0) {
+      S.halo[qh[k]] = halo_value(qn[k].x, qn[k].y);
+      S.halo[qh[k] + 1] = halo_value(qn[k].z, qn[k].w);
+    }
+  __syncthreads();
+  // ---- b. cube types, refresh marks, changed-cube list, needed edges (the type,
+  //         previous-type and vertex-flag bytes of the 4 cubes move as 32-bit words)
   int dtri = 0;
   {
     if (mode & M_UPDATE) *reinterpret_cast<uint32_t*>(V.code_prev + ci0) = eff_w;
-    // existing vertices of the 4 voxels: listed for the refresh in stage d
-    const uint32_t live_w = vm_w & 0x07070707u;
-    {
-      const int cnt = __popc(live_w);
-      int r = warp_reserve(&S.nref, cnt);
+    // edges of the 4 voxels that carry a vertex: 12 consecutive bits of the refresh bitmap
+    uint32_t live12 = 0;
 #pragma unroll
-      for (int q = 0; q < 12; ++q)
-        if ((live_w >> (8 * (q / 3) + q % 3)) & 1) S.rlist[r++] = (uint16_t)((c0 + q / 3) * 3 + q % 3);
+    for (int j = 0; j < 4; ++j) live12 |= ((vm_w >> (8 * j)) & 7u) << (3 * j);
+    if (live12) {
+      const int es0 = edge_slot(cx, cy, cz, 0), sh = es0 & 31;
+      atomicOr(&S.lmark[es0 >> 5], live12 << sh);
+      if (sh > 20) atomicOr(&S.lmark[(es0 >> 5) + 1], live12 >> (32 - sh));
     }
     uint32_t new_w = eff_w;
 #pragma unroll 1
     for (int j = 0; j < 4; ++j) {  // rolled: the kernel's code must stay small (instruction cache)
       const int c = c0 + j;
-      const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
+      const int x = cx + j, y = cy, z = cz;
       bool valid = true;
       int raw = 0, small = 0;
 #pragma unroll
@@ -332,21 +365,25 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
       int e = valid ? raw : 0;
       if (valid && (mode & M_REFINE)) e = refine_type(raw, prev, small);
       if (e == eff_old) continue;
-      ++changed;
+      ++cnt.changed;
       new_w = (new_w & ~(0xFFu << (8 * j))) | ((uint32_t)e << (8 * j));
       const uint64_t tw64 = S.tri64[e];
       const int nold = packed_ntri(S.tri64[eff_old]), nnew = packed_ntri(tw64);
+      const int tb = j == 0 ? tb4.x : (j == 1 ? tb4.y : (j == 2 ? tb4.z : tb4.w));
+      const int obase = nold > 0 ? tb : -1;
       const int slot = atomicAdd(&S.nchg, 1);  // a few changed cubes per thread at most
       S.chg_cube[slot] = (uint16_t)c;
       S.chg_new[slot] = (uint8_t)e;
       S.chg_old[slot] = (uint8_t)eff_old;
-      S.chg_base[slot] = nold > 0 ? (j == 0 ? tb4.x : (j == 1 ? tb4.y : (j == 2 ? tb4.z : tb4.w))) : -1;
+      S.chg_base[slot] = obase;
+      S.chg_drank[slot] = (uint16_t)(obase >= 0 ? atomicAdd(&S.ndr, 1) : 0);
+      S.chg_rrank[slot] = (uint16_t)(nnew > 0 ? atomicAdd(&S.nrun[nnew - 1], 1) : 0);
       dtri += nnew - nold;
       for (int t = 0; t < nnew; ++t)
         for (int jj = 0; jj < 3; ++jj) {
           const int ob = owner_bits(packed_edge(tw64, t, jj));
           const int es = edge_slot(x + (ob & 1), y + ((ob >> 1) & 1), z + ((ob >> 2) & 1), ob >> 3);
-          atomicOr(&S.emark[es >> 5], 1u << (es & 31));
+          atomicOr(&S.nmark[es >> 5], 1u << (es & 31));
         }
     }
     if (new_w != eff_w) *reinterpret_cast<uint32_t*>(V.code_eff + ci0) = new_w;
@@ -354,78 +391,90 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
   if (dtri) atomicAdd(&S.dtri, dtri);
   __syncthreads();
   const int nchg = S.nchg;
-  // ---- c. count the needed edges (warp 0 scans the bitmap's word counts; stage d finds the
-  //         j-th marked edge from these prefixes)
+  // ---- c. the edges stage d visits (needed or refreshed), counted per bitmap word
   if (threadIdx.x < 32) {
     int carry = 0;
     for (int w0 = 0; w0 < EDGE_WORDS; w0 += 32) {
       const int w = w0 + threadIdx.x;
-      const int cnt = w < EDGE_WORDS ? __popc(S.emark[w]) : 0;
-      int x = cnt;
+      const unsigned u = w < EDGE_WORDS ? (S.nmark[w] | S.lmark[w]) : 0u;
+      if (w < EDGE_WORDS) S.emark[w] = u;
+      const int c = __popc(u);
+      int x = c;
       for (int o = 1; o < 32; o <<= 1) {
         const int y = __shfl_up_sync(0xffffffffu, x, o);
         if ((int)threadIdx.x >= o) x += y;
       }
-      if (w < EDGE_WORDS) S.ecount[w] = carry + x - cnt;
+      if (w < EDGE_WORDS) S.ecount[w] = carry + x - c;
       carry += __shfl_sync(0xffffffffu, x, 31);
     }
     if (threadIdx.x == 0) S.nedge = carry;
   }
   __syncthreads();
-  // ---- d. one loop over three independent kinds of work, so the stage lasts as long as the
-  //         longest chain rather than their sum:
-  //         per needed edge: its vertex, created on first use;
-  //         per existing vertex of the block: position and normal from the new TSDF;
-  //         per changed cube: release the old triangles, pop a run for the new ones.
-  const int nedge = S.nedge, nref = S.nref;
-  for (int j = threadIdx.x; j < nedge + nref + nchg; j += MESH_THREADS) {
-    if (j < nedge + nref) {
-      // a vertex to (re)compute: a needed edge's new vertex, or an existing vertex
-      int x, y, z, a, vid;
-      bool fresh;
-      if (j < nedge) {
-        int lo = 0, hi = EDGE_WORDS - 1;  // the word holding marked edge j
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (S.ecount[mid] <= j) lo = mid;
-          else hi = mid - 1;
+  // ---- d. one loop over independent work, so the stage lasts as long as the longest chain
+  //         rather than their sum: items 0-4 pop the block's new runs of length 1-5, item 5
+  //         reserves the released runs' recycling slots; then one item per visited edge and
+  //         one per changed cube
+  const int nedge = S.nedge;
+  for (int j = threadIdx.x; j < 6 + nedge + nchg; j += MESH_THREADS) {
+    if (j < 6) {
+      if (j < 5) {
+        const int n = S.nrun[j], L = j + 1;
+        if (n > 0) {  // n runs of L slots: from the free stack, the rest from the bump range
+          const int old = atomicSub(&V.ctl->c[run_top(j + 1)], n);
+          const int fs = old <= 0 ? 0 : (old < n ? old : n);
+          int bump0 = 0;
+          if (fs < n) {
+            bump0 = atomicAdd(&V.ctl->c[C_TRI_BUMP], (n - fs) * L);
+            atomicAdd(&V.ctl->c[run_top(j + 1)], n - fs);  // top back to >= 0 (as pool_pop)
+          }
+          S.run_old[j] = old;
+          S.run_fs[j] = fs;
+          S.run_bump[j] = bump0;
         }
-        const int es = lo * 32 + (int)__fns(S.emark[lo], 0, j - S.ecount[lo] + 1);
-        const int o = es / 3;
-        a = es - 3 * o;
-        x = o % 9, y = (o / 9) % 9, z = o / 81;
-        vid = vertex_of_edge<CE>(V, S, x, y, z, a, fresh);
-        S.evid[es] = vid;
-        created += fresh;
-      } else {
-        const int r = S.rlist[j - nedge];
-        const int c = r / 3;
-        a = r - c * 3;
-        x = c & 7, y = (c >> 3) & 7, z = c >> 6;
-        if constexpr (CE) {
-          const int rec = S.rec[c];
-          vid = rec >= 0 ? __ldcg(&V.erec[(size_t)rec * 3 + a]) : -1;
-        } else {
-          vid = __ldcg(&V.edge_vtx[((size_t)blk * BV + c) * 3 + a]);
-        }
-        fresh = vid >= 0;
-        refreshed += fresh;
+      } else if (S.ndr > 0) {
+        S.dr_base = atomicAdd(&V.ctl->c[C_N_DEADRUN], S.ndr);
       }
-      if (!fresh) continue;
-      float4 p, nn;
-      edge_vertex(S, l, key, x, y, z, a, &p, &nn);
-      V.vpos[vid] = p;
-      V.vnrm[vid] = nn;
+    } else if (j < 6 + nedge) {
+      const int i = j - 6;
+      int lo = 0, hi = EDGE_WORDS - 1;  // the word holding visited edge i
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (S.ecount[mid] <= i) lo = mid;
+        else hi = mid - 1;
+      }
+      const int es = lo * 32 + (int)__fns(S.emark[lo], 0, i - S.ecount[lo] + 1);
+      const unsigned bit = 1u << (es & 31);
+      const bool needed = (S.nmark[lo] & bit) != 0, live = (S.lmark[lo] & bit) != 0;
+      const int o = es / 3;
+      const int a = es - 3 * o;
+      const int x = o % 9, y = (o / 9) % 9, z = o / 81;
+      const bool own = (x | y | z) < 8;
+      int vid = own ? S.evid[es] : -1;
+      bool compute = live && vid >= 0;  // an existing vertex of the block: refresh
+      cnt.refreshed += compute;
+      if (needed && (!own || vid < 0)) {
+        bool fresh;
+        vid = vertex_of_edge<CE>(V, S, x, y, z, a, own, fresh);
+        S.evid[es] = vid;
+        cnt.created += fresh;
+        compute |= fresh;
+      }
+      if (compute) {
+        float4 p, nn;
+        edge_vertex(S, l, key, x, y, z, a, &p, &nn);
+        V.vpos[vid] = p;
+        V.vnrm[vid] = nn;
+      }
     } else {
-      const int q = j - nedge - nref;
-      const int nold = packed_ntri(S.tri64[S.chg_old[q]]), obase = S.chg_base[q];
-      const int nt = packed_ntri(S.tri64[S.chg_new[q]]);
+      const int q = j - 6 - nedge;
+      const int obase = S.chg_base[q];
       if (obase >= 0) {
+        const int nold = packed_ntri(S.tri64[S.chg_old[q]]);
         int4 tr[5];
 #pragma unroll
         for (int t = 0; t < 5; ++t) tr[t] = t < nold ? __ldcg(&V.tris[obase + t]) : make_int4(-1, -1, -1, -1);
         // all 15 reference drops in flight together; the vertices they leave unreferenced
-        // go to the recycling list through one (rolled) loop
+        // go to the recycling list, one reservation for all of them
         unsigned zero = 0;
 #pragma unroll
         for (int t = 0; t < 5; ++t) {
@@ -435,51 +484,71 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
             if (vs[jj] >= 0 && atomicSub(&V.vref[vs[jj]], 1) == 1) zero |= 1u << (3 * t + jj);
         }
         for (int t = 0; t < nold; ++t) V.tris[obase + t] = make_int4(-1, -1, -1, -1);
-        while (zero) {
-          const int b = __ffs(zero) - 1;
-          zero &= zero - 1;
-          const int4 tb = tr[0];
-          int4 tt = b < 3 ? tb : (b < 6 ? tr[1] : (b < 9 ? tr[2] : (b < 12 ? tr[3] : tr[4])));
-          const int k = b % 3;
-          list_push(V, V.dead, C_N_DEAD, V.list_cap_dead, k == 0 ? tt.x : (k == 1 ? tt.y : tt.z));
+        if (zero) {
+          int slot = list_reserve(V, C_N_DEAD, __popc(zero));
+          while (zero) {
+            const int b = __ffs(zero) - 1;
+            zero &= zero - 1;
+            const int4 tt = b < 3 ? tr[0] : (b < 6 ? tr[1] : (b < 9 ? tr[2] : (b < 12 ? tr[3] : tr[4])));
+            const int k = b % 3;
+            if (slot < V.list_cap_dead) V.dead[slot] = k == 0 ? tt.x : (k == 1 ? tt.y : tt.z);
+            else set_status(V, ST_POOL_FULL, P_DEAD_VERTEX_LIST);
+            ++slot;
+          }
         }
-        deadrun_push(V, obase, nold);
-        released += nold;
+        cnt.released += nold;
       }
-      const int base = nt > 0 ? run_pop(V, nt) : -1;
-      S.chg_base[q] = base;
-      V.tri_base[(size_t)blk * BV + S.chg_cube[q]] = base;
-      if (base >= 0) emitted += nt;
     }
   }
   __syncthreads();
-  // ---- e. one thread per new triangle
-  for (int j = threadIdx.x; j < nchg * 5; j += MESH_THREADS) {
-    const int q = j / 5, t = j - q * 5;
-    const int e = S.chg_new[q], base = S.chg_base[q];
-    const uint64_t tw64 = S.tri64[e];
-    if (t >= packed_ntri(tw64) || base < 0) continue;
-    const int c = S.chg_cube[q];
-    const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
-    int vs[3];
-#pragma unroll
-    for (int jj = 0; jj < 3; ++jj) {
-      const int ob = owner_bits(packed_edge(tw64, t, jj));
-      vs[jj] = S.evid[edge_slot(x + (ob & 1), y + ((ob >> 1) & 1), z + ((ob >> 2) & 1), ob >> 3)];
+  // ---- e. per changed cube: its new run, the released run queued for recycling, the new
+  //         triangles and their references
+  for (int q = threadIdx.x; q < nchg; q += MESH_THREADS) {
+    const int c = S.chg_cube[q], obase = S.chg_base[q];
+    const uint64_t tw64 = S.tri64[S.chg_new[q]];
+    const int nt = packed_ntri(tw64);
+    if (obase >= 0) {
+      const int slot = S.dr_base + S.chg_drank[q];
+      if (slot < V.list_cap_deadrun) V.deadrun[slot] = make_int2(obase, packed_ntri(S.tri64[S.chg_old[q]]));
+      else set_status(V, ST_POOL_FULL, P_DEAD_RUN_LIST);
+    }
+    int base = -1;
+    if (nt > 0) {
+      const int r = S.chg_rrank[q], fs = S.run_fs[nt - 1];
+      if (r < fs) {
+        base = __ldcg(&V.run_free[nt - 1][S.run_old[nt - 1] - 1 - r]);
+      } else {
+        const long long b = (long long)S.run_bump[nt - 1] + (long long)(r - fs) * nt;
+        if (b + nt > V.max_triangles) set_status(V, ST_POOL_FULL, P_TRIANGLES);
+        else base = (int)b;
+      }
     }
     const int ci = blk * BV + c;
-    if (vs[0] < 0 || vs[1] < 0 || vs[2] < 0) {  // vertex pool exhausted
-      set_status(V, ST_POOL_FULL, P_VERTICES);
-      V.tris[base + t] = make_int4(-1, -1, -1, ci);
-      continue;
-    }
+    V.tri_base[ci] = base;
+    if (base < 0) continue;
+    cnt.emitted += nt;
+    const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
+#pragma unroll 1
+    for (int t = 0; t < nt; ++t) {
+      int vs[3];
 #pragma unroll
-    for (int jj = 0; jj < 3; ++jj) atomicAdd(&V.vref[vs[jj]], 1);
-    V.tris[base + t] = make_int4(vs[0], vs[1], vs[2], ci);
+      for (int jj = 0; jj < 3; ++jj) {
+        const int ob = owner_bits(packed_edge(tw64, t, jj));
+        vs[jj] = S.evid[edge_slot(x + (ob & 1), y + ((ob >> 1) & 1), z + ((ob >> 2) & 1), ob >> 3)];
+      }
+      if (vs[0] < 0 || vs[1] < 0 || vs[2] < 0) {  // vertex pool exhausted
+        set_status(V, ST_POOL_FULL, P_VERTICES);
+        V.tris[base + t] = make_int4(-1, -1, -1, ci);
+        continue;
+      }
+#pragma unroll
+      for (int jj = 0; jj < 3; ++jj) atomicAdd(&V.vref[vs[jj]], 1);
+      V.tris[base + t] = make_int4(vs[0], vs[1], vs[2], ci);
+    }
   }
   if (threadIdx.x == 0 && S.dtri) {
     atomicAdd(&V.bntri[blk], S.dtri);
-    atomicAdd(&V.ctl->c[C_LIVE_TRIS], S.dtri);
+    cnt.dtri += S.dtri;
   }
   __syncthreads();
 }
@@ -490,6 +559,7 @@ __device__ __forceinline__ void mesh_flush(const Vol& V, MeshCounts& c) {
   if (c.emitted) counter_add(V, C_ST_EMITTED, c.emitted);
   if (c.released) counter_add(V, C_ST_RELEASED, c.released);
   if (c.refreshed) counter_add(V, C_ST_REFRESHED, c.refreshed);
+  if (c.dtri) counter_add(V, C_LIVE_TRIS, c.dtri);
   if (c.created) {
     counter_add(V, C_LIVE_VERTS, c.created);
     counter_add(V, C_ST_NEW_VERTS, c.created);

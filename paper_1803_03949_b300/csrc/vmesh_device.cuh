@@ -28,6 +28,7 @@
 
 #include <cooperative_groups.h>
 #include <cooperative_groups/reduce.h>
+#include <cooperative_groups/scan.h>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -47,30 +48,60 @@ constexpr float Z_NEAR = 0.05f;           // nearest camera depth of a collectio
 
 enum Status { ST_OK = 0, ST_INVALID = 1, ST_HASH_FULL = 2, ST_POOL_FULL = 3 };
 
-// counters of the control block (int slots of Ctl::c)
+// Counters of the control block (int slots of Ctl::c), one 128-byte line apart: the atomics
+// of a mesh pass or a gc pass hit a dozen of them from every CTA, and counters sharing a line
+// would queue at one L2 slice.
+constexpr int CLINE = 32;
 enum Counter {
-  C_STATUS = 0,
-  C_STATUS_POOL,    // which capacity set the status (PoolCode)
-  C_FRAME,          // integrate calls so far + 1
-  C_EPOCH,          // mesh epoch, advanced by the first integrate after a mesh update
-  C_N_TOUCHED,      // buckets collected by the current integrate call
-  C_N_UPDATE,       // blocks in the update set
-  C_N_DEAD,         // zero-reference vertices awaiting gc
-  C_N_DEADRUN,      // released triangle runs awaiting gc
-  C_N_DEADREC,      // spare edge records of lost record claims, awaiting gc
-  C_REC_TOP, C_REC_BUMP,
-  C_BLK_TOP, C_BLK_BUMP,
-  C_VTX_TOP, C_VTX_BUMP,
-  C_RUN_TOP0, C_RUN_TOP1, C_RUN_TOP2, C_RUN_TOP3, C_RUN_TOP4,
-  C_TRI_BUMP,
-  C_LIVE_BLOCKS, C_LIVE_VERTS, C_LIVE_TRIS,
-  C_TOMBS,
-  C_REHASH,         // 1 while a hash rebuild is under way
-  C_ST_FRAME_BLOCKS, C_ST_UPDATE_BLOCKS, C_ST_COLLECTED, C_ST_MESHED, C_ST_NEW_BLOCKS, C_ST_CHANGED, C_ST_FREED_BLOCKS, C_ST_FREED_VERTS, C_ST_NEW_VERTS, C_ST_REHASHES,
-  C_ST_EMITTED, C_ST_RELEASED, C_ST_REFRESHED,
-  C_DONE0, C_DONE1, C_DONE2, C_DONE3, C_DONE4, C_DONE5, C_DONE6, C_DONE7,
-  C_COUNT
+  C_STATUS = 0 * CLINE,
+  C_STATUS_POOL = 1 * CLINE,  // which capacity set the status (PoolCode)
+  C_FRAME = 2 * CLINE,  // integrate calls so far + 1
+  C_EPOCH = 3 * CLINE,  // mesh epoch, advanced by the first integrate after a mesh update
+  C_N_TOUCHED = 4 * CLINE,  // buckets collected by the current integrate call
+  C_N_UPDATE = 5 * CLINE,  // blocks in the update set
+  C_N_DEAD = 6 * CLINE,  // zero-reference vertices awaiting gc
+  C_N_DEADRUN = 7 * CLINE,  // released triangle runs awaiting gc
+  C_N_DEADREC = 8 * CLINE,  // spare edge records of lost record claims, awaiting gc
+  C_REC_TOP = 9 * CLINE,
+  C_REC_BUMP = 10 * CLINE,
+  C_BLK_TOP = 11 * CLINE,
+  C_BLK_BUMP = 12 * CLINE,
+  C_VTX_TOP = 13 * CLINE,
+  C_VTX_BUMP = 14 * CLINE,
+  C_RUN_TOP0 = 15 * CLINE,  // free-run stack tops of lengths 1..5, one line apart (run_top)
+  C_TRI_BUMP = 20 * CLINE,
+  C_LIVE_BLOCKS = 21 * CLINE,
+  C_LIVE_VERTS = 22 * CLINE,
+  C_LIVE_TRIS = C_LIVE_VERTS + 1,  // beside C_LIVE_VERTS: the mesh size is read as one pair
+  C_TOMBS = 23 * CLINE,
+  C_REHASH = 24 * CLINE,  // 1 while a hash rebuild is under way
+  C_ST_FRAME_BLOCKS = 25 * CLINE,
+  C_ST_UPDATE_BLOCKS = 26 * CLINE,
+  C_ST_COLLECTED = 27 * CLINE,
+  C_ST_MESHED = 28 * CLINE,
+  C_ST_NEW_BLOCKS = 29 * CLINE,
+  C_ST_CHANGED = 30 * CLINE,
+  C_ST_FREED_BLOCKS = 31 * CLINE,
+  C_ST_FREED_VERTS = 32 * CLINE,
+  C_ST_NEW_VERTS = 33 * CLINE,
+  C_ST_REHASHES = 34 * CLINE,
+  C_ST_EMITTED = 35 * CLINE,
+  C_ST_RELEASED = 36 * CLINE,
+  C_ST_REFRESHED = 37 * CLINE,
+  C_DONE0 = 38 * CLINE,
+  C_DONE1 = 39 * CLINE,
+  C_DONE2 = 40 * CLINE,
+  C_DONE3 = 41 * CLINE,
+  C_DONE4 = 42 * CLINE,
+  C_DONE5 = 43 * CLINE,
+  C_DONE6 = 44 * CLINE,
+  C_DONE7 = 45 * CLINE,
+  C_COUNT = 46 * CLINE
 };
+
+// Stack top of the free runs of L triangle slots (L = 1..5).
+__host__ __device__ constexpr int run_top(int L) { return C_RUN_TOP0 + (L - 1) * CLINE; }
+
 
 struct FrameParams {
   const float* depth;
@@ -266,6 +297,17 @@ __device__ __forceinline__ bool list_push(const Vol& V, T* list, int c_count, in
   }
   set_status(V, ST_POOL_FULL, list_pool_code(c_count));
   return false;
+}
+
+// Reserve n consecutive slots of a work list per calling lane, aggregated over the calling
+// lanes; returns the first (the caller checks each slot against the capacity).
+__device__ __forceinline__ int list_reserve(const Vol& V, int c_count, int n) {
+  cg::coalesced_group g = cg::coalesced_threads();
+  const int off = cg::exclusive_scan(g, n);
+  const int last = (int)g.size() - 1;
+  int base = 0;
+  if ((int)g.thread_rank() == last) base = atomicAdd(&V.ctl->c[c_count], off + n);
+  return g.shfl(base, last) + off;
 }
 
 // Add `v` to a counter, aggregated over the calling lanes.
