@@ -12,19 +12,22 @@
 //      travel with the halo; the edge slots (vertex ids) go to shared memory;
 //   b. per cube: type (and refinement), previous type; the block's edges that carry a
 //      vertex are marked for a refresh; cubes whose effective type changes go to a shared
-//      list, take a rank among the block's new runs of their length and among its released
-//      runs, and mark the edges their new triangles use;
-//   c. count the marked edges per bitmap word (stage d locates the j-th from the counts);
-//   d. one loop over independent work: per marked edge its vertex -- refreshed (position
-//      and normal from the new TSDF) if the block owns it, created on first use if a new
-//      triangle needs it: the first thread to claim the edge pops an id and publishes it
-//      with atomicCAS on the owner's edge slot; a thread that loses the race takes the
-//      winner's id and returns its own through the recycling list, so nobody waits and
-//      every vertex exists once; per changed cube the release of its old triangles
-//      (reference counts down); per run length one pop of all the block's new runs, and
-//      one reservation of recycling-list slots for the released runs;
-//   e. per changed cube: its new run (from the pop and its rank), the released run queued
-//      for recycling, the new triangles written and their references counted.
+//      list and take a rank among the block's new runs of their length; the edges their new
+//      triangles use are marked for a claim unless the block's own staged slot shows the
+//      vertex;
+//   c. count the claim and refresh edges per bitmap word (stage d locates the j-th of each
+//      from the counts);
+//   d. independent work in warp-sized units of one kind, so that the lanes of a warp take
+//      one path and the chains of different warps overlap: one pop per run length of all
+//      the block's new runs and one reservation of recycling-list slots for the released
+//      runs; per claim edge its vertex, created on first use -- the first thread to claim
+//      the edge pops an id and publishes it with atomicCAS on the owner's edge slot; a
+//      thread that loses the race takes the winner's id and returns its own through the
+//      recycling list, so nobody waits and every vertex exists once; per released run the
+//      reference counts of its old triangles down; per refresh edge the vertex's position
+//      and normal from the new TSDF;
+//   e. the released runs queued for recycling; per changed cube its new run (from the pop
+//      and its rank), its new triangles written and their references counted.
 // The paper resolves concurrent vertex creation with an atomic first-claimer lock or with
 // grouped serial launches (Sec. V-C); publishing the id with the claim replaces both.
 #pragma once
@@ -61,18 +64,21 @@ struct __align__(16) MeshSmem {
   uint64_t tri64[256];
   int nb[8];
   int dtri;
-  int nchg, nedge, ndr;  // changed cubes, visited edges, released runs
+  int nchg, ncand, nref, ndr;  // changed cubes, claim edges, refresh edges, released runs
+  int unext;                   // next free unit of stage d
   int nrun[5];           // new runs per length L = 1..5 (stage b), then their pop (stage d):
   int run_old[5], run_fs[5], run_bump[5];  // stack top seen, entries taken from it, first bump slot
   int dr_base;                             // first recycling-list slot of the released runs
   uint16_t chg_cube[BV];                   // changed cubes of the block
   uint8_t chg_new[BV], chg_old[BV];
-  uint16_t chg_rrank[BV], chg_drank[BV];  // rank among the new runs of its length / the released runs
+  uint16_t chg_rrank[BV];                  // rank among the block's new runs of its length
+  uint16_t rel[BV];                        // changed cubes (list slots) with a released run
   int chg_base[BV];                        // run of the released triangles, -1 none
-  unsigned nmark[EDGE_WORDS];              // edges the new triangles use
-  unsigned lmark[EDGE_WORDS];              // the block's own edges that carry a vertex
-  unsigned emark[EDGE_WORDS];              // their union: the edges stage d visits
-  int ecount[EDGE_WORDS];                  // exclusive prefix of emark's bits over its words
+  unsigned cmark[EDGE_WORDS];  // edges the new triangles use whose vertex may be missing (claims)
+  unsigned lmark[EDGE_WORDS];  // the block's own edges that carry a vertex
+  unsigned rmark[EDGE_WORDS];  // lmark without cmark: the refreshes
+  int ccount[EDGE_WORDS];      // exclusive prefixes of cmark's and rmark's bits over the words
+  int rcount[EDGE_WORDS];
   alignas(16) int rec[BV];                 // the block's edge records (voxel -> record, -1 none)
   int evid[EDGE_SLOTS];                    // vertex id per edge slot (own slots from stage a)
 };
@@ -230,6 +236,18 @@ __device__ __forceinline__ int vertex_of_edge(const Vol& V, const MeshSmem& S, i
 // Shared-memory slot of the edge owned by the voxel at halo coordinates (x, y, z) along a.
 __device__ __forceinline__ int edge_slot(int x, int y, int z, int a) { return ((z * 9 + y) * 9 + x) * 3 + a; }
 
+// Edge slot of the i-th set bit of a shared bitmap, from the exclusive prefix of its words'
+// bit counts (binary search for the word, then the bit within it).
+__device__ __forceinline__ int nth_marked(const unsigned* mark, const int* count, int i) {
+  int lo = 0, hi = EDGE_WORDS - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (count[mid] <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo * 32 + (int)__fns(mark[lo], 0, i - count[lo] + 1);
+}
+
 // Counters a mesh pass accumulates per CTA.
 struct MeshCounts {
   int changed = 0, created = 0, emitted = 0, released = 0, refreshed = 0, dtri = 0;
@@ -266,10 +284,11 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
     S.dtri = 0;
     S.nchg = 0;
     S.ndr = 0;
+    S.unext = 0;
   }
   if (threadIdx.x < 5) S.nrun[threadIdx.x] = 0;
   for (int w = threadIdx.x; w < EDGE_WORDS; w += MESH_THREADS) {
-    S.nmark[w] = 0;
+    S.cmark[w] = 0;
     S.lmark[w] = 0;
   }
   __syncthreads();
@@ -376,14 +395,17 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
       S.chg_new[slot] = (uint8_t)e;
       S.chg_old[slot] = (uint8_t)eff_old;
       S.chg_base[slot] = obase;
-      S.chg_drank[slot] = (uint16_t)(obase >= 0 ? atomicAdd(&S.ndr, 1) : 0);
+      if (obase >= 0) S.rel[atomicAdd(&S.ndr, 1)] = (uint16_t)slot;
       S.chg_rrank[slot] = (uint16_t)(nnew > 0 ? atomicAdd(&S.nrun[nnew - 1], 1) : 0);
       dtri += nnew - nold;
       for (int t = 0; t < nnew; ++t)
         for (int jj = 0; jj < 3; ++jj) {
           const int ob = owner_bits(packed_edge(tw64, t, jj));
-          const int es = edge_slot(x + (ob & 1), y + ((ob >> 1) & 1), z + ((ob >> 2) & 1), ob >> 3);
-          atomicOr(&S.nmark[es >> 5], 1u << (es & 31));
+          const int ox = x + (ob & 1), oy = y + ((ob >> 1) & 1), oz = z + ((ob >> 2) & 1);
+          const int es = edge_slot(ox, oy, oz, ob >> 3);
+          // an existing vertex of the block's own voxels needs nothing more (its slot is
+          // staged); a neighbour's edge or a missing vertex needs a claim in stage d
+          if ((ox | oy | oz) >= 8 || S.evid[es] < 0) atomicOr(&S.cmark[es >> 5], 1u << (es & 31));
         }
     }
     if (new_w != eff_w) *reinterpret_cast<uint32_t*>(V.code_eff + ci0) = new_w;
@@ -391,85 +413,66 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
   if (dtri) atomicAdd(&S.dtri, dtri);
   __syncthreads();
   const int nchg = S.nchg;
-  // ---- c. the edges stage d visits (needed or refreshed), counted per bitmap word
-  if (threadIdx.x < 32) {
+  // ---- c. count the claim edges (warp 0) and the refresh edges (warp 1) per bitmap word;
+  //         stage d locates the j-th of each from the prefixes
+  if (threadIdx.x < 64) {
+    const int lane = threadIdx.x & 31;
+    const bool refresh = threadIdx.x >= 32;
     int carry = 0;
     for (int w0 = 0; w0 < EDGE_WORDS; w0 += 32) {
-      const int w = w0 + threadIdx.x;
-      const unsigned u = w < EDGE_WORDS ? (S.nmark[w] | S.lmark[w]) : 0u;
-      if (w < EDGE_WORDS) S.emark[w] = u;
+      const int w = w0 + lane;
+      unsigned u = 0;
+      if (w < EDGE_WORDS) {
+        u = refresh ? S.lmark[w] & ~S.cmark[w] : S.cmark[w];
+        if (refresh) S.rmark[w] = u;
+      }
       const int c = __popc(u);
       int x = c;
       for (int o = 1; o < 32; o <<= 1) {
         const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if ((int)threadIdx.x >= o) x += y;
+        if (lane >= o) x += y;
       }
-      if (w < EDGE_WORDS) S.ecount[w] = carry + x - c;
+      if (w < EDGE_WORDS) (refresh ? S.rcount : S.ccount)[w] = carry + x - c;
       carry += __shfl_sync(0xffffffffu, x, 31);
     }
-    if (threadIdx.x == 0) S.nedge = carry;
+    if (lane == 0) (refresh ? S.nref : S.ncand) = carry;
   }
   __syncthreads();
-  // ---- d. one loop over independent work, so the stage lasts as long as the longest chain
-  //         rather than their sum: items 0-4 pop the block's new runs of length 1-5, item 5
-  //         reserves the released runs' recycling slots; then one item per visited edge and
-  //         one per changed cube
-  const int nedge = S.nedge;
-  for (int j = threadIdx.x; j < 6 + nedge + nchg; j += MESH_THREADS) {
-    if (j < 6) {
-      if (j < 5) {
-        const int n = S.nrun[j], L = j + 1;
+  // ---- d. independent work in units of up to 32 items of one kind, so that the lanes of a
+  //         warp take the same path: unit 0 pops the block's new runs of length 1-5 (lanes
+  //         0-4) and reserves the released runs' recycling slots (lane 5); then the claims,
+  //         the releases (round-trip chains) and the refreshes (arithmetic only), 32 per
+  //         unit.  Each warp starts on the unit of its index and takes the next free unit
+  //         when it is done, so the chains of different warps overlap
+  const int ncand = S.ncand, nref = S.nref, ndr = S.ndr;
+  const int uc = (ncand + 31) >> 5, ur = (ndr + 31) >> 5;
+  const int nunits = 1 + uc + ur + ((nref + 31) >> 5);
+  const int lane = threadIdx.x & 31;
+  for (int u = threadIdx.x >> 5; u < nunits;) {
+    int es = -1, vid = -1;
+    if (u == 0) {
+      if (lane < 5) {
+        const int n = S.nrun[lane], L = lane + 1;
         if (n > 0) {  // n runs of L slots: from the free stack, the rest from the bump range
-          const int old = atomicSub(&V.ctl->c[run_top(j + 1)], n);
+          const int old = atomicSub(&V.ctl->c[run_top(L)], n);
           const int fs = old <= 0 ? 0 : (old < n ? old : n);
           int bump0 = 0;
           if (fs < n) {
             bump0 = atomicAdd(&V.ctl->c[C_TRI_BUMP], (n - fs) * L);
-            atomicAdd(&V.ctl->c[run_top(j + 1)], n - fs);  // top back to >= 0 (as pool_pop)
+            atomicAdd(&V.ctl->c[run_top(L)], n - fs);  // top back to >= 0 (as pool_pop)
           }
-          S.run_old[j] = old;
-          S.run_fs[j] = fs;
-          S.run_bump[j] = bump0;
+          S.run_old[lane] = old;
+          S.run_fs[lane] = fs;
+          S.run_bump[lane] = bump0;
         }
-      } else if (S.ndr > 0) {
-        S.dr_base = atomicAdd(&V.ctl->c[C_N_DEADRUN], S.ndr);
+      } else if (lane == 5 && ndr > 0) {
+        S.dr_base = atomicAdd(&V.ctl->c[C_N_DEADRUN], ndr);
       }
-    } else if (j < 6 + nedge) {
-      const int i = j - 6;
-      int lo = 0, hi = EDGE_WORDS - 1;  // the word holding visited edge i
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (S.ecount[mid] <= i) lo = mid;
-        else hi = mid - 1;
-      }
-      const int es = lo * 32 + (int)__fns(S.emark[lo], 0, i - S.ecount[lo] + 1);
-      const unsigned bit = 1u << (es & 31);
-      const bool needed = (S.nmark[lo] & bit) != 0, live = (S.lmark[lo] & bit) != 0;
-      const int o = es / 3;
-      const int a = es - 3 * o;
-      const int x = o % 9, y = (o / 9) % 9, z = o / 81;
-      const bool own = (x | y | z) < 8;
-      int vid = own ? S.evid[es] : -1;
-      bool compute = live && vid >= 0;  // an existing vertex of the block: refresh
-      cnt.refreshed += compute;
-      if (needed && (!own || vid < 0)) {
-        bool fresh;
-        vid = vertex_of_edge<CE>(V, S, x, y, z, a, own, fresh);
-        S.evid[es] = vid;
-        cnt.created += fresh;
-        compute |= fresh;
-      }
-      if (compute) {
-        float4 p, nn;
-        edge_vertex(S, l, key, x, y, z, a, &p, &nn);
-        V.vpos[vid] = p;
-        V.vnrm[vid] = nn;
-      }
-    } else {
-      const int q = j - 6 - nedge;
-      const int obase = S.chg_base[q];
-      if (obase >= 0) {
-        const int nold = packed_ntri(S.tri64[S.chg_old[q]]);
+    } else if (u > uc && u <= uc + ur) {
+      const int i = ((u - 1 - uc) << 5) + lane;
+      if (i < ndr) {
+        const int q = S.rel[i];
+        const int obase = S.chg_base[q], nold = packed_ntri(S.tri64[S.chg_old[q]]);
         int4 tr[5];
 #pragma unroll
         for (int t = 0; t < 5; ++t) tr[t] = t < nold ? __ldcg(&V.tris[obase + t]) : make_int4(-1, -1, -1, -1);
@@ -498,20 +501,50 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
         }
         cnt.released += nold;
       }
+    } else {
+      const bool claim = u <= uc;
+      const int i = ((claim ? u - 1 : u - 1 - uc - ur) << 5) + lane;
+      if (i < (claim ? ncand : nref)) {
+        es = nth_marked(claim ? S.cmark : S.rmark, claim ? S.ccount : S.rcount, i);
+        if (claim) {
+          const int o = es / 3;
+          const int x = o % 9, y = (o / 9) % 9, z = o / 81;
+          bool fresh;
+          vid = vertex_of_edge<CE>(V, S, x, y, z, es - 3 * o, (x | y | z) < 8, fresh);
+          S.evid[es] = vid;
+          cnt.created += fresh;
+          if (!fresh) es = -1;
+        } else {
+          vid = S.evid[es];  // an existing vertex of the block: position and normal refreshed
+          if (vid < 0) es = -1;
+          cnt.refreshed += es >= 0;
+        }
+      }
     }
+    if (es >= 0) {  // a created or refreshed vertex
+      const int o = es / 3;
+      float4 p, nn;
+      edge_vertex(S, l, key, o % 9, (o / 9) % 9, o / 81, es - 3 * o, &p, &nn);
+      V.vpos[vid] = p;
+      V.vnrm[vid] = nn;
+    }
+    __syncwarp();
+    int next = 0;
+    if (lane == 0) next = atomicAdd(&S.unext, 1) + MESH_THREADS / 32;
+    u = __shfl_sync(0xffffffffu, next, 0);
   }
   __syncthreads();
-  // ---- e. per changed cube: its new run, the released run queued for recycling, the new
+  // ---- e. the released runs queued for recycling; per changed cube its new run, the new
   //         triangles and their references
+  for (int r = threadIdx.x; r < ndr; r += MESH_THREADS) {
+    const int q = S.rel[r], slot = S.dr_base + r;
+    if (slot < V.list_cap_deadrun) V.deadrun[slot] = make_int2(S.chg_base[q], packed_ntri(S.tri64[S.chg_old[q]]));
+    else set_status(V, ST_POOL_FULL, P_DEAD_RUN_LIST);
+  }
   for (int q = threadIdx.x; q < nchg; q += MESH_THREADS) {
-    const int c = S.chg_cube[q], obase = S.chg_base[q];
+    const int c = S.chg_cube[q];
     const uint64_t tw64 = S.tri64[S.chg_new[q]];
     const int nt = packed_ntri(tw64);
-    if (obase >= 0) {
-      const int slot = S.dr_base + S.chg_drank[q];
-      if (slot < V.list_cap_deadrun) V.deadrun[slot] = make_int2(obase, packed_ntri(S.tri64[S.chg_old[q]]));
-      else set_status(V, ST_POOL_FULL, P_DEAD_RUN_LIST);
-    }
     int base = -1;
     if (nt > 0) {
       const int r = S.chg_rrank[q], fs = S.run_fs[nt - 1];
