@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(MESH_THREADS, MESH_CTAS_PER_SM) kb_mesh(const 
                                                            int* bdone) {
   __shared__ MeshSmem S;
   __shared__ int pre[MAX_SCENES + 1];
-  for (int i = threadIdx.x; i < 128; i += MESH_THREADS) reinterpret_cast<uint4*>(S.tri64)[i] = vols[0].tri_table[i];
+  mesh_tables(S, vols[0].tri_table);
   grid_dependency_wait();
   scene_prefix(nscenes, pre, [&](int t) { return min(__ldcg(&vols[t].ctl->c[C_N_UPDATE]), vols[t].list_cap_update); });
   const int total = pre[nscenes];

@@ -62,6 +62,7 @@ constexpr int HALO_PAIRS = 244;      // 16-byte pairs of neighbour voxels in the
 struct __align__(16) MeshSmem {
   float halo[HALO_N];  // d of the voxel, NaN where W = 0 or its block is absent
   uint64_t tri64[256];
+  uint16_t emask[256];  // the cube edges each type's triangles use (bit k: edge k)
   int nb[8];
   int dtri;
   int nchg, ncand, nref, ndr;  // changed cubes, claim edges, refresh edges, released runs
@@ -131,6 +132,18 @@ __device__ __forceinline__ float4 ld_early_f4(const float2* p) {
   float4 v;
   asm volatile("ld.global.cg.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
   return v;
+}
+
+// atomicAdd(p, v) returning the old value when `on`, else no access and 0; predicated rather
+// than branched, so that a run of them issues back to back.
+__device__ __forceinline__ int atom_add_if(int* p, int v, bool on) {
+  int old = 0;
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q atom.global.add.s32 %0, [%1], %2;\n\t}"
+      : "+r"(old)
+      : "l"(p), "r"(v), "r"((unsigned)on)
+      : "memory");
+  return old;
 }
 
 // Halo entry of a voxel (d, W): d, or NaN where W = 0.
@@ -398,15 +411,14 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
       if (obase >= 0) S.rel[atomicAdd(&S.ndr, 1)] = (uint16_t)slot;
       S.chg_rrank[slot] = (uint16_t)(nnew > 0 ? atomicAdd(&S.nrun[nnew - 1], 1) : 0);
       dtri += nnew - nold;
-      for (int t = 0; t < nnew; ++t)
-        for (int jj = 0; jj < 3; ++jj) {
-          const int ob = owner_bits(packed_edge(tw64, t, jj));
-          const int ox = x + (ob & 1), oy = y + ((ob >> 1) & 1), oz = z + ((ob >> 2) & 1);
-          const int es = edge_slot(ox, oy, oz, ob >> 3);
-          // an existing vertex of the block's own voxels needs nothing more (its slot is
-          // staged); a neighbour's edge or a missing vertex needs a claim in stage d
-          if ((ox | oy | oz) >= 8 || S.evid[es] < 0) atomicOr(&S.cmark[es >> 5], 1u << (es & 31));
-        }
+      for (unsigned m = S.emask[e]; m; m &= m - 1) {
+        const int ob = owner_bits(__ffs(m) - 1);
+        const int ox = x + (ob & 1), oy = y + ((ob >> 1) & 1), oz = z + ((ob >> 2) & 1);
+        const int es = edge_slot(ox, oy, oz, ob >> 3);
+        // an existing vertex of the block's own voxels needs nothing more (its slot is
+        // staged); a neighbour's edge or a missing vertex needs a claim in stage d
+        if ((ox | oy | oz) >= 8 || S.evid[es] < 0) atomicOr(&S.cmark[es >> 5], 1u << (es & 31));
+      }
     }
     if (new_w != eff_w) *reinterpret_cast<uint32_t*>(V.code_eff + ci0) = new_w;
   }
@@ -469,38 +481,55 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
         S.dr_base = atomicAdd(&V.ctl->c[C_N_DEADRUN], ndr);
       }
     } else if (u > uc && u <= uc + ur) {
+      // the whole warp takes part (lanes past the last released run with nothing to release),
+      // so the recycling-list reservation below is one warp-wide scan and one atomic
       const int i = ((u - 1 - uc) << 5) + lane;
+      int obase = -1, nold = 0;
       if (i < ndr) {
         const int q = S.rel[i];
-        const int obase = S.chg_base[q], nold = packed_ntri(S.tri64[S.chg_old[q]]);
-        int4 tr[5];
-#pragma unroll
-        for (int t = 0; t < 5; ++t) tr[t] = t < nold ? __ldcg(&V.tris[obase + t]) : make_int4(-1, -1, -1, -1);
-        // all 15 reference drops in flight together; the vertices they leave unreferenced
-        // go to the recycling list, one reservation for all of them
-        unsigned zero = 0;
-#pragma unroll
-        for (int t = 0; t < 5; ++t) {
-          const int vs[3] = {tr[t].x, tr[t].y, tr[t].z};
-#pragma unroll
-          for (int jj = 0; jj < 3; ++jj)
-            if (vs[jj] >= 0 && atomicSub(&V.vref[vs[jj]], 1) == 1) zero |= 1u << (3 * t + jj);
-        }
-        for (int t = 0; t < nold; ++t) V.tris[obase + t] = make_int4(-1, -1, -1, -1);
-        if (zero) {
-          int slot = list_reserve(V, C_N_DEAD, __popc(zero));
-          while (zero) {
-            const int b = __ffs(zero) - 1;
-            zero &= zero - 1;
-            const int4 tt = b < 3 ? tr[0] : (b < 6 ? tr[1] : (b < 9 ? tr[2] : (b < 12 ? tr[3] : tr[4])));
-            const int k = b % 3;
-            if (slot < V.list_cap_dead) V.dead[slot] = k == 0 ? tt.x : (k == 1 ? tt.y : tt.z);
-            else set_status(V, ST_POOL_FULL, P_DEAD_VERTEX_LIST);
-            ++slot;
-          }
-        }
-        cnt.released += nold;
+        obase = S.chg_base[q];
+        nold = packed_ntri(S.tri64[S.chg_old[q]]);
       }
+      int4 tr[5];
+#pragma unroll
+      for (int t = 0; t < 5; ++t) tr[t] = t < nold ? __ldcg(&V.tris[obase + t]) : make_int4(-1, -1, -1, -1);
+      // the 15 reference drops issued back to back, their results read afterwards
+      int old[15];
+#pragma unroll
+      for (int k = 0; k < 15; ++k) {
+        const int4 tt = tr[k / 3];
+        const int v = k % 3 == 0 ? tt.x : (k % 3 == 1 ? tt.y : tt.z);
+        old[k] = atom_add_if(V.vref + (v >= 0 ? v : 0), -1, v >= 0);
+      }
+      unsigned zero = 0;  // references this release dropped to zero
+#pragma unroll
+      for (int k = 0; k < 15; ++k) {
+        const int4 tt = tr[k / 3];
+        const int v = k % 3 == 0 ? tt.x : (k % 3 == 1 ? tt.y : tt.z);
+        if (v >= 0 && old[k] == 1) zero |= 1u << k;
+      }
+      for (int t = 0; t < nold; ++t) V.tris[obase + t] = make_int4(-1, -1, -1, -1);
+      // the unreferenced vertices go to the recycling list
+      const int nz = __popc(zero);
+      int incl = nz;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      int slot = 0;
+      if (lane == 31 && incl > 0) slot = atomicAdd(&V.ctl->c[C_N_DEAD], incl);
+      slot = __shfl_sync(0xffffffffu, slot, 31) + incl - nz;
+      while (zero) {
+        const int b = __ffs(zero) - 1;
+        zero &= zero - 1;
+        const int4 tt = b < 3 ? tr[0] : (b < 6 ? tr[1] : (b < 9 ? tr[2] : (b < 12 ? tr[3] : tr[4])));
+        const int k = b % 3;
+        if (slot < V.list_cap_dead) V.dead[slot] = k == 0 ? tt.x : (k == 1 ? tt.y : tt.z);
+        else set_status(V, ST_POOL_FULL, P_DEAD_VERTEX_LIST);
+        ++slot;
+      }
+      cnt.released += nold;
     } else {
       const bool claim = u <= uc;
       const int i = ((claim ? u - 1 : u - 1 - uc - ur) << 5) + lane;
@@ -586,6 +615,23 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
   __syncthreads();
 }
 
+// The triangle table into shared memory, and from it each type's edge mask (whole CTA; the
+// first barrier of the first block orders it before its use).
+__device__ __forceinline__ void mesh_tables(MeshSmem& S, const uint4* tri_table) {
+  for (int i = threadIdx.x; i < 128; i += MESH_THREADS) {
+    const uint4 w = tri_table[i];
+    reinterpret_cast<uint4*>(S.tri64)[i] = w;
+    const uint64_t t2[2] = {((uint64_t)w.y << 32) | w.x, ((uint64_t)w.w << 32) | w.z};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      unsigned m = 0;
+      for (int t = 0; t < packed_ntri(t2[h]); ++t)
+        for (int j = 0; j < 3; ++j) m |= 1u << packed_edge(t2[h], t, j);
+      S.emask[2 * i + h] = (uint16_t)m;
+    }
+  }
+}
+
 // Flush a CTA's counters into the volume's statistics.
 __device__ __forceinline__ void mesh_flush(const Vol& V, MeshCounts& c) {
   if (c.changed) counter_add(V, C_ST_CHANGED, c.changed);
@@ -613,7 +659,7 @@ __device__ __forceinline__ void mesh_begin(const Vol& V, int n) {
 template <bool CE>
 __global__ void __launch_bounds__(MESH_THREADS, MESH_CTAS_PER_SM) k_mesh(Vol V, int mode) {
   __shared__ MeshSmem S;
-  for (int i = threadIdx.x; i < 128; i += MESH_THREADS) reinterpret_cast<uint4*>(S.tri64)[i] = V.tri_table[i];
+  mesh_tables(S, V.tri_table);
   grid_dependency_wait();
   const int n = min(__ldcg(&V.ctl->c[C_N_UPDATE]), V.list_cap_update);
   if (blockIdx.x == 0 && threadIdx.x == 0) mesh_begin(V, n);
