@@ -246,6 +246,22 @@ __device__ __forceinline__ int vertex_of_edge(const Vol& V, const MeshSmem& S, i
   return mine;
 }
 
+// Reserve `cnt` consecutive slots of a shared counter for every lane of the (full, converged)
+// warp, with one shared atomic per warp; returns this lane's first slot.
+__device__ __forceinline__ int warp_reserve(int* counter, int cnt) {
+  const int lane = threadIdx.x & 31;
+  int x = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  int base = 0;
+  if (lane == 31 && x > 0) base = atomicAdd(counter, x);
+  base = __shfl_sync(0xffffffffu, base, 31);
+  return base + x - cnt;
+}
+
 // Shared-memory slot of the edge owned by the voxel at halo coordinates (x, y, z) along a.
 __device__ __forceinline__ int edge_slot(int x, int y, int z, int a) { return ((z * 9 + y) * 9 + x) * 3 + a; }
 
@@ -364,9 +380,8 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
       S.halo[qh[k] + 1] = halo_value(qn[k].z, qn[k].w);
     }
   __syncthreads();
-  // ---- b. cube types, refresh marks, changed-cube list, needed edges (the type,
-  //         previous-type and vertex-flag bytes of the 4 cubes move as 32-bit words)
-  int dtri = 0;
+  // ---- b. cube types, refresh marks, changed-cube list (the type, previous-type and
+  //         vertex-flag bytes of the 4 cubes move as 32-bit words)
   {
     if (mode & M_UPDATE) *reinterpret_cast<uint32_t*>(V.code_prev + ci0) = eff_w;
     // edges of the 4 voxels that carry a vertex: 12 consecutive bits of the refresh bitmap
@@ -381,7 +396,6 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
     uint32_t new_w = eff_w;
 #pragma unroll 1
     for (int j = 0; j < 4; ++j) {  // rolled: the kernel's code must stay small (instruction cache)
-      const int c = c0 + j;
       const int x = cx + j, y = cy, z = cz;
       bool valid = true;
       int raw = 0, small = 0;
@@ -392,25 +406,44 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
         raw |= (hv < 0.0f) << k;
         small |= (fabsf(hv) < eps) << k;
       }
-      const int eff_old = (eff_w >> (8 * j)) & 0xFF;
       const int prev = (prev_w >> (8 * j)) & 0xFF;
       int e = valid ? raw : 0;
       if (valid && (mode & M_REFINE)) e = refine_type(raw, prev, small);
-      if (e == eff_old) continue;
-      ++cnt.changed;
       new_w = (new_w & ~(0xFFu << (8 * j))) | ((uint32_t)e << (8 * j));
-      const uint64_t tw64 = S.tri64[e];
-      const int nold = packed_ntri(S.tri64[eff_old]), nnew = packed_ntri(tw64);
-      const int tb = j == 0 ? tb4.x : (j == 1 ? tb4.y : (j == 2 ? tb4.z : tb4.w));
-      const int obase = nold > 0 ? tb : -1;
-      const int slot = atomicAdd(&S.nchg, 1);  // a few changed cubes per thread at most
-      S.chg_cube[slot] = (uint16_t)c;
-      S.chg_new[slot] = (uint8_t)e;
+    }
+    if (new_w != eff_w) *reinterpret_cast<uint32_t*>(V.code_eff + ci0) = new_w;
+    // the changed cubes into the shared list: one shared atomic per warp
+    unsigned chm = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) chm |= (((new_w ^ eff_w) >> (8 * j)) & 0xFFu) ? 1u << j : 0u;
+    const int nc = __popc(chm);
+    cnt.changed += nc;
+    int slot = warp_reserve(&S.nchg, nc);
+    while (chm) {
+      const int j = __ffs(chm) - 1;
+      chm &= chm - 1;
+      const int eff_old = (eff_w >> (8 * j)) & 0xFF;
+      S.chg_cube[slot] = (uint16_t)(c0 + j);
+      S.chg_new[slot] = (uint8_t)((new_w >> (8 * j)) & 0xFF);
       S.chg_old[slot] = (uint8_t)eff_old;
-      S.chg_base[slot] = obase;
-      if (obase >= 0) S.rel[atomicAdd(&S.ndr, 1)] = (uint16_t)slot;
-      S.chg_rrank[slot] = (uint16_t)(nnew > 0 ? atomicAdd(&S.nrun[nnew - 1], 1) : 0);
+      S.chg_base[slot] = packed_ntri(S.tri64[eff_old]) > 0 ? (j == 0 ? tb4.x : (j == 1 ? tb4.y : (j == 2 ? tb4.z : tb4.w))) : -1;
+      ++slot;
+    }
+  }
+  __syncthreads();
+  const int nchg = S.nchg;
+  // ---- b2. per changed cube (spread over the CTA, wherever the changes cluster): its rank
+  //          among the new runs of its length, its released run listed, the edges its new
+  //          triangles use marked
+  {
+    int dtri = 0;
+    for (int q = threadIdx.x; q < nchg; q += MESH_THREADS) {
+      const int c = S.chg_cube[q], e = S.chg_new[q];
+      const int nold = packed_ntri(S.tri64[S.chg_old[q]]), nnew = packed_ntri(S.tri64[e]);
+      if (S.chg_base[q] >= 0) S.rel[atomicAdd(&S.ndr, 1)] = (uint16_t)q;
+      if (nnew > 0) S.chg_rrank[q] = (uint16_t)atomicAdd(&S.nrun[nnew - 1], 1);
       dtri += nnew - nold;
+      const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
       for (unsigned m = S.emask[e]; m; m &= m - 1) {
         const int ob = owner_bits(__ffs(m) - 1);
         const int ox = x + (ob & 1), oy = y + ((ob >> 1) & 1), oz = z + ((ob >> 2) & 1);
@@ -420,11 +453,9 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
         if ((ox | oy | oz) >= 8 || S.evid[es] < 0) atomicOr(&S.cmark[es >> 5], 1u << (es & 31));
       }
     }
-    if (new_w != eff_w) *reinterpret_cast<uint32_t*>(V.code_eff + ci0) = new_w;
+    if (dtri) atomicAdd(&S.dtri, dtri);
   }
-  if (dtri) atomicAdd(&S.dtri, dtri);
   __syncthreads();
-  const int nchg = S.nchg;
   // ---- c. count the claim edges (warp 0) and the refresh edges (warp 1) per bitmap word;
   //         stage d locates the j-th of each from the prefixes
   if (threadIdx.x < 64) {
