@@ -21,7 +21,8 @@ struct BatchFrames {
   int advance[MAX_SCENES];  // start a new mesh epoch for this scene (as k_alloc's argument)
 };
 
-// Batch control: last-CTA tickets of the five batched kernels.
+// Batch control: last-CTA tickets of the batched kernels that finish in their last CTA, and
+// the mesh pass's block hand-out counter (reset by the fusion's last CTA).
 enum BatchDone { BD_ALLOC = 0, BD_INTEGRATE, BD_MESH, BD_GC_VERTICES, BD_GC_BLOCKS, BD_COUNT };
 
 // pre[s] = sum of count(t) over scenes t < s, pre[n] = total (shared memory, whole CTA).
@@ -89,7 +90,10 @@ __global__ void __launch_bounds__(INTEG_THREADS) kb_integrate(const Vol* __restr
   allow_dependent_launch();
   if (last_block_at(bdone + BD_INTEGRATE)) {
     for (int t = threadIdx.x; t < nscenes; t += blockDim.x) integrate_finish(vols[t], pre[t + 1] - pre[t]);
-    if (threadIdx.x == 0) bdone[BD_INTEGRATE] = 0;
+    if (threadIdx.x == 0) {
+      bdone[BD_INTEGRATE] = 0;
+      bdone[BD_MESH] = 0;
+    }
   }
 }
 
@@ -107,7 +111,8 @@ __global__ void __launch_bounds__(MESH_THREADS, MESH_CTAS_PER_SM) kb_mesh(const 
     for (int t = threadIdx.x; t < nscenes; t += blockDim.x) mesh_begin(vols[t], pre[t + 1] - pre[t]);
   MeshCounts cnt;
   int cur = -1;
-  for (int g = blockIdx.x; g < total; g += gridDim.x) {
+  // one block per CTA, then the rest to whichever CTA is free first
+  for (int g = blockIdx.x, k = 0; g < total; k ^= 1) {
     const int s = scene_of(pre, nscenes, g);
     if (s != cur) {
       if (cur >= 0) mesh_flush(vols[cur], cnt);
@@ -115,6 +120,9 @@ __global__ void __launch_bounds__(MESH_THREADS, MESH_CTAS_PER_SM) kb_mesh(const 
     }
     const Vol& V = vols[s];
     mesh_block<CE>(V, S, V.update[g - pre[s]], mode, cnt);
+    if (threadIdx.x == 0) S.next[k] = (int)gridDim.x + atomicAdd(&bdone[BD_MESH], 1);
+    __syncthreads();
+    g = S.next[k];
   }
   if (cur >= 0) mesh_flush(vols[cur], cnt);
   allow_dependent_launch();

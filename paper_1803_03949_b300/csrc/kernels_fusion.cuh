@@ -338,6 +338,7 @@ __device__ __forceinline__ void integrate_finish(const Vol& V, int n) {
   reinterpret_cast<unsigned*>(V.ctl->c)[C_ST_COLLECTED] += (unsigned)n;  // wraps modulo 2^32
   V.ctl->c[C_N_TOUCHED] = 0;
   V.ctl->c[C_FRAME] += 1;
+  V.ctl->c[C_MESH_NEXT] = 0;  // for the mesh pass that follows
 }
 
 // Every collected block, one per CTA iteration (FUSE = false: resolve only, for analytic

@@ -67,6 +67,7 @@ struct __align__(16) MeshSmem {
   int dtri;
   int nchg, ncand, nref, ndr;  // changed cubes, claim edges, refresh edges, released runs
   int unext;                   // next free unit of stage d
+  int next[2];                 // the CTA's next update-set block (alternating slots)
   int nrun[5];           // new runs per length L = 1..5 (stage b), then their pop (stage d):
   int run_old[5], run_fs[5], run_bump[5];  // stack top seen, entries taken from it, first bump slot
   int dr_base;                             // first recycling-list slot of the released runs
@@ -695,7 +696,14 @@ __global__ void __launch_bounds__(MESH_THREADS, MESH_CTAS_PER_SM) k_mesh(Vol V, 
   const int n = min(__ldcg(&V.ctl->c[C_N_UPDATE]), V.list_cap_update);
   if (blockIdx.x == 0 && threadIdx.x == 0) mesh_begin(V, n);
   MeshCounts cnt;
-  for (int i = blockIdx.x; i < n; i += gridDim.x) mesh_block<CE>(V, S, V.update[i], mode, cnt);
+  // one block per CTA, then the blocks beyond the grid go to whichever CTA is free first
+  // (the cost of a block varies tenfold with its changes)
+  for (int i = blockIdx.x, k = 0; i < n; k ^= 1) {
+    mesh_block<CE>(V, S, V.update[i], mode, cnt);
+    if (threadIdx.x == 0) S.next[k] = (int)gridDim.x + atomicAdd(&V.ctl->c[C_MESH_NEXT], 1);
+    __syncthreads();
+    i = S.next[k];
+  }
   mesh_flush(V, cnt);
   allow_dependent_launch();
 }

@@ -228,19 +228,23 @@ vm_status enqueue_list_all(vm_volume* v) {
   return launch(v, K_LIST_ALL, [&] { k_list_all<<<grid_for(v, 4), 256, 0, v->cur>>>(v->V); });
 }
 
-vm_status enqueue_mesh_pass(vm_volume* v, int mode) {
+// after_integrate: the pass directly follows an integrate call, whose last CTA resets the
+// pass's block hand-out counter; otherwise it is reset here.
+vm_status enqueue_mesh_pass(vm_volume* v, int mode, bool after_integrate) {
   const bool ce = (v->p.flags & VM_PARAM_COMPACT_EDGES) != 0;
+  if (!after_integrate && cudaMemsetAsync(&v->V.ctl->c[C_MESH_NEXT], 0, sizeof(int), v->cur) != cudaSuccess)
+    return VM_ERR_CUDA;
   return launch(v, K_MESH, [&] {
     launch_dependent(ce ? k_mesh<true> : k_mesh<false>, grid_for(v, MESH_CTAS_PER_SM), MESH_THREADS, v->cur, v->V,
                      mode);
   });
 }
 
-vm_status enqueue_update(vm_volume* v, int flags) {
+vm_status enqueue_update(vm_volume* v, int flags, bool after_integrate) {
   vm_status st = VM_OK;
   if (flags & VM_FULL) st = enqueue_list_all(v);
   if (st) return st;
-  st = enqueue_mesh_pass(v, M_UPDATE | ((flags & VM_REFINE) ? M_REFINE : 0));
+  st = enqueue_mesh_pass(v, M_UPDATE | ((flags & VM_REFINE) ? M_REFINE : 0), after_integrate && !(flags & VM_FULL));
   v->advance_pending = true;
   return st;
 }
@@ -468,7 +472,7 @@ vm_status vm_integrate_depth(vm_volume* v, const float* depth, const vm_intrinsi
 
 vm_status vm_update_mesh(vm_volume* v, int flags) {
   if (!v || (flags & ~(VM_FULL | VM_REFINE))) return VM_ERR_INVALID_ARG;
-  return enqueue_update(v, flags);
+  return enqueue_update(v, flags, false);
 }
 
 vm_status vm_refine_mesh(vm_volume* v, int full) {
@@ -476,7 +480,7 @@ vm_status vm_refine_mesh(vm_volume* v, int full) {
   vm_status st = VM_OK;
   if (full) st = enqueue_list_all(v);
   if (st) return st;
-  return enqueue_mesh_pass(v, M_REFINE);
+  return enqueue_mesh_pass(v, M_REFINE, false);
 }
 
 vm_status vm_gc(vm_volume* v) {
@@ -492,7 +496,7 @@ vm_status vm_step(vm_volume* v, const float* depth, const vm_intrinsics* K, cons
   auto body = [&]() -> vm_status {
     vm_status s = enqueue_integrate(v, fp);
     if (s) return s;
-    s = enqueue_update(v, flags & (VM_FULL | VM_REFINE));
+    s = enqueue_update(v, flags & (VM_FULL | VM_REFINE), true);
     if (s) return s;
     if (flags & VM_GC) s = enqueue_gc(v);
     return s;

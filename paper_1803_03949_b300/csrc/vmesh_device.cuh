@@ -96,7 +96,8 @@ enum Counter {
   C_DONE5 = 43 * CLINE,
   C_DONE6 = 44 * CLINE,
   C_DONE7 = 45 * CLINE,
-  C_COUNT = 46 * CLINE
+  C_MESH_NEXT = 46 * CLINE,  // next update-set block a mesh pass hands out (beyond one per CTA)
+  C_COUNT = 47 * CLINE
 };
 
 // Stack top of the free runs of L triangle slots (L = 1..5).
