@@ -10,10 +10,12 @@
 namespace vmk {
 
 // ------------------------------------------------------------------ block collection
-constexpr int ALLOC_TILE_W = 64;     // pixels per tile row
+constexpr int ALLOC_TILE_W = 64;     // pixels per tile row (batched collection)
+constexpr int ALLOC_TILE_W1 = 32;    // pixels per tile row (k_alloc: 600 tiles of a 640 x 480
+                                     // frame spread over the SMs more evenly than 300)
 constexpr int ALLOC_TILE_H = 16;     // tile rows
 constexpr int ALLOC_PPT = 2;         // vertically adjacent pixels per thread (k_alloc)
-constexpr int ALLOC_THREADS = ALLOC_TILE_W * ALLOC_TILE_H / ALLOC_PPT;
+constexpr int ALLOC_THREADS = ALLOC_TILE_W1 * ALLOC_TILE_H / ALLOC_PPT;
 constexpr int ALLOC_SET_LOG2 = 10;
 constexpr int ALLOC_SET = 1 << ALLOC_SET_LOG2;  // CTA-local set of block keys
 constexpr int DDA_MAX_CELLS = 1 << 16;
@@ -27,9 +29,11 @@ __device__ int hash_insert(const Vol& V, uint64_t key, int bx, int by, int bz, u
   uint32_t s = (uint32_t)mix64(key) & V.hmask;
   blk_out = -1;
   for (uint32_t p = 0; p <= V.hmask; ++p) {
-    uint64_t k = __ldcg(&V.keys[s]);
+    // the value is loaded with the key (one round trip when the key is found)
+    const uint64_t k = __ldcg(&V.keys[s]);
+    const int val = __ldcg(&V.vals[s]);
     if (k == key) {
-      blk_out = __ldcg(&V.vals[s]);
+      blk_out = val;
       return (int)s;
     }
     if (k == KEY_EMPTY) {
@@ -69,7 +73,6 @@ __device__ int hash_insert(const Vol& V, uint64_t key, int bx, int by, int bz, u
 // Record a collected bucket once per integrate call, as {packed key (low, high word), block
 // index or -1, bucket}: the fusion kernel then needs no hash or key lookups of its own.
 __device__ __forceinline__ void touch_bucket(const Vol& V, int s, uint64_t key, int blk, uint32_t frame) {
-  if (__ldcg(&V.stamp[s]) == frame) return;
   if (atomicExch(&V.stamp[s], frame) != frame)
     list_push(V, V.touched, C_N_TOUCHED, V.list_cap_touched, make_int4((int)(uint32_t)key, (int)(key >> 32), blk, s));
 }
@@ -169,17 +172,17 @@ __device__ __forceinline__ void collect_pixel(const Vol& V, const FrameParams& f
   }
 }
 
-// One 64 x 16 pixel tile (tile column tx, row ty) walked by the calling CTA of
-// 1024 / PPT threads, PPT vertically adjacent pixels per thread: each pixel's segment goes
+// One TW x 16 pixel tile (tile column tx, row ty) walked by the calling CTA of
+// TW * 16 / PPT threads, PPT vertically adjacent pixels per thread: each pixel's segment goes
 // into the CTA-local key set `set`, then the set's unique keys are inserted into the global
 // hash and recorded as collected.
-template <int PPT>
+template <int PPT, int TW>
 __device__ __forceinline__ void alloc_tile(const Vol& V, const FrameParams& fp, int tx, int ty,
                                            unsigned long long* set) {
   const uint32_t frame = (uint32_t)__ldcg(&V.ctl->c[C_FRAME]);
   for (int i = threadIdx.x; i < ALLOC_SET; i += blockDim.x) set[i] = KEY_EMPTY;
-  const int u = tx * ALLOC_TILE_W + (threadIdx.x & (ALLOC_TILE_W - 1));
-  const int v = ty * ALLOC_TILE_H + PPT * (threadIdx.x / ALLOC_TILE_W);
+  const int u = tx * TW + (threadIdx.x & (TW - 1));
+  const int v = ty * ALLOC_TILE_H + PPT * (threadIdx.x / TW);
   float D[PPT];
 #pragma unroll
   for (int r = 0; r < PPT; ++r) D[r] = (u < fp.W && v + r < fp.H) ? __ldg(fp.depth + (size_t)(v + r) * fp.W + u) : 0.0f;
@@ -211,8 +214,8 @@ __device__ __forceinline__ void alloc_begin(const Vol& V, int advance_epoch) {
   }
 }
 
-// One CTA per 64 x 16 pixel tile, two vertically adjacent pixels per thread (so a 640 x 480
-// frame fits in one wave of CTAs).  The frame's parameters arrive as a launch argument; the
+// One CTA per 32 x 16 pixel tile, two vertically adjacent pixels per thread (a 640 x 480
+// frame is one wave of CTAs).  The frame's parameters arrive as a launch argument; the
 // first CTA stores them in the control block for the kernels that follow and starts the
 // epoch.  No CTA waits for the others: the kernel ends with its last tile.
 __global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(Vol V, const __grid_constant__ FrameParams fp,
@@ -222,7 +225,7 @@ __global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(Vol V, const __grid_con
     V.ctl->fp = fp;  // for the later kernels
     alloc_begin(V, advance_epoch);
   }
-  alloc_tile<ALLOC_PPT>(V, fp, blockIdx.x, blockIdx.y, set);
+  alloc_tile<ALLOC_PPT, ALLOC_TILE_W1>(V, fp, blockIdx.x, blockIdx.y, set);
   allow_dependent_launch();
 }
 

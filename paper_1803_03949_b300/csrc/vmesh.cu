@@ -207,7 +207,7 @@ void launch_dependent(void (*kernel)(Params...), int grid, int block, cudaStream
 
 // ---- enqueue helpers (no validation)
 dim3 alloc_grid(const FrameParams& fp) {
-  return dim3((fp.W + ALLOC_TILE_W - 1) / ALLOC_TILE_W, (fp.H + ALLOC_TILE_H - 1) / ALLOC_TILE_H);
+  return dim3((fp.W + ALLOC_TILE_W1 - 1) / ALLOC_TILE_W1, (fp.H + ALLOC_TILE_H - 1) / ALLOC_TILE_H);
 }
 
 vm_status enqueue_integrate(vm_volume* v, const FrameParams& fp) {
