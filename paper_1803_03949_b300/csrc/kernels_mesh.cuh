@@ -58,11 +58,27 @@ __device__ __forceinline__ int packed_edge(uint64_t w, int t, int j) { return (i
 
 constexpr int MESH_CTAS_PER_SM = 8;  // bounded by registers (64) and shared memory (24 KB)
 constexpr int HALO_PAIRS = 244;      // 16-byte pairs of neighbour voxels in the halo (488 voxels)
+constexpr int MESH_TABLE_UINT4 = 192;  // 256 packed triangle words, 256 edge masks, 256 pair codes
+
+// The halo's neighbour voxels as pairs adjacent along x (X, X + 1 at halo row Y, Z), packed
+// X | Y << 4 | Z << 8: rows y, z < 8 take x = 8..9 from the +x neighbour; the 36 rows with y
+// or z at 8..9 take x = 0..9 in five pairs.  Entries past HALO_PAIRS are 0.
+__host__ __device__ inline void halo_pairs(uint16_t* out) {
+  int i = 0;
+  for (int z = 0; z < 8; ++z)
+    for (int y = 0; y < 8; ++y) out[i++] = (uint16_t)(8 | y << 4 | z << 8);
+  for (int r = 0; r < 36; ++r) {
+    const int Y = r < 16 ? 8 + (r & 1) : (r - 16) % 10, Z = r < 16 ? r >> 1 : 8 + (r - 16) / 10;
+    for (int s = 0; s < 5; ++s) out[i++] = (uint16_t)(2 * s | Y << 4 | Z << 8);
+  }
+  for (; i < 256; ++i) out[i] = 0;
+}
 
 struct __align__(16) MeshSmem {
   float halo[HALO_N];  // d of the voxel, NaN where W = 0 or its block is absent
   uint64_t tri64[256];
-  uint16_t emask[256];  // the cube edges each type's triangles use (bit k: edge k)
+  alignas(16) uint16_t emask[256];  // the cube edges each type's triangles use (bit k: edge k)
+  alignas(16) uint16_t pairs[256];  // the halo's neighbour voxel pairs (halo_pairs)
   int nb[8];
   int dtri;
   int nchg, ncand, nref, ndr;  // changed cubes, claim edges, refresh edges, released runs
@@ -322,9 +338,7 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
     S.lmark[w] = 0;
   }
   __syncthreads();
-  // the neighbours' 488 halo voxels as 244 pairs adjacent along x (16 bytes each): rows
-  // y, z < 8 take x = 8..9 from the +x neighbour; the 36 rows with y or z at 8..9 take
-  // x = 0..9 in five pairs
+  // the neighbours' 488 halo voxels as 244 pairs adjacent along x (16 bytes each)
   float4 qn[2];
   int qh[2];
 #pragma unroll
@@ -333,15 +347,8 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
     qh[k] = -1;
     qn[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (i < HALO_PAIRS) {
-      int X, Y, Z;
-      if (i < 64) {
-        X = 8, Y = i & 7, Z = i >> 3;
-      } else {
-        const int r = (i - 64) / 5;
-        X = 2 * (i - 64 - 5 * r);
-        if (r < 16) Y = 8 + (r & 1), Z = r >> 1;
-        else Y = (r - 16) % 10, Z = 8 + (r - 16) / 10;
-      }
+      const int pc = S.pairs[i];
+      const int X = pc & 15, Y = (pc >> 4) & 15, Z = pc >> 8;
       const int b = S.nb[(X >> 3) | ((Y >> 3) << 1) | ((Z >> 3) << 2)];
       qh[k] = X + HALO * Y + HALO * HALO * Z;
       if (b >= 0)
@@ -647,20 +654,14 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
   __syncthreads();
 }
 
-// The triangle table into shared memory, and from it each type's edge mask (whole CTA; the
-// first barrier of the first block orders it before its use).
-__device__ __forceinline__ void mesh_tables(MeshSmem& S, const uint4* tri_table) {
-  for (int i = threadIdx.x; i < 128; i += MESH_THREADS) {
-    const uint4 w = tri_table[i];
-    reinterpret_cast<uint4*>(S.tri64)[i] = w;
-    const uint64_t t2[2] = {((uint64_t)w.y << 32) | w.x, ((uint64_t)w.w << 32) | w.z};
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      unsigned m = 0;
-      for (int t = 0; t < packed_ntri(t2[h]); ++t)
-        for (int j = 0; j < 3; ++j) m |= 1u << packed_edge(t2[h], t, j);
-      S.emask[2 * i + h] = (uint16_t)m;
-    }
+// The mesh tables into shared memory (whole CTA; the first barrier of the first block
+// orders the copy before any use).
+__device__ __forceinline__ void mesh_tables(MeshSmem& S, const uint4* tables) {
+  for (int i = threadIdx.x; i < MESH_TABLE_UINT4; i += MESH_THREADS) {
+    const uint4 w = tables[i];
+    if (i < 128) reinterpret_cast<uint4*>(S.tri64)[i] = w;
+    else if (i < 160) reinterpret_cast<uint4*>(S.emask)[i - 128] = w;
+    else reinterpret_cast<uint4*>(S.pairs)[i - 160] = w;
   }
 }
 

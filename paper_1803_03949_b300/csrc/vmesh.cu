@@ -409,16 +409,25 @@ vm_status vm_create_volume(const vm_params* p, void* cuda_stream, vm_volume** ou
             dalloc(v, &V.ctl, 1, 0);
   for (int L = 0; L < 5 && ok; ++L) ok = dalloc(v, &V.run_free[L], (size_t)V.run_cap[L], 0);
   uint4* tt = nullptr;
-  if (ok) ok = dalloc(v, &tt, 128, 0);
+  if (ok) ok = dalloc(v, &tt, MESH_TABLE_UINT4, 0);
   if (ok) {
-    // packed: 15 edge ids of 4 bits (triangle t, corner j at bit 4 (3 t + j)), count in bits 60..63
-    uint64_t packed[256];
+    // the mesh pass's tables, copied to shared memory by every CTA:
+    // packed triangles: 15 edge ids of 4 bits (triangle t, corner j at bit 4 (3 t + j)), the
+    // count in bits 60..63; the edge mask of each type; the halo's neighbour voxel pairs
+    struct {
+      uint64_t packed[256];
+      uint16_t emask[256];
+      uint16_t pairs[256];
+    } tab = {};
     for (int c = 0; c < 256; ++c) {
       uint64_t w = (uint64_t)table.ntri[c] << 60;
       for (int i = 0; i < 3 * table.ntri[c]; ++i) w |= (uint64_t)(table.tri[c][i] & 15) << (4 * i);
-      packed[c] = w;
+      tab.packed[c] = w;
+      tab.emask[c] = table.edgemask[c];
     }
-    ok = cudaMemcpyAsync(tt, packed, sizeof(packed), cudaMemcpyHostToDevice, v->stream) == cudaSuccess &&
+    halo_pairs(tab.pairs);
+    static_assert(sizeof(tab) == MESH_TABLE_UINT4 * sizeof(uint4), "mesh table layout");
+    ok = cudaMemcpyAsync(tt, &tab, sizeof(tab), cudaMemcpyHostToDevice, v->stream) == cudaSuccess &&
          cudaStreamSynchronize(v->stream) == cudaSuccess;
     V.tri_table = tt;
   }

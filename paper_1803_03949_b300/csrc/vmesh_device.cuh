@@ -156,7 +156,7 @@ struct Vol {
 
   int4* tris;
 
-  const uint4* tri_table;  // packed triangle table, 256 x 64 bits (edge ids and count)
+  const uint4* tri_table;  // mesh tables: packed triangles, edge masks, halo pairs (MESH_TABLE_UINT4)
 
   int* blk_free;
   int* vtx_free;
