@@ -171,7 +171,8 @@ __global__ void __launch_bounds__(256) kb_gc_vertices(const Vol* __restrict__ vo
   allow_dependent_launch();
 }
 
-// Block recycling of every scene, one warp per pool slot in use.  The last CTA finishes the
+// Block recycling of every scene: a lane per pool slot in use tests it, the warp frees the
+// candidates.  The last CTA finishes the
 // scenes one after another (a hash rebuild takes the whole CTA).
 __global__ void __launch_bounds__(256) kb_gc_blocks(const Vol* __restrict__ vols, int nscenes, int consumed,
                                                     int* bdone) {
@@ -184,17 +185,25 @@ __global__ void __launch_bounds__(256) kb_gc_blocks(const Vol* __restrict__ vols
   scene_prefix(nscenes, pre, [&](int t) { return min(__ldcg(&vols[t].ctl->c[C_BLK_BUMP]), vols[t].max_blocks); });
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  int freed = 0, cur = -1;
-  for (int g = warp; g < pre[nscenes]; g += nwarps) {
-    const int s = scene_of(pre, nscenes, g);
-    if (s != cur) {
-      if (cur >= 0) gc_flush_blocks(vols[cur], freed);
-      cur = s;
+  const int lane = threadIdx.x & 31;
+  const int total = pre[nscenes];
+  for (int base = warp * 32; base < total; base += nwarps * 32) {
+    const int g = base + lane;
+    int s = 0;
+    bool cand = false;
+    if (g < total) {
+      s = scene_of(pre, nscenes, g);
+      cand = gc_candidate(vols[s], g - pre[s], sepoch[s], consumed);
     }
-    const Vol& V = vols[s];
-    freed += gc_block(V, g - pre[s], sepoch[s], consumed);
+    unsigned m = __ballot_sync(0xffffffffu, cand);
+    while (m) {
+      const int b = __ffs(m) - 1;
+      m &= m - 1;
+      const int sb = __shfl_sync(0xffffffffu, s, b);
+      int freed = gc_free_block(vols[sb], base + b - pre[sb]);
+      gc_flush_blocks(vols[sb], freed);
+    }
   }
-  if (cur >= 0) gc_flush_blocks(vols[cur], freed);
   if (last_block_at(bdone + BD_GC_BLOCKS)) {
     for (int t = 0; t < nscenes; ++t) gc_blocks_finish(vols[t], consumed);
     if (threadIdx.x == 0) bdone[BD_GC_BLOCKS] = 0;

@@ -25,8 +25,8 @@ __device__ __forceinline__ void run_push(const Vol& V, int L, int base) {
 // whether a detached vertex was freed.
 template <bool CE>
 __device__ __forceinline__ bool gc_vertex(const Vol& V, int vid) {
+  const uint32_t e = V.vedge[vid];  // loaded alongside the claim; no gc thread writes it
   if (atomicCAS(&V.vref[vid], 0, -1) != 0) return false;
-  const uint32_t e = V.vedge[vid];
   bool detached = false;
   if (e != NO_EDGE) {
     const int ob = (int)(e / EPB), r = (int)(e - (uint32_t)ob * EPB), ov = r / 3, a = r - ov * 3;
@@ -121,25 +121,32 @@ __device__ void rehash_in_cta(const Vol& V) {
   __syncthreads();
 }
 
-// Block slot `blk` (the calling warp): freed when it was not collected in the current
-// epoch, has no triangles and owns no vertex, all of its voxels have W = 0 or d >= mu, and
-// none of its 7 lower neighbours (whose cubes reach into it) has triangles.  Its bucket
-// becomes a tombstone, its voxels are cleared, its neighbours forget it, its index returns
-// to the pool.  `consumed`: the update set has been meshed since it was collected (else its
-// blocks are kept, so that the pending update never lists a recycled block index).
-// Returns (in lane 0) whether the block was freed.
-__device__ __forceinline__ bool gc_block(const Vol& V, int blk, uint32_t epoch, int consumed) {
-  const int lane = threadIdx.x & 31;
+// Block slot `blk` (one lane) may be freed when it was not collected in the current epoch,
+// has no triangles and owns no vertex, and all of its voxels have W = 0 or d >= mu.
+// `consumed`: the update set has been meshed since it was collected (else its blocks are
+// kept, so that the pending update never lists a recycled block index).  The six records
+// are loaded before any is tested (one round trip), lanes reading consecutive slots.
+__device__ __forceinline__ bool gc_candidate(const Vol& V, int blk, uint32_t epoch, int consumed) {
   const int4 key = V.bkey[blk];
-  const bool cand = key.w >= 0 && V.bepoch[blk] != epoch && V.bntri[blk] == 0 && V.bnvert[blk] == 0 &&
-                    V.bnear[blk] == 0 && (consumed || V.ustamp[blk] != epoch);
-  if (!cand) return false;  // warp-uniform
+  const uint32_t be = V.bepoch[blk], us = V.ustamp[blk];
+  const int nt = V.bntri[blk], nv = V.bnvert[blk];
+  const int nr = V.bnear[blk];
+  return (key.w >= 0) & (be != epoch) & (nt == 0) & (nv == 0) & (nr == 0) & (consumed || us != epoch);
+}
+
+// Free candidate slot `blk` (the calling warp) unless one of its 7 lower neighbours (whose
+// cubes reach into it) has triangles: its bucket becomes a tombstone, its voxels are
+// cleared, its neighbours forget it, its index returns to the pool.  Returns (in every lane)
+// whether the block was freed.
+__device__ __forceinline__ bool gc_free_block(const Vol& V, int blk) {
+  const int lane = threadIdx.x & 31;
   bool lower_tri = false;
   if (lane >= 1 && lane < 8) {
     const int nbk = V.nbr[blk * 16 + 8 + lane];
     lower_tri = nbk >= 0 && V.bntri[nbk] != 0;
   }
   if (__any_sync(0xffffffffu, lower_tri)) return false;
+  const int bucket = V.bkey[blk].w;
   float4* tw = reinterpret_cast<float4*>(V.tw + (size_t)blk * BV);
   for (int j = lane; j < BV / 2; j += 32) tw[j] = make_float4(0.f, 0.f, 0.f, 0.f);
   reinterpret_cast<uint4*>(V.code_eff + (size_t)blk * BV)[lane] = make_uint4(0, 0, 0, 0);
@@ -153,8 +160,8 @@ __device__ __forceinline__ bool gc_block(const Vol& V, int blk, uint32_t epoch, 
   __syncwarp();
   if (lane < 16) V.nbr[blk * 16 + lane] = -1;
   if (lane == 0) {
-    V.keys[key.w] = KEY_TOMB;
-    V.vals[key.w] = -1;
+    V.keys[bucket] = KEY_TOMB;
+    V.vals[bucket] = -1;
     V.bkey[blk] = make_int4(0, 0, 0, -1);
     V.bnear[blk] = 0;
     pool_push(V, V.blk_free, C_BLK_TOP, V.max_blocks, blk);
@@ -191,7 +198,8 @@ __device__ __forceinline__ void gc_blocks_finish(const Vol& V, int consumed) {
   __syncthreads();
 }
 
-// Block recycling, one warp per pool slot.  The last CTA finishes the pass.
+// Block recycling: a lane per pool slot tests it, the warp frees the candidates.  The last
+// CTA finishes the pass.
 __global__ void __launch_bounds__(256) k_gc_blocks(Vol V, int consumed) {
   grid_dependency_wait();
   if (blockIdx.x == 0 && threadIdx.x == 0) gc_lists_reset(V);
@@ -199,8 +207,17 @@ __global__ void __launch_bounds__(256) k_gc_blocks(Vol V, int consumed) {
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int hw = min(__ldcg(&V.ctl->c[C_BLK_BUMP]), V.max_blocks);
   const uint32_t epoch = (uint32_t)__ldcg(&V.ctl->c[C_EPOCH]);
+  const int lane = threadIdx.x & 31;
   int freed = 0;
-  for (int blk = warp; blk < hw; blk += nwarps) freed += gc_block(V, blk, epoch, consumed);
+  for (int base = warp * 32; base < hw; base += nwarps * 32) {
+    const int blk = base + lane;
+    unsigned m = __ballot_sync(0xffffffffu, blk < hw && gc_candidate(V, blk, epoch, consumed));
+    while (m) {
+      const int b = __ffs(m) - 1;
+      m &= m - 1;
+      freed += gc_free_block(V, base + b);
+    }
+  }
   gc_flush_blocks(V, freed);
   if (last_block(V, C_DONE7)) {
     gc_blocks_finish(V, consumed);

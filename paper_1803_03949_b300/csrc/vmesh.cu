@@ -257,7 +257,7 @@ vm_status enqueue_gc(vm_volume* v) {
   if (st) return st;
   const int consumed = v->advance_pending ? 1 : 0;
   return launch(v, K_GC_BLOCKS,
-                [&] { launch_dependent(k_gc_blocks, grid_for(v, 8), 256, v->cur, v->V, consumed); });
+                [&] { launch_dependent(k_gc_blocks, grid_for(v, 2), 256, v->cur, v->V, consumed); });
 }
 
 vm_status sync_status(vm_volume* v) {
