@@ -21,8 +21,8 @@ struct BatchFrames {
   int advance[MAX_SCENES];  // start a new mesh epoch for this scene (as k_alloc's argument)
 };
 
-// Batch control: last-CTA tickets of the batched kernels that finish in their last CTA, and
-// the mesh pass's block hand-out counter (reset by the fusion's last CTA).
+// Batch control: the last-CTA ticket of the block gc, and the mesh pass's block hand-out
+// counter (reset by the fusion's first CTA).
 enum BatchDone { BD_ALLOC = 0, BD_INTEGRATE, BD_MESH, BD_GC_VERTICES, BD_GC_BLOCKS, BD_COUNT };
 
 // pre[s] = sum of count(t) over scenes t < s, pre[n] = total (shared memory, whole CTA).
@@ -77,24 +77,22 @@ __global__ void __launch_bounds__(INTEG_THREADS) kb_integrate(const Vol* __restr
   __shared__ int pre[MAX_SCENES + 1];
   __shared__ uint32_t sframe[MAX_SCENES], sepoch[MAX_SCENES];
   if (threadIdx.x < nscenes) {
-    sframe[threadIdx.x] = (uint32_t)__ldcg(&vols[threadIdx.x].ctl->c[C_FRAME]);
+    sframe[threadIdx.x] = __ldcg(&vols[threadIdx.x].ctl->fp.frame);
     sepoch[threadIdx.x] = (uint32_t)__ldcg(&vols[threadIdx.x].ctl->c[C_EPOCH]);
   }
-  scene_prefix(nscenes, pre, [&](int t) { return min(__ldcg(&vols[t].ctl->c[C_N_TOUCHED]), vols[t].list_cap_touched); });
+  scene_prefix(nscenes, pre,
+               [&](int t) { return min(__ldcg(&vols[t].ctl->c[touched_count(sframe[t])]), vols[t].list_cap_touched); });
   const int total = pre[nscenes];
+  if (blockIdx.x == 0) {
+    for (int t = threadIdx.x; t < nscenes; t += blockDim.x) integrate_begin(vols[t], pre[t + 1] - pre[t], sframe[t]);
+    if (threadIdx.x == 0) bdone[BD_MESH] = 0;
+  }
   for (int g = blockIdx.x; g < total; g += gridDim.x) {
     const int s = scene_of(pre, nscenes, g);
     const Vol& V = vols[s];
     integrate_block<true>(V, V.ctl->fp, __ldcg(&V.touched[g - pre[s]]), sframe[s], sepoch[s]);
   }
   allow_dependent_launch();
-  if (last_block_at(bdone + BD_INTEGRATE)) {
-    for (int t = threadIdx.x; t < nscenes; t += blockDim.x) integrate_finish(vols[t], pre[t + 1] - pre[t]);
-    if (threadIdx.x == 0) {
-      bdone[BD_INTEGRATE] = 0;
-      bdone[BD_MESH] = 0;
-    }
-  }
 }
 
 // Mesh pass: every scene's update set, one block per CTA iteration.

@@ -74,7 +74,8 @@ __device__ int hash_insert(const Vol& V, uint64_t key, int bx, int by, int bz, u
 // index or -1, bucket}: the fusion kernel then needs no hash or key lookups of its own.
 __device__ __forceinline__ void touch_bucket(const Vol& V, int s, uint64_t key, int blk, uint32_t frame) {
   if (atomicExch(&V.stamp[s], frame) != frame)
-    list_push(V, V.touched, C_N_TOUCHED, V.list_cap_touched, make_int4((int)(uint32_t)key, (int)(key >> 32), blk, s));
+    list_push(V, V.touched, touched_count(frame), V.list_cap_touched,
+              make_int4((int)(uint32_t)key, (int)(key >> 32), blk, s));
 }
 
 __device__ __forceinline__ void smem_set_insert(unsigned long long* set, const Vol& V, uint64_t key, int bx, int by,
@@ -179,7 +180,7 @@ __device__ __forceinline__ void collect_pixel(const Vol& V, const FrameParams& f
 template <int PPT, int TW>
 __device__ __forceinline__ void alloc_tile(const Vol& V, const FrameParams& fp, int tx, int ty,
                                            unsigned long long* set) {
-  const uint32_t frame = (uint32_t)__ldcg(&V.ctl->c[C_FRAME]);
+  const uint32_t frame = fp.frame;
   for (int i = threadIdx.x; i < ALLOC_SET; i += blockDim.x) set[i] = KEY_EMPTY;
   const int u = tx * TW + (threadIdx.x & (TW - 1));
   const int v = ty * ALLOC_TILE_H + PPT * (threadIdx.x / TW);
@@ -259,7 +260,6 @@ __device__ __forceinline__ void resolve_block(const Vol& V, int blk, int4 key, u
   }
   if (t == 0) V.bepoch[blk] = epoch;
   if (sgn > 0 || nb < 0) return;
-  if (__ldcg(&V.ustamp[nb]) == epoch) return;
   if (atomicExch(&V.ustamp[nb], epoch) != epoch) list_push(V, V.update, C_N_UPDATE, V.list_cap_update, nb);
 }
 
@@ -334,32 +334,29 @@ __device__ __forceinline__ void integrate_block(const Vol& V, const FrameParams&
   if (threadIdx.x == 0) V.bnear[blk] = (uint8_t)(any != 0);
 }
 
-// After the last collected block of an integrate call (one thread): statistics, an empty
-// collected list, the next integrate call's number.
-__device__ __forceinline__ void integrate_finish(const Vol& V, int n) {
+// At the start of integrate call `frame` over n collected blocks (one thread; nothing in the
+// call reads what it writes): statistics, the next call's collected count emptied, the mesh
+// pass's block hand-out counter reset for the pass that follows.
+__device__ __forceinline__ void integrate_begin(const Vol& V, int n, uint32_t frame) {
   V.ctl->c[C_ST_FRAME_BLOCKS] = n;
   reinterpret_cast<unsigned*>(V.ctl->c)[C_ST_COLLECTED] += (unsigned)n;  // wraps modulo 2^32
-  V.ctl->c[C_N_TOUCHED] = 0;
-  V.ctl->c[C_FRAME] += 1;
-  V.ctl->c[C_MESH_NEXT] = 0;  // for the mesh pass that follows
+  V.ctl->c[touched_count(frame + 1)] = 0;
+  V.ctl->c[C_FRAME] = (int)(frame + 1);
+  V.ctl->c[C_MESH_NEXT] = 0;
 }
 
 // Every collected block, one per CTA iteration (FUSE = false: resolve only, for analytic
-// fills).  The last CTA empties the collected list and advances the integrate-call counter.
+// fills).  The call's number and parameters come from the control block (stored by the
+// collection).
 template <bool FUSE>
 __global__ void __launch_bounds__(INTEG_THREADS, INTEG_CTAS_PER_SM) k_integrate(Vol V, const FrameParams* __restrict__ fpp) {
   grid_dependency_wait();
-  const int n = min(__ldcg(&V.ctl->c[C_N_TOUCHED]), V.list_cap_touched);
-  const uint32_t frame = (uint32_t)__ldcg(&V.ctl->c[C_FRAME]);
+  const uint32_t frame = fpp->frame;
+  const int n = min(__ldcg(&V.ctl->c[touched_count(frame)]), V.list_cap_touched);
   const uint32_t epoch = (uint32_t)__ldcg(&V.ctl->c[C_EPOCH]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) integrate_begin(V, n, frame);
   for (int i = blockIdx.x; i < n; i += gridDim.x) integrate_block<FUSE>(V, *fpp, __ldcg(&V.touched[i]), frame, epoch);
   allow_dependent_launch();
-  if (last_block(V, C_DONE2)) {
-    if (threadIdx.x == 0) {
-      integrate_finish(V, n);
-      V.ctl->c[C_DONE2] = 0;
-    }
-  }
 }
 
 }  // namespace vmk

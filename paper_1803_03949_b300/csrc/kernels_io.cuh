@@ -173,8 +173,11 @@ __global__ void __launch_bounds__(256) k_export_blocks(Vol V, int* counter, int*
 }
 
 // Analytic fill, phase 1: insert the given keys as if collected by a frame.
-__global__ void __launch_bounds__(256) k_fill_insert(Vol V, const int* keys, int n, int advance_epoch) {
-  const uint32_t frame = (uint32_t)__ldcg(&V.ctl->c[C_FRAME]);
+__global__ void __launch_bounds__(256) k_fill_insert(Vol V, const int* keys, int n, int advance_epoch, uint32_t frame) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    V.ctl->fp.frame = frame;  // the resolve pass that follows reads the call's number there
+    alloc_begin(V, advance_epoch);
+  }
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     int x = keys[3 * j], y = keys[3 * j + 1], z = keys[3 * j + 2];
     if (abs(x) > KEY_LIMIT || abs(y) > KEY_LIMIT || abs(z) > KEY_LIMIT) {
@@ -185,15 +188,6 @@ __global__ void __launch_bounds__(256) k_fill_insert(Vol V, const int* keys, int
     int blk;
     int s = hash_insert(V, key, x, y, z, frame, blk);
     if (s >= 0) touch_bucket(V, s, key, blk, frame);
-  }
-  if (last_block(V, C_DONE0)) {
-    if (threadIdx.x == 0) {
-      if (advance_epoch) {
-        V.ctl->c[C_EPOCH] += 1;
-        V.ctl->c[C_N_UPDATE] = 0;
-      }
-      V.ctl->c[C_DONE0] = 0;
-    }
   }
 }
 

@@ -53,6 +53,8 @@ struct vm_volume {
   cudaStream_t cap_stream = nullptr;  // owned non-blocking stream for graph capture
   int num_sms = 148;
   bool advance_pending = false;
+  uint32_t frame = 1;  // number of the next integrate call (consecutive: the collected-count
+                       // counters alternate with its parity)
   std::vector<void*> allocs;
   size_t bytes_allocated = 0;  // device memory held through allocs
   // download scratch
@@ -471,8 +473,11 @@ vm_status vm_integrate_depth(vm_volume* v, const float* depth, const vm_intrinsi
   FrameParams fp;
   if (!make_frame(K, Twc, Tcw, depth, &fp)) return VM_ERR_INVALID_ARG;
   if (v->diff_on && (v->diff_frames >= v->diff_max || v->grad_next >= 0)) return VM_ERR_INVALID_ARG;
+  fp.frame = v->frame;
   vm_status st = enqueue_integrate(v, fp);
-  if (st || !v->diff_on) return st;
+  if (st) return st;
+  ++v->frame;
+  if (!v->diff_on) return st;
   (void)cudaGetLastError();
   k_diff_record<<<grid_for(v, INTEG_CTAS_PER_SM), INTEG_THREADS, 0, v->stream>>>(v->V, v->diff_frames);
   ++v->diff_frames;
@@ -502,6 +507,7 @@ vm_status vm_step(vm_volume* v, const float* depth, const vm_intrinsics* K, cons
   if (!v || (flags & ~(VM_FULL | VM_REFINE | VM_GC)) || v->diff_on) return VM_ERR_INVALID_ARG;
   FrameParams fp;
   if (!make_frame(K, Twc, Tcw, depth, &fp)) return VM_ERR_INVALID_ARG;
+  fp.frame = v->frame;
   auto body = [&]() -> vm_status {
     vm_status s = enqueue_integrate(v, fp);
     if (s) return s;
@@ -512,7 +518,11 @@ vm_status vm_step(vm_volume* v, const float* depth, const vm_intrinsics* K, cons
   };
   // A frame graph is captured with the epoch advancing at its start, i.e. for frames that
   // follow a mesh update; other frames run as plain launches.
-  if (!use_graph || !v->advance_pending) return body();
+  if (!use_graph || !v->advance_pending) {
+    const vm_status s = body();
+    if (!s) ++v->frame;
+    return s;
+  }
   if (!v->graph_exec || v->graph_flags != flags || v->graph_W != fp.W || v->graph_H != fp.H) {
     drop_graph(v);
     // Capture on an owned stream (the legacy NULL stream cannot be captured); the graph is
@@ -574,6 +584,7 @@ vm_status vm_step(vm_volume* v, const float* depth, const vm_intrinsics* K, cons
   }
   e = cudaGraphLaunch(v->graph_exec, v->stream);
   v->graph_pending = v->timing_mask && !v->graph_recs.empty();
+  if (e == cudaSuccess) ++v->frame;
   return cuda_status(e);
 }
 
@@ -913,12 +924,13 @@ vm_status vm_set_blocks(vm_volume* v, const int32_t* keys, int64_t n, const floa
   }
   if (ok) {
     const int adv = v->advance_pending ? 1 : 0;
-    k_fill_insert<<<grid_for(v, 2), 256, 0, v->stream>>>(v->V, (const int*)dk, (int)n, adv);
+    k_fill_insert<<<grid_for(v, 2), 256, 0, v->stream>>>(v->V, (const int*)dk, (int)n, adv, v->frame);
     k_integrate<false><<<grid_for(v, INTEG_CTAS_PER_SM), INTEG_THREADS, 0, v->stream>>>(v->V, &v->V.ctl->fp);
     k_fill_copy<<<grid_for(v, 4), 256, 0, v->stream>>>(v->V, (const int*)dk, (const float*)dt, (const float*)dw,
                                                        (int)n);
     ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(v->stream) == cudaSuccess;
     v->advance_pending = false;
+    ++v->frame;
   }
   cudaFree(dk);
   cudaFree(dt);
@@ -1331,6 +1343,7 @@ vm_status vm_batch_step(vm_batch* b, const float* const* depths, const vm_intrin
   for (int i = 0; i < b->n; ++i) {
     if (b->vols[i]->diff_on) return VM_ERR_INVALID_ARG;
     if (!make_frame(&K[i], T_wc + 16 * i, T_cw + 16 * i, depths[i], &bf.fp[i])) return VM_ERR_INVALID_ARG;
+    bf.fp[i].frame = b->vols[i]->frame;
     tx = std::max(tx, (bf.fp[i].W + ALLOC_TILE_W - 1) / ALLOC_TILE_W);
     ty = std::max(ty, (bf.fp[i].H + ALLOC_TILE_H - 1) / ALLOC_TILE_H);
   }
@@ -1405,7 +1418,10 @@ vm_status vm_batch_step(vm_batch* b, const float* const* depths, const vm_intrin
     st = cuda_status(e);
   }
   if (!st)
-    for (auto* v : b->vols) v->advance_pending = true;
+    for (auto* v : b->vols) {
+      v->advance_pending = true;
+      ++v->frame;
+    }
   return st;
 }
 

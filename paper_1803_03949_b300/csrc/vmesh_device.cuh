@@ -55,9 +55,9 @@ constexpr int CLINE = 32;
 enum Counter {
   C_STATUS = 0 * CLINE,
   C_STATUS_POOL = 1 * CLINE,  // which capacity set the status (PoolCode)
-  C_FRAME = 2 * CLINE,  // integrate calls so far + 1
+  C_FRAME = 2 * CLINE,  // integrate calls so far + 1 (the host numbers the calls; statistics)
   C_EPOCH = 3 * CLINE,  // mesh epoch, advanced by the first integrate after a mesh update
-  C_N_TOUCHED = 4 * CLINE,  // buckets collected by the current integrate call
+  C_N_TOUCHED = 4 * CLINE,  // buckets collected by an even-numbered integrate call (touched_count)
   C_N_UPDATE = 5 * CLINE,  // blocks in the update set
   C_N_DEAD = 6 * CLINE,  // zero-reference vertices awaiting gc
   C_N_DEADRUN = 7 * CLINE,  // released triangle runs awaiting gc
@@ -97,8 +97,13 @@ enum Counter {
   C_DONE6 = 44 * CLINE,
   C_DONE7 = 45 * CLINE,
   C_MESH_NEXT = 46 * CLINE,  // next update-set block a mesh pass hands out (beyond one per CTA)
-  C_COUNT = 47 * CLINE
+  C_N_TOUCHED1 = 47 * CLINE,  // buckets collected by an odd-numbered integrate call (touched_count)
+  C_COUNT = 48 * CLINE
 };
+
+// Count of the buckets integrate call `frame` collects.  Calls alternate between two counters,
+// so that a call can empty the next call's counter at its start while its own is read.
+__host__ __device__ constexpr int touched_count(uint32_t frame) { return (frame & 1u) ? C_N_TOUCHED1 : C_N_TOUCHED; }
 
 // Stack top of the free runs of L triangle slots (L = 1..5).
 __host__ __device__ constexpr int run_top(int L) { return C_RUN_TOP0 + (L - 1) * CLINE; }
@@ -110,6 +115,7 @@ struct FrameParams {
   float fx, fy, cx, cy;
   float Twc[12];  // rows of [R | t], camera -> world
   float Tcw[12];  // world -> camera
+  uint32_t frame;  // number of the integrate call (from 1, consecutive), set by the host
 };
 
 struct Ctl {
@@ -216,17 +222,23 @@ __device__ __forceinline__ void set_status(const Vol& V, int st, int pool = P_NO
   if (pool != P_NONE) atomicCAS(&V.ctl->c[C_STATUS_POOL], 0, pool);
 }
 __device__ __forceinline__ int list_pool_code(int c_count) {
-  return c_count == C_N_TOUCHED ? P_COLLECTED_LIST
+  return (c_count == C_N_TOUCHED || c_count == C_N_TOUCHED1) ? P_COLLECTED_LIST
                                 : (c_count == C_N_UPDATE ? P_UPDATE_LIST
                                                          : (c_count == C_N_DEADREC ? P_EDGE_RECORDS : P_DEAD_VERTEX_LIST));
 }
 
-// Hash lookup: bucket holding `key`, or -1.  Linear probing, at most hmask+1 probes.
-__device__ __forceinline__ int hash_find(const Vol& V, uint64_t key) {
+// Hash lookup: bucket holding `key`, or -1, and its value (loaded with the key, so a hit at
+// the first probe costs one round trip).  Linear probing, at most hmask+1 probes.
+__device__ __forceinline__ int hash_find(const Vol& V, uint64_t key, int& val) {
   uint32_t s = (uint32_t)mix64(key) & V.hmask;
+  val = -1;
   for (uint32_t p = 0; p <= V.hmask; ++p) {
-    uint64_t k = __ldcg(&V.keys[s]);
-    if (k == key) return (int)s;
+    const uint64_t k = __ldcg(&V.keys[s]);
+    const int v = __ldcg(&V.vals[s]);
+    if (k == key) {
+      val = v;
+      return (int)s;
+    }
     if (k == KEY_EMPTY) return -1;
     s = (s + 1) & V.hmask;
   }
@@ -235,8 +247,8 @@ __device__ __forceinline__ int hash_find(const Vol& V, uint64_t key) {
 
 // Block index of block key (x, y, z), or -1.
 __device__ __forceinline__ int find_block(const Vol& V, int x, int y, int z) {
-  int s = hash_find(V, pack_key(x, y, z));
-  return s < 0 ? -1 : __ldcg(&V.vals[s]);
+  int blk;
+  return hash_find(V, pack_key(x, y, z), blk) < 0 ? -1 : blk;
 }
 
 // Pop of `stride` consecutive ids per calling lane from a free stack of run starts backed
