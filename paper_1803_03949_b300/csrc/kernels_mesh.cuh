@@ -315,14 +315,7 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
   const uint32_t vm_w = ld_early_u32(V.vmask + ci0);
   const uint32_t prev_w = (mode & M_UPDATE) ? eff_w : ld_early_u32(V.code_prev + ci0);
   const int4 tb4 = ld_early_i4(V.tri_base + ci0);
-  int4 ev0, ev1, ev2;  // wide layout: the 12 edge slots of the 4 voxels
-  if constexpr (CE) {
-    ev0 = ld_early_i4(V.edge_rec + ci0);  // compact layout: the 4 voxels' edge records
-  } else {
-    ev0 = ld_early_i4(V.edge_vtx + ci0 * 3);
-    ev1 = ld_early_i4(V.edge_vtx + ci0 * 3 + 4);
-    ev2 = ld_early_i4(V.edge_vtx + ci0 * 3 + 8);
-  }
+  const int4 rec4 = CE ? ld_early_i4(V.edge_rec + ci0) : make_int4(-1, -1, -1, -1);  // compact: edge records
   const int4 key = V.bkey[blk];
   if (key.w < 0) return;  // freed since it joined the set (uniform over the CTA)
   if (threadIdx.x < 8) S.nb[threadIdx.x] = nbv;
@@ -355,19 +348,20 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
         qn[k] = __ldcg(reinterpret_cast<const float4*>(V.tw + (size_t)b * BV + (X & 7) + 8 * (Y & 7) + 64 * (Z & 7)));
     }
   }
+  // the vertex ids of the 4 voxels' edges that carry one (vertex-flag bits), issued with the
+  // neighbour halo loads; the other slots hold no vertex
   int ev[12];
-  if constexpr (CE) {
-    const int rv[4] = {ev0.x, ev0.y, ev0.z, ev0.w};
+  {
+    const int rv[4] = {rec4.x, rec4.y, rec4.z, rec4.w};
 #pragma unroll
-    for (int q = 0; q < 12; ++q) ev[q] = rv[q / 3] >= 0 ? __ldcg(&V.erec[(size_t)rv[q / 3] * 3 + q % 3]) : -1;
-    reinterpret_cast<int4*>(S.rec)[threadIdx.x] = ev0;  // read from stage d on
-  } else {
-    const int4 e4[3] = {ev0, ev1, ev2};
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      ev[4 * q] = e4[q].x, ev[4 * q + 1] = e4[q].y;
-      ev[4 * q + 2] = e4[q].z, ev[4 * q + 3] = e4[q].w;
+    for (int q = 0; q < 12; ++q) {
+      const bool live = (vm_w >> (8 * (q / 3) + q % 3)) & 1u;
+      if constexpr (CE)
+        ev[q] = live && rv[q / 3] >= 0 ? __ldcg(&V.erec[(size_t)rv[q / 3] * 3 + q % 3]) : -1;
+      else
+        ev[q] = live ? __ldcg(&V.edge_vtx[(ci0 + q / 3) * 3 + q % 3]) : -1;
     }
+    if (CE) reinterpret_cast<int4*>(S.rec)[threadIdx.x] = rec4;  // read from stage d on
   }
   const int cx = c0 & 7, cy = (c0 >> 3) & 7, cz = c0 >> 6;
   {
