@@ -88,6 +88,52 @@ def test_separate_refine_equals_fused_refine():
     np.testing.assert_array_equal(t1, t2)
 
 
+def test_mixed_entry_points_keep_parity():
+    """One 640x480 room volume (6 mm voxels) driven through every entry point in turn: graph
+    steps, plain steps, separate calls, integrate-only frames (two collection calls before a mesh pass),
+    repeated mesh passes without an integrate call between them (one of them full, more
+    blocks than the grid has CTAs), and steps after them.  The integrate calls' numbering and
+    the mesh pass's block hand-out counter must carry over every sequence; compared with the
+    oracle after each frame."""
+    import dataclasses
+
+    s = synth.room_scene(num_frames=7, seed=synth.SEED_BASE + 23)
+    vc = dataclasses.replace(s.volume, voxel_size=0.006, trunc=0.024)  # ~2k blocks after 5 frames
+    g, o = gpu_volume(vc), oracle.Volume.from_config(vc)
+    K = intrinsics(s)
+    Ko = (s.fx, s.fy, s.cx, s.cy)
+    plan = ["graph", "calls", "integrate", "integrate", "passes", "step", "graph"]
+    full_blocks = 0
+    for k, how in enumerate(plan):
+        d = s.depth(k)
+        Twc, Tcw = poses32(s.pose(k))
+        dt = torch.from_numpy(d).cuda()
+        o.integrate(d, Ko, Twc.astype(np.float64), Tcw.astype(np.float64))
+        if how in ("graph", "step"):
+            g.step(dt, K, Twc, Tcw, refine=True, gc=True, graph=(how == "graph"))
+            o.update_mesh(refine=True)
+            o.gc()
+        elif how == "integrate":
+            g.integrate(dt, K, Twc, Tcw)
+        else:
+            g.integrate(dt, K, Twc, Tcw)
+            g.update_mesh(refine=True)
+            o.update_mesh(refine=True)
+            if how == "passes":  # a full pass and a refine-only pass over the same sets
+                g.update_mesh(full=True, refine=True)
+                o.update_mesh(full=True, refine=True)
+                full_blocks = g.stats()["update_blocks"]
+                g.refine_mesh()
+                o.refine_mesh()
+            g.gc()
+            o.gc()
+        g.check()
+        compare_blocks(g.blocks(), o.blocks())
+        if how != "integrate":
+            compare_mesh(g.download(), o.mesh(), vc.voxel_size)
+    assert full_blocks > 1184  # that pass handed out blocks beyond one per CTA of its grid
+
+
 def test_ragged_image_with_invalid_pixels():
     """97 x 61 frames (not a multiple of the 64 x 16 tile or of 4), NaN / inf / negative /
     zero depths sprinkled in: such pixels are skipped identically on both sides."""
