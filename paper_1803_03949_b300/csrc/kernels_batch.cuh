@@ -97,9 +97,9 @@ __global__ void __launch_bounds__(INTEG_THREADS) kb_integrate(const Vol* __restr
 
 // Mesh pass: every scene's update set, one block per CTA iteration.
 template <bool CE>
-__global__ void __launch_bounds__(MESH_THREADS, MESH_CTAS_PER_SM) kb_mesh(const Vol* __restrict__ vols, int nscenes, int mode,
+__global__ void __launch_bounds__(MESH_THREADS, mesh_ctas_per_sm(true)) kb_mesh(const Vol* __restrict__ vols, int nscenes, int mode,
                                                            int* bdone) {
-  __shared__ MeshSmem S;
+  __shared__ MeshSmem<CE> S;
   __shared__ int pre[MAX_SCENES + 1];
   mesh_tables(S, vols[0].tri_table);
   grid_dependency_wait();

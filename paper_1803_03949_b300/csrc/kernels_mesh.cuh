@@ -56,7 +56,9 @@ __device__ __forceinline__ int owner_bits(int k) { return (int)((EDGE_OWNER_BITS
 __device__ __forceinline__ int packed_ntri(uint64_t w) { return (int)(w >> 60); }
 __device__ __forceinline__ int packed_edge(uint64_t w, int t, int j) { return (int)((w >> (4 * (3 * t + j))) & 15); }
 
-constexpr int MESH_CTAS_PER_SM = 8;  // bounded by registers (64) and shared memory (24 KB)
+// CTAs per SM, bounded by registers (64) and shared memory (23-25 KB).  Nine (56 registers,
+// possible with the default record's 23 KB) measured no faster.
+__host__ __device__ constexpr int mesh_ctas_per_sm(bool compact) { return compact ? 8 : 8; }
 constexpr int HALO_PAIRS = 244;      // 16-byte pairs of neighbour voxels in the halo (488 voxels)
 constexpr int MESH_TABLE_UINT4 = 192;  // 256 packed triangle words, 256 edge masks, 256 pair codes
 
@@ -74,6 +76,7 @@ __host__ __device__ inline void halo_pairs(uint16_t* out) {
   for (; i < 256; ++i) out[i] = 0;
 }
 
+template <bool CE>
 struct __align__(16) MeshSmem {
   float halo[HALO_N];  // d of the voxel, NaN where W = 0 or its block is absent
   uint64_t tri64[256];
@@ -97,7 +100,7 @@ struct __align__(16) MeshSmem {
   unsigned rmark[EDGE_WORDS];  // lmark without cmark: the refreshes
   int ccount[EDGE_WORDS];      // exclusive prefixes of cmark's and rmark's bits over the words
   int rcount[EDGE_WORDS];
-  alignas(16) int rec[BV];                 // the block's edge records (voxel -> record, -1 none)
+  alignas(16) int rec[CE ? BV : 4];        // compact layout: the block's edge records (voxel -> record, -1 none)
   int evid[EDGE_SLOTS];                    // vertex id per edge slot (own slots from stage a)
 };
 
@@ -166,8 +169,8 @@ __device__ __forceinline__ int atom_add_if(int* p, int v, bool on) {
 // Halo entry of a voxel (d, W): d, or NaN where W = 0.
 __device__ __forceinline__ float halo_value(float d, float w) { return w > 0.0f ? d : __int_as_float(0x7fc00000); }
 
-__device__ __forceinline__ float halo_at(const MeshSmem& S, int x, int y, int z) {
-  return S.halo[x + HALO * y + HALO * HALO * z];
+__device__ __forceinline__ float halo_at(const float* halo, int x, int y, int z) {
+  return halo[x + HALO * y + HALO * HALO * z];
 }
 
 // Vertex on the owned edge g -> g + e_a (Sec. V-C), from the halo (g at halo coordinates
@@ -175,11 +178,11 @@ __device__ __forceinline__ float halo_at(const MeshSmem& S, int x, int y, int z)
 // cubes extrapolate boundedly; position g l + t l e_a; normal = normalised gradient of
 // the owner cube's trilinear interpolant at the vertex, component b != a from the corners
 // g+e_b and g+e_a+e_b, 0 when either is unusable.
-__device__ __forceinline__ void edge_vertex(const MeshSmem& S, float l, int4 key, int x, int y, int z, int a,
+__device__ __forceinline__ void edge_vertex(const float* halo, float l, int4 key, int x, int y, int z, int a,
                                             float4* pos, float4* nrm) {
   const int ax = a == 0, ay = a == 1, az = a == 2;
-  const float d0 = halo_at(S, x, y, z);
-  const float d1 = halo_at(S, x + ax, y + ay, z + az);
+  const float d0 = halo_at(halo, x, y, z);
+  const float d1 = halo_at(halo, x + ax, y + ay, z + az);
   float t = d0 == d1 ? 0.5f : d0 / (d0 - d1);
   if (t < -1.0f) t = -1.0f;
   if (t > 2.0f) t = 2.0f;
@@ -195,8 +198,8 @@ __device__ __forceinline__ void edge_vertex(const MeshSmem& S, float l, int4 key
       continue;
     }
     const int bx = b == 0, by = b == 1, bz = b == 2;
-    const float q0 = halo_at(S, x + bx, y + by, z + bz);
-    const float q1 = halo_at(S, x + ax + bx, y + ay + by, z + az + bz);
+    const float q0 = halo_at(halo, x + bx, y + by, z + bz);
+    const float q1 = halo_at(halo, x + ax + bx, y + ay + by, z + az + bz);
     n[b] = (!isnan(q0) && !isnan(q1)) ? (1.0f - t) * (q0 - d0) + t * (q1 - d1) : 0.0f;
   }
   const float len = sqrtf((n[0] * n[0] + n[1] * n[1]) + n[2] * n[2]);
@@ -217,7 +220,7 @@ __device__ __forceinline__ void edge_vertex(const MeshSmem& S, float l, int4 key
 // and hands it to gc.
 // CE: the compact layout (edge records) rather than three vertex ids per voxel.
 template <bool CE>
-__device__ __forceinline__ int vertex_of_edge(const Vol& V, const MeshSmem& S, int x, int y, int z, int a,
+__device__ __forceinline__ int vertex_of_edge(const Vol& V, const MeshSmem<CE>& S, int x, int y, int z, int a,
                                               bool own, bool& claimed) {
   claimed = false;
   const int ob = S.nb[(x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2)];
@@ -302,7 +305,7 @@ struct MeshCounts {
 // One update-set block `blk` through stages a-e, the calling CTA of MESH_THREADS with its
 // shared staging area S (S.tri64 already holds the triangle table).
 template <bool CE>
-__device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, int mode, MeshCounts& cnt) {
+__device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem<CE>& S, int blk, int mode, MeshCounts& cnt) {
   const float eps = V.eps, l = V.l;
   // ---- a. this thread's 4 cubes (c0..c0+3, consecutive along x): their voxels, type,
   //         previous-type and vertex-flag bytes, run slots and edge slots (or edge records),
@@ -403,7 +406,7 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
       int raw = 0, small = 0;
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
-        const float hv = halo_at(S, x + corner_x(k), y + corner_y(k), z + corner_z(k));
+        const float hv = halo_at(S.halo, x + corner_x(k), y + corner_y(k), z + corner_z(k));
         valid &= !isnan(hv);
         raw |= (hv < 0.0f) << k;
         small |= (fabsf(hv) < eps) << k;
@@ -586,7 +589,7 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
     if (es >= 0) {  // a created or refreshed vertex
       const int o = es / 3;
       float4 p, nn;
-      edge_vertex(S, l, key, o % 9, (o / 9) % 9, o / 81, es - 3 * o, &p, &nn);
+      edge_vertex(S.halo, l, key, o % 9, (o / 9) % 9, o / 81, es - 3 * o, &p, &nn);
       V.vpos[vid] = p;
       V.vnrm[vid] = nn;
     }
@@ -650,7 +653,8 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem& S, int blk, i
 
 // The mesh tables into shared memory (whole CTA; the first barrier of the first block
 // orders the copy before any use).
-__device__ __forceinline__ void mesh_tables(MeshSmem& S, const uint4* tables) {
+template <bool CE>
+__device__ __forceinline__ void mesh_tables(MeshSmem<CE>& S, const uint4* tables) {
   for (int i = threadIdx.x; i < MESH_TABLE_UINT4; i += MESH_THREADS) {
     const uint4 w = tables[i];
     if (i < 128) reinterpret_cast<uint4*>(S.tri64)[i] = w;
@@ -684,8 +688,8 @@ __device__ __forceinline__ void mesh_begin(const Vol& V, int n) {
 // the positions and normals of the block's existing vertices), M_REFINE (Eqs. 3-5 with the
 // stored t_{i-1}).
 template <bool CE>
-__global__ void __launch_bounds__(MESH_THREADS, MESH_CTAS_PER_SM) k_mesh(Vol V, int mode) {
-  __shared__ MeshSmem S;
+__global__ void __launch_bounds__(MESH_THREADS, mesh_ctas_per_sm(CE)) k_mesh(Vol V, int mode) {
+  __shared__ MeshSmem<CE> S;
   mesh_tables(S, V.tri_table);
   grid_dependency_wait();
   const int n = min(__ldcg(&V.ctl->c[C_N_UPDATE]), V.list_cap_update);

@@ -237,7 +237,7 @@ vm_status enqueue_mesh_pass(vm_volume* v, int mode, bool after_integrate) {
   if (!after_integrate && cudaMemsetAsync(&v->V.ctl->c[C_MESH_NEXT], 0, sizeof(int), v->cur) != cudaSuccess)
     return VM_ERR_CUDA;
   return launch(v, K_MESH, [&] {
-    launch_dependent(ce ? k_mesh<true> : k_mesh<false>, grid_for(v, MESH_CTAS_PER_SM), MESH_THREADS, v->cur, v->V,
+    launch_dependent(ce ? k_mesh<true> : k_mesh<false>, grid_for(v, mesh_ctas_per_sm(ce)), MESH_THREADS, v->cur, v->V,
                      mode);
   });
 }
