@@ -23,7 +23,7 @@ struct BatchFrames {
 
 // Batch control: the last-CTA ticket of the block gc, and the mesh pass's block hand-out
 // counter (reset by the fusion's first CTA).
-enum BatchDone { BD_ALLOC = 0, BD_INTEGRATE, BD_MESH, BD_GC_VERTICES, BD_GC_BLOCKS, BD_COUNT };
+enum BatchDone { BD_MESH = 0, BD_GC_BLOCKS, BD_COUNT };
 
 // pre[s] = sum of count(t) over scenes t < s, pre[n] = total (shared memory, whole CTA).
 template <typename F>
@@ -57,7 +57,7 @@ __device__ __forceinline__ int scene_of(const int* pre, int n, int g) {
 // its scene's image does nothing; each scene's first CTA starts its epoch.
 template <int PPT>
 __global__ void __launch_bounds__(ALLOC_TILE_W * ALLOC_TILE_H / PPT)
-    kb_alloc(const Vol* __restrict__ vols, int nscenes, const __grid_constant__ BatchFrames bf, int* bdone) {
+    kb_alloc(const Vol* __restrict__ vols, int nscenes, const __grid_constant__ BatchFrames bf) {
   __shared__ unsigned long long set[ALLOC_SET];
   const int s = blockIdx.z;
   const Vol& V = vols[s];
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(MESH_THREADS, mesh_ctas_per_sm(true)) kb_mesh(
 // Zero-reference vertices and released runs of every scene, in chunks of 32 list entries
 // (one warp per chunk, so the lanes of a warp share a scene).
 template <bool CE>
-__global__ void __launch_bounds__(256) kb_gc_vertices(const Vol* __restrict__ vols, int nscenes, int* bdone) {
+__global__ void __launch_bounds__(256) kb_gc_vertices(const Vol* __restrict__ vols, int nscenes) {
   grid_dependency_wait();
   __shared__ int pre_d[MAX_SCENES + 1], pre_r[MAX_SCENES + 1], pre_e[MAX_SCENES + 1];
   scene_prefix(nscenes, pre_d, [&](int t) { return (min(__ldcg(&vols[t].ctl->c[C_N_DEAD]), vols[t].list_cap_dead) + 31) >> 5; });
@@ -170,8 +170,8 @@ __global__ void __launch_bounds__(256) kb_gc_vertices(const Vol* __restrict__ vo
 }
 
 // Block recycling of every scene: a lane per pool slot in use tests it, the warp frees the
-// candidates.  The last CTA finishes the
-// scenes one after another (a hash rebuild takes the whole CTA).
+// candidates.  The last CTA finishes the scenes one after another (a hash rebuild takes the
+// whole CTA).
 __global__ void __launch_bounds__(256) kb_gc_blocks(const Vol* __restrict__ vols, int nscenes, int consumed,
                                                     int* bdone) {
   grid_dependency_wait();

@@ -230,7 +230,7 @@ vm_status enqueue_list_all(vm_volume* v) {
   return launch(v, K_LIST_ALL, [&] { k_list_all<<<grid_for(v, 4), 256, 0, v->cur>>>(v->V); });
 }
 
-// after_integrate: the pass directly follows an integrate call, whose last CTA resets the
+// after_integrate: the pass directly follows an integrate call, whose first CTA resets the
 // pass's block hand-out counter; otherwise it is reset here.
 vm_status enqueue_mesh_pass(vm_volume* v, int mode, bool after_integrate) {
   const bool ce = (v->p.flags & VM_PARAM_COMPACT_EDGES) != 0;
@@ -1228,9 +1228,9 @@ vm_status batch_enqueue(vm_batch* b, cudaStream_t st, const int* sc, int flags, 
   const dim3 grid(tx, ty, b->n);
   const int threads = ALLOC_TILE_W * ALLOC_TILE_H / sc[0];
   switch (sc[0]) {
-    case 1: kb_alloc<1><<<grid, threads, 0, st>>>(b->d_vols, b->n, *b->frames, b->d_done); break;
-    case 4: kb_alloc<4><<<grid, threads, 0, st>>>(b->d_vols, b->n, *b->frames, b->d_done); break;
-    default: kb_alloc<2><<<grid, threads, 0, st>>>(b->d_vols, b->n, *b->frames, b->d_done); break;
+    case 1: kb_alloc<1><<<grid, threads, 0, st>>>(b->d_vols, b->n, *b->frames); break;
+    case 4: kb_alloc<4><<<grid, threads, 0, st>>>(b->d_vols, b->n, *b->frames); break;
+    default: kb_alloc<2><<<grid, threads, 0, st>>>(b->d_vols, b->n, *b->frames); break;
   }
   if (rec) cudaEventRecord(rec->ev[1], st);
   launch_dependent(kb_integrate, b->num_sms * sc[1], INTEG_THREADS, st, (const Vol*)b->d_vols, b->n, b->d_done);
@@ -1240,7 +1240,7 @@ vm_status batch_enqueue(vm_batch* b, cudaStream_t st, const int* sc, int flags, 
   if (rec) cudaEventRecord(rec->ev[3], st);
   if (flags & VM_GC) {
     launch_dependent(b->compact ? kb_gc_vertices<true> : kb_gc_vertices<false>, b->num_sms * sc[3], 256, st,
-                     (const Vol*)b->d_vols, b->n, b->d_done);
+                     (const Vol*)b->d_vols, b->n);
     if (rec) cudaEventRecord(rec->ev[4], st);
     launch_dependent(kb_gc_blocks, b->num_sms * sc[4], 256, st, (const Vol*)b->d_vols, b->n, 1, b->d_done);
   } else if (rec) {
@@ -1403,8 +1403,7 @@ vm_status vm_batch_step(vm_batch* b, const float* const* depths, const vm_intrin
     }
     const Vol* dv = b->d_vols;
     int n = b->n;
-    int* dd = b->d_done;
-    void* args[4] = {&dv, &n, b->frames, &dd};
+    void* args[3] = {&dv, &n, b->frames};
     cudaKernelNodeParams kp = {};
     kp.func = batch_alloc_kernel(b->sched[0]);
     kp.gridDim = dim3(tx, ty, b->n);
