@@ -8,8 +8,9 @@
 //   a. stage the 10^3 voxel halo (the block, local 0..7, plus the +x/+y/+z neighbours'
 //      voxels at local 8..9) in shared memory as d, NaN where W = 0, with 16-byte loads;
 //      every cube type, and every vertex an edge of these cubes can need, is computed from
-//      it.  The block's own cube bytes, run slots and edge slots are loaded first, so they
-//      travel with the halo; the edge slots (vertex ids) go to shared memory;
+//      it.  The block's own cube bytes and run slots are loaded first, the edge slots that
+//      carry a vertex (its vertex-flag bytes tell which) with the neighbours' halo voxels;
+//      the vertex ids go to shared memory;
 //   b. per cube: type (and refinement), previous type; the block's edges that carry a
 //      vertex are marked for a refresh; cubes whose effective type changes go to a shared
 //      list and take a rank among the block's new runs of their length; the edges their new
@@ -308,8 +309,9 @@ template <bool CE>
 __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem<CE>& S, int blk, int mode, MeshCounts& cnt) {
   const float eps = V.eps, l = V.l;
   // ---- a. this thread's 4 cubes (c0..c0+3, consecutive along x): their voxels, type,
-  //         previous-type and vertex-flag bytes, run slots and edge slots (or edge records),
-  //         all loaded before anything waits; the addresses are valid for a freed block too
+  //         previous-type and vertex-flag bytes, run slots (and, compact layout, edge
+  //         records), all loaded before anything waits; the addresses are valid for a freed
+  //         block too
   const int c0 = 4 * threadIdx.x;  // MESH_THREADS * 4 == BV
   const size_t ci0 = (size_t)blk * BV + c0;
   const int nbv = (threadIdx.x >= 1 && threadIdx.x < 8) ? ld_early_s32(&V.nbr[blk * 16 + threadIdx.x]) : blk;
