@@ -87,10 +87,17 @@ __global__ void __launch_bounds__(INTEG_THREADS) kb_integrate(const Vol* __restr
     for (int t = threadIdx.x; t < nscenes; t += blockDim.x) integrate_begin(vols[t], pre[t + 1] - pre[t], sframe[t]);
     if (threadIdx.x == 0) bdone[BD_MESH] = 0;
   }
-  for (int g = blockIdx.x; g < total; g += gridDim.x) {
+  __shared__ IntegNear N;
+  if (threadIdx.x < INTEG_RING) {
+    N.any[threadIdx.x] = 0;
+    N.done[threadIdx.x] = 0;
+  }
+  __syncthreads();
+  for (int g = blockIdx.x, it = 0; g < total; g += gridDim.x, ++it) {
     const int s = scene_of(pre, nscenes, g);
     const Vol& V = vols[s];
-    integrate_block<true>(V, V.ctl->fp, __ldcg(&V.touched[g - pre[s]]), sframe[s], sepoch[s]);
+    integrate_block<true>(V, V.ctl->fp, __ldcg(&V.touched[g - pre[s]]), sframe[s], sepoch[s], it, N);
+    if ((it & (INTEG_RING - 1)) == INTEG_RING - 1) __syncthreads();
   }
   allow_dependent_launch();
 }

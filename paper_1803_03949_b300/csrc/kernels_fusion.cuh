@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(Vol V, const __grid_con
   allow_dependent_launch();
 }
 
-// Resolve one collected bucket (threads 0..15 of the calling CTA):
+// Resolve one collected bucket (lanes t = 0..15 of the resolving warp):
 //   - the block and its existing neighbours at offsets {0,-1}^3 join the update set once
 //     per epoch (their cubes read corners in the collected block);
 //   - a block created by this integrate call links itself into the neighbour table (and
@@ -238,8 +238,7 @@ __global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(Vol V, const __grid_con
 // Old blocks read their lower neighbours from the table.  A new block's table entries may
 // race with an old neighbour reading them, but new blocks are collected themselves, so no
 // update-set member is lost.
-__device__ __forceinline__ void resolve_block(const Vol& V, int blk, int4 key, uint32_t frame, uint32_t epoch) {
-  const int t = threadIdx.x;
+__device__ __forceinline__ void resolve_block(const Vol& V, int blk, int4 key, uint32_t frame, uint32_t epoch, int t) {
   if (t >= 16) return;
   const int o = t & 7;
   const int sgn = t < 8 ? -1 : 1;  // threads 0..7: lower neighbours (and self), 8..15: upper
@@ -286,23 +285,35 @@ __device__ __forceinline__ bool project_voxel(const FrameParams& fp, float mu, f
 constexpr int INTEG_THREADS = 128;  // 4 voxels per thread, one block per CTA iteration
 constexpr int INTEG_CTAS_PER_SM = 12;  // ~1.8k blocks (a 640 x 480 frame) in one wave
 
-// One collected block (entry `t` of the collected list), the calling CTA of INTEG_THREADS:
-// resolve it (update set, neighbour table), then (FUSE) fuse the frame into its 512 voxels.
-// Voxels stream as float2 (d, W) pairs, 32 bytes per thread; depth is gathered through the
-// read-only path.  Also records whether any voxel of the block has W > 0 and d < mu (used
-// by gc).
+// Per-CTA state of the fusion loop: the near flags of the blocks in flight, OR-ed by their
+// warps (a ring; the loop synchronises the CTA once per ring length, so no slot is reused
+// while a warp still works on its block).
+constexpr int INTEG_RING = 8;
+struct IntegNear {
+  unsigned any[INTEG_RING];
+  int done[INTEG_RING];
+};
+
+// One collected block (entry `t` of the collected list, the calling CTA's `it`-th), the CTA of
+// INTEG_THREADS: resolve it (update set, neighbour table) in one warp, chosen in turn so that
+// the resolutions' round-trip chains of successive blocks run in different warps, then (FUSE)
+// fuse the frame into its 512 voxels.  Voxels stream as float2 (d, W) pairs, 32 bytes per
+// thread; depth is gathered through the read-only path.  Also records whether any voxel of
+// the block has W > 0 and d < mu (used by gc): the block's last warp to finish writes it.
+// No barrier: each warp moves on to the CTA's next block as soon as its own part is done.
 template <bool FUSE>
 __device__ __forceinline__ void integrate_block(const Vol& V, const FrameParams& fp, int4 t, uint32_t frame,
-                                                uint32_t epoch) {
+                                                uint32_t epoch, int it, IntegNear& N) {
   const float mu = V.mu, l = V.l, wmax = V.wmax;
   const int v0 = threadIdx.x * 4;
   const int lx = v0 & 7, ly = (v0 >> 3) & 7, lz = v0 >> 6;
+  const int lane = threadIdx.x & 31;
   const int blk = t.z >= 0 ? t.z : __ldcg(&V.vals[t.w]);
   if (blk < 0) return;  // uniform over the CTA
   const uint64_t kk = ((uint64_t)(uint32_t)t.y << 32) | (uint32_t)t.x;
   const int4 key = make_int4((int)((kk >> 42) & 0x1FFFFF) - KEY_BIAS, (int)((kk >> 21) & 0x1FFFFF) - KEY_BIAS,
                              (int)(kk & 0x1FFFFF) - KEY_BIAS, t.w);
-  resolve_block(V, blk, key, frame, epoch);
+  if ((threadIdx.x >> 5) == (it & (INTEG_THREADS / 32 - 1))) resolve_block(V, blk, key, frame, epoch, lane);
   if (!FUSE) return;
   float4* p = reinterpret_cast<float4*>(V.tw + (size_t)blk * BV + v0);
   float4 q0 = __ldcg(p), q1 = __ldcg(p + 1);
@@ -330,8 +341,33 @@ __device__ __forceinline__ void integrate_block(const Vol& V, const FrameParams&
   bool near = false;
 #pragma unroll
   for (int j = 0; j < 4; ++j) near |= (ww[j] > 0.0f && dd[j] < mu);
-  const int any = __syncthreads_or(near);
-  if (threadIdx.x == 0) V.bnear[blk] = (uint8_t)(any != 0);
+  const bool wnear = __any_sync(0xffffffffu, near);
+  if (lane == 0) {
+    const int slot = it & (INTEG_RING - 1);
+    if (wnear) atomicOr(&N.any[slot], 1u);
+    __threadfence_block();
+    if (atomicAdd(&N.done[slot], 1) == INTEG_THREADS / 32 - 1) {  // the block's last warp
+      V.bnear[blk] = (uint8_t)(atomicOr(&N.any[slot], 0u) != 0);
+      N.any[slot] = 0;
+      N.done[slot] = 0;
+    }
+  }
+}
+
+// The calling CTA's share of the collected list (entries first, first + stride, ...).
+template <bool FUSE>
+__device__ __forceinline__ void integrate_share(const Vol& V, const FrameParams& fp, int first, int stride, int n,
+                                                uint32_t frame, uint32_t epoch) {
+  __shared__ IntegNear N;
+  if (threadIdx.x < INTEG_RING) {
+    N.any[threadIdx.x] = 0;
+    N.done[threadIdx.x] = 0;
+  }
+  __syncthreads();
+  for (int i = first, it = 0; i < n; i += stride, ++it) {
+    integrate_block<FUSE>(V, fp, __ldcg(&V.touched[i]), frame, epoch, it, N);
+    if ((it & (INTEG_RING - 1)) == INTEG_RING - 1) __syncthreads();
+  }
 }
 
 // At the start of integrate call `frame` over n collected blocks (one thread; nothing in the
@@ -355,7 +391,7 @@ __global__ void __launch_bounds__(INTEG_THREADS, INTEG_CTAS_PER_SM) k_integrate(
   const int n = min(__ldcg(&V.ctl->c[touched_count(frame)]), V.list_cap_touched);
   const uint32_t epoch = (uint32_t)__ldcg(&V.ctl->c[C_EPOCH]);
   if (blockIdx.x == 0 && threadIdx.x == 0) integrate_begin(V, n, frame);
-  for (int i = blockIdx.x; i < n; i += gridDim.x) integrate_block<FUSE>(V, *fpp, __ldcg(&V.touched[i]), frame, epoch);
+  integrate_share<FUSE>(V, *fpp, blockIdx.x, gridDim.x, n, frame, epoch);
   allow_dependent_launch();
 }
 
