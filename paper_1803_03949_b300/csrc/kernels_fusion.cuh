@@ -107,11 +107,11 @@ __device__ __forceinline__ void dda_axis(float a, float b, int& c, int& rem, int
   const float dir = b - a;
   if (dir > 0.0f) {
     step = 1;
-    tdel = 1.0f / dir;
+    tdel = __frcp_rn(dir);  // the correctly rounded 1 / dir
     tmax = (((float)c + 1.0f) - a) * tdel;
   } else if (dir < 0.0f) {
     step = -1;
-    tdel = 1.0f / (-dir);
+    tdel = __frcp_rn(-dir);
     tmax = (a - (float)c) * tdel;
   } else {
     step = 0;
@@ -127,14 +127,15 @@ __device__ __forceinline__ void collect_pixel(const Vol& V, const FrameParams& f
                                               unsigned long long* set, uint32_t frame, uint64_t& last) {
   if (!(D > 0.0f) || !isfinite(D)) return;
   // divisions as products with reciprocals (of fx, fy, the block side)
-  const float xn = ((float)u - fp.cx) * (1.0f / fp.fx);
-  const float yn = ((float)v - fp.cy) * (1.0f / fp.fy);
+  // (__frcp_rn: the correctly rounded reciprocal, the value of 1.0f / x in IEEE arithmetic)
+  const float xn = ((float)u - fp.cx) * __frcp_rn(fp.fx);
+  const float yn = ((float)v - fp.cy) * __frcp_rn(fp.fy);
   float z0 = D - V.mu;
   if (z0 < Z_NEAR) z0 = Z_NEAR;
   const float z1 = D + V.mu;
   const float pa0 = xn * z0, pa1 = yn * z0, pa2 = z0;
   const float pb0 = xn * z1, pb1 = yn * z1, pb2 = z1;
-  const float ibs = 1.0f / (V.l * (float)BS);
+  const float ibs = __frcp_rn(V.l * (float)BS);
   float A[3], B[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
