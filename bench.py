@@ -580,10 +580,11 @@ def run_vmesh(args, rank, world, local):
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(args.steps)]
         s0 = vol.stats()
-        # hold the stream while the host enqueues the frames (about 125 us of GPU time per
+        # hold the stream while the host enqueues the frames (about 0.5 ms of GPU time per
         # frame, outside every frame's event window), so that no window waits on the host: on
-        # a shared host, enqueue jitter would otherwise enter the timing
-        torch.cuda._sleep(int(min(n - args.warmup, 2000) * 250000))
+        # a shared host, enqueue jitter (and the clock sampler's driver queries) would
+        # otherwise enter the timing
+        torch.cuda._sleep(int(min(n - args.warmup, 2000) * 1000000))
         for i, f in enumerate(range(args.warmup, n)):
             flush.fill_(f)
             evs[i][0].record(stream)
