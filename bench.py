@@ -576,7 +576,6 @@ def run_vmesh(args, rank, world, local):
         a camera stream would run): per frame an L2 flush, then a CUDA-event pair around the
         frame alone.  Returns per-frame ms and the blocks collected / meshed over the run."""
         res_host = torch.empty(2, dtype=torch.int32).pin_memory()
-        dev_buf = torch.empty((H, W), dtype=torch.float32, device="cuda")
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(args.steps)]
         s0 = vol.stats()
@@ -589,8 +588,9 @@ def run_vmesh(args, rank, world, local):
             flush.fill_(f)
             evs[i][0].record(stream)
             if e2e:
-                dev_buf.copy_(depth_host[f], non_blocking=True)
-                vol.step(dev_buf, K, *poses[f], refine=True, gc=True, graph=graph)
+                # the frame from pinned host memory: the collection kernel reads it across the
+                # host link (4 W H bytes) and keeps the device copy the later kernels read
+                vol.step(depth_host[f], K, *poses[f], refine=True, gc=True, graph=graph)
                 vol.mesh_size_async(res_host)
             else:
                 vol.step(depth_dev[f], K, *poses[f], refine=True, gc=True, graph=graph)

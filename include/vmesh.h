@@ -142,14 +142,18 @@ vm_status vm_destroy_volume(vm_volume* vol);
 /* Change the stream later calls enqueue on. */
 vm_status vm_set_stream(vm_volume* vol, void* cuda_stream);
 
-/* Sec. V-A.  depth_dev: device pointer to height x width float32, row-major, 0 or
- * non-finite = invalid.  Collects every block crossed by the segment of camera depths
+/* Sec. V-A.  depth: height x width float32, row-major, 0 or non-finite = invalid, in device
+ * memory or in pinned (page-locked, device-mapped) host memory; the latter is read across
+ * the host link by the collection kernel, which keeps a device copy for the fusion (the
+ * frame's transfer overlaps the collection); the caller keeps it unchanged until the call's
+ * work has run.  Pageable host memory: VM_ERR_INVALID_ARG.  Collects every block crossed by
+ * the segment of camera depths
  * [max(D - mu, 0.05), D + mu] on each valid pixel's ray (Eq. 1), allocates the new ones,
  * then fuses the frame into every voxel of the collected blocks (Eq. 2): nearest pixel
  * floor(u + 0.5), sdf = D - z_c, skip when sdf < -mu, d <- (d W + min(sdf, mu)) / (W + 1),
  * W <- min(W + 1, w_max).  Blocks collected since the last vm_update_mesh accumulate
  * into the next update set. */
-vm_status vm_integrate_depth(vm_volume* vol, const float* depth_dev, const vm_intrinsics* intr,
+vm_status vm_integrate_depth(vm_volume* vol, const float* depth, const vm_intrinsics* intr,
                              const float T_wc[16], const float T_cw[16]);
 
 /* Secs. V-B..V-D.  Recomputes the cube types of the update set (blocks collected since
@@ -175,10 +179,10 @@ vm_status vm_refine_mesh(vm_volume* vol, int full);
  * triangles were already recycled by the mesh passes. */
 vm_status vm_gc(vm_volume* vol);
 
-/* One frame: integrate_depth, then update_mesh(flags & (VM_FULL | VM_REFINE)), then gc
- * when flags has VM_GC.  With use_graph != 0 the device work after the first call is
+/* One frame: integrate_depth (depth as there: device or pinned host memory), then
+ * update_mesh(flags & (VM_FULL | VM_REFINE)), then gc when flags has VM_GC.  With use_graph != 0 the device work after the first call is
  * replayed from a CUDA graph captured on that first call with the same flags. */
-vm_status vm_step(vm_volume* vol, const float* depth_dev, const vm_intrinsics* intr, const float T_wc[16],
+vm_status vm_step(vm_volume* vol, const float* depth, const vm_intrinsics* intr, const float T_wc[16],
                   const float T_cw[16], int flags, int use_graph);
 
 /* Synchronises; counts of the vertices with a positive reference count and of the live

@@ -185,10 +185,17 @@ __device__ __forceinline__ void alloc_tile(const Vol& V, const FrameParams& fp, 
   for (int i = threadIdx.x; i < ALLOC_SET; i += blockDim.x) set[i] = KEY_EMPTY;
   const int u = tx * TW + (threadIdx.x & (TW - 1));
   const int v = ty * ALLOC_TILE_H + PPT * (threadIdx.x / TW);
+  // the depth pixels: from device memory, or from pinned host memory across the host link (then
+  // kept in the device copy the later kernels read)
   float D[PPT];
 #pragma unroll
-  for (int r = 0; r < PPT; ++r) D[r] = (u < fp.W && v + r < fp.H) ? __ldg(fp.depth + (size_t)(v + r) * fp.W + u) : 0.0f;
+  for (int r = 0; r < PPT; ++r) D[r] = (u < fp.W && v + r < fp.H) ? fp.depth_in[(size_t)(v + r) * fp.W + u] : 0.0f;
   __syncthreads();
+  if (fp.depth_copy) {
+#pragma unroll
+    for (int r = 0; r < PPT; ++r)
+      if (u < fp.W && v + r < fp.H) fp.depth_copy[(size_t)(v + r) * fp.W + u] = D[r];
+  }
   uint64_t last = KEY_EMPTY;
 #pragma unroll
   for (int r = 0; r < PPT; ++r)

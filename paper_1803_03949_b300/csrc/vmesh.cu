@@ -57,6 +57,8 @@ struct vm_volume {
                        // counters alternate with its parity)
   std::vector<void*> allocs;
   size_t bytes_allocated = 0;  // device memory held through allocs
+  float* depth_buf = nullptr;  // device copy of a depth frame passed in pinned host memory
+  size_t depth_cap = 0;        // its capacity in floats
   // download scratch
   int* cta_counts = nullptr;
   int* scan_total = nullptr;
@@ -175,6 +177,8 @@ bool make_frame(const vm_intrinsics* K, const float* Twc, const float* Tcw, cons
   const double sy = std::fmax(std::fabs((double)K->cy), std::fabs(K->height - 1 - (double)K->cy)) / K->fy;
   if (!(sx <= 64.0) || !(sy <= 64.0)) return false;
   fp->depth = depth;
+  fp->depth_in = depth;
+  fp->depth_copy = nullptr;
   fp->W = K->width;
   fp->H = K->height;
   fp->fx = K->fx;
@@ -189,6 +193,39 @@ bool make_frame(const vm_intrinsics* K, const float* Twc, const float* Tcw, cons
 }
 
 int grid_for(vm_volume* v, int per_sm) { return v->num_sms * per_sm; }
+
+// A depth frame in device memory is read where it is.  One in pinned host memory (mapped into
+// the device's address space) is read by the collection kernel across the host link, and that
+// kernel keeps a device copy for the kernels after it: the frame's transfer overlaps the
+// collection instead of preceding it.  Pageable host memory is refused.
+vm_status prepare_depth(vm_volume* v, FrameParams* fp) {
+  cudaPointerAttributes a = {};
+  if (cudaPointerGetAttributes(&a, fp->depth_in) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return VM_ERR_INVALID_ARG;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return VM_OK;
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return VM_ERR_INVALID_ARG;
+  const size_t n = (size_t)fp->W * fp->H;
+  if (n > v->depth_cap) {
+    if (v->depth_buf) {  // frames already enqueued may still read the old copy
+      if (cudaStreamSynchronize(v->stream) != cudaSuccess) return VM_ERR_CUDA;
+      cudaFree(v->depth_buf);
+      v->depth_buf = nullptr;
+      v->depth_cap = 0;
+    }
+    if (cudaMalloc(&v->depth_buf, n * sizeof(float)) != cudaSuccess) {
+      (void)cudaGetLastError();
+      v->depth_buf = nullptr;
+      return VM_ERR_OOM;
+    }
+    v->depth_cap = n;
+  }
+  fp->depth_in = static_cast<const float*>(a.devicePointer);
+  fp->depth_copy = v->depth_buf;
+  fp->depth = v->depth_buf;
+  return VM_OK;
+}
 
 // Launch with programmatic stream serialization: the kernel may be scheduled while the
 // previous kernel in the stream drains; it waits for that kernel's results in-kernel.
@@ -315,6 +352,9 @@ void free_all(vm_volume* v) {
   for (auto e : v->event_pool) cudaEventDestroy(e);
   for (void* p : v->allocs) cudaFree(p);
   v->allocs.clear();
+  if (v->depth_buf) cudaFree(v->depth_buf);
+  v->depth_buf = nullptr;
+  v->depth_cap = 0;
   for (void* p : v->diff_allocs) cudaFree(p);
   v->diff_allocs.clear();
   if (v->cap_stream) cudaStreamDestroy(v->cap_stream);
@@ -474,7 +514,9 @@ vm_status vm_integrate_depth(vm_volume* v, const float* depth, const vm_intrinsi
   if (!make_frame(K, Twc, Tcw, depth, &fp)) return VM_ERR_INVALID_ARG;
   if (v->diff_on && (v->diff_frames >= v->diff_max || v->grad_next >= 0)) return VM_ERR_INVALID_ARG;
   fp.frame = v->frame;
-  vm_status st = enqueue_integrate(v, fp);
+  vm_status st = prepare_depth(v, &fp);
+  if (st) return st;
+  st = enqueue_integrate(v, fp);
   if (st) return st;
   ++v->frame;
   if (!v->diff_on) return st;
@@ -508,6 +550,7 @@ vm_status vm_step(vm_volume* v, const float* depth, const vm_intrinsics* K, cons
   FrameParams fp;
   if (!make_frame(K, Twc, Tcw, depth, &fp)) return VM_ERR_INVALID_ARG;
   fp.frame = v->frame;
+  if (const vm_status ps = prepare_depth(v, &fp)) return ps;
   auto body = [&]() -> vm_status {
     vm_status s = enqueue_integrate(v, fp);
     if (s) return s;

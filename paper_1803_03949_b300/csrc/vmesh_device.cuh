@@ -110,7 +110,9 @@ __host__ __device__ constexpr int run_top(int L) { return C_RUN_TOP0 + (L - 1) *
 
 
 struct FrameParams {
-  const float* depth;
+  const float* depth;     // the frame's depth in device memory, read after the collection
+  const float* depth_in;  // what the collection reads: depth itself, or mapped pinned host memory
+  float* depth_copy;      // null, or where the collection copies depth_in (then depth == depth_copy)
   int W, H;
   float fx, fy, cx, cy;
   float Twc[12];  // rows of [R | t], camera -> world

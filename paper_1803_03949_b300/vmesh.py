@@ -194,7 +194,8 @@ class Volume:
 
     # --------------------------------------------------------------- per-frame path
     def integrate(self, depth, intr: Intrinsics, T_wc, T_cw):
-        """depth: CUDA float32 tensor (H, W); poses 4x4 (host, rounded to float32)."""
+        """depth: float32 tensor (H, W), CUDA or pinned CPU (read across the host link by the
+        collection kernel); poses 4x4 (host, rounded to float32)."""
         _check(self._lib.vm_integrate_depth(self._h, ctypes.c_void_p(_ptr(depth)), ctypes.byref(intr.c()),
                                             _f16(T_wc), _f16(T_cw)), "vm_integrate_depth")
 
