@@ -694,7 +694,9 @@ def run_vmesh(args, rank, world, local):
         "kernel_ms_per_frame_warmup": kernel_ms,
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * W * H, "d2h_bytes_per_step": 8},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * W * H, "d2h_bytes_per_step": 8,
+                "path": "vm_step on the depth frame in pinned host memory (read across the host link by the "
+                        "collection kernel), then vm_mesh_size_async into pinned host memory, per frame"},
         "gpu_launches": launches_total,
         "clocks": cs.summary(),
         "mesh_memory": {
