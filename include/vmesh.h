@@ -342,7 +342,8 @@ typedef struct vm_batch vm_batch;
 vm_status vm_batch_create(vm_volume* const* vols, int n, vm_batch** out);
 vm_status vm_batch_destroy(vm_batch* batch);
 
-/* One tick: for scene i, depth depths[i] (DEVICE, K[i].height x K[i].width float32),
+/* One tick: for scene i, depth depths[i] (K[i].height x K[i].width float32, in device
+ * memory or pinned host memory as for vm_integrate_depth),
  * intrinsics K[i], poses T_wc + 16 i, T_cw + 16 i (host, row-major), as vm_step with
  * `flags` (VM_REFINE, VM_GC; VM_FULL is not available).  use_graph != 0 replays the
  * tick's five launches from a CUDA graph (captured on first use, re-captured when the

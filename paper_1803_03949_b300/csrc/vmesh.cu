@@ -208,8 +208,8 @@ vm_status prepare_depth(vm_volume* v, FrameParams* fp) {
   if (a.type != cudaMemoryTypeHost || !a.devicePointer) return VM_ERR_INVALID_ARG;
   const size_t n = (size_t)fp->W * fp->H;
   if (n > v->depth_cap) {
-    if (v->depth_buf) {  // frames already enqueued may still read the old copy
-      if (cudaStreamSynchronize(v->stream) != cudaSuccess) return VM_ERR_CUDA;
+    if (v->depth_buf) {  // frames already enqueued (on any stream) may still read the old copy
+      if (cudaDeviceSynchronize() != cudaSuccess) return VM_ERR_CUDA;
       cudaFree(v->depth_buf);
       v->depth_buf = nullptr;
       v->depth_cap = 0;
@@ -1387,6 +1387,7 @@ vm_status vm_batch_step(vm_batch* b, const float* const* depths, const vm_intrin
     if (b->vols[i]->diff_on) return VM_ERR_INVALID_ARG;
     if (!make_frame(&K[i], T_wc + 16 * i, T_cw + 16 * i, depths[i], &bf.fp[i])) return VM_ERR_INVALID_ARG;
     bf.fp[i].frame = b->vols[i]->frame;
+    if (const vm_status ps = prepare_depth(b->vols[i], &bf.fp[i])) return ps;
     tx = std::max(tx, (bf.fp[i].W + ALLOC_TILE_W - 1) / ALLOC_TILE_W);
     ty = std::max(ty, (bf.fp[i].H + ALLOC_TILE_H - 1) / ALLOC_TILE_H);
   }

@@ -372,11 +372,13 @@ class Scenes:
         self.close()
 
     def step_all(self, depths, intrinsics, poses, refine=True, gc=True, graph=True):
-        """depths: CUDA float32 (H, W) tensors, one per scene; intrinsics: Intrinsics per scene;
-        poses: (T_wc, T_cw) per scene (host 4x4, rounded to float32)."""
+        """depths: float32 (H, W) tensors, one per scene, CUDA or pinned CPU; intrinsics:
+        Intrinsics per scene; poses: (T_wc, T_cw) per scene (host 4x4, rounded to float32)."""
         n = len(self.volumes)
         assert len(depths) == len(intrinsics) == len(poses) == n
-        _contig_cuda(*depths)
+        for d in depths:
+            if not d.is_contiguous():
+                raise ValueError("expected contiguous depth tensors")
         dp = (ctypes.c_void_p * n)(*[_ptr(d) for d in depths])
         ks = (vm_intrinsics * n)(*[k.c() for k in intrinsics])
         twc = np.ascontiguousarray(np.stack([np.asarray(p[0], np.float32).reshape(16) for p in poses]))

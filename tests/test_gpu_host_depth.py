@@ -67,3 +67,26 @@ def test_pageable_host_depth_is_refused():
         v.integrate(torch.from_numpy(s.depth(0)), intrinsics(s), Twc, Tcw)
     v.check()
     assert v.num_blocks() == 0
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batched_step_with_pinned_host_depths(graph):
+    import torch
+
+    from paper_1803_03949_b300 import Scenes
+
+    scenes = [synth.small_room_scene(num_frames=3, seed=synth.SEED_BASE + 50 + i) for i in range(3)]
+    dev_vols = [gpu_volume(s.volume) for s in scenes]
+    host_vols = [gpu_volume(s.volume) for s in scenes]
+    bd, bh = Scenes(dev_vols), Scenes(host_vols)
+    Ks = [intrinsics(s) for s in scenes]
+    for k in range(3):
+        frames = [torch.from_numpy(s.depth(k)) for s in scenes]
+        poses = [poses32(s.pose(k)) for s in scenes]
+        bd.step_all([f.cuda() for f in frames], Ks, poses, graph=graph)
+        bh.step_all([f.pin_memory() for f in frames], Ks, poses, graph=graph)
+    for a, b in zip(dev_vols, host_vols):
+        b.check()
+        _same(a, b)
+    bd.close()
+    bh.close()
