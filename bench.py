@@ -339,8 +339,8 @@ def run_large(args, stream, flush, peak):
     warm-up frames of the configuration's 2000-frame trajectory (the default keeps the
     benchmark within minutes; `--large-frames 1990` runs all of it), each
     frame integrate + update(refine) + gc from the frame graph, enqueued back to back, L2
-    flushed before every frame.  A second pass on a fresh volume times k_mesh and
-    k_integrate with event nodes for their roofline."""
+    flushed before every frame.  A second pass on a fresh volume times every kernel with event
+    nodes (k_mesh and k_integrate for their roofline, all five for the per-frame breakdown)."""
     import torch
 
     from paper_1803_03949_b300 import Intrinsics, Volume
@@ -366,7 +366,7 @@ def run_large(args, stream, flush, peak):
         for k in range(Wm):
             v.step(dev[k], K, *poses[k], refine=True, gc=True, graph=True)
         if timing:
-            v.enable_timing(["k_mesh", "k_integrate"])
+            v.enable_timing(True)
         torch.cuda.synchronize()
         s0 = v.stats()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(T)]
@@ -418,6 +418,10 @@ def run_large(args, stream, flush, peak):
         "voxels_per_s": 512 * collected / tot, "mean_blocks_per_frame": collected / T,
         "live_blocks_at_end": s1["live_blocks"], "l2": "flushed before every frame (256 MB write)",
         "roofline": roof,
+        "kernel_us_per_frame": {k: 1000.0 * t / max(c, 1) for k, (t, c) in kt.items()},
+        "work_per_frame": dict({k: v / T for k, v in work.items()},
+                               freed_vertices=(s1["freed_vertices"] - s0["freed_vertices"]) / T,
+                               freed_blocks=(s1["freed_blocks"] - s0["freed_blocks"]) / T),
     }
 
 

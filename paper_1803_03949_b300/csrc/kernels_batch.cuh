@@ -133,15 +133,18 @@ __global__ void __launch_bounds__(MESH_THREADS, mesh_ctas_per_sm(true)) kb_mesh(
   allow_dependent_launch();
 }
 
-// Zero-reference vertices and released runs of every scene, in chunks of 32 list entries
-// (one warp per chunk, so the lanes of a warp share a scene).
+// Zero-reference vertices and released runs of every scene, in chunks of 64 entries of each
+// list (one warp per chunk, so the lanes of a warp share a scene).
 template <bool CE>
 __global__ void __launch_bounds__(256) kb_gc_vertices(const Vol* __restrict__ vols, int nscenes) {
   grid_dependency_wait();
-  __shared__ int pre_d[MAX_SCENES + 1], pre_r[MAX_SCENES + 1], pre_e[MAX_SCENES + 1];
-  scene_prefix(nscenes, pre_d, [&](int t) { return (min(__ldcg(&vols[t].ctl->c[C_N_DEAD]), vols[t].list_cap_dead) + 31) >> 5; });
-  scene_prefix(nscenes, pre_r,
-               [&](int t) { return (min(__ldcg(&vols[t].ctl->c[C_N_DEADRUN]), vols[t].list_cap_deadrun) + 31) >> 5; });
+  __shared__ int pre_d[MAX_SCENES + 1], pre_e[MAX_SCENES + 1];
+  constexpr int CHUNK = 32 * GCV_PER_LIST;
+  scene_prefix(nscenes, pre_d, [&](int t) {
+    const int n = min(__ldcg(&vols[t].ctl->c[C_N_DEAD]), vols[t].list_cap_dead);
+    const int nr = min(__ldcg(&vols[t].ctl->c[C_N_DEADRUN]), vols[t].list_cap_deadrun);
+    return (max(n, nr) + CHUNK - 1) / CHUNK;
+  });
   scene_prefix(nscenes, pre_e,
                [&](int t) { return (min(__ldcg(&vols[t].ctl->c[C_N_DEADREC]), vols[t].max_vertices) + 31) >> 5; });
   const int lane = threadIdx.x & 31;
@@ -151,20 +154,10 @@ __global__ void __launch_bounds__(256) kb_gc_vertices(const Vol* __restrict__ vo
     const int s = scene_of(pre_d, nscenes, u);
     const Vol& V = vols[s];
     const int n = min(__ldcg(&V.ctl->c[C_N_DEAD]), V.list_cap_dead);
-    const int i = ((u - pre_d[s]) << 5) + lane;
+    const int nr = min(__ldcg(&V.ctl->c[C_N_DEADRUN]), V.list_cap_deadrun);
     int freed = 0;
-    if (i < n) freed = gc_vertex<CE>(V, V.dead[i]);
+    gc_vertices_pass<CE>(V, (u - pre_d[s]) * CHUNK, 32, n, nr, freed);
     gc_flush_vertices(V, freed);
-  }
-  for (int u = warp; u < pre_r[nscenes]; u += nwarps) {
-    const int s = scene_of(pre_r, nscenes, u);
-    const Vol& V = vols[s];
-    const int n = min(__ldcg(&V.ctl->c[C_N_DEADRUN]), V.list_cap_deadrun);
-    const int i = ((u - pre_r[s]) << 5) + lane;
-    if (i < n) {
-      const int2 r = V.deadrun[i];
-      if (r.y >= 1 && r.y <= 5) run_push(V, r.y, r.x);
-    }
   }
   for (int u = warp; CE && u < pre_e[nscenes]; u += nwarps) {
     const int s = scene_of(pre_e, nscenes, u);

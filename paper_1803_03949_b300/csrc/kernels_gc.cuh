@@ -7,26 +7,10 @@
 
 namespace vmk {
 
-// Push a triangle run onto the free stack of its length, aggregated over lanes with the
-// same length.
-__device__ __forceinline__ void run_push(const Vol& V, int L, int base) {
-  cg::coalesced_group g0 = cg::coalesced_threads();
-  cg::coalesced_group g = cg::labeled_partition(g0, L);
-  int slot = 0;
-  if (g.thread_rank() == 0) slot = atomicAdd(&V.ctl->c[run_top(L)], (int)g.size());
-  slot = g.shfl(slot, 0) + (int)g.thread_rank();
-  if (slot < V.run_cap[L - 1]) V.run_free[L - 1][slot] = base;
-  else set_status(V, ST_POOL_FULL, P_FREE_STACK);
-}
-
-// Zero-reference vertex `vid` (listed by a mesh pass): claim with CAS(0 -> -1), so a vertex
-// listed twice, or one that regained a reference after it was listed, is freed at most once
-// and only when unreferenced; a vertex still attached to its edge is detached.  Returns
-// whether a detached vertex was freed.
+// Detach a claimed zero-reference vertex from its edge `e` (NO_EDGE: attached to none).
+// Returns whether it was attached.
 template <bool CE>
-__device__ __forceinline__ bool gc_vertex(const Vol& V, int vid) {
-  const uint32_t e = V.vedge[vid];  // loaded alongside the claim; no gc thread writes it
-  if (atomicCAS(&V.vref[vid], 0, -1) != 0) return false;
+__device__ __forceinline__ bool gc_detach(const Vol& V, uint32_t e) {
   bool detached = false;
   if (e != NO_EDGE) {
     const int ob = (int)(e / EPB), r = (int)(e - (uint32_t)ob * EPB), ov = r / 3, a = r - ov * 3;
@@ -47,8 +31,110 @@ __device__ __forceinline__ bool gc_vertex(const Vol& V, int vid) {
     atomicSub(&V.bnvert[ob], 1);
     detached = true;
   }
-  pool_push(V, V.vtx_free, C_VTX_TOP, V.max_vertices, vid);
   return detached;
+}
+
+// atomicCAS(p, cmp, val) returning the old value when `on`, else no access and cmp + 1;
+// predicated rather than branched, so that a run of them issues back to back.
+__device__ __forceinline__ int atom_cas_if(int* p, int cmp, int val, bool on) {
+  int old = cmp + 1;
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %4, 0;\n\t@q atom.global.cas.b32 %0, [%1], %2, %3;\n\t}"
+      : "+r"(old)
+      : "l"(p), "r"(cmp), "r"(val), "r"((unsigned)on)
+      : "memory");
+  return old;
+}
+
+// Inclusive sum over the lanes of a full, converged warp.
+template <typename T>
+__device__ __forceinline__ T warp_inclusive_sum(T x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+constexpr int GCV_PER_LIST = 2;  // entries of each list per thread and pass, in flight together
+constexpr int GCV_CTAS_PER_SM = 6;
+
+// One pass of a full warp over the zero-reference vertex list and the released-run list:
+// lane j takes entries b + j + k * stride (k < GCV_PER_LIST) of each.  A listed vertex is
+// claimed with CAS(0 -> -1), so a vertex listed twice, or one that regained a reference after
+// it was listed, is freed at most once and only when unreferenced; a vertex still attached to
+// its edge is detached.  Three round trips for all entries: the list entries; the vertices'
+// edges and claims, with one free-stack reservation per run length; one free-stack
+// reservation for the freed vertices.
+template <bool CE>
+__device__ __forceinline__ void gc_vertices_pass(const Vol& V, int b, int stride, int n, int nr, int& freed) {
+  constexpr int K = GCV_PER_LIST;
+  const int lane = threadIdx.x & 31;
+  int vid[K];
+  int2 run[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int i = b + lane + k * stride;
+    vid[k] = i < n ? __ldcg(&V.dead[i]) : -1;
+    run[k] = i < nr ? __ldcg(&V.deadrun[i]) : make_int2(0, 0);
+  }
+  uint32_t e[K];
+  int old[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int v = vid[k] >= 0 ? vid[k] : 0;
+    e[k] = __ldcg(&V.vedge[v]);  // no gc thread writes it
+    old[k] = atom_cas_if(V.vref + v, 0, -1, vid[k] >= 0);
+  }
+  // released runs: per length L (8 bits at 8 (L - 1)) this lane's count, its exclusive prefix
+  // over the warp, and one free-stack reservation per length (lanes 0..4)
+  unsigned long long rc = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (run[k].y >= 1 && run[k].y <= 5) rc += 1ull << (8 * (run[k].y - 1));
+  const unsigned long long rinc = warp_inclusive_sum(rc);
+  const unsigned long long rtot = __shfl_sync(0xffffffffu, rinc, 31);
+  int rbase = 0;
+  if (lane < 5) {
+    const int c = (int)((rtot >> (8 * lane)) & 0xFF);
+    if (c) rbase = atomicAdd(&V.ctl->c[run_top(lane + 1)], c);
+  }
+  // vertices whose claim succeeded: one free-stack reservation
+  unsigned ok = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (vid[k] >= 0 && old[k] == 0) ok |= 1u << k;
+  const int nok = __popc(ok);
+  const int vinc = warp_inclusive_sum(nok);
+  int vbase = 0;
+  if (lane == 31 && vinc > 0) vbase = atomicAdd(&V.ctl->c[C_VTX_TOP], vinc);
+  vbase = __shfl_sync(0xffffffffu, vbase, 31) + vinc - nok;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if ((ok >> k) & 1u) {
+      freed += gc_detach<CE>(V, e[k]);
+      if (vbase < V.max_vertices) V.vtx_free[vbase] = vid[k];
+      else set_status(V, ST_POOL_FULL, P_FREE_STACK);
+      ++vbase;
+    }
+  // per length, this lane's first slot: the reservation plus the lanes before
+  const unsigned long long rex = rinc - rc;
+  int rb[5];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) rb[j] = __shfl_sync(0xffffffffu, rbase, j) + (int)((rex >> (8 * j)) & 0xFF);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int L = run[k].y;
+    int slot = -1;
+#pragma unroll
+    for (int j = 0; j < 5; ++j)
+      if (L == j + 1) slot = rb[j]++;
+    if (slot < 0) continue;
+    if (slot < V.run_cap[L - 1]) V.run_free[L - 1][slot] = run[k].x;
+    else set_status(V, ST_POOL_FULL, P_FREE_STACK);
+  }
 }
 
 __device__ __forceinline__ void gc_flush_vertices(const Vol& V, int& freed) {
@@ -73,16 +159,14 @@ __device__ __forceinline__ void gc_record(const Vol& V, int rec) { pool_push(V, 
 // Zero-reference vertices and released triangle runs (and, CE, spare edge records) back to
 // their free stacks.
 template <bool CE>
-__global__ void __launch_bounds__(256) k_gc_vertices(Vol V) {
+__global__ void __launch_bounds__(256, GCV_CTAS_PER_SM) k_gc_vertices(Vol V) {
   grid_dependency_wait();
   const int n = min(__ldcg(&V.ctl->c[C_N_DEAD]), V.list_cap_dead);
   const int nr = min(__ldcg(&V.ctl->c[C_N_DEADRUN]), V.list_cap_deadrun);
   int freed = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) freed += gc_vertex<CE>(V, V.dead[i]);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
-    const int2 r = V.deadrun[i];
-    if (r.y >= 1 && r.y <= 5) run_push(V, r.y, r.x);
-  }
+  const int stride = gridDim.x * blockDim.x, m = max(n, nr);
+  for (int b = blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < m; b += stride * GCV_PER_LIST)
+    gc_vertices_pass<CE>(V, b, stride, n, nr, freed);
   if (CE) {
     const int nrec = min(__ldcg(&V.ctl->c[C_N_DEADREC]), V.max_vertices);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nrec; i += gridDim.x * blockDim.x) gc_record(V, V.dead_rec[i]);
