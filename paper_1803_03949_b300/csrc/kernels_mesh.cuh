@@ -80,7 +80,7 @@ __host__ __device__ inline void halo_pairs(uint16_t* out) {
 template <bool CE>
 struct __align__(16) MeshSmem {
   float halo[HALO_N];  // d of the voxel, NaN where W = 0 or its block is absent
-  uint64_t tri64[256];
+  alignas(16) uint64_t tri64[256];
   alignas(16) uint16_t emask[256];  // the cube edges each type's triangles use (bit k: edge k)
   alignas(16) uint16_t pairs[256];  // the halo's neighbour voxel pairs (halo_pairs)
   int nb[8];
@@ -104,6 +104,11 @@ struct __align__(16) MeshSmem {
   alignas(16) int rec[CE ? BV : 4];        // compact layout: the block's edge records (voxel -> record, -1 none)
   int evid[EDGE_SLOTS];                    // vertex id per edge slot (own slots from stage a)
 };
+// members written or read with 16-byte vector accesses
+static_assert(offsetof(MeshSmem<false>, tri64) % 16 == 0 && offsetof(MeshSmem<true>, tri64) % 16 == 0, "tri64");
+static_assert(offsetof(MeshSmem<false>, emask) % 16 == 0 && offsetof(MeshSmem<true>, emask) % 16 == 0, "emask");
+static_assert(offsetof(MeshSmem<false>, pairs) % 16 == 0 && offsetof(MeshSmem<true>, pairs) % 16 == 0, "pairs");
+static_assert(offsetof(MeshSmem<true>, rec) % 16 == 0, "rec");
 
 // Eqs. 3-5: snap a disturbed raw type to the nearest admissible regular type.  `small` has
 // bit k set when |d(c_k)| < eps, so a regular type is admissible iff every corner where it
