@@ -60,6 +60,19 @@ __device__ __forceinline__ T warp_inclusive_sum(T x) {
 
 constexpr int GCV_PER_LIST = 2;  // entries of each list per thread and pass, in flight together
 constexpr int GCV_CTAS_PER_SM = 6;
+constexpr int GCV_THREADS = 256;
+constexpr int GCV_WARPS = GCV_THREADS / 32;
+
+// Free-stack reservations of a whole CTA's pass (k_gc_vertices): every warp's counts of freed
+// vertices and of released runs per length (then their exclusive prefixes over the warps),
+// the CTA's first slot on each stack, and its freed count.  The stack tops and the vertex
+// counters then take one atomic per CTA instead of one per warp.
+struct GcvCta {
+  int v[GCV_WARPS];
+  int r[GCV_WARPS][5];
+  int vbase, rbase[5];
+  int freed;
+};
 
 // One pass of a full warp over the zero-reference vertex list and the released-run list:
 // lane j takes entries b + j + k * stride (k < GCV_PER_LIST) of each.  A listed vertex is
@@ -67,9 +80,11 @@ constexpr int GCV_CTAS_PER_SM = 6;
 // it was listed, is freed at most once and only when unreferenced; a vertex still attached to
 // its edge is detached.  Three round trips for all entries: the list entries; the vertices'
 // edges and claims, with one free-stack reservation per run length; one free-stack
-// reservation for the freed vertices.
+// reservation for the freed vertices.  The reservations are the warp's own (sh null) or the
+// CTA's (sh: the whole CTA calls the pass together; two barriers).
 template <bool CE>
-__device__ __forceinline__ void gc_vertices_pass(const Vol& V, int b, int stride, int n, int nr, int& freed) {
+__device__ __forceinline__ void gc_vertices_pass(const Vol& V, int b, int stride, int n, int nr, int& freed,
+                                                 GcvCta* sh = nullptr) {
   constexpr int K = GCV_PER_LIST;
   const int lane = threadIdx.x & 31;
   int vid[K];
@@ -96,21 +111,46 @@ __device__ __forceinline__ void gc_vertices_pass(const Vol& V, int b, int stride
     if (run[k].y >= 1 && run[k].y <= 5) rc += 1ull << (8 * (run[k].y - 1));
   const unsigned long long rinc = warp_inclusive_sum(rc);
   const unsigned long long rtot = __shfl_sync(0xffffffffu, rinc, 31);
-  int rbase = 0;
-  if (lane < 5) {
-    const int c = (int)((rtot >> (8 * lane)) & 0xFF);
-    if (c) rbase = atomicAdd(&V.ctl->c[run_top(lane + 1)], c);
-  }
-  // vertices whose claim succeeded: one free-stack reservation
+  // vertices whose claim succeeded
   unsigned ok = 0;
 #pragma unroll
   for (int k = 0; k < K; ++k)
     if (vid[k] >= 0 && old[k] == 0) ok |= 1u << k;
   const int nok = __popc(ok);
   const int vinc = warp_inclusive_sum(nok);
-  int vbase = 0;
-  if (lane == 31 && vinc > 0) vbase = atomicAdd(&V.ctl->c[C_VTX_TOP], vinc);
-  vbase = __shfl_sync(0xffffffffu, vbase, 31) + vinc - nok;
+  // the first slots of the warp on the vertex stack (vbase) and on each run stack (lanes
+  // 0..4: rbase of length lane + 1)
+  int vbase = 0, rbase = 0;
+  if (sh) {
+    const int warp = threadIdx.x >> 5;
+    if (lane == 31) sh->v[warp] = vinc;
+    if (lane < 5) sh->r[warp][lane] = (int)((rtot >> (8 * lane)) & 0xFF);
+    __syncthreads();
+    if (threadIdx.x < 6) {  // thread 0: the vertex stack; threads 1..5: run length 1..5
+      const int t = threadIdx.x;
+      int tot = 0;
+      for (int w = 0; w < GCV_WARPS; ++w) {
+        int* p = t == 0 ? &sh->v[w] : &sh->r[w][t - 1];
+        const int c = *p;
+        *p = tot;
+        tot += c;
+      }
+      const int base = tot ? atomicAdd(&V.ctl->c[t == 0 ? C_VTX_TOP : run_top(t)], tot) : 0;
+      if (t == 0) sh->vbase = base;
+      else sh->rbase[t - 1] = base;
+    }
+    __syncthreads();
+    vbase = sh->vbase + sh->v[warp];
+    if (lane < 5) rbase = sh->rbase[lane] + sh->r[warp][lane];
+  } else {
+    if (lane < 5) {
+      const int c = (int)((rtot >> (8 * lane)) & 0xFF);
+      if (c) rbase = atomicAdd(&V.ctl->c[run_top(lane + 1)], c);
+    }
+    if (lane == 31 && vinc > 0) vbase = atomicAdd(&V.ctl->c[C_VTX_TOP], vinc);
+    vbase = __shfl_sync(0xffffffffu, vbase, 31);
+  }
+  vbase += vinc - nok;
 #pragma unroll
   for (int k = 0; k < K; ++k)
     if ((ok >> k) & 1u) {
@@ -159,19 +199,29 @@ __device__ __forceinline__ void gc_record(const Vol& V, int rec) { pool_push(V, 
 // Zero-reference vertices and released triangle runs (and, CE, spare edge records) back to
 // their free stacks.
 template <bool CE>
-__global__ void __launch_bounds__(256, GCV_CTAS_PER_SM) k_gc_vertices(Vol V) {
+__global__ void __launch_bounds__(GCV_THREADS, GCV_CTAS_PER_SM) k_gc_vertices(Vol V) {
+  __shared__ GcvCta sh;
+  if (threadIdx.x == 0) sh.freed = 0;
   grid_dependency_wait();
   const int n = min(__ldcg(&V.ctl->c[C_N_DEAD]), V.list_cap_dead);
   const int nr = min(__ldcg(&V.ctl->c[C_N_DEADRUN]), V.list_cap_deadrun);
   int freed = 0;
   const int stride = gridDim.x * blockDim.x, m = max(n, nr);
-  for (int b = blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < m; b += stride * GCV_PER_LIST)
-    gc_vertices_pass<CE>(V, b, stride, n, nr, freed);
+  // the CTA's passes together (CTA-wide reservations)
+  for (int b0 = blockIdx.x * blockDim.x; b0 < m; b0 += stride * GCV_PER_LIST) {
+    gc_vertices_pass<CE>(V, b0 + (threadIdx.x & ~31), stride, n, nr, freed, &sh);
+    __syncthreads();  // the next pass rewrites sh
+  }
   if (CE) {
     const int nrec = min(__ldcg(&V.ctl->c[C_N_DEADREC]), V.max_vertices);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nrec; i += gridDim.x * blockDim.x) gc_record(V, V.dead_rec[i]);
   }
-  gc_flush_vertices(V, freed);
+  if (freed) atomicAdd(&sh.freed, freed);
+  __syncthreads();
+  if (threadIdx.x == 0 && sh.freed) {
+    atomicAdd(&V.ctl->c[C_LIVE_VERTS], -sh.freed);
+    atomicAdd(&V.ctl->c[C_ST_FREED_VERTS], sh.freed);
+  }
   allow_dependent_launch();
 }
 

@@ -291,7 +291,7 @@ vm_status enqueue_update(vm_volume* v, int flags, bool after_integrate) {
 vm_status enqueue_gc(vm_volume* v) {
   const bool ce = (v->p.flags & VM_PARAM_COMPACT_EDGES) != 0;
   vm_status st = launch(v, K_GC_VERTICES, [&] {
-    launch_dependent(ce ? k_gc_vertices<true> : k_gc_vertices<false>, grid_for(v, GCV_CTAS_PER_SM), 256, v->cur, v->V);
+    launch_dependent(ce ? k_gc_vertices<true> : k_gc_vertices<false>, grid_for(v, GCV_CTAS_PER_SM), GCV_THREADS, v->cur, v->V);
   });
   if (st) return st;
   const int consumed = v->advance_pending ? 1 : 0;
