@@ -133,13 +133,16 @@ __global__ void __launch_bounds__(MESH_THREADS, mesh_ctas_per_sm(true)) kb_mesh(
   allow_dependent_launch();
 }
 
-// Zero-reference vertices and released runs of every scene, in chunks of 64 entries of each
-// list (one warp per chunk, so the lanes of a warp share a scene).
+// Zero-reference vertices and released runs of every scene, in chunks of 512 entries of each
+// list (one CTA per chunk, so that the CTA's warps share a scene and its free stacks take one
+// reservation per CTA).
 template <bool CE>
-__global__ void __launch_bounds__(256) kb_gc_vertices(const Vol* __restrict__ vols, int nscenes) {
+__global__ void __launch_bounds__(GCV_THREADS) kb_gc_vertices(const Vol* __restrict__ vols, int nscenes) {
   grid_dependency_wait();
   __shared__ int pre_d[MAX_SCENES + 1], pre_e[MAX_SCENES + 1];
-  constexpr int CHUNK = 32 * GCV_PER_LIST;
+  __shared__ GcvCta sh;
+  if (threadIdx.x == 0) sh.freed = 0;
+  constexpr int CHUNK = GCV_THREADS * GCV_PER_LIST;
   scene_prefix(nscenes, pre_d, [&](int t) {
     const int n = min(__ldcg(&vols[t].ctl->c[C_N_DEAD]), vols[t].list_cap_dead);
     const int nr = min(__ldcg(&vols[t].ctl->c[C_N_DEADRUN]), vols[t].list_cap_deadrun);
@@ -150,14 +153,21 @@ __global__ void __launch_bounds__(256) kb_gc_vertices(const Vol* __restrict__ vo
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int u = warp; u < pre_d[nscenes]; u += nwarps) {
+  for (int u = blockIdx.x; u < pre_d[nscenes]; u += gridDim.x) {
     const int s = scene_of(pre_d, nscenes, u);
     const Vol& V = vols[s];
     const int n = min(__ldcg(&V.ctl->c[C_N_DEAD]), V.list_cap_dead);
     const int nr = min(__ldcg(&V.ctl->c[C_N_DEADRUN]), V.list_cap_deadrun);
     int freed = 0;
-    gc_vertices_pass<CE>(V, (u - pre_d[s]) * CHUNK, 32, n, nr, freed);
-    gc_flush_vertices(V, freed);
+    gc_vertices_pass<CE>(V, (u - pre_d[s]) * CHUNK + (threadIdx.x & ~31), GCV_THREADS, n, nr, freed, &sh);
+    if (freed) atomicAdd(&sh.freed, freed);
+    __syncthreads();
+    if (threadIdx.x == 0 && sh.freed) {
+      atomicAdd(&V.ctl->c[C_LIVE_VERTS], -sh.freed);
+      atomicAdd(&V.ctl->c[C_ST_FREED_VERTS], sh.freed);
+      sh.freed = 0;
+    }
+    __syncthreads();  // the next chunk rewrites sh
   }
   for (int u = warp; CE && u < pre_e[nscenes]; u += nwarps) {
     const int s = scene_of(pre_e, nscenes, u);
