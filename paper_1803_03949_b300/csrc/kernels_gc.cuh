@@ -272,6 +272,7 @@ __device__ __forceinline__ bool gc_candidate(const Vol& V, int blk, uint32_t epo
 // cubes reach into it) has triangles: its bucket becomes a tombstone, its voxels are
 // cleared, its neighbours forget it, its index returns to the pool.  Returns (in every lane)
 // whether the block was freed.
+__device__ __forceinline__ void gc_release_block(const Vol& V, int blk);
 __device__ __forceinline__ bool gc_free_block(const Vol& V, int blk) {
   const int lane = threadIdx.x & 31;
   bool lower_tri = false;
@@ -280,6 +281,14 @@ __device__ __forceinline__ bool gc_free_block(const Vol& V, int blk) {
     lower_tri = nbk >= 0 && V.bntri[nbk] != 0;
   }
   if (__any_sync(0xffffffffu, lower_tri)) return false;
+  gc_release_block(V, blk);
+  return true;
+}
+
+// Free block `blk` (the calling warp; its checks passed): its bucket becomes a tombstone,
+// its voxels are cleared, its neighbours forget it, its index returns to the pool.
+__device__ __forceinline__ void gc_release_block(const Vol& V, int blk) {
+  const int lane = threadIdx.x & 31;
   const int bucket = V.bkey[blk].w;
   float4* tw = reinterpret_cast<float4*>(V.tw + (size_t)blk * BV);
   for (int j = lane; j < BV / 2; j += 32) tw[j] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -300,7 +309,6 @@ __device__ __forceinline__ bool gc_free_block(const Vol& V, int blk) {
     V.bnear[blk] = 0;
     pool_push(V, V.blk_free, C_BLK_TOP, V.max_blocks, blk);
   }
-  return true;
 }
 
 __device__ __forceinline__ void gc_flush_blocks(const Vol& V, int& freed) {
@@ -347,9 +355,26 @@ __global__ void __launch_bounds__(256) k_gc_blocks(Vol V, int consumed) {
     const int blk = base + lane;
     unsigned m = __ballot_sync(0xffffffffu, blk < hw && gc_candidate(V, blk, epoch, consumed));
     while (m) {
-      const int b = __ffs(m) - 1;
-      m &= m - 1;
-      freed += gc_free_block(V, base + b);
+      // four candidates at a time, lanes 8 g + 1..7 testing the lower neighbours of the g-th
+      const int g = lane >> 3, o = lane & 7;
+      unsigned mg = m;
+      for (int j = 0; j < g; ++j) mg &= mg - 1;
+      const int cb = mg ? __ffs(mg) - 1 : -1;
+      for (int j = 0; j < 4; ++j) m &= m - 1;
+      bool lower_tri = false;
+      if (cb >= 0 && o >= 1) {
+        const int nbk = V.nbr[(base + cb) * 16 + 8 + o];
+        lower_tri = nbk >= 0 && V.bntri[nbk] != 0;
+      }
+      const unsigned kept = __ballot_sync(0xffffffffu, lower_tri);
+      for (int gg = 0; gg < 4; ++gg) {
+        const int c = __shfl_sync(0xffffffffu, cb, 8 * gg);
+        if (c < 0) break;
+        if (((kept >> (8 * gg)) & 0xFFu) == 0) {
+          gc_release_block(V, base + c);
+          ++freed;
+        }
+      }
     }
   }
   gc_flush_blocks(V, freed);
