@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(ALLOC_TILE_W * ALLOC_TILE_H / PPT)
     alloc_begin(V, bf.advance[s]);
   }
   if ((int)blockIdx.x * ALLOC_TILE_W < fp.W && (int)blockIdx.y * ALLOC_TILE_H < fp.H)
-    alloc_tile<PPT, ALLOC_TILE_W>(V, fp, blockIdx.x, blockIdx.y, set);
+    alloc_tile<PPT, ALLOC_TILE_W, false>(V, fp, blockIdx.x, blockIdx.y, set);
   allow_dependent_launch();
 }
 

@@ -78,8 +78,26 @@ __device__ __forceinline__ void touch_bucket(const Vol& V, int s, uint64_t key, 
               make_int4((int)(uint32_t)key, (int)(key >> 32), blk, s));
 }
 
-__device__ __forceinline__ void smem_set_insert(unsigned long long* set, const Vol& V, uint64_t key, int bx, int by,
-                                                int bz, uint32_t frame) {
+// Insert a key of the CTA set into the global hash and record the collection.
+__device__ __forceinline__ void alloc_global_insert(const Vol& V, uint64_t key, uint32_t frame) {
+  const int bx = (int)((key >> 42) & 0x1FFFFF) - KEY_BIAS;
+  const int by = (int)((key >> 21) & 0x1FFFFF) - KEY_BIAS;
+  const int bz = (int)(key & 0x1FFFFF) - KEY_BIAS;
+  int blk;
+  const int s = hash_insert(V, key, bx, by, bz, frame, blk);
+  if (s >= 0) touch_bucket(V, s, key, blk, frame);
+}
+
+// Per warp of a collection CTA, the set slots whose key one of its threads put in the set
+// first: the warp inserts those keys into the global hash once its own pixels are walked, so
+// the round trips of a tile's inserts overlap the other warps' walks.
+constexpr int ALLOC_WLIST = 64;
+
+// Put `key` in the CTA set; a key new to the set goes on the list `wl` (count `wn`) of the
+// calling warp (or, when that list is full, into the hash at once); wl null: no list (the
+// caller inserts the set's keys after the walks).
+__device__ __forceinline__ void smem_set_insert(unsigned long long* set, uint16_t* wl, int* wn, const Vol& V,
+                                                uint64_t key, uint32_t frame) {
   // any spread of the 63 key bits serves here (the set lives for one CTA): fold and multiply
   uint32_t h = (((uint32_t)key ^ (uint32_t)(key >> 21) ^ (uint32_t)(key >> 42)) * 0x9E3779B1u) >> (32 - ALLOC_SET_LOG2);
   for (int p = 0; p < 32; ++p) {
@@ -89,14 +107,19 @@ __device__ __forceinline__ void smem_set_insert(unsigned long long* set, const V
     if (cur == key) return;
     if (cur == KEY_EMPTY) {
       unsigned long long old = atomicCAS(&set[h], (unsigned long long)KEY_EMPTY, (unsigned long long)key);
-      if (old == KEY_EMPTY || old == key) return;
+      if (old == KEY_EMPTY) {
+        if (wl) {
+          const int pos = atomicAdd(wn, 1);
+          if (pos < ALLOC_WLIST) wl[pos] = (uint16_t)h;
+          else alloc_global_insert(V, key, frame);
+        }
+        return;
+      }
+      if (old == key) return;
     }
     h = (h + 1) & (ALLOC_SET - 1);
   }
-  // CTA set saturated: insert directly
-  int blk;
-  int s = hash_insert(V, key, bx, by, bz, frame, blk);
-  if (s >= 0) touch_bucket(V, s, key, blk, frame);
+  alloc_global_insert(V, key, frame);  // CTA set saturated: insert directly
 }
 
 // DDA set-up along one axis: start cell c, remaining steps rem, step direction, the ray
@@ -124,7 +147,8 @@ __device__ __forceinline__ void dda_axis(float a, float b, int& c, int& rem, int
 // Walk the block cells of one pixel's segment (Eq. 1) into the CTA set; `last` holds the
 // key this thread inserted most recently (neighbouring pixels mostly cross the same cells).
 __device__ __forceinline__ void collect_pixel(const Vol& V, const FrameParams& fp, int u, int v, float D,
-                                              unsigned long long* set, uint32_t frame, uint64_t& last) {
+                                              unsigned long long* set, uint16_t* wl, int* wn, uint32_t frame,
+                                              uint64_t& last) {
   if (!(D > 0.0f) || !isfinite(D)) return;
   // divisions as products with reciprocals (of fx, fy, the block side)
   // (__frcp_rn: the correctly rounded reciprocal, the value of 1.0f / x in IEEE arithmetic)
@@ -160,7 +184,7 @@ __device__ __forceinline__ void collect_pixel(const Vol& V, const FrameParams& f
   for (int it = 0; it < DDA_MAX_CELLS; ++it) {
     const uint64_t key = pack_key(cx, cy, cz);
     if (key != last) {
-      smem_set_insert(set, V, key, cx, cy, cz, frame);
+      smem_set_insert(set, wl, wn, V, key, frame);
       last = key;
     }
     if (rx + ry + rz == 0) break;
@@ -176,13 +200,20 @@ __device__ __forceinline__ void collect_pixel(const Vol& V, const FrameParams& f
 
 // One TW x 16 pixel tile (tile column tx, row ty) walked by the calling CTA of
 // TW * 16 / PPT threads, PPT vertically adjacent pixels per thread: each pixel's segment goes
-// into the CTA-local key set `set`, then the set's unique keys are inserted into the global
-// hash and recorded as collected.
-template <int PPT, int TW>
+// into the CTA-local key set `set`, and each key new to the set is inserted into the global
+// hash and recorded as collected: EARLY, by the warp that found it, after its own walks
+// (k_alloc); else by the whole CTA after all walks (the batched collection, measured faster
+// that way with its larger CTAs).
+template <int PPT, int TW, bool EARLY>
 __device__ __forceinline__ void alloc_tile(const Vol& V, const FrameParams& fp, int tx, int ty,
                                            unsigned long long* set) {
+  constexpr int NW = EARLY ? TW * ALLOC_TILE_H / PPT / 32 : 1;
+  __shared__ uint16_t wlist[NW][ALLOC_WLIST];
+  __shared__ int wcount[NW];
   const uint32_t frame = fp.frame;
+  const int w = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < ALLOC_SET; i += blockDim.x) set[i] = KEY_EMPTY;
+  if (EARLY && threadIdx.x < NW) wcount[threadIdx.x] = 0;
   const int u = tx * TW + (threadIdx.x & (TW - 1));
   const int v = ty * ALLOC_TILE_H + PPT * (threadIdx.x / TW);
   // the depth pixels: from device memory, or from pinned host memory across the host link (then
@@ -199,17 +230,16 @@ __device__ __forceinline__ void alloc_tile(const Vol& V, const FrameParams& fp, 
   uint64_t last = KEY_EMPTY;
 #pragma unroll
   for (int r = 0; r < PPT; ++r)
-    if (u < fp.W && v + r < fp.H) collect_pixel(V, fp, u, v + r, D[r], set, frame, last);
-  __syncthreads();
-  for (int i = threadIdx.x; i < ALLOC_SET; i += blockDim.x) {
-    uint64_t key = set[i];
-    if (key == KEY_EMPTY) continue;
-    int bx = (int)((key >> 42) & 0x1FFFFF) - KEY_BIAS;
-    int by = (int)((key >> 21) & 0x1FFFFF) - KEY_BIAS;
-    int bz = (int)(key & 0x1FFFFF) - KEY_BIAS;
-    int blk;
-    int s = hash_insert(V, key, bx, by, bz, frame, blk);
-    if (s >= 0) touch_bucket(V, s, key, blk, frame);
+    if (u < fp.W && v + r < fp.H)
+      collect_pixel(V, fp, u, v + r, D[r], set, EARLY ? wlist[w] : nullptr, EARLY ? &wcount[w] : nullptr, frame, last);
+  if (EARLY) {
+    __syncwarp();
+    const int nw = min(wcount[w], ALLOC_WLIST);
+    for (int i = threadIdx.x & 31; i < nw; i += 32) alloc_global_insert(V, set[wlist[w][i]], frame);
+  } else {
+    __syncthreads();
+    for (int i = threadIdx.x; i < ALLOC_SET; i += blockDim.x)
+      if (set[i] != KEY_EMPTY) alloc_global_insert(V, set[i], frame);
   }
 }
 
@@ -226,15 +256,16 @@ __device__ __forceinline__ void alloc_begin(const Vol& V, int advance_epoch) {
 // One CTA per 32 x 16 pixel tile, two vertically adjacent pixels per thread (a 640 x 480
 // frame is one wave of CTAs).  The frame's parameters arrive as a launch argument; the
 // first CTA stores them in the control block for the kernels that follow and starts the
-// epoch.  No CTA waits for the others: the kernel ends with its last tile.
-__global__ void __launch_bounds__(ALLOC_THREADS) k_alloc(Vol V, const __grid_constant__ FrameParams fp,
+// epoch.  No CTA waits for the others: the kernel ends with its last tile.  Registers are
+// bounded for 5 CTAs per SM (740 on 148 SMs, over the 600 tiles of a 640 x 480 frame).
+__global__ void __launch_bounds__(ALLOC_THREADS, 5) k_alloc(Vol V, const __grid_constant__ FrameParams fp,
                                                          int advance_epoch) {
   __shared__ unsigned long long set[ALLOC_SET];
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
     V.ctl->fp = fp;  // for the later kernels
     alloc_begin(V, advance_epoch);
   }
-  alloc_tile<ALLOC_PPT, ALLOC_TILE_W1>(V, fp, blockIdx.x, blockIdx.y, set);
+  alloc_tile<ALLOC_PPT, ALLOC_TILE_W1, true>(V, fp, blockIdx.x, blockIdx.y, set);
   allow_dependent_launch();
 }
 
