@@ -150,16 +150,16 @@ __device__ __forceinline__ void collect_pixel(const Vol& V, const FrameParams& f
                                               unsigned long long* set, uint16_t* wl, int* wn, uint32_t frame,
                                               uint64_t& last) {
   if (!(D > 0.0f) || !isfinite(D)) return;
-  // divisions as products with reciprocals (of fx, fy, the block side)
-  // (__frcp_rn: the correctly rounded reciprocal, the value of 1.0f / x in IEEE arithmetic)
-  const float xn = ((float)u - fp.cx) * __frcp_rn(fp.fx);
-  const float yn = ((float)v - fp.cy) * __frcp_rn(fp.fy);
+  // divisions as products with the correctly rounded reciprocals of fx, fy and the block side
+  // (computed once on the host: the value of 1.0f / x in IEEE arithmetic)
+  const float xn = ((float)u - fp.cx) * fp.rfx;
+  const float yn = ((float)v - fp.cy) * fp.rfy;
   float z0 = D - V.mu;
   if (z0 < Z_NEAR) z0 = Z_NEAR;
   const float z1 = D + V.mu;
   const float pa0 = xn * z0, pa1 = yn * z0, pa2 = z0;
   const float pb0 = xn * z1, pb1 = yn * z1, pb2 = z1;
-  const float ibs = __frcp_rn(V.l * (float)BS);
+  const float ibs = V.ibs;
   float A[3], B[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {

@@ -185,6 +185,8 @@ bool make_frame(const vm_intrinsics* K, const float* Twc, const float* Tcw, cons
   fp->fy = K->fy;
   fp->cx = K->cx;
   fp->cy = K->cy;
+  fp->rfx = 1.0f / K->fx;
+  fp->rfy = 1.0f / K->fy;
   for (int i = 0; i < 12; ++i) {
     fp->Twc[i] = Twc[i];
     fp->Tcw[i] = Tcw[i];
@@ -420,6 +422,7 @@ vm_status vm_create_volume(const vm_params* p, void* cuda_stream, vm_volume** ou
 
   Vol& V = v->V;
   V.l = p->voxel_size;
+  V.ibs = 1.0f / (V.l * (float)BS);
   V.mu = p->trunc;
   V.eps = p->eps_refine;
   V.wmax = p->w_max;

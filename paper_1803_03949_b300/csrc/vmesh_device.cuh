@@ -115,6 +115,7 @@ struct FrameParams {
   float* depth_copy;      // null, or where the collection copies depth_in (then depth == depth_copy)
   int W, H;
   float fx, fy, cx, cy;
+  float rfx, rfy;  // 1 / fx and 1 / fy, rounded to float (IEEE division on the host)
   float Twc[12];  // rows of [R | t], camera -> world
   float Tcw[12];  // world -> camera
   uint32_t frame;  // number of the integrate call (from 1, consecutive), set by the host
@@ -128,6 +129,7 @@ struct Ctl {
 // Plain-old-data view of a volume passed by value to every kernel.
 struct Vol {
   float l, mu, eps, wmax;
+  float ibs;  // 1 / (l * 8), the block side's reciprocal rounded to float (IEEE division on the host)
   uint32_t hmask;
   int max_blocks, max_vertices, max_triangles;
   int run_cap[5];
