@@ -196,35 +196,6 @@ __device__ __forceinline__ void gc_lists_reset(const Vol& V) {
 // A spare edge record of a lost claim back to its free stack.
 __device__ __forceinline__ void gc_record(const Vol& V, int rec) { pool_push(V, V.rec_free, C_REC_TOP, V.max_vertices, rec); }
 
-// Zero-reference vertices and released triangle runs (and, CE, spare edge records) back to
-// their free stacks.
-template <bool CE>
-__global__ void __launch_bounds__(GCV_THREADS, GCV_CTAS_PER_SM) k_gc_vertices(Vol V) {
-  __shared__ GcvCta sh;
-  if (threadIdx.x == 0) sh.freed = 0;
-  grid_dependency_wait();
-  const int n = min(__ldcg(&V.ctl->c[C_N_DEAD]), V.list_cap_dead);
-  const int nr = min(__ldcg(&V.ctl->c[C_N_DEADRUN]), V.list_cap_deadrun);
-  int freed = 0;
-  const int stride = gridDim.x * blockDim.x, m = max(n, nr);
-  // the CTA's passes together (CTA-wide reservations)
-  for (int b0 = blockIdx.x * blockDim.x; b0 < m; b0 += stride * GCV_PER_LIST) {
-    gc_vertices_pass<CE>(V, b0 + (threadIdx.x & ~31), stride, n, nr, freed, &sh);
-    __syncthreads();  // the next pass rewrites sh
-  }
-  if (CE) {
-    const int nrec = min(__ldcg(&V.ctl->c[C_N_DEADREC]), V.max_vertices);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nrec; i += gridDim.x * blockDim.x) gc_record(V, V.dead_rec[i]);
-  }
-  if (freed) atomicAdd(&sh.freed, freed);
-  __syncthreads();
-  if (threadIdx.x == 0 && sh.freed) {
-    atomicAdd(&V.ctl->c[C_LIVE_VERTS], -sh.freed);
-    atomicAdd(&V.ctl->c[C_ST_FREED_VERTS], sh.freed);
-  }
-  allow_dependent_launch();
-}
-
 // Rebuild the hash without tombstones (one CTA): empty every bucket, then re-insert every
 // live block from the block array (bkey holds its key; its new bucket is written back).
 // Block indices, and with them the update-set marks, do not change.
@@ -320,9 +291,9 @@ __device__ __forceinline__ void gc_flush_blocks(const Vol& V, int& freed) {
   freed = 0;
 }
 
-// After the last CTA (the whole CTA): rebuild the hash when live plus dead buckets pass
-// half the table; with `consumed`, empty the update set.
-__device__ __forceinline__ void gc_blocks_finish(const Vol& V, int consumed) {
+// Rebuild the hash (the whole CTA) when live plus dead buckets pass half the table.  The
+// table must be quiet: no kernel inserts, frees or looks up blocks meanwhile.
+__device__ __forceinline__ void gc_rehash_if_needed(const Vol& V) {
   __shared__ int need;
   if (threadIdx.x == 0) {
     const long long live = V.ctl->c[C_LIVE_BLOCKS], tomb = V.ctl->c[C_TOMBS];
@@ -336,15 +307,57 @@ __device__ __forceinline__ void gc_blocks_finish(const Vol& V, int consumed) {
       V.ctl->c[C_ST_REHASHES] += 1;
     }
   }
+  __syncthreads();
+}
+
+// After the last CTA of a batched block gc (the whole CTA): the rebuild check; with
+// `consumed`, empty the update set.
+__device__ __forceinline__ void gc_blocks_finish(const Vol& V, int consumed) {
+  gc_rehash_if_needed(V);
   if (threadIdx.x == 0 && consumed) V.ctl->c[C_N_UPDATE] = 0;
   __syncthreads();
 }
 
-// Block recycling: a lane per pool slot tests it, the warp frees the candidates.  The last
-// CTA finishes the pass.
+// Zero-reference vertices and released triangle runs (and, CE, spare edge records) back to
+// their free stacks.
+template <bool CE>
+__global__ void __launch_bounds__(GCV_THREADS, GCV_CTAS_PER_SM) k_gc_vertices(Vol V) {
+  __shared__ GcvCta sh;
+  if (threadIdx.x == 0) sh.freed = 0;
+  grid_dependency_wait();
+  // the hash is quiet during this kernel: the last CTA (which the lists reach last, if at all)
+  // rebuilds it when the previous block gc left live plus dead buckets past half the table
+  if (blockIdx.x == gridDim.x - 1) gc_rehash_if_needed(V);
+  const int n = min(__ldcg(&V.ctl->c[C_N_DEAD]), V.list_cap_dead);
+  const int nr = min(__ldcg(&V.ctl->c[C_N_DEADRUN]), V.list_cap_deadrun);
+  int freed = 0;
+  const int stride = gridDim.x * blockDim.x, m = max(n, nr);
+  // the CTA's passes together (CTA-wide reservations)
+  for (int b0 = blockIdx.x * blockDim.x; b0 < m; b0 += stride * GCV_PER_LIST) {
+    gc_vertices_pass<CE>(V, b0 + (threadIdx.x & ~31), stride, n, nr, freed, &sh);
+    __syncthreads();  // the next pass rewrites sh
+  }
+  if (CE) {
+    const int nrec = min(__ldcg(&V.ctl->c[C_N_DEADREC]), V.max_vertices);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nrec; i += gridDim.x * blockDim.x) gc_record(V, V.dead_rec[i]);
+  }
+  if (freed) atomicAdd(&sh.freed, freed);
+  __syncthreads();
+  if (threadIdx.x == 0 && sh.freed) {
+    atomicAdd(&V.ctl->c[C_LIVE_VERTS], -sh.freed);
+    atomicAdd(&V.ctl->c[C_ST_FREED_VERTS], sh.freed);
+  }
+  allow_dependent_launch();
+}
+
+// Block recycling: a lane per pool slot tests it, the warp frees the candidates (the tombstones
+// it leaves are cleared by the next vertex gc's rebuild check).
 __global__ void __launch_bounds__(256) k_gc_blocks(Vol V, int consumed) {
   grid_dependency_wait();
-  if (blockIdx.x == 0 && threadIdx.x == 0) gc_lists_reset(V);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    gc_lists_reset(V);
+    if (consumed) V.ctl->c[C_N_UPDATE] = 0;  // the update set (read by nothing here) emptied
+  }
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int hw = min(__ldcg(&V.ctl->c[C_BLK_BUMP]), V.max_blocks);
@@ -378,10 +391,6 @@ __global__ void __launch_bounds__(256) k_gc_blocks(Vol V, int consumed) {
     }
   }
   gc_flush_blocks(V, freed);
-  if (last_block(V, C_DONE7)) {
-    gc_blocks_finish(V, consumed);
-    if (threadIdx.x == 0) V.ctl->c[C_DONE7] = 0;
-  }
 }
 
 }  // namespace vmk
