@@ -177,14 +177,6 @@ __device__ __forceinline__ void gc_vertices_pass(const Vol& V, int b, int stride
   }
 }
 
-__device__ __forceinline__ void gc_flush_vertices(const Vol& V, int& freed) {
-  if (freed) {
-    counter_add(V, C_LIVE_VERTS, -freed);
-    counter_add(V, C_ST_FREED_VERTS, freed);
-  }
-  freed = 0;
-}
-
 // Empty the three lists the vertex gc consumed (one thread; the block gc does it at its
 // start, after the vertex gc has ended).
 __device__ __forceinline__ void gc_lists_reset(const Vol& V) {

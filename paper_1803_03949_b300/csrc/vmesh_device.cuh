@@ -28,7 +28,6 @@
 
 #include <cooperative_groups.h>
 #include <cooperative_groups/reduce.h>
-#include <cooperative_groups/scan.h>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -88,17 +87,9 @@ enum Counter {
   C_ST_EMITTED = 35 * CLINE,
   C_ST_RELEASED = 36 * CLINE,
   C_ST_REFRESHED = 37 * CLINE,
-  C_DONE0 = 38 * CLINE,
-  C_DONE1 = 39 * CLINE,
-  C_DONE2 = 40 * CLINE,
-  C_DONE3 = 41 * CLINE,
-  C_DONE4 = 42 * CLINE,
-  C_DONE5 = 43 * CLINE,
-  C_DONE6 = 44 * CLINE,
-  C_DONE7 = 45 * CLINE,
-  C_MESH_NEXT = 46 * CLINE,  // next update-set block a mesh pass hands out (beyond one per CTA)
-  C_N_TOUCHED1 = 47 * CLINE,  // buckets collected by an odd-numbered integrate call (touched_count)
-  C_COUNT = 48 * CLINE
+  C_MESH_NEXT = 38 * CLINE,  // next update-set block a mesh pass hands out (beyond one per CTA)
+  C_N_TOUCHED1 = 39 * CLINE,  // buckets collected by an odd-numbered integrate call (touched_count)
+  C_COUNT = 40 * CLINE
 };
 
 // Count of the buckets integrate call `frame` collects.  Calls alternate between two counters,
@@ -316,17 +307,6 @@ __device__ __forceinline__ bool list_push(const Vol& V, T* list, int c_count, in
   return false;
 }
 
-// Reserve n consecutive slots of a work list per calling lane, aggregated over the calling
-// lanes; returns the first (the caller checks each slot against the capacity).
-__device__ __forceinline__ int list_reserve(const Vol& V, int c_count, int n) {
-  cg::coalesced_group g = cg::coalesced_threads();
-  const int off = cg::exclusive_scan(g, n);
-  const int last = (int)g.size() - 1;
-  int base = 0;
-  if ((int)g.thread_rank() == last) base = atomicAdd(&V.ctl->c[c_count], off + n);
-  return g.shfl(base, last) + off;
-}
-
 // Add `v` to a counter, aggregated over the calling lanes.
 __device__ __forceinline__ void counter_add(const Vol& V, int c, int v) {
   cg::coalesced_group g = cg::coalesced_threads();
@@ -365,7 +345,6 @@ __device__ __forceinline__ bool last_block_at(int* done) {
   }
   return false;
 }
-__device__ __forceinline__ bool last_block(const Vol& V, int c_done) { return last_block_at(&V.ctl->c[c_done]); }
 
 // Programmatic dependent launch: a kernel launched with programmatic stream serialization
 // may start while the previous kernel drains; it waits here (the hardware grid-dependency
