@@ -63,9 +63,9 @@ constexpr int GCV_CTAS_PER_SM = 6;
 constexpr int GCV_THREADS = 256;
 constexpr int GCV_WARPS = GCV_THREADS / 32;
 
-// Free-stack reservations of a whole CTA's pass (k_gc_vertices): every warp's counts of freed
-// vertices and of released runs per length (then their exclusive prefixes over the warps),
-// the CTA's first slot on each stack, and its freed count.  The stack tops and the vertex
+// Free-stack reservations of a whole CTA's pass (both vertex gc kernels): every warp's counts
+// of freed vertices and of released runs per length (then their exclusive prefixes over the
+// warps), the CTA's first slot on each stack, and its freed count.  The stack tops and the vertex
 // counters then take one atomic per CTA instead of one per warp.
 struct GcvCta {
   int v[GCV_WARPS];
