@@ -283,15 +283,25 @@ __device__ __forceinline__ void gc_flush_blocks(const Vol& V, int& freed) {
   freed = 0;
 }
 
-// Rebuild the hash (the whole CTA) when live plus dead buckets pass half the table.  The
-// table must be quiet: no kernel inserts, frees or looks up blocks meanwhile.
+__device__ __forceinline__ void gc_rehash_now(const Vol& V, bool need);
+
+// Whether the hash needs a rebuild: live plus dead buckets (the live-block and tombstone
+// counts) past half the table.
+__device__ __forceinline__ bool gc_rehash_needed(const Vol& V, long long live, long long tomb) {
+  return (live + tomb) * 2 > (long long)V.hmask + 1 && tomb > 0;
+}
+
+// Rebuild the hash (the whole CTA) when it needs it.  The table must be quiet: no kernel
+// inserts, frees or looks up blocks meanwhile.
 __device__ __forceinline__ void gc_rehash_if_needed(const Vol& V) {
   __shared__ int need;
-  if (threadIdx.x == 0) {
-    const long long live = V.ctl->c[C_LIVE_BLOCKS], tomb = V.ctl->c[C_TOMBS];
-    need = (live + tomb) * 2 > (long long)V.hmask + 1 && tomb > 0;
-  }
+  if (threadIdx.x == 0) need = gc_rehash_needed(V, V.ctl->c[C_LIVE_BLOCKS], V.ctl->c[C_TOMBS]);
   __syncthreads();
+  gc_rehash_now(V, need);
+}
+
+// The rebuild itself when `need` (the whole CTA; `need` uniform over it).
+__device__ __forceinline__ void gc_rehash_now(const Vol& V, bool need) {
   if (need) {
     rehash_in_cta(V);
     if (threadIdx.x == 0) {
@@ -317,13 +327,17 @@ __global__ void __launch_bounds__(GCV_THREADS, GCV_CTAS_PER_SM) k_gc_vertices(Vo
   __shared__ GcvCta sh;
   if (threadIdx.x == 0) sh.freed = 0;
   grid_dependency_wait();
-  // the hash is quiet during this kernel: the last CTA (which the lists reach last, if at all)
-  // rebuilds it when the previous block gc left live plus dead buckets past half the table
-  if (blockIdx.x == gridDim.x - 1) gc_rehash_if_needed(V);
+  // the list lengths, and the live-block and tombstone counts the previous block gc left (one
+  // round trip for all four)
   const int n = min(__ldcg(&V.ctl->c[C_N_DEAD]), V.list_cap_dead);
   const int nr = min(__ldcg(&V.ctl->c[C_N_DEADRUN]), V.list_cap_deadrun);
+  const long long live = __ldcg(&V.ctl->c[C_LIVE_BLOCKS]), tomb = __ldcg(&V.ctl->c[C_TOMBS]);
   int freed = 0;
   const int stride = gridDim.x * blockDim.x, m = max(n, nr);
+  // the hash is quiet during this kernel: the first CTA the lists do not reach (else the last)
+  // rebuilds it when live plus dead buckets passed half the table
+  if ((int)blockIdx.x == min((m + GCV_THREADS * GCV_PER_LIST - 1) / (GCV_THREADS * GCV_PER_LIST), (int)gridDim.x - 1))
+    gc_rehash_now(V, gc_rehash_needed(V, live, tomb));
   // the CTA's passes together (CTA-wide reservations)
   for (int b0 = blockIdx.x * blockDim.x; b0 < m; b0 += stride * GCV_PER_LIST) {
     gc_vertices_pass<CE>(V, b0 + (threadIdx.x & ~31), stride, n, nr, freed, &sh);
