@@ -610,9 +610,7 @@ def run_vmesh(args, rank, world, local):
     vol = Volume.from_config(vc, stream=stream)
     calib = warm_up(vol, calibrate=True)
     barrier(world)
-    clock_path = os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else None
-    with ClockSampler(local, clock_path if rank == 0 else None) as cs:
+    with ClockSampler(local, args.clock_csv if rank == 0 else None) as cs:
         ms, collected, meshed = streamed(vol)
         torch.cuda.synchronize()
     barrier(world)
@@ -735,6 +733,7 @@ def main():
                     help="time frames without per-kernel event nodes (no roofline)")
     ap.add_argument("--cpu-frames", type=int, default=200)
     ap.add_argument("--skip-forms", action="store_true", help="skip the batched and differentiable forms")
+    ap.add_argument("--clock-csv", default=None, help="also write the clock samples of the timed pass to this CSV")
     ap.add_argument("--large-frames", type=int, default=300)
     ap.add_argument("--only-large", action="store_true", help="run only the large workload's plain pass")
     ap.add_argument("--batch-scenes", type=int, default=32)
