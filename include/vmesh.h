@@ -246,8 +246,10 @@ vm_status vm_last_error(vm_volume* vol);
  * Otherwise pos, nrm, tris (and the optional edge_keys, refcount) are DEVICE buffers in
  * the vm_download_mesh layout holding at least cap_vertices / cap_triangles entries;
  * counts above those capacities give VM_ERR_INVALID_ARG with the outputs untouched.
- * The first call on each device looks up the scratch array's device address, so make it
- * before any stream capture on that device.  All calls share the one scratch array and
+ * The device that was current when the volume was created must be current (else
+ * VM_ERR_INVALID_ARG).  The first call on each device looks up the scratch array's device
+ * address, so make it before any stream capture on that device.  All calls share the one
+ * scratch array and
  * every call rewrites the parts it reads; calls whose work overlaps on the GPU (other
  * host threads, other streams) race on it and must be serialised by the caller. */
 vm_status vm_download_mesh_noalloc(vm_volume* vol, float* pos, float* nrm, int32_t* tris, uint64_t* edge_keys,

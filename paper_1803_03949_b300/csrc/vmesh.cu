@@ -2,6 +2,7 @@
 // per-frame calls, CUDA-graph replay of a whole frame, per-kernel timing and the
 // download / export paths.  All device work is the kernels in this directory.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -51,6 +52,7 @@ struct vm_volume {
   cudaStream_t stream = nullptr;      // the caller's stream: every call enqueues here
   cudaStream_t cur = nullptr;         // stream launches go to (the capture stream while capturing)
   cudaStream_t cap_stream = nullptr;  // owned non-blocking stream for graph capture
+  int device = 0;                     // the device current when the volume was created
   int num_sms = 148;
   bool advance_pending = false;
   uint32_t frame = 1;  // number of the next integrate call (consecutive: the collected-count
@@ -405,6 +407,7 @@ vm_status vm_create_volume(const vm_params* p, void* cuda_stream, vm_volume** ou
   v->cur = v->stream;
   int dev = 0;
   cudaGetDevice(&dev);
+  v->device = dev;
   cudaDeviceGetAttribute(&v->num_sms, cudaDevAttrMultiProcessorCount, dev);
   if (v->num_sms <= 0) v->num_sms = 148;
   // the mesh kernel keeps ~32 KB of shared memory per CTA: ask for the largest carveout
@@ -1045,7 +1048,10 @@ constexpr int NA_VCHUNKS = NA_MAX_VERTICES / SCAN_ITEMS;
 constexpr int NA_TCHUNKS = NA_MAX_TRIANGLES / SCAN_ITEMS;
 constexpr size_t NA_INTS = 2 * (size_t)NA_WORDS + NA_VCHUNKS + NA_TCHUNKS + 64;  // ~4.5 MB
 constexpr int NA_MAX_DEVICES = 64;
-int* na_scratch_addr[NA_MAX_DEVICES] = {nullptr};
+// Device address of na_scratch per device, filled on the first call with that device current.
+// Concurrent first calls from several host threads store the same address, so a plain atomic
+// store suffices.
+std::atomic<int*> na_scratch_addr[NA_MAX_DEVICES];
 }  // namespace
 
 static __device__ __align__(256) int na_scratch[NA_INTS];
@@ -1157,21 +1163,25 @@ extern "C" vm_status vm_download_mesh_noalloc(vm_volume* v, float* pos, float* n
   if (v->p.max_vertices > (uint32_t)NA_MAX_VERTICES || v->p.max_triangles > (uint32_t)NA_MAX_TRIANGLES)
     return VM_ERR_INVALID_ARG;  // pools larger than the static scratch covers
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) {
+  if (cudaGetDevice(&dev) != cudaSuccess) {
     (void)cudaGetLastError();
     return VM_ERR_CUDA;
   }
+  // the scratch array used is the one of the volume's device, which must be current
+  if (dev != v->device || dev < 0 || dev >= NA_MAX_DEVICES) return VM_ERR_INVALID_ARG;
   // First call on this device: look up the device address of the static scratch array.
-  if (!na_scratch_addr[dev]) {
+  int* scratch = na_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!scratch) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, na_scratch) != cudaSuccess || !p) {
       (void)cudaGetLastError();
       return VM_ERR_CUDA;
     }
-    na_scratch_addr[dev] = static_cast<int*>(p);
+    scratch = static_cast<int*>(p);
+    na_scratch_addr[dev].store(scratch, std::memory_order_release);
   }
-  unsigned* mask = reinterpret_cast<unsigned*>(na_scratch_addr[dev]);
-  int* wprefix = na_scratch_addr[dev] + NA_WORDS;
+  unsigned* mask = reinterpret_cast<unsigned*>(scratch);
+  int* wprefix = scratch + NA_WORDS;
   int* vchunk = wprefix + NA_WORDS;
   int* tchunk = vchunk + NA_VCHUNKS;
   int* totals = tchunk + NA_TCHUNKS;
