@@ -1,27 +1,36 @@
 #!/usr/bin/env python3
-"""Benchmark: integrate + incremental mesh (+ refine + gc) per depth frame on one B300.
+"""Benchmark: integrate + incremental mesh + refine + gc per depth frame on one B300.
 
-Workload: the seeded 6 x 4 x 3 m room with 20 random primitives, 640 x 480 float32
-depth (fx = fy = 525), smooth random-walk trajectory, noise sigma = 0.0012 z^2 and 2 %
-dropped pixels; voxel 8 mm, truncation 3.2 cm, 2^20 hash buckets (synthetic stand-in for
-the RGB-D sequences of the paper's Sec. VI).  A step is one frame: vm_step =
-integrate_depth + update_mesh(refine) + gc, replayed from a CUDA graph, depth already
-resident in HBM.  L2 is flushed (256 MB write) before every timed frame; each frame is
-timed with CUDA events on the volume's stream.
+Headline workload (the largest single-GPU configuration): the seeded 20 x 20 x 4 m floor of
+4 x 4 rooms with doorways and 8 primitives per room, 640 x 480 float32 depth (fx = fy = 525),
+a serpentine trajectory of 2000 frames through the doorways, noise sigma = 0.0012 z^2, 2 %
+dropped pixels and a 4.5 m sensor range; voxel 5 mm, truncation 2 cm, 2^23 hash buckets,
+pools of 2^21 blocks, 2^26 vertices, 2^27 triangles (synthetic stand-in for the RGB-D
+sequences of the paper's Sec. VI).  A step is one frame: vm_step = integrate_depth +
+update_mesh(refine) + gc, replayed from a CUDA graph, depth already resident in HBM.  The
+timed steps are frames W .. W+K-1 of the trajectory after W untimed warm-up frames.  L2 is
+flushed (256 MB write) before every timed frame; each frame is timed with CUDA events on the
+volume's stream.
 
-The same JSON line also reports the large workload ("large": the 20x20x4 m floor at 5 mm)
-and the two forms the method grows into, measured on the same GPU: "batched" (32 independent scenes of uneven sizes, one frame each per tick, five
-launches per tick from one CUDA graph, autotuned schedules, against the same scenes stepped
-one after another) and "differentiable" (forward and backward of the 60-frame sphere orbit
-with 50 leaf depth frames, against the plain path on the same frames).
+The same JSON line reports, measured in the same run on the same GPU: the whole-frame
+roofline (algorithmic bytes per frame over the frame time) beside the dominant kernel's, two
+end-to-end figures through the public API (depth from pinned host memory and the mesh size
+read back; the same plus the mesh compacted every frame, the "compress" step of Table I),
+the float32 CPU oracle on a bounded sample of the same frames, "full_sequence" (all 2000
+frames of the floor), "room" (the 6 x 4 x 3 m room at 8 mm, the previous headline), and the
+two forms the method grows into: "batched" (independent scenes of uneven sizes, one frame each
+per tick, five launches per tick from one CUDA graph, against the same scenes stepped one
+after another) and "differentiable" (forward and backward of the 60-frame sphere orbit with 50
+leaf depth frames, against the plain path on the same frames).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl vmesh|reference]
 With N > 1 (torchrun, one rank per GPU) every rank runs an independent replica on its own
-seeded scene (no data-path collective); value = frames of all ranks / max rank time.
+seeded floor (no data-path collective); value = frames of all ranks / max rank time.
 """
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -38,40 +47,50 @@ import synth  # noqa: E402
 
 METRIC = "depth frames/s (integrate+incremental mesh) and voxels/s; % of HBM peak"
 UNIT = "frames/s"
-WORKLOAD = ("room 6x4x3 m, 20 primitives, 640x480 float32 depth, voxel 8 mm, trunc 3.2 cm, 2^20 buckets; "
-            "per frame integrate + incremental mesh + refine + gc")
+FLOOR_WORKLOAD = ("floor 20x20x4 m (4x4 rooms with doorways, 8 primitives each), 640x480 float32 depth, voxel 5 mm, "
+                  "trunc 2 cm, 2^23 buckets; per frame integrate + incremental mesh + refine + gc")
+ROOM_WORKLOAD = ("room 6x4x3 m, 20 primitives, 640x480 float32 depth, voxel 8 mm, trunc 3.2 cm, 2^20 buckets; "
+                 "per frame integrate + incremental mesh + refine + gc")
+FLOOR_FRAMES = 2000  # the floor trajectory's length; the timed frames are a window of it
+NOMINAL_HBM_GBS = 8000.0  # HBM3e bandwidth quoted for B300 (the measured copy rate is the main denominator)
 L2_FLUSH_BYTES = 256 << 20
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-# Algorithmic bytes per launch of the per-frame kernels (the minimum each must move;
-# counts come from the library's device counters, per frame):
-#   k_integrate  16 B per voxel of the collected blocks (d, W read + write) + 20 B per block
-#   k_mesh       11 B per voxel of the update set (d, W read; type read; previous type
-#                write; vertex flags read) + 9 B per changed cube (type write, run slot
-#                read + write) + 52 B per emitted triangle (16 B record, 3 vertex slots,
-#                3 reference-count updates) + 56 B per released triangle (record read +
-#                write, 3 reference-count updates) + 36 B per refreshed vertex (slot read,
-#                position + normal write) + 52 B per created vertex
-#   k_alloc      4 B per depth pixel + 16 B hash bucket per collected block
-#   k_gc_blocks  29 B per block pool slot ever used (key, epoch, counts, near flag)
+# Algorithmic bytes per launch of the per-frame kernels (the minimum each must move; counts
+# come from the library's device counters, per frame):
+#   k_alloc       4 B per depth pixel + 16 B hash bucket per collected block
+#   k_integrate   16 B per voxel of the collected blocks (d, W read + write) + 20 B per block
+#   k_mesh_types  11 B per voxel of the update set (d, W read; type read; previous type write;
+#                 vertex flags read) + 36 B per refreshed vertex (slot read, position + normal
+#                 write) + 9 B per changed cube (type write, list record write)
+#   k_mesh_cubes  16 B per changed cube (list record read, run start read + write) + 52 B per
+#                 emitted triangle (16 B record, 3 vertex slots, 3 reference-count updates) +
+#                 56 B per released triangle (record read + write, 3 reference-count updates) +
+#                 52 B per created vertex (slot claim, position, normal, count, edge, flags)
+#   k_gc_vertices 29 B per freed vertex (list entry, edge, count, edge slot, flag byte, block
+#                 count, stack slot); the released runs' few bytes are left out (a lower bound)
+#   k_gc_blocks   29 B per block pool slot ever used (key, epoch, counts, near flag)
 BYTES_MODEL = {
-    "k_integrate": lambda s: 16 * 512 * s["frame_blocks"] + 20 * s["frame_blocks"],
-    "k_mesh": lambda s: (11 * 512 * s["update_blocks"] + 9 * s["changed"] + 52 * s["emitted"] + 56 * s["released"]
-                         + 36 * s["refreshed"] + 52 * s["created"]),
     "k_alloc": lambda s: 4 * s["pixels"] + 16 * s["frame_blocks"],
+    "k_integrate": lambda s: 16 * 512 * s["frame_blocks"] + 20 * s["frame_blocks"],
+    "k_mesh_types": lambda s: 11 * 512 * s["update_blocks"] + 36 * s["refreshed"] + 9 * s["changed"],
+    "k_mesh_cubes": lambda s: 16 * s["changed"] + 52 * s["emitted"] + 56 * s["released"] + 52 * s["created"],
+    "k_gc_vertices": lambda s: 29 * s["freed_vertices"],
     "k_gc_blocks": lambda s: 29 * s["high_water"],
 }
+FRAME_KERNELS = ["k_alloc", "k_integrate", "k_mesh_types", "k_mesh_cubes", "k_gc_vertices", "k_gc_blocks"]
+
+
+def frame_bytes(c):
+    return sum(BYTES_MODEL[k](c) for k in FRAME_KERNELS)
 
 
 # DRAM traffic of a kernel (dram__bytes_read.sum + dram__bytes_write.sum) relative to its byte
-# model, from the ncu capture summarised in profiles/ (kernels unchanged since that capture
-# only).  The capture runs a smaller launch (frames 30-31, ~785 update-set blocks); the
-# reported traffic scales it to this run's mean launch by the byte model.
-TRAFFIC_RATIO = {
-    "k_mesh": (1.004, "ncu --set full of frames 30-31 (15.00 MB DRAM / 14.94 MB modelled), scaled by the byte model"),
-}
+# model, from the ncu captures summarised in profiles/, per workload (kernels unchanged since
+# the capture only).  The reported traffic scales the ratio to this run's mean launch.
+TRAFFIC_RATIO = {}
 
 
 def load_peaks():
@@ -160,50 +179,62 @@ def barrier(world: int):
         dist.barrier()
 
 
-def scene_for(rank: int, frames: int):
-    # rank 0 runs the canonical seeded room sequence; other replicas use their own seeds
+def scene_for(rank: int, frames: int = FLOOR_FRAMES):
+    """The headline workload of a replica: rank 0 runs the canonical seeded floor; other replicas
+    use their own seeds.  The trajectory always has the configuration's 2000 frames (a shorter one
+    would move the camera faster); runs use a window of it."""
+    if frames > FLOOR_FRAMES:
+        raise ValueError("the floor trajectory has %d frames" % FLOOR_FRAMES)
+    return synth.floor_scene(num_frames=FLOOR_FRAMES, seed=synth.SEED_BASE + 3 + 1000 * rank)
+
+
+def room_scene_for(rank: int, frames: int):
     return synth.room_scene(num_frames=frames, seed=synth.SEED_BASE + 2 + 1000 * rank)
 
 
-def oracle_frames(scene, frames, warmup=0):
-    """Time the float32 oracle (single-threaded C) over `frames` after `warmup` frames."""
+def oracle_frames(scene, frames, warmup=0, budget_s=None):
+    """Time the float32 oracle (single-threaded C) on frames warmup .. warmup + frames - 1 (after
+    the untimed warm-up frames), stopping early once `budget_s` seconds of timed work have run
+    (at least one frame).  Returns (frames/s, voxels/s, seconds, frames timed)."""
     import oracle
 
     V = oracle.Volume.from_config(scene.volume, prec="f32")
     K = (scene.fx, scene.fy, scene.cx, scene.cy)
-    depths = [scene.depth(k) for k in range(warmup + frames)]
-    poses = []
-    for k in range(warmup + frames):
-        T = scene.pose(k).astype(np.float32)
-        Ti = synth.pose_inverse_f64(scene.pose(k)).astype(np.float32)
-        poses.append((T.astype(np.float64), Ti.astype(np.float64)))
     voxels = 0
     t_total = 0.0
+    timed = 0
     for k in range(warmup + frames):
+        d = scene.depth(k)
+        T = scene.pose(k).astype(np.float32)
+        Ti = synth.pose_inverse_f64(scene.pose(k)).astype(np.float32)
         t0 = time.perf_counter()
-        V.integrate(depths[k], K, *poses[k])
+        V.integrate(d, K, T.astype(np.float64), Ti.astype(np.float64))
         V.update_mesh(refine=True)
         V.gc()
         dt = time.perf_counter() - t0
         if k >= warmup:
             t_total += dt
+            timed += 1
             voxels += 512 * V.stats()["frame_blocks"]
-    return frames / t_total, voxels / t_total, t_total
+            if budget_s is not None and t_total >= budget_s:
+                break
+    return timed / t_total, voxels / t_total, t_total, timed
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    n = args.warmup + args.steps
-    scene = scene_for(0, n)
-    fps, vps, secs = oracle_frames(scene, args.steps, args.warmup)
-    sample = "frames %d..%d of the room sequence (after %d warm-up frames), integrate+update(refine)+gc each" % (
-        args.warmup, n - 1, args.warmup)
+    scene = scene_for(0)
+    fps, vps, secs, timed = oracle_frames(scene, args.steps, args.warmup, budget_s=args.reference_seconds)
+    sample = ("frames %d..%d of the floor sequence (after %d untimed warm-up frames), integrate+update(refine)+gc "
+              "each, %.1f s%s" % (args.warmup, args.warmup + timed - 1, args.warmup, secs,
+                                 "" if timed == args.steps else "; stopped after %d of the %d steps at the %.0f s budget"
+                                 % (timed, args.steps, args.reference_seconds)))
     line = {
         "impl": "reference", "metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 / fps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "impl": "float32 CPU oracle (plain single-threaded C)"},
+        "config": {"workload": FLOOR_WORKLOAD, "impl": "float32 CPU oracle (plain single-threaded C)"},
         "voxels_per_s": vps,
         "cpu_baseline": {"value": fps, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": fps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -212,7 +243,9 @@ def run_reference(args, rank, world):
 
 
 def mesh_bytes(c):
-    return BYTES_MODEL["k_mesh"](c)
+    """Bytes of the batched step's one-kernel mesh pass: both split kernels' models, less the
+    changed-cube list it does not write (8 B per changed cube each way)."""
+    return BYTES_MODEL["k_mesh_types"](c) + BYTES_MODEL["k_mesh_cubes"](c) - 16 * c["changed"]
 
 
 def run_batched(args, stream, flush, peak):
@@ -333,104 +366,12 @@ def run_batched(args, stream, flush, peak):
     }
 
 
-def run_large(args, stream, flush, peak):
-    """The large workload (BASELINE config 3): the 20x20x4 m floor of 4x4 rooms, 640x480,
-    voxel 5 mm, truncation 2 cm, 2^23 buckets; the first `--large-frames` frames after 10
-    warm-up frames of the configuration's 2000-frame trajectory (the default keeps the
-    benchmark within minutes; `--large-frames 1990` runs all of it), each
-    frame integrate + update(refine) + gc from the frame graph, enqueued back to back, L2
-    flushed before every frame.  A second pass on a fresh volume times every kernel with event
-    nodes (k_mesh and k_integrate for their roofline, all five for the per-frame breakdown)."""
-    import torch
-
-    from paper_1803_03949_b300 import Intrinsics, Volume
-
-    T, Wm = args.large_frames, 10
-    n = Wm + T
-    sc = synth.floor_scene()  # the configuration's 2000-frame trajectory, its first n frames
-    vc = sc.volume
-    if args.small_pools:  # the first few hundred frames fit; keeps profiling captures small
-        import dataclasses
-
-        vc = dataclasses.replace(vc, hash_buckets=1 << 20, max_blocks=1 << 18, max_vertices=1 << 23,
-                                 max_triangles=1 << 24)
-    dev = torch.from_numpy(np.stack([sc.depth(k) for k in range(n)])).cuda()
-    K = Intrinsics(sc.W, sc.H, sc.fx, sc.fy, sc.cx, sc.cy)
-    poses = []
-    for k in range(n):
-        T4 = sc.pose(k)
-        poses.append((T4.astype(np.float32), synth.pose_inverse_f64(T4).astype(np.float32)))
-
-    def run(timing):
-        v = Volume.from_config(vc, stream=stream)
-        for k in range(Wm):
-            v.step(dev[k], K, *poses[k], refine=True, gc=True, graph=True)
-        if timing:
-            v.enable_timing(True)
-        torch.cuda.synchronize()
-        s0 = v.stats()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(T)]
-        work = dict(update_blocks=0, frame_blocks=0, changed=0, emitted=0, released=0, refreshed=0, created=0)
-        prev = s0
-        for i, k in enumerate(range(Wm, n)):
-            flush.fill_(k)
-            evs[i][0].record(stream)
-            v.step(dev[k], K, *poses[k], refine=True, gc=True, graph=True)
-            evs[i][1].record(stream)
-            if timing:  # per-frame work counters for the byte model
-                st = v.stats()
-                work["update_blocks"] += st["update_blocks"]
-                work["frame_blocks"] += st["frame_blocks"]
-                work["changed"] += st["changed_cubes"] - prev["changed_cubes"]
-                work["emitted"] += st["emitted_triangles"] - prev["emitted_triangles"]
-                work["released"] += st["released_triangles"] - prev["released_triangles"]
-                work["refreshed"] += st["refreshed_vertices"] - prev["refreshed_vertices"]
-                work["created"] += st["created_vertices"] - prev["created_vertices"]
-                prev = st
-        torch.cuda.synchronize()
-        ms = [a.elapsed_time(b) for a, b in evs]
-        s1 = v.stats()
-        kt = v.kernel_times() if timing else {}
-        v.check()
-        v.close()
-        return ms, s0, s1, kt, work
-
-    ms, s0, s1, _, _ = run(False)
-    if args.only_large:  # one pass (profiling captures)
-        kt, work = {}, {}
-    else:
-        _, _, _, kt, work = run(True)
-    del dev
-    torch.cuda.empty_cache()
-    tot = sum(ms) / 1000.0
-    collected = (s1["collected_blocks"] - s0["collected_blocks"]) % (1 << 32)
-    roof = {}
-    for name, model in (("k_mesh", mesh_bytes), ("k_integrate", BYTES_MODEL["k_integrate"])):
-        t_ms, cnt = kt.get(name, (0.0, 0))
-        if t_ms > 0:
-            gbs = model(work) / (t_ms / 1000.0) / 1e9
-            roof[name] = {"avg_launch_us": 1000.0 * t_ms / cnt, "achieved": gbs, "peak": peak, "unit": "GB/s",
-                          "frac": gbs / peak, "bytes_per_launch": model(work) / max(cnt, 1)}
-    return {
-        "workload": "floor 20x20x4 m (4x4 rooms with doorways, 8 primitives each), 640x480 float32 depth, voxel 5 mm, "
-                    "trunc 2 cm, 2^23 buckets; per frame integrate + incremental mesh + refine + gc",
-        "frames": T, "warmup": Wm, "value": T / tot, "unit": "frames/s", "ms_per_step": 1000.0 * tot / T,
-        "voxels_per_s": 512 * collected / tot, "mean_blocks_per_frame": collected / T,
-        "live_blocks_at_end": s1["live_blocks"], "l2": "flushed before every frame (256 MB write)",
-        "roofline": roof,
-        "kernel_us_per_frame": {k: 1000.0 * t / max(c, 1) for k, (t, c) in kt.items()},
-        "work_per_frame": dict({k: v / T for k, v in work.items()},
-                               freed_vertices=(s1["freed_vertices"] - s0["freed_vertices"]) / T,
-                               freed_blocks=(s1["freed_blocks"] - s0["freed_blocks"]) / T),
-    }
-
-
 def run_differentiable(args, stream):
     """The differentiable form (BASELINE config 4 reading): the sphere orbit extended to 60
     frames, frames 0-9 integrated as constants, frames 10-59 leaf tensors; forward = the 50
     recorded integrations + one full refined mesh + download, backward = loss.backward()
     (vertex -> TSDF -> depth kernels, 50 reverse steps).  Against it: the plain path on the
-    same frames (50 integrations + full refined mesh + download).  CUDA events; median of 5."""
+    same frames (50 integrations + full refined mesh + download).  CUDA events; median of --diff-reps runs."""
     import torch
 
     from paper_1803_03949_b300 import Intrinsics, Volume, diff_mesh
@@ -455,7 +396,7 @@ def run_differentiable(args, stream):
         return (sdf ** 2).mean() + 0.1 * (1.0 - (nrm * u).sum(1)).mean()
 
     plain, fwd, bwd, nverts = [], [], [], 0
-    for rep in range(5):
+    for rep in range(args.diff_reps):
         v = Volume.from_config(sc.volume, stream=stream)
         for k in range(10):
             v.integrate(dev[k], K, *poses[k])
@@ -495,25 +436,30 @@ def run_differentiable(args, stream):
         "plain_forward_ms": med(plain), "diff_forward_ms": med(fwd), "backward_ms": med(bwd),
         "forward_overhead": med(fwd) / med(plain), "backward_over_forward": med(bwd) / med(fwd),
         "vertices": nverts, "leaf_pixels": 50 * sc.W * sc.H,
-        "timing": "CUDA events on the volume's stream, median of 5 runs, caches warm",
+        "timing": "CUDA events on the volume's stream, median of %d runs, caches warm" % args.diff_reps,
+        "backward_over_forward_p10_p90": [float(x) for x in np.quantile(np.array(bwd) / np.array(fwd), [0.1, 0.9])],
     }
 
 
-def run_vmesh(args, rank, world, local):
+
+
+def measure(args, scene, vc, W, K, stream, flush, peak, peak_kind, world, rank, local, label, clocks=False,
+            memory=False):
+    """One workload's measurements over frames W .. W+K-1 after W warm-up frames (each pass on a
+    fresh volume, the same frames, so the same deterministic work):
+      pass 1 -- value: frames enqueued back to back, no event node inside the frame graph;
+      pass 2 -- kernels: CUDA-event pairs around every kernel of the frame, per-frame work counters
+                (the byte models); the dominant kernel's and the whole frame's rooflines;
+      pass 3 -- e2e: depth from pinned host memory, the mesh size read back every frame;
+      pass 4 -- e2e with compress: as pass 3, plus the whole mesh compacted into fresh device
+                buffers every frame (vm_mesh_counts + vm_download_mesh on the device)."""
     import torch
 
     from paper_1803_03949_b300 import Intrinsics, Volume
 
-    torch.cuda.set_device(local)
-    if args.only_large:
-        if rank == 0:
-            flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
-            print(json.dumps({"large": run_large(args, torch.cuda.current_stream(), flush, load_peaks()[0])}), flush=True)
-        return
-    n = args.warmup + args.steps
-    scene = scene_for(rank, n)
-    H, W = scene.H, scene.W
-    depth_host = torch.empty((n, H, W), dtype=torch.float32).pin_memory()
+    n = W + K
+    H, Wd = scene.H, scene.W
+    depth_host = torch.empty((n, H, Wd), dtype=torch.float32).pin_memory()
     for k in range(n):
         depth_host[k].copy_(torch.from_numpy(scene.depth(k)))
     depth_dev = depth_host.cuda()
@@ -521,47 +467,72 @@ def run_vmesh(args, rank, world, local):
     for k in range(n):
         T = scene.pose(k)
         poses.append((T.astype(np.float32), synth.pose_inverse_f64(T).astype(np.float32)))
-    K = Intrinsics(W, H, scene.fx, scene.fy, scene.cx, scene.cy)
-    stream = torch.cuda.current_stream()
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    Kc = Intrinsics(Wd, H, scene.fx, scene.fy, scene.cx, scene.cy)
     graph = not args.no_graph
-    vc = scene.volume
-    if args.small_pools:  # same workload, smaller pool allocations (profiling captures)
-        import dataclasses
-
-        vc = dataclasses.replace(vc, max_blocks=1 << 15, max_vertices=1 << 21, max_triangles=1 << 22)
 
     def warm_up(vol, calibrate=False):
-        """Frames 0..W-1, untimed.  With calibrate, every kernel is timed on frames 0..W-2
-        (a per-kernel breakdown); the last warm-up frame captures the graph without events."""
+        """Frames 0..W-1, untimed.  With calibrate, every kernel is timed on frames 0..W-2 (the
+        launch count per frame); the last warm-up frame captures the graph without events."""
         calib = {}
         if calibrate:
             vol.enable_timing(True)
-        for f in range(args.warmup):
-            if calibrate and f == args.warmup - 1:
+        for f in range(W):
+            if calibrate and f == W - 1:
                 calib = vol.kernel_times()
                 vol.enable_timing(False)
-            vol.step(depth_dev[f], K, *poses[f], refine=True, gc=True, graph=graph)
+            vol.step(depth_dev[f], Kc, *poses[f], refine=True, gc=True, graph=graph)
         torch.cuda.synchronize()
         return calib
 
-    def timed(vol, timing_kernels=()):
-        """Frames W..W+K-1 one at a time, each bracketed by CUDA events on the volume's stream
-        after a 256 MB L2 flush; returns per-frame ms, per-frame work counters and kernel
-        times (the host reads the counters after every frame)."""
-        if timing_kernels:
-            vol.enable_timing(list(timing_kernels))
-        ms, counters = [], []
-        prev = vol.stats()
-        for f in range(args.warmup, n):
+    def streamed(vol, mode="device"):
+        """Frames W..W+K-1 enqueued back to back, the host never waiting between frames (as a
+        camera stream would run; mode 'compress' waits inside every frame for the mesh size):
+        per frame an L2 flush, then a CUDA-event pair around the frame alone.  Returns per-frame
+        ms, the blocks collected / meshed over the run and the bytes copied per frame."""
+        res_host = torch.empty(2, dtype=torch.int32).pin_memory()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        s0 = vol.stats()
+        if mode != "compress":
+            # hold the stream while the host enqueues the frames (about 0.5 ms of GPU time per
+            # frame, outside every frame's event window), so that no window waits on the host: on
+            # a shared host, enqueue jitter (and the clock sampler's driver queries) would
+            # otherwise enter the timing
+            torch.cuda._sleep(int(min(K, 2000) * 1000000))
+        d2h = 0
+        for i, f in enumerate(range(W, n)):
             flush.fill_(f)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            vol.step(depth_dev[f], K, *poses[f], refine=True, gc=True, graph=graph)
-            e1.record(stream)
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
+            evs[i][0].record(stream)
+            if mode == "device":
+                vol.step(depth_dev[f], Kc, *poses[f], refine=True, gc=True, graph=graph)
+            else:
+                # the frame from pinned host memory: the collection kernel reads it across the host
+                # link (4 W H bytes) and keeps the device copy the later kernels read
+                vol.step(depth_host[f], Kc, *poses[f], refine=True, gc=True, graph=graph)
+                if mode == "host":
+                    vol.mesh_size_async(res_host)
+                    d2h = 8
+                else:
+                    m = vol.download(device=True)  # counts (two 4-byte reads) + on-device compaction
+                    d2h = 16
+                    del m
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        s1 = vol.stats()
+        vol.check()
+        wrap = lambda d: d % (1 << 32)
+        return ms, wrap(s1["collected_blocks"] - s0["collected_blocks"]), wrap(
+            s1["meshed_blocks"] - s0["meshed_blocks"]), d2h
+
+    def timed_kernels(vol):
+        """Frames W..W+K-1 one at a time with event-record nodes around every kernel; the host
+        reads the work counters after every frame."""
+        vol.enable_timing(FRAME_KERNELS)
+        counters = []
+        prev = vol.stats()
+        for f in range(W, n):
+            flush.fill_(f)
+            vol.step(depth_dev[f], Kc, *poses[f], refine=True, gc=True, graph=graph)
             st = vol.stats()
             counters.append(dict(frame_blocks=st["frame_blocks"], update_blocks=st["update_blocks"],
                                  changed=st["changed_cubes"] - prev["changed_cubes"],
@@ -569,152 +540,244 @@ def run_vmesh(args, rank, world, local):
                                  released=st["released_triangles"] - prev["released_triangles"],
                                  refreshed=st["refreshed_vertices"] - prev["refreshed_vertices"],
                                  created=st["created_vertices"] - prev["created_vertices"],
-                                 high_water=st["block_high_water"], pixels=W * H))
+                                 freed_vertices=st["freed_vertices"] - prev["freed_vertices"],
+                                 freed_blocks=st["freed_blocks"] - prev["freed_blocks"],
+                                 high_water=st["block_high_water"], pixels=Wd * H))
             prev = st
-        kt = vol.kernel_times() if timing_kernels else {}
+        kt = vol.kernel_times()
         vol.check()
-        return ms, counters, kt
+        return counters, kt
 
-    def streamed(vol, e2e=False):
-        """Frames W..W+K-1 enqueued back to back, the host never waiting between frames (as
-        a camera stream would run): per frame an L2 flush, then a CUDA-event pair around the
-        frame alone.  Returns per-frame ms and the blocks collected / meshed over the run."""
-        res_host = torch.empty(2, dtype=torch.int32).pin_memory()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
-        s0 = vol.stats()
-        # hold the stream while the host enqueues the frames (about 0.5 ms of GPU time per
-        # frame, outside every frame's event window), so that no window waits on the host: on
-        # a shared host, enqueue jitter (and the clock sampler's driver queries) would
-        # otherwise enter the timing
-        torch.cuda._sleep(int(min(n - args.warmup, 2000) * 1000000))
-        for i, f in enumerate(range(args.warmup, n)):
-            flush.fill_(f)
-            evs[i][0].record(stream)
-            if e2e:
-                # the frame from pinned host memory: the collection kernel reads it across the
-                # host link (4 W H bytes) and keeps the device copy the later kernels read
-                vol.step(depth_host[f], K, *poses[f], refine=True, gc=True, graph=graph)
-                vol.mesh_size_async(res_host)
-            else:
-                vol.step(depth_dev[f], K, *poses[f], refine=True, gc=True, graph=graph)
-            evs[i][1].record(stream)
-        torch.cuda.synchronize()
-        ms = [a.elapsed_time(b) for a, b in evs]
-        s1 = vol.stats()
-        vol.check()
-        wrap = lambda d: d % (1 << 32)
-        return ms, wrap(s1["collected_blocks"] - s0["collected_blocks"]), wrap(s1["meshed_blocks"] - s0["meshed_blocks"])
-
-    # pass 1 -- the benchmark value: no event nodes inside the frame graph
+    # pass 1 -- the value: no event nodes inside the frame graph
     vol = Volume.from_config(vc, stream=stream)
     calib = warm_up(vol, calibrate=True)
     barrier(world)
-    with ClockSampler(local, args.clock_csv if rank == 0 else None) as cs:
-        ms, collected, meshed = streamed(vol)
-        torch.cuda.synchronize()
+    cs = None
+    if clocks:
+        with ClockSampler(local, args.clock_csv if rank == 0 else None) as cs:
+            ms, collected, meshed, _ = streamed(vol)
+            torch.cuda.synchronize()
+    else:
+        ms, collected, meshed, _ = streamed(vol)
     barrier(world)
-    mem = vol.mesh_memory()
+    mem = vol.mesh_memory() if memory else None
     vol.close()
+    del vol
     total_ms = sum(ms)
     max_ms = reduce_max(total_ms, world)
-    value = world * args.steps / (max_ms / 1000.0)
-    vps = 512 * collected / (total_ms / 1000.0)
+    out = {
+        "value": world * K / (max_ms / 1000.0), "unit": UNIT, "ms_per_step": max_ms / K,
+        "voxels_per_s": 512 * collected / (total_ms / 1000.0),
+        "mean_blocks_per_frame": collected / K, "mean_update_blocks_per_frame": meshed / K,
+        "frames": "%d..%d" % (W, n - 1),
+    }
+    if cs is not None:
+        out["clocks"] = cs.summary()
+    if mem is not None:
+        out["mesh_memory"] = mem
+    calib_frames = max(W - 1, 1)
+    out["launches_per_frame"] = round(sum(v[1] for v in calib.values()) / calib_frames) if calib else None
 
-    # the compact cube record on the same frames (value pass only): speed and memory
-    import dataclasses
+    # pass 2 -- kernel durations and the rooflines
+    if not args.no_kernel_timing:
+        vol = Volume.from_config(vc, stream=stream)
+        warm_up(vol)
+        counters, kt = timed_kernels(vol)
+        vol.close()
+        del vol
+        kernels = {}
+        for k in FRAME_KERNELS:
+            t_ms, cnt = kt.get(k, (0.0, 0))
+            if cnt <= 0:
+                continue
+            b = sum(BYTES_MODEL[k](c) for c in counters)
+            kernels[k] = {"avg_launch_us": 1000.0 * t_ms / cnt, "bytes_per_launch": b / cnt,
+                          "achieved": b / (t_ms / 1000.0) / 1e9, "frac": b / (t_ms / 1000.0) / 1e9 / peak}
+        dom = max(kernels, key=lambda k: kernels[k]["avg_launch_us"])
+        d = kernels[dom]
+        tr = TRAFFIC_RATIO.get((label, dom))
+        fb = sum(frame_bytes(c) for c in counters) / K
+        frame_s = (total_ms / K) / 1000.0
+        out["roofline"] = {
+            "bound": "hbm", "kernel": dom, "achieved": d["achieved"], "peak": peak, "unit": "GB/s",
+            "frac": d["achieved"] / peak, "peak_source": peak_kind,
+            "traffic": tr[0] * d["bytes_per_launch"] if tr else None, "traffic_source": tr[1] if tr else None,
+            "bytes_per_launch": d["bytes_per_launch"], "avg_launch_us": d["avg_launch_us"],
+            "timing": "CUDA events around each kernel, same frames replayed on a fresh volume",
+            "frame": {"bytes_per_frame": fb, "ms_per_frame": 1000.0 * frame_s, "achieved": fb / frame_s / 1e9,
+                      "frac_measured": fb / frame_s / 1e9 / peak, "frac_nominal": fb / frame_s / 1e9 / NOMINAL_HBM_GBS,
+                      "nominal_peak": NOMINAL_HBM_GBS,
+                      "how": "sum of the frame kernels' byte models per frame over the value pass's mean frame time"},
+            "kernels": kernels,
+        }
+        out["work_per_frame"] = {k: sum(c[k] for c in counters) / K for k in counters[0] if k != "pixels"}
 
-    volc = Volume.from_config(dataclasses.replace(vc, compact_edges=True), stream=stream)
-    warm_up(volc)
-    ms_c, _, _ = streamed(volc)
-    mem_c = volc.mesh_memory()
-    volc.close()
-    compact = {"value": args.steps / (sum(ms_c) / 1000.0), "unit": UNIT, "cube_bytes": mem_c["cube_bytes"],
-               "edge_records": mem_c["edge_records"], "bytes_in_use": mem_c["bytes_in_use"],
-               "bytes_allocated": mem_c["bytes_allocated"]}
+    # pass 3 -- end to end through the public API: pinned host depth, step, mesh size to the host
+    if not args.no_e2e:
+        vol = Volume.from_config(vc, stream=stream)
+        warm_up(vol)
+        ms3, _, _, d2h = streamed(vol, "host")
+        vol.close()
+        del vol
+        out["e2e"] = {"value": world * K / (reduce_max(sum(ms3), world) / 1000.0), "unit": UNIT,
+                      "h2d_bytes_per_step": 4 * Wd * H, "d2h_bytes_per_step": d2h,
+                      "path": "vm_step on the depth frame in pinned host memory (read across the host link by the "
+                              "collection kernel), then vm_mesh_size_async into pinned host memory, per frame"}
+        # pass 4 -- the same with the mesh compacted on the device every frame
+        vol = Volume.from_config(vc, stream=stream)
+        warm_up(vol)
+        ms4, _, _, d2h = streamed(vol, "compress")
+        vol.close()
+        del vol
+        out["e2e_compress"] = {"value": world * K / (reduce_max(sum(ms4), world) / 1000.0), "unit": UNIT,
+                               "h2d_bytes_per_step": 4 * Wd * H, "d2h_bytes_per_step": d2h,
+                               "path": "as e2e, plus the live mesh compacted every frame into dense device arrays "
+                                       "(vm_mesh_counts, then vm_download_mesh with on_device = 1: positions, "
+                                       "normals, triangles, edge keys, reference counts), the host waiting for "
+                                       "the counts"}
+    torch.cuda.empty_cache()
+    return out
 
-    # pass 2 -- kernel durations: the same frames on a fresh volume (identical, deterministic
-    # work), with CUDA-event pairs around the two kernels the calibration ranked highest
+
+def run_full_sequence(args, stream, flush):
+    """All frames of the floor trajectory after 10 warm-up frames, value pass only (frames enqueued
+    back to back, L2 flushed before each, CUDA events around each)."""
+    import torch
+
+    from paper_1803_03949_b300 import Intrinsics, Volume
+
+    sc = scene_for(0)
+    n = min(args.full_frames, FLOOR_FRAMES)
+    W = 10
+    t0 = time.time()
+    dev = torch.empty((n, sc.H, sc.W), dtype=torch.float32, device="cuda")
+    for k in range(n):
+        dev[k].copy_(torch.from_numpy(sc.depth(k)))
+    render_s = time.time() - t0
+    Kc = Intrinsics(sc.W, sc.H, sc.fx, sc.fy, sc.cx, sc.cy)
+    poses = []
+    for k in range(n):
+        T = sc.pose(k)
+        poses.append((T.astype(np.float32), synth.pose_inverse_f64(T).astype(np.float32)))
+    vol = Volume.from_config(sc.volume, stream=stream)
+    for k in range(W):
+        vol.step(dev[k], Kc, *poses[k], refine=True, gc=True, graph=True)
+    torch.cuda.synchronize()
+    s0 = vol.stats()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n - W)]
+    torch.cuda._sleep(int(min(n - W, 2000) * 1000000))
+    for i, k in enumerate(range(W, n)):
+        flush.fill_(k)
+        evs[i][0].record(stream)
+        vol.step(dev[k], Kc, *poses[k], refine=True, gc=True, graph=True)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    s1 = vol.stats()
+    vol.check()
+    vol.close()
+    del dev, vol
+    torch.cuda.empty_cache()
+    tot = sum(ms) / 1000.0
+    q = np.quantile(ms, [0.5, 0.99, 1.0])
+    collected = (s1["collected_blocks"] - s0["collected_blocks"]) % (1 << 32)
+    return {"workload": FLOOR_WORKLOAD, "frames": "%d..%d" % (W, n - 1), "value": (n - W) / tot, "unit": UNIT,
+            "ms_per_step": 1000.0 * tot / (n - W), "frame_ms_p50_p99_max": [float(x) for x in q],
+            "voxels_per_s": 512 * collected / tot, "mean_blocks_per_frame": collected / (n - W),
+            "live_blocks_at_end": s1["live_blocks"], "live_vertices_at_end": s1["live_vertices"],
+            "live_triangles_at_end": s1["live_triangles"], "rehashes": s1["rehashes"] - s0["rehashes"],
+            "l2": "flushed before every frame (256 MB write)", "render_s": render_s}
+
+
+def floor_config(args, sc):
+    vc = sc.volume
+    if args.small_pools:  # the first few hundred frames fit; keeps profiling captures small
+        vc = dataclasses.replace(vc, hash_buckets=1 << 20, max_blocks=1 << 18, max_vertices=1 << 23,
+                                 max_triangles=1 << 24)
+    return vc
+
+
+def run_vmesh(args, rank, world, local):
+    import torch
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     peak, peak_kind = load_peaks()
-    ranked = sorted((k for k in calib if k in BYTES_MODEL and calib[k][1] > 0), key=lambda k: -calib[k][0])[:2]
-    roof = None
-    if ranked and not args.no_kernel_timing:
-        vol2 = Volume.from_config(vc, stream=stream)
-        warm_up(vol2)
-        ms2, counters2, kt = timed(vol2, timing_kernels=ranked)
-        vol2.close()
-        main = {k: kt[k] for k in ranked if kt.get(k, (0, 0))[1] > 0}
-        dom = max(main, key=lambda k: main[k][0])
-        tot_ms_k, launches = main[dom]
-        bytes_total = sum(BYTES_MODEL[dom](c) for c in counters2)
-        achieved = bytes_total / (tot_ms_k / 1000.0) / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind,
-                "traffic": TRAFFIC_RATIO[dom][0] * bytes_total / max(launches, 1) if dom in TRAFFIC_RATIO else None,
-                "traffic_source": TRAFFIC_RATIO[dom][1] if dom in TRAFFIC_RATIO else None,
-                "bytes_per_launch": bytes_total / max(launches, 1),
-                "avg_launch_us": 1000.0 * tot_ms_k / max(launches, 1),
-                "timing": "CUDA events around the kernel, same frames replayed on a fresh volume"}
-        for k in main:
-            if k != dom:
-                kb = sum(BYTES_MODEL[k](c) for c in counters2)
-                roof["runner_up"] = {"kernel": k, "avg_launch_us": 1000.0 * main[k][0] / max(main[k][1], 1),
-                                     "achieved": kb / (main[k][0] / 1000.0) / 1e9}
-    # kernels per frame, counted on the calibration frames (every launch timed there)
-    calib_frames = max(args.warmup - 1, 1)
-    per_frame_launches = round(sum(v[1] for v in calib.values()) / calib_frames) if calib else None
-    launches_total = per_frame_launches * args.steps if per_frame_launches else None
-
-    # pass 3 -- end to end through the public API: pinned host depth -> device, step, result -> host
-    vol3 = Volume.from_config(vc, stream=stream)
-    warm_up(vol3)
-    ms_e2e, _, _ = streamed(vol3, e2e=True)
-    vol3.close()
-    e2e_value = world * args.steps / (reduce_max(sum(ms_e2e), world) / 1000.0)
-
+    W, K = args.warmup, args.steps
+    if W + K > FLOOR_FRAMES:
+        raise SystemExit("--warmup + --steps must not exceed the floor's %d frames" % FLOOR_FRAMES)
+    sc = scene_for(rank)
+    vc = floor_config(args, sc)
+    if args.only_headline:  # the headline's value pass alone (profiling captures)
+        args.no_kernel_timing = True
+        args.no_e2e = True
+        r = measure(args, sc, vc, W, K, stream, flush, peak, peak_kind, world, rank, local, "floor")
+        if rank == 0:
+            print(json.dumps({"floor_value_only": r}), flush=True)
+        return
+    head = measure(args, sc, vc, W, K, stream, flush, peak, peak_kind, world, rank, local, "floor", clocks=True)
     if rank != 0:
         return
     cpu = None
     if not args.skip_cpu_baseline:
-        nframes = min(args.cpu_frames, n)
-        fps, cvps, secs = oracle_frames(scene_for(0, nframes), nframes)
+        fps, cvps, secs, timed = oracle_frames(scene_for(0), FLOOR_FRAMES, budget_s=args.cpu_seconds)
         cpu = {"value": fps, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "frames 0..%d of the same room sequence, integrate+update(refine)+gc each (%.1f s)" % (
-                   nframes - 1, secs), "voxels_per_s": cvps}
-    kernel_ms = {k: round(v[0] / calib_frames, 5) for k, v in calib.items() if v[1] > 0}
+               "sample": "frames 0..%d of the same floor sequence, integrate+update(refine)+gc each (%.1f s of "
+                         "single-threaded work; the run stops at a %.0f s budget)" % (timed - 1, secs, args.cpu_seconds),
+               "voxels_per_s": cvps}
+    lpf = head.pop("launches_per_frame")
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": head.pop("value"), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": head.pop("ms_per_step"), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "frames": "%d..%d" % (args.warmup, n - 1),
-                   "graph": graph, "l2": "flushed before every timed frame (256 MB write)",
+        "config": {"workload": FLOOR_WORKLOAD, "frames": head.pop("frames"), "graph": not args.no_graph,
+                   "l2": "flushed before every timed frame (256 MB write)",
                    "submission": "frames enqueued back to back; per-frame CUDA events exclude the flush",
-                   "parallelism": "replicas" if world > 1 else "single"},
-        "voxels_per_s": vps,
-        "mean_blocks_per_frame": collected / args.steps,
-        "mean_update_blocks_per_frame": meshed / args.steps,
-        "kernel_ms_per_frame_warmup": kernel_ms,
-        "roofline": roof,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "pools": "blocks %d, vertices %d, triangles %d, buckets %d" % (
+                       vc.max_blocks, vc.max_vertices, vc.max_triangles, vc.hash_buckets)},
+        "roofline": head.pop("roofline", None),
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * W * H, "d2h_bytes_per_step": 8,
-                "path": "vm_step on the depth frame in pinned host memory (read across the host link by the "
-                        "collection kernel), then vm_mesh_size_async into pinned host memory, per frame"},
-        "gpu_launches": launches_total,
-        "clocks": cs.summary(),
-        "mesh_memory": {
-            "after_frames": n, "vertices": mem["vertices"], "triangles": mem["triangles"],
-            "per_block_extraction_vertices": mem["block_vertices"], "loose_triangle_vertices": mem["loose_vertices"],
+        "e2e": head.pop("e2e", None),
+        "e2e_compress": head.pop("e2e_compress", None),
+        "gpu_launches": lpf * K if lpf else None,
+        "clocks": head.pop("clocks"),
+    }
+    line.update(head)  # voxels_per_s, mean blocks, work per frame
+    if not args.skip_forms:
+        if not args.skip_full_sequence:
+            line["full_sequence"] = run_full_sequence(args, stream, flush)
+        rs = room_scene_for(0, args.room_warmup + args.room_steps)
+        room = measure(args, rs, rs.volume, args.room_warmup, args.room_steps, stream, flush, peak, peak_kind, 1, 0,
+                       local, "room", memory=True)
+        room["workload"] = ROOM_WORKLOAD
+        mem = room.pop("mesh_memory")
+        # the compact cube record on the same frames (value pass only): speed and memory
+        a2 = argparse.Namespace(**vars(args))
+        a2.no_kernel_timing, a2.no_e2e = True, True
+        rc = measure(a2, rs, dataclasses.replace(rs.volume, compact_edges=True), args.room_warmup, args.room_steps,
+                     stream, flush, peak, peak_kind, 1, 0, local, "room", memory=True)
+        mem_c = rc["mesh_memory"]
+        room["mesh_memory"] = {
+            "after_frames": args.room_warmup + args.room_steps, "vertices": mem["vertices"],
+            "triangles": mem["triangles"], "per_block_extraction_vertices": mem["block_vertices"],
+            "loose_triangle_vertices": mem["loose_vertices"],
             "per_block_over_ours": mem["block_vertices"] / max(mem["vertices"], 1),
             "loose_over_ours": mem["loose_vertices"] / max(mem["vertices"], 1),
             "blocks": mem["blocks"], "cube_bytes": mem["cube_bytes"], "edge_records": mem["edge_records"],
-            "paper_cube_bytes": 56,
-            "paper_compact_cube_bytes": 24, "bytes_in_use": mem["bytes_in_use"],
+            "paper_cube_bytes": 56, "paper_compact_cube_bytes": 24, "bytes_in_use": mem["bytes_in_use"],
             "bytes_allocated": mem["bytes_allocated"],
-            "compact_layout": compact,
-        },
-    }
-    if not args.skip_forms:
-        line["large"] = run_large(args, stream, flush, peak)
+            "compact_layout": {"value": rc["value"], "unit": UNIT, "cube_bytes": mem_c["cube_bytes"],
+                               "edge_records": mem_c["edge_records"], "bytes_in_use": mem_c["bytes_in_use"],
+                               "bytes_allocated": mem_c["bytes_allocated"]},
+        }
+        if not args.skip_cpu_baseline:
+            fps, cvps, secs, timed = oracle_frames(room_scene_for(0, args.room_cpu_frames), args.room_cpu_frames)
+            room["cpu_baseline"] = {"value": fps, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": "frames 0..%d of the room sequence (%.1f s)" % (timed - 1, secs),
+                                    "voxels_per_s": cvps}
+        line["room"] = room
         line["batched"] = run_batched(args, stream, flush, peak)
         line["differentiable"] = run_differentiable(args, stream)
     print(json.dumps(line), flush=True)
@@ -728,17 +791,25 @@ def main():
     ap.add_argument("--impl", choices=["vmesh", "reference"], default="vmesh")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
-    ap.add_argument("--small-pools", action="store_true", help="smaller pool allocations (ncu captures)")
+    ap.add_argument("--small-pools", action="store_true", help="smaller floor pool allocations (ncu captures)")
     ap.add_argument("--no-kernel-timing", action="store_true",
                     help="time frames without per-kernel event nodes (no roofline)")
-    ap.add_argument("--cpu-frames", type=int, default=200)
-    ap.add_argument("--skip-forms", action="store_true", help="skip the batched and differentiable forms")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the two end-to-end passes")
+    ap.add_argument("--only-headline", action="store_true", help="run only the headline's value pass")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle's timed sample")
+    ap.add_argument("--reference-seconds", type=float, default=150.0, help="budget of the reference arm's timing")
+    ap.add_argument("--skip-forms", action="store_true",
+                    help="skip the full sequence, the room and the batched and differentiable forms")
+    ap.add_argument("--skip-full-sequence", action="store_true")
+    ap.add_argument("--full-frames", type=int, default=FLOOR_FRAMES)
     ap.add_argument("--clock-csv", default=None, help="also write the clock samples of the timed pass to this CSV")
-    ap.add_argument("--large-frames", type=int, default=300)
-    ap.add_argument("--only-large", action="store_true", help="run only the large workload's plain pass")
+    ap.add_argument("--room-steps", type=int, default=300)
+    ap.add_argument("--room-warmup", type=int, default=10)
+    ap.add_argument("--room-cpu-frames", type=int, default=200)
     ap.add_argument("--batch-scenes", type=int, default=32)
     ap.add_argument("--batch-ticks", type=int, default=60)
     ap.add_argument("--batch-warmup", type=int, default=10)
+    ap.add_argument("--diff-reps", type=int, default=21)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

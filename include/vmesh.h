@@ -88,7 +88,9 @@ typedef struct {
  * (max_triangles), the per-frame collected-block list (min(max_blocks, hash_buckets)), the
  * update-set list (max_blocks), the zero-reference vertex list (2 max_vertices), the
  * released-run list (max_triangles), a free stack, the hash table, the edge-record pool
- * (max_vertices records, one per voxel that owns a vertex). */
+ * (max_vertices records, one per voxel that owns a vertex), the changed-cube list of a mesh
+ * pass (max_triangles records: a cube is listed when its effective type changes and either
+ * type has triangles). */
 typedef enum {
   VM_POOL_NONE = 0,
   VM_POOL_BLOCKS,
@@ -100,7 +102,8 @@ typedef enum {
   VM_POOL_DEAD_RUN_LIST,
   VM_POOL_FREE_STACK,
   VM_POOL_HASH,
-  VM_POOL_EDGE_RECORDS
+  VM_POOL_EDGE_RECORDS,
+  VM_POOL_CHANGED_LIST
 } vm_pool;
 
 /* Per-call counters, filled by vm_get_stats (which synchronises). */
@@ -125,6 +128,10 @@ typedef struct {
   int64_t meshed_blocks;     /* update-set sizes summed over mesh passes (kept modulo 2^32) */
   int64_t full_pool;         /* vm_pool: the capacity a VM_ERR_POOL_FULL / HASH_FULL status ran
                                 out of first (VM_POOL_NONE while the status is clear) */
+  int64_t vertex_high_water;   /* vertex pool slots ever used (below created_vertices once freed
+                                  ids are reused) */
+  int64_t triangle_high_water; /* triangle pool slots ever used (below emitted_triangles once
+                                  released runs are reused) */
 } vm_frame_stats;
 
 /* Flags of vm_update_mesh / vm_step. */

@@ -9,7 +9,8 @@ namespace vmk {
 
 constexpr int SCAN_ITEMS = 1024;  // items per CTA (256 threads x 4)
 
-// Phase 1: per-CTA count of live vertices (refcount > 0) or live triangles (x >= 0).
+// Per-CTA count of live vertices (refcount > 0) or live triangles (x >= 0), one CTA per
+// chunk of the whole pool (the allocation-free download's counting pass).
 template <bool TRI>
 __global__ void __launch_bounds__(256) k_count_live(Vol V, int* cta_counts) {
   const int n = TRI ? min(__ldcg(&V.ctl->c[C_TRI_BUMP]), V.max_triangles)
@@ -30,8 +31,8 @@ __global__ void __launch_bounds__(256) k_count_live(Vol V, int* cta_counts) {
   if (threadIdx.x == 0) cta_counts[blockIdx.x] = s;
 }
 
-// Phase 2 (one CTA): exclusive scan of the CTA counts in place; total to *total.
-__global__ void __launch_bounds__(1024) k_scan_counts(int* cta_counts, int n, int* total) {
+// Exclusive scan of n counts in place by one CTA of 1024 threads; the total to *total.
+__device__ __forceinline__ void scan_in_cta(int* cta_counts, int n, int* total) {
   __shared__ int carry;
   __shared__ int warp_sums[32];
   if (threadIdx.x == 0) carry = 0;
@@ -65,6 +66,53 @@ __global__ void __launch_bounds__(1024) k_scan_counts(int* cta_counts, int n, in
   if (threadIdx.x == 0) *total = carry;
 }
 
+// Phase 2 (one CTA): exclusive scan of the CTA counts in place; total to *total.
+__global__ void __launch_bounds__(1024) k_scan_counts(int* cta_counts, int n, int* total) {
+  scan_in_cta(cta_counts, n, total);
+}
+
+// Pool slots below the vertex (TRI false) or triangle pool's high-water mark, and their
+// chunks of SCAN_ITEMS slots: the download's kernels visit no slot above it.
+template <bool TRI>
+__device__ __forceinline__ int live_slots(const Vol& V) {
+  return TRI ? min(__ldcg(&V.ctl->c[C_TRI_BUMP]), V.max_triangles) : min(__ldcg(&V.ctl->c[C_VTX_BUMP]), V.max_vertices);
+}
+template <bool TRI>
+__device__ __forceinline__ int live_chunks(const Vol& V) {
+  return (live_slots<TRI>(V) + SCAN_ITEMS - 1) / SCAN_ITEMS;
+}
+
+// Download, phase 1: live vertices (refcount > 0) or live triangles (x >= 0) per chunk of
+// SCAN_ITEMS slots below the high-water mark (a persistent grid walks the chunks).
+template <bool TRI>
+__global__ void __launch_bounds__(256) k_chunk_counts(Vol V, int* counts) {
+  const int n = live_slots<TRI>(V);
+  const int nch = (n + SCAN_ITEMS - 1) / SCAN_ITEMS;
+  __shared__ int s;
+  if (threadIdx.x == 0) s = 0;
+  __syncthreads();
+  for (int ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+    const int base = ch * SCAN_ITEMS;
+    int cnt = 0;
+    for (int j = threadIdx.x; j < SCAN_ITEMS && base + j < n; j += 256)
+      cnt += TRI ? (V.tris[base + j].x >= 0) : (V.vref[base + j] > 0);
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&s, cnt);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      counts[ch] = s;
+      s = 0;
+    }
+    __syncthreads();
+  }
+}
+
+// Download, phase 2 (one CTA): exclusive scan of the chunk counts below the high-water mark.
+template <bool TRI>
+__global__ void __launch_bounds__(1024) k_scan_chunks(Vol V, int* counts, int* total) {
+  scan_in_cta(counts, live_chunks<TRI>(V), total);
+}
+
 __device__ __forceinline__ uint64_t edge_key_of(const Vol& V, uint32_t e) {
   const int ob = (int)(e / EPB), r = (int)(e - (uint32_t)ob * EPB), ov = r / 3, a = r - ov * 3;
   int4 k = V.bkey[ob];
@@ -73,77 +121,81 @@ __device__ __forceinline__ uint64_t edge_key_of(const Vol& V, uint32_t e) {
          ((uint64_t)(uint32_t)(gz + (1 << 19)) << 2) | (uint64_t)a;
 }
 
-// Phase 3 (vertices): stable compaction; remap[v] = new index (or -1).
+// Download, phase 3 (vertices): stable compaction; remap[v] = new index (or -1).
 __global__ void __launch_bounds__(256) k_compact_vertices(Vol V, const int* cta_offsets, int* remap, float* pos,
                                                           float* nrm, uint64_t* keys, int* refcount) {
-  const int n = min(__ldcg(&V.ctl->c[C_VTX_BUMP]), V.max_vertices);
-  const int base = blockIdx.x * SCAN_ITEMS;
-  if (base >= n) return;
+  const int n = live_slots<false>(V);
+  const int nch = (n + SCAN_ITEMS - 1) / SCAN_ITEMS;
   __shared__ int warp_tot[8];
   __shared__ int running;
-  if (threadIdx.x == 0) running = cta_offsets[blockIdx.x];
-  __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int j0 = 0; j0 < SCAN_ITEMS; j0 += 256) {
-    int v = base + j0 + threadIdx.x;
-    bool live = v < n && V.vref[v] > 0;
-    unsigned b = __ballot_sync(0xffffffffu, live);
-    if (lane == 0) warp_tot[w] = __popc(b);
+  for (int ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+    const int base = ch * SCAN_ITEMS;
+    if (threadIdx.x == 0) running = cta_offsets[ch];
     __syncthreads();
-    int off = running;
-    for (int q = 0; q < w; ++q) off += warp_tot[q];
-    off += __popc(b & ((1u << lane) - 1));
-    if (v < n) remap[v] = live ? off : -1;
-    if (live) {
-      float4 p = V.vpos[v], q4 = V.vnrm[v];
-      pos[3 * (size_t)off] = p.x; pos[3 * (size_t)off + 1] = p.y; pos[3 * (size_t)off + 2] = p.z;
-      nrm[3 * (size_t)off] = q4.x; nrm[3 * (size_t)off + 1] = q4.y; nrm[3 * (size_t)off + 2] = q4.z;
-      if (keys) keys[off] = edge_key_of(V, V.vedge[v]);
-      if (refcount) refcount[off] = V.vref[v];
+    for (int j0 = 0; j0 < SCAN_ITEMS; j0 += 256) {
+      int v = base + j0 + threadIdx.x;
+      bool live = v < n && V.vref[v] > 0;
+      unsigned b = __ballot_sync(0xffffffffu, live);
+      if (lane == 0) warp_tot[w] = __popc(b);
+      __syncthreads();
+      int off = running;
+      for (int q = 0; q < w; ++q) off += warp_tot[q];
+      off += __popc(b & ((1u << lane) - 1));
+      if (v < n) remap[v] = live ? off : -1;
+      if (live) {
+        float4 p = V.vpos[v], q4 = V.vnrm[v];
+        pos[3 * (size_t)off] = p.x; pos[3 * (size_t)off + 1] = p.y; pos[3 * (size_t)off + 2] = p.z;
+        nrm[3 * (size_t)off] = q4.x; nrm[3 * (size_t)off + 1] = q4.y; nrm[3 * (size_t)off + 2] = q4.z;
+        if (keys) keys[off] = edge_key_of(V, V.vedge[v]);
+        if (refcount) refcount[off] = V.vref[v];
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int t = 0;
+        for (int q = 0; q < 8; ++q) t += warp_tot[q];
+        running += t;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int t = 0;
-      for (int q = 0; q < 8; ++q) t += warp_tot[q];
-      running += t;
-    }
-    __syncthreads();
   }
 }
 
-// Phase 3 (triangles): stable compaction with vertex indices remapped.
+// Download, phase 3 (triangles): stable compaction with vertex indices remapped.
 __global__ void __launch_bounds__(256) k_compact_triangles(Vol V, const int* cta_offsets, const int* remap,
                                                            int* tris_out) {
-  const int n = min(__ldcg(&V.ctl->c[C_TRI_BUMP]), V.max_triangles);
-  const int base = blockIdx.x * SCAN_ITEMS;
-  if (base >= n) return;
+  const int n = live_slots<true>(V);
+  const int nch = (n + SCAN_ITEMS - 1) / SCAN_ITEMS;
   __shared__ int warp_tot[8];
   __shared__ int running;
-  if (threadIdx.x == 0) running = cta_offsets[blockIdx.x];
-  __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int j0 = 0; j0 < SCAN_ITEMS; j0 += 256) {
-    int t = base + j0 + threadIdx.x;
-    int4 tr = t < n ? V.tris[t] : make_int4(-1, -1, -1, -1);
-    bool live = tr.x >= 0;
-    unsigned b = __ballot_sync(0xffffffffu, live);
-    if (lane == 0) warp_tot[w] = __popc(b);
+  for (int ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+    const int base = ch * SCAN_ITEMS;
+    if (threadIdx.x == 0) running = cta_offsets[ch];
     __syncthreads();
-    int off = running;
-    for (int q = 0; q < w; ++q) off += warp_tot[q];
-    off += __popc(b & ((1u << lane) - 1));
-    if (live) {
-      tris_out[3 * (size_t)off] = remap[tr.x];
-      tris_out[3 * (size_t)off + 1] = tr.y >= 0 ? remap[tr.y] : -1;
-      tris_out[3 * (size_t)off + 2] = tr.z >= 0 ? remap[tr.z] : -1;
+    for (int j0 = 0; j0 < SCAN_ITEMS; j0 += 256) {
+      int t = base + j0 + threadIdx.x;
+      int4 tr = t < n ? V.tris[t] : make_int4(-1, -1, -1, -1);
+      bool live = tr.x >= 0;
+      unsigned b = __ballot_sync(0xffffffffu, live);
+      if (lane == 0) warp_tot[w] = __popc(b);
+      __syncthreads();
+      int off = running;
+      for (int q = 0; q < w; ++q) off += warp_tot[q];
+      off += __popc(b & ((1u << lane) - 1));
+      if (live) {
+        tris_out[3 * (size_t)off] = remap[tr.x];
+        tris_out[3 * (size_t)off + 1] = tr.y >= 0 ? remap[tr.y] : -1;
+        tris_out[3 * (size_t)off + 2] = tr.z >= 0 ? remap[tr.z] : -1;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int s = 0;
+        for (int q = 0; q < 8; ++q) s += warp_tot[q];
+        running += s;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int s = 0;
-      for (int q = 0; q < 8; ++q) s += warp_tot[q];
-      running += s;
-    }
-    __syncthreads();
   }
 }
 

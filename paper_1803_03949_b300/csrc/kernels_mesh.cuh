@@ -179,20 +179,19 @@ __device__ __forceinline__ float halo_at(const float* halo, int x, int y, int z)
   return halo[x + HALO * y + HALO * HALO * z];
 }
 
-// Vertex on the owned edge g -> g + e_a (Sec. V-C), from the halo (g at halo coordinates
-// x, y, z in 0..8): t = d0 / (d0 - d1) (0.5 when equal), clamped to [-1, 2] so refined
-// cubes extrapolate boundedly; position g l + t l e_a; normal = normalised gradient of
-// the owner cube's trilinear interpolant at the vertex, component b != a from the corners
-// g+e_b and g+e_a+e_b, 0 when either is unusable.
-__device__ __forceinline__ void edge_vertex(const float* halo, float l, int4 key, int x, int y, int z, int a,
-                                            float4* pos, float4* nrm) {
-  const int ax = a == 0, ay = a == 1, az = a == 2;
-  const float d0 = halo_at(halo, x, y, z);
-  const float d1 = halo_at(halo, x + ax, y + ay, z + az);
+// Vertex on the owned edge g -> g + e_a (Sec. V-C) at global voxel (gx, gy, gz), from the
+// values d0 = d(g), d1 = d(g + e_a) and, for the two axes b != a, q0[b] = d(g + e_b),
+// q1[b] = d(g + e_a + e_b) (NaN where W = 0 or the block is absent): t = d0 / (d0 - d1) (0.5
+// when equal), clamped to [-1, 2] so refined cubes extrapolate boundedly; position
+// g l + t l e_a; normal = normalised gradient of the owner cube's trilinear interpolant at
+// the vertex, component b != a from the corners g+e_b and g+e_a+e_b, 0 when either is
+// unusable.  Both mesh passes evaluate vertices through this one function (one operation
+// order).
+__device__ __forceinline__ void vertex_from_values(float l, int gx, int gy, int gz, int a, float d0, float d1,
+                                                   const float* q0, const float* q1, float4* pos, float4* nrm) {
   float t = d0 == d1 ? 0.5f : d0 / (d0 - d1);
   if (t < -1.0f) t = -1.0f;
   if (t > 2.0f) t = 2.0f;
-  const int gx = key.x * BS + x, gy = key.y * BS + y, gz = key.z * BS + z;
   const int ga = a == 0 ? gx : (a == 1 ? gy : gz);
   const float pa = (float)ga * l + t * l;
   const float p[3] = {a == 0 ? pa : (float)gx * l, a == 1 ? pa : (float)gy * l, a == 2 ? pa : (float)gz * l};
@@ -203,15 +202,29 @@ __device__ __forceinline__ void edge_vertex(const float* halo, float l, int4 key
       n[b] = d1 - d0;
       continue;
     }
-    const int bx = b == 0, by = b == 1, bz = b == 2;
-    const float q0 = halo_at(halo, x + bx, y + by, z + bz);
-    const float q1 = halo_at(halo, x + ax + bx, y + ay + by, z + az + bz);
-    n[b] = (!isnan(q0) && !isnan(q1)) ? (1.0f - t) * (q0 - d0) + t * (q1 - d1) : 0.0f;
+    n[b] = (!isnan(q0[b]) && !isnan(q1[b])) ? (1.0f - t) * (q0[b] - d0) + t * (q1[b] - d1) : 0.0f;
   }
   const float len = sqrtf((n[0] * n[0] + n[1] * n[1]) + n[2] * n[2]);
   *pos = make_float4(p[0], p[1], p[2], 0.0f);
   if (len > 0.0f) *nrm = make_float4(n[0] / len, n[1] / len, n[2] / len, 0.0f);
   else *nrm = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
+// The vertex of the owned edge of the voxel at halo coordinates (x, y, z) (0..8) along a,
+// from the halo of the block whose key is `key`.
+__device__ __forceinline__ void edge_vertex(const float* halo, float l, int4 key, int x, int y, int z, int a,
+                                            float4* pos, float4* nrm) {
+  const int ax = a == 0, ay = a == 1, az = a == 2;
+  const float d0 = halo_at(halo, x, y, z);
+  const float d1 = halo_at(halo, x + ax, y + ay, z + az);
+  float q0[3], q1[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    const int bx = b == 0, by = b == 1, bz = b == 2;
+    q0[b] = b == a ? 0.0f : halo_at(halo, x + bx, y + by, z + bz);
+    q1[b] = b == a ? 0.0f : halo_at(halo, x + ax + bx, y + ay + by, z + az + bz);
+  }
+  vertex_from_values(l, key.x * BS + x, key.y * BS + y, key.z * BS + z, a, d0, d1, q0, q1, pos, nrm);
 }
 
 // Id of the vertex on the edge owned by the voxel at halo coordinates (x, y, z) (0..8) along
@@ -688,30 +701,6 @@ __device__ __forceinline__ void mesh_flush(const Vol& V, MeshCounts& c) {
 __device__ __forceinline__ void mesh_begin(const Vol& V, int n) {
   V.ctl->c[C_ST_UPDATE_BLOCKS] = n;
   reinterpret_cast<unsigned*>(V.ctl->c)[C_ST_MESHED] += (unsigned)n;  // wraps modulo 2^32
-}
-
-// Every update-set block, one per CTA iteration.
-// mode: M_UPDATE (types from the current TSDF; t_{i-1} := previous effective type; refresh
-// the positions and normals of the block's existing vertices), M_REFINE (Eqs. 3-5 with the
-// stored t_{i-1}).
-template <bool CE>
-__global__ void __launch_bounds__(MESH_THREADS, mesh_ctas_per_sm(CE)) k_mesh(Vol V, int mode) {
-  __shared__ MeshSmem<CE> S;
-  mesh_tables(S, V.tri_table);
-  grid_dependency_wait();
-  const int n = min(__ldcg(&V.ctl->c[C_N_UPDATE]), V.list_cap_update);
-  if (blockIdx.x == 0 && threadIdx.x == 0) mesh_begin(V, n);
-  MeshCounts cnt;
-  // one block per CTA, then the blocks beyond the grid go to whichever CTA is free first
-  // (the cost of a block varies tenfold with its changes)
-  for (int i = blockIdx.x, k = 0; i < n; k ^= 1) {
-    mesh_block<CE>(V, S, V.update[i], mode, cnt);
-    if (threadIdx.x == 0) S.next[k] = (int)gridDim.x + atomicAdd(&V.ctl->c[C_MESH_NEXT], 1);
-    __syncthreads();
-    i = S.next[k];
-  }
-  mesh_flush(V, cnt);
-  allow_dependent_launch();
 }
 
 }  // namespace vmk

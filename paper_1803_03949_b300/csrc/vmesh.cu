@@ -17,6 +17,7 @@
 #include "kernels_io.cuh"
 #include "kernels_memory.cuh"
 #include "kernels_mesh.cuh"
+#include "kernels_mesh_split.cuh"
 #include "mc_table.h"
 #include "vmesh_device.cuh"
 
@@ -24,8 +25,9 @@ using namespace vmk;
 
 namespace {
 
-enum KernelId { K_ALLOC = 0, K_INTEGRATE, K_LIST_ALL, K_MESH, K_GC_VERTICES, K_GC_BLOCKS, K_COUNT_ };
-const char* kKernelNames[K_COUNT_] = {"k_alloc", "k_integrate", "k_list_all", "k_mesh", "k_gc_vertices", "k_gc_blocks"};
+enum KernelId { K_ALLOC = 0, K_INTEGRATE, K_LIST_ALL, K_MESH_TYPES, K_MESH_CUBES, K_GC_VERTICES, K_GC_BLOCKS, K_COUNT_ };
+const char* kKernelNames[K_COUNT_] = {"k_alloc",      "k_integrate",   "k_list_all", "k_mesh_types",
+                                      "k_mesh_cubes", "k_gc_vertices", "k_gc_blocks"};
 
 // Every allocated block joins the update set (full extraction).
 __global__ void __launch_bounds__(256) k_list_all(Vol V) {
@@ -61,8 +63,10 @@ struct vm_volume {
   size_t bytes_allocated = 0;  // device memory held through allocs
   float* depth_buf = nullptr;  // device copy of a depth frame passed in pinned host memory
   size_t depth_cap = 0;        // its capacity in floats
-  // download scratch
+  // download scratch: per-chunk counts (then offsets) of live vertices and triangles, the two
+  // totals, the vertex remap table
   int* cta_counts = nullptr;
+  int* cta_counts_t = nullptr;
   int* scan_total = nullptr;
   int* remap = nullptr;
   int cta_cap = 0;
@@ -234,11 +238,11 @@ vm_status prepare_depth(vm_volume* v, FrameParams* fp) {
 // Launch with programmatic stream serialization: the kernel may be scheduled while the
 // previous kernel in the stream drains; it waits for that kernel's results in-kernel.
 template <typename... Params, typename... Args>
-void launch_dependent(void (*kernel)(Params...), int grid, int block, cudaStream_t s, Args... args) {
+void launch_dependent(void (*kernel)(Params...), int grid, int block, size_t smem, cudaStream_t s, Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -259,7 +263,7 @@ vm_status enqueue_integrate(vm_volume* v, const FrameParams& fp) {
   vm_status st = launch(v, K_ALLOC, [&] { k_alloc<<<alloc_grid(fp), ALLOC_THREADS, 0, v->cur>>>(v->V, fp, adv); });
   if (st) return st;
   st = launch(v, K_INTEGRATE, [&] {
-    launch_dependent(k_integrate<true>, grid_for(v, INTEG_CTAS_PER_SM), INTEG_THREADS, v->cur, v->V, (const FrameParams*)&ctl->fp);
+    launch_dependent(k_integrate<true>, grid_for(v, INTEG_CTAS_PER_SM), INTEG_THREADS, 0, v->cur, v->V, (const FrameParams*)&ctl->fp);
   });
   v->advance_pending = false;
   return st;
@@ -271,15 +275,21 @@ vm_status enqueue_list_all(vm_volume* v) {
   return launch(v, K_LIST_ALL, [&] { k_list_all<<<grid_for(v, 4), 256, 0, v->cur>>>(v->V); });
 }
 
-// after_integrate: the pass directly follows an integrate call, whose first CTA resets the
-// pass's block hand-out counter; otherwise it is reset here.
+// A mesh pass: the types kernel over the update set, then the changed-cube kernel over the
+// list the first one wrote.  after_integrate: the pass directly follows an integrate call,
+// whose first CTA empties the changed-cube list; otherwise it is emptied here.
 vm_status enqueue_mesh_pass(vm_volume* v, int mode, bool after_integrate) {
   const bool ce = (v->p.flags & VM_PARAM_COMPACT_EDGES) != 0;
-  if (!after_integrate && cudaMemsetAsync(&v->V.ctl->c[C_MESH_NEXT], 0, sizeof(int), v->cur) != cudaSuccess)
+  if (!after_integrate && cudaMemsetAsync(&v->V.ctl->c[C_N_CHANGED], 0, sizeof(int), v->cur) != cudaSuccess)
     return VM_ERR_CUDA;
-  return launch(v, K_MESH, [&] {
-    launch_dependent(ce ? k_mesh<true> : k_mesh<false>, grid_for(v, mesh_ctas_per_sm(ce)), MESH_THREADS, v->cur, v->V,
-                     mode);
+  vm_status st = launch(v, K_MESH_TYPES, [&] {
+    launch_dependent(ce ? k_mesh_types<true> : k_mesh_types<false>, grid_for(v, MT_CTAS_PER_SM), MT_THREADS, 0, v->cur,
+                     v->V, mode);
+  });
+  if (st) return st;
+  return launch(v, K_MESH_CUBES, [&] {
+    launch_dependent(ce ? k_mesh_cubes<true> : k_mesh_cubes<false>, grid_for(v, MC_CTAS_PER_SM), MC_THREADS, MC_SMEM,
+                     v->cur, v->V);
   });
 }
 
@@ -295,12 +305,12 @@ vm_status enqueue_update(vm_volume* v, int flags, bool after_integrate) {
 vm_status enqueue_gc(vm_volume* v) {
   const bool ce = (v->p.flags & VM_PARAM_COMPACT_EDGES) != 0;
   vm_status st = launch(v, K_GC_VERTICES, [&] {
-    launch_dependent(ce ? k_gc_vertices<true> : k_gc_vertices<false>, grid_for(v, GCV_CTAS_PER_SM), GCV_THREADS, v->cur, v->V);
+    launch_dependent(ce ? k_gc_vertices<true> : k_gc_vertices<false>, grid_for(v, GCV_CTAS_PER_SM), GCV_THREADS, 0, v->cur, v->V);
   });
   if (st) return st;
   const int consumed = v->advance_pending ? 1 : 0;
   return launch(v, K_GC_BLOCKS,
-                [&] { launch_dependent(k_gc_blocks, grid_for(v, 2), 256, v->cur, v->V, consumed); });
+                [&] { launch_dependent(k_gc_blocks, grid_for(v, 2), 256, 0, v->cur, v->V, consumed); });
 }
 
 vm_status sync_status(vm_volume* v) {
@@ -365,17 +375,28 @@ void free_all(vm_volume* v) {
   v->cap_stream = nullptr;
 }
 
-// vertex / triangle counts through the scan kernels; leaves offsets in cta_counts
-vm_status count_live(vm_volume* v, bool tri, int* total_out) {
-  const int items = tri ? v->p.max_triangles : v->p.max_vertices;
-  const int nct = (items + SCAN_ITEMS - 1) / SCAN_ITEMS;
-  if (tri) k_count_live<true><<<nct, 256, 0, v->stream>>>(v->V, v->cta_counts);
-  else k_count_live<false><<<nct, 256, 0, v->stream>>>(v->V, v->cta_counts);
-  k_scan_counts<<<1, 1024, 0, v->stream>>>(v->cta_counts, nct, v->scan_total);
-  if (cudaGetLastError() != cudaSuccess) return VM_ERR_CUDA;
-  if (cudaMemcpyAsync(total_out, v->scan_total, sizeof(int), cudaMemcpyDeviceToHost, v->stream) != cudaSuccess)
+// Enqueue the counts of the live vertices and triangles below their pools' high-water marks:
+// per-chunk offsets in cta_counts / cta_counts_t, the totals in scan_total[0] / [1].
+vm_status enqueue_live_counts(vm_volume* v) {
+  const int grid = grid_for(v, 8);
+  k_chunk_counts<false><<<grid, 256, 0, v->stream>>>(v->V, v->cta_counts);
+  k_scan_chunks<false><<<1, 1024, 0, v->stream>>>(v->V, v->cta_counts, v->scan_total);
+  k_chunk_counts<true><<<grid, 256, 0, v->stream>>>(v->V, v->cta_counts_t);
+  k_scan_chunks<true><<<1, 1024, 0, v->stream>>>(v->V, v->cta_counts_t, v->scan_total + 1);
+  return cudaGetLastError() == cudaSuccess ? VM_OK : VM_ERR_CUDA;
+}
+
+// The live counts on the host (one synchronisation).
+vm_status live_counts(vm_volume* v, int* nv, int* nt) {
+  vm_status st = enqueue_live_counts(v);
+  if (st) return st;
+  int tot[2] = {0, 0};
+  if (cudaMemcpyAsync(tot, v->scan_total, sizeof(tot), cudaMemcpyDeviceToHost, v->stream) != cudaSuccess)
     return VM_ERR_CUDA;
-  return sync_status(v);
+  if ((st = sync_status(v))) return st;
+  *nv = tot[0];
+  *nt = tot[1];
+  return VM_OK;
 }
 
 }  // namespace
@@ -411,8 +432,12 @@ vm_status vm_create_volume(const vm_params* p, void* cuda_stream, vm_volume** ou
   cudaDeviceGetAttribute(&v->num_sms, cudaDevAttrMultiProcessorCount, dev);
   if (v->num_sms <= 0) v->num_sms = 148;
   // the mesh kernel keeps ~32 KB of shared memory per CTA: ask for the largest carveout
-  cudaFuncSetAttribute(k_mesh<false>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-  cudaFuncSetAttribute(k_mesh<true>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  cudaFuncSetAttribute(k_mesh_types<false>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  cudaFuncSetAttribute(k_mesh_types<true>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  cudaFuncSetAttribute(k_mesh_cubes<false>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  cudaFuncSetAttribute(k_mesh_cubes<true>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  cudaFuncSetAttribute(k_mesh_cubes<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MC_SMEM);
+  cudaFuncSetAttribute(k_mesh_cubes<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MC_SMEM);
   cudaFuncSetAttribute(kb_mesh<false>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   cudaFuncSetAttribute(kb_mesh<true>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   (void)cudaGetLastError();
@@ -438,6 +463,7 @@ vm_status vm_create_volume(const vm_params* p, void* cuda_stream, vm_volume** ou
   V.list_cap_update = (int)p->max_blocks;
   V.list_cap_dead = (int)((2ull * p->max_vertices) < (1ull << 31) - 1 ? 2ull * p->max_vertices : (1ull << 31) - 1);
   V.list_cap_deadrun = (int)p->max_triangles;
+  V.list_cap_chg = (int)p->max_triangles;
   const size_t NB = p->max_blocks, NV = p->max_vertices, NT = p->max_triangles;
   const bool compact = (p->flags & VM_PARAM_COMPACT_EDGES) != 0;
   bool ok = dalloc(v, &V.keys, hb, 0xFF) && dalloc(v, &V.vals, hb, 0xFF) && dalloc(v, &V.stamp, hb, 0) &&
@@ -454,6 +480,7 @@ vm_status vm_create_volume(const vm_params* p, void* cuda_stream, vm_volume** ou
             dalloc(v, &V.blk_free, NB, 0) && dalloc(v, &V.vtx_free, NV, 0) &&
             dalloc(v, &V.touched, (size_t)V.list_cap_touched, 0) && dalloc(v, &V.update, NB, 0) &&
             dalloc(v, &V.dead, (size_t)V.list_cap_dead, 0) && dalloc(v, &V.deadrun, (size_t)V.list_cap_deadrun, 0) &&
+            dalloc(v, &V.chg, (size_t)V.list_cap_chg, 0) &&
             dalloc(v, &V.ctl, 1, 0);
   for (int L = 0; L < 5 && ok; ++L) ok = dalloc(v, &V.run_free[L], (size_t)V.run_cap[L], 0);
   uint4* tt = nullptr;
@@ -648,7 +675,8 @@ static vm_status ensure_scan_scratch(vm_volume* v) {
   if (v->remap) return VM_OK;
   const int items = v->p.max_vertices > v->p.max_triangles ? v->p.max_vertices : v->p.max_triangles;
   v->cta_cap = (items + SCAN_ITEMS - 1) / SCAN_ITEMS + 1;
-  if (!dalloc(v, &v->cta_counts, (size_t)v->cta_cap, 0) || !dalloc(v, &v->scan_total, 1, 0) ||
+  if (!dalloc(v, &v->cta_counts, (size_t)v->cta_cap, 0) || !dalloc(v, &v->cta_counts_t, (size_t)v->cta_cap, 0) ||
+      !dalloc(v, &v->scan_total, 2, 0) ||
       !dalloc(v, &v->remap, v->p.max_vertices, 0xFF))
     return VM_ERR_OOM;
   return VM_OK;
@@ -659,8 +687,7 @@ vm_status vm_mesh_counts(vm_volume* v, int64_t* nv, int64_t* nt) {
   vm_status st = ensure_scan_scratch(v);
   if (st) return st;
   int a = 0, b = 0;
-  if ((st = count_live(v, false, &a))) return st;
-  if ((st = count_live(v, true, &b))) return st;
+  if ((st = live_counts(v, &a, &b))) return st;
   *nv = a;
   *nt = b;
   return VM_OK;
@@ -718,13 +745,17 @@ vm_status vm_download_mesh(vm_volume* v, float* pos, float* nrm, int32_t* tris, 
   if (!v || !pos || !nrm || !tris) return VM_ERR_INVALID_ARG;
   vm_status st = ensure_scan_scratch(v);
   if (st) return st;
+  const int grid = grid_for(v, 8);
+  if (on_device) {  // counts, offsets and both compactions in stream order; one synchronisation
+    if ((st = enqueue_live_counts(v))) return st;
+    k_compact_vertices<<<grid, 256, 0, v->stream>>>(v->V, v->cta_counts, v->remap, pos, nrm, keys, refcount);
+    k_compact_triangles<<<grid, 256, 0, v->stream>>>(v->V, v->cta_counts_t, v->remap, tris);
+    if (cudaGetLastError() != cudaSuccess) return VM_ERR_CUDA;
+    return sync_status(v);
+  }
+  // host buffers: the counts first (device staging buffers of those sizes), then the same
   int nv = 0, nt = 0;
-  // vertices: count, scan, compact (writes remap)
-  if ((st = count_live(v, false, &nv))) return st;
-  float *dpos = pos, *dnrm = nrm;
-  int32_t* dtris = tris;
-  uint64_t* dkeys = keys;
-  int32_t* dref = refcount;
+  if ((st = live_counts(v, &nv, &nt))) return st;
   std::vector<void*> tmp;
   auto tmp_alloc = [&](size_t bytes) -> void* {
     void* q = nullptr;
@@ -735,50 +766,26 @@ vm_status vm_download_mesh(vm_volume* v, float* pos, float* nrm, int32_t* tris, 
   auto cleanup = [&]() {
     for (void* q : tmp) cudaFree(q);
   };
-  if (!on_device) {
-    dpos = (float*)tmp_alloc((size_t)nv * 12);
-    dnrm = (float*)tmp_alloc((size_t)nv * 12);
-    dkeys = keys ? (uint64_t*)tmp_alloc((size_t)nv * 8) : nullptr;
-    dref = refcount ? (int32_t*)tmp_alloc((size_t)nv * 4) : nullptr;
-    if (!dpos || !dnrm || (keys && !dkeys) || (refcount && !dref)) {
-      cleanup();
-      return VM_ERR_OOM;
-    }
-  }
-  const int nctv = (v->p.max_vertices + SCAN_ITEMS - 1) / SCAN_ITEMS;
-  k_compact_vertices<<<nctv, 256, 0, v->stream>>>(v->V, v->cta_counts, v->remap, dpos, dnrm, dkeys, dref);
-  if (cudaGetLastError() != cudaSuccess) {
+  float* dpos = (float*)tmp_alloc((size_t)nv * 12);
+  float* dnrm = (float*)tmp_alloc((size_t)nv * 12);
+  uint64_t* dkeys = keys ? (uint64_t*)tmp_alloc((size_t)nv * 8) : nullptr;
+  int32_t* dref = refcount ? (int32_t*)tmp_alloc((size_t)nv * 4) : nullptr;
+  int32_t* dtris = (int32_t*)tmp_alloc((size_t)nt * 12);
+  if (!dpos || !dnrm || (keys && !dkeys) || (refcount && !dref) || !dtris) {
+    (void)cudaGetLastError();
     cleanup();
-    return VM_ERR_CUDA;
+    return VM_ERR_OOM;
   }
-  if ((st = count_live(v, true, &nt))) {
-    cleanup();
-    return st;
-  }
-  if (!on_device) {
-    dtris = (int32_t*)tmp_alloc((size_t)nt * 12);
-    if (!dtris) {
-      cleanup();
-      return VM_ERR_OOM;
-    }
-  }
-  const int nctt = (v->p.max_triangles + SCAN_ITEMS - 1) / SCAN_ITEMS;
-  k_compact_triangles<<<nctt, 256, 0, v->stream>>>(v->V, v->cta_counts, v->remap, dtris);
-  if (cudaGetLastError() != cudaSuccess) {
-    cleanup();
-    return VM_ERR_CUDA;
-  }
-  if (!on_device) {
-    cudaStreamSynchronize(v->stream);
-    bool ok = cudaMemcpy(pos, dpos, (size_t)nv * 12, cudaMemcpyDeviceToHost) == cudaSuccess &&
-              cudaMemcpy(nrm, dnrm, (size_t)nv * 12, cudaMemcpyDeviceToHost) == cudaSuccess &&
-              cudaMemcpy(tris, dtris, (size_t)nt * 12, cudaMemcpyDeviceToHost) == cudaSuccess &&
-              (!keys || cudaMemcpy(keys, dkeys, (size_t)nv * 8, cudaMemcpyDeviceToHost) == cudaSuccess) &&
-              (!refcount || cudaMemcpy(refcount, dref, (size_t)nv * 4, cudaMemcpyDeviceToHost) == cudaSuccess);
-    cleanup();
-    return ok ? VM_OK : VM_ERR_CUDA;
-  }
-  return sync_status(v);
+  k_compact_vertices<<<grid, 256, 0, v->stream>>>(v->V, v->cta_counts, v->remap, dpos, dnrm, dkeys, dref);
+  k_compact_triangles<<<grid, 256, 0, v->stream>>>(v->V, v->cta_counts_t, v->remap, dtris);
+  bool ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(v->stream) == cudaSuccess;
+  ok = ok && cudaMemcpy(pos, dpos, (size_t)nv * 12, cudaMemcpyDeviceToHost) == cudaSuccess &&
+       cudaMemcpy(nrm, dnrm, (size_t)nv * 12, cudaMemcpyDeviceToHost) == cudaSuccess &&
+       cudaMemcpy(tris, dtris, (size_t)nt * 12, cudaMemcpyDeviceToHost) == cudaSuccess &&
+       (!keys || cudaMemcpy(keys, dkeys, (size_t)nv * 8, cudaMemcpyDeviceToHost) == cudaSuccess) &&
+       (!refcount || cudaMemcpy(refcount, dref, (size_t)nv * 4, cudaMemcpyDeviceToHost) == cudaSuccess);
+  cleanup();
+  return ok ? VM_OK : VM_ERR_CUDA;
 }
 
 vm_status vm_mesh_size_async(vm_volume* v, int32_t* dst, int on_device) {
@@ -813,6 +820,8 @@ vm_status vm_get_stats(vm_volume* v, vm_frame_stats* s) {
   s->collected_blocks = (uint32_t)c[C_ST_COLLECTED];
   s->meshed_blocks = (uint32_t)c[C_ST_MESHED];
   s->full_pool = c[C_STATUS_POOL];
+  s->vertex_high_water = c[C_VTX_BUMP] < (int)v->p.max_vertices ? c[C_VTX_BUMP] : (int)v->p.max_vertices;
+  s->triangle_high_water = c[C_TRI_BUMP] < (int)v->p.max_triangles ? c[C_TRI_BUMP] : (int)v->p.max_triangles;
   return VM_OK;
 }
 
@@ -1289,16 +1298,16 @@ vm_status batch_enqueue(vm_batch* b, cudaStream_t st, const int* sc, int flags, 
     default: kb_alloc<2><<<grid, threads, 0, st>>>(b->d_vols, b->n, *b->frames); break;
   }
   if (rec) cudaEventRecord(rec->ev[1], st);
-  launch_dependent(kb_integrate, b->num_sms * sc[1], INTEG_THREADS, st, (const Vol*)b->d_vols, b->n, b->d_done);
+  launch_dependent(kb_integrate, b->num_sms * sc[1], INTEG_THREADS, 0, st, (const Vol*)b->d_vols, b->n, b->d_done);
   if (rec) cudaEventRecord(rec->ev[2], st);
-  launch_dependent(b->compact ? kb_mesh<true> : kb_mesh<false>, b->num_sms * sc[2], MESH_THREADS, st,
+  launch_dependent(b->compact ? kb_mesh<true> : kb_mesh<false>, b->num_sms * sc[2], MESH_THREADS, 0, st,
                    (const Vol*)b->d_vols, b->n, mode, b->d_done);
   if (rec) cudaEventRecord(rec->ev[3], st);
   if (flags & VM_GC) {
-    launch_dependent(b->compact ? kb_gc_vertices<true> : kb_gc_vertices<false>, b->num_sms * sc[3], 256, st,
+    launch_dependent(b->compact ? kb_gc_vertices<true> : kb_gc_vertices<false>, b->num_sms * sc[3], 256, 0, st,
                      (const Vol*)b->d_vols, b->n);
     if (rec) cudaEventRecord(rec->ev[4], st);
-    launch_dependent(kb_gc_blocks, b->num_sms * sc[4], 256, st, (const Vol*)b->d_vols, b->n, 1, b->d_done);
+    launch_dependent(kb_gc_blocks, b->num_sms * sc[4], 256, 0, st, (const Vol*)b->d_vols, b->n, 1, b->d_done);
   } else if (rec) {
     cudaEventRecord(rec->ev[4], st);
   }
