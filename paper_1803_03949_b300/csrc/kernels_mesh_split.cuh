@@ -31,7 +31,7 @@ namespace vmk {
 constexpr int MT_THREADS = 128;  // 4 cubes per thread (MT_THREADS * 4 == BV)
 constexpr int MT_WARPS = MT_THREADS / 32;
 constexpr int MT_CTAS_PER_SM = 10;
-constexpr int MT_STAGE = 2048;  // changed-cube records a CTA stages (4 blocks' worth at most)
+constexpr int MT_STAGE = 1024;  // changed-cube records a CTA stages (2 blocks' worth at most)
 constexpr int MT_STAGE_BLOCKS = 64;  // blocks whose records a stage holds
 
 // Shared state of the types pass.  The halo (floats, for the vertex refresh) and the row masks
@@ -45,7 +45,11 @@ struct __align__(16) TypesSmem {
   int nb[2][8];                     // the block and its upper neighbours
   // per halo row (y, z), bit x: d < 0, |d| < eps, unusable (W = 0 or block absent)
   uint32_t rmask[2][3][HALO * HALO];
+  uint32_t rnear[256];              // per raw type, the regular types within 3 flips (refine_near)
   int bdtri[2];                     // the block's triangle-count change
+  int nlive[2];                     // the block's own edges that carry a vertex
+  int ev[12 * MT_THREADS];          // their vertex ids, per thread and edge (strided)
+  uint16_t rlist[EPB];              // the block's live own edges (voxel * 3 + axis)
   // staged changed-cube records: stage-block index << 25 | cube << 16 | old type << 8 | new type
   // (the list record's second word is the low 16 bits: new | old << 8)
   uint32_t rec[MT_STAGE];
@@ -54,12 +58,30 @@ struct __align__(16) TypesSmem {
   int red[3][MT_WARPS];             // end-of-kernel counter sums
 };
 
-// ev[q] for a runtime q in 0..11 without indexing the register array (no local memory).
-__device__ __forceinline__ int select12(const int* ev, int q) {
-  int r = ev[0];
-#pragma unroll
-  for (int k = 1; k < 12; ++k) r = q == k ? ev[k] : r;
-  return r;
+// Per raw type: the regular types of Sec. V-F within Hamming distance 3, nearest first, ties
+// in the paper's order (3 bits each from bit 3, their count in bits 0..2).
+__device__ __forceinline__ uint32_t refine_near(int raw) {
+  uint32_t out = 0;
+  int n = 0;
+  for (int dist = 0; dist <= 3; ++dist)
+    for (int j = 0; j < 6; ++j) {
+      const int rj = (int)((0x0FF0669933CCull >> (8 * j)) & 0xFF);
+      if (__popc(raw ^ rj) == dist) out |= (uint32_t)j << (3 + 3 * n++);
+    }
+  return out | (uint32_t)n;
+}
+
+// Eqs. 3-5 as refine_type, with the candidates of `raw` taken from its refine_near entry: the
+// first admissible one is the nearest (ties: the paper's order), the same choice.
+__device__ __forceinline__ int refine_type_near(int raw, int prev, int small, uint32_t near) {
+  if (raw == 0 || raw == 255 || __popc(raw ^ prev) > 3) return raw;
+  const int n = (int)(near & 7u);
+  for (int i = 0; i < n; ++i) {
+    const int j = (int)((near >> (3 + 3 * i)) & 7u);
+    const int rj = (int)((0x0FF0669933CCull >> (8 * j)) & 0xFF);
+    if (((raw ^ rj) & ~small) == 0) return rj;
+  }
+  return raw;
 }
 
 // The 8-bit cube mask (Bourke corner order) of the cube at x from the masks of the 4 halo
@@ -116,7 +138,10 @@ __device__ __forceinline__ void types_block(const Vol& V, TypesSmem& S, int buf,
   uint32_t* rinv = S.rmask[buf][2];
   if (threadIdx.x < 8) nb[threadIdx.x] = nbv;
   for (int i = threadIdx.x; i < 3 * HALO * HALO; i += MT_THREADS) S.rmask[buf][0][i] = 0u;
-  if (threadIdx.x == 0) S.bdtri[buf] = 0;
+  if (threadIdx.x == 0) {
+    S.bdtri[buf] = 0;
+    S.nlive[buf] = 0;
+  }
   __syncthreads();
   // the neighbours' 488 halo voxels as 244 pairs adjacent along x (16 bytes each)
   float4 qn[2];
@@ -151,6 +176,17 @@ __device__ __forceinline__ void types_block(const Vol& V, TypesSmem& S, int buf,
       else
         ev[q] = live ? __ldcg(&V.edge_vtx[(ci0 + q / 3) * 3 + q % 3]) : -1;
       live12 |= (uint32_t)live << q;
+    }
+  }
+  // the block's edges that carry a vertex, listed for the refresh (spread over the CTA after
+  // the next barrier: a thread's own edges would leave the warps' lanes unevenly loaded)
+  {
+#pragma unroll
+    for (int q = 0; q < 12; ++q) S.ev[q * MT_THREADS + threadIdx.x] = ev[q];
+    const int nl = __popc(live12);
+    if (nl) {
+      int pos = atomicAdd(&S.nlive[buf], nl);
+      for (uint32_t m = live12; m; m &= m - 1) S.rlist[pos++] = (uint16_t)(3 * c0 + __ffs(m) - 1);
     }
   }
   // the halo and its row masks: this thread's 4 voxels, then its neighbour pairs
@@ -202,7 +238,7 @@ __device__ __forceinline__ void types_block(const Vol& V, TypesSmem& S, int buf,
       const int raw = cube_bits(n00, n10, n01, n11, x);
       const int prev = (prev_w >> (8 * j)) & 0xFF;
       int e = valid ? raw : 0;
-      if (valid && (mode & M_REFINE)) e = refine_type(raw, prev, cube_bits(s00, s10, s01, s11, x));
+      if (valid && (mode & M_REFINE)) e = refine_type_near(raw, prev, cube_bits(s00, s10, s01, s11, x), S.rnear[raw]);
       new_w = (new_w & ~(0xFFu << (8 * j))) | ((uint32_t)e << (8 * j));
     }
   }
@@ -235,16 +271,21 @@ __device__ __forceinline__ void types_block(const Vol& V, TypesSmem& S, int buf,
     }
     if (dtri) atomicAdd(&S.bdtri[buf], dtri);
   }
-  // the block's existing vertices (on its own edges) from the new TSDF
+  // the block's existing vertices (on its own edges) from the new TSDF, the list's entries
+  // spread over the CTA's threads
   refreshed += __popc(live12);
+  {
+    const int nlive = S.nlive[buf];
 #pragma unroll 1
-  for (uint32_t m = live12; m; m &= m - 1) {
-    const int q = __ffs(m) - 1;
-    float4 p, nn;
-    edge_vertex(halo, l, key, cx + q / 3, cy, cz, q % 3, &p, &nn);
-    const int id = select12(ev, q);
-    V.vpos[id] = p;
-    V.vnrm[id] = nn;
+    for (int i = threadIdx.x; i < nlive; i += MT_THREADS) {
+      const int e = S.rlist[i];
+      const int v = e / 3, a = e - 3 * v;  // voxel of the block, axis
+      float4 p, nn;
+      edge_vertex(halo, l, key, v & 7, (v >> 3) & 7, v >> 6, a, &p, &nn);
+      const int id = S.ev[(3 * (v & 3) + a) * MT_THREADS + (v >> 2)];
+      V.vpos[id] = p;
+      V.vnrm[id] = nn;
+    }
   }
   dtri_all += dtri;
   if (any) {
@@ -267,8 +308,10 @@ template <bool CE>
 __global__ void __launch_bounds__(MT_THREADS, MT_CTAS_PER_SM) k_mesh_types(Vol V, int mode) {
   __shared__ TypesSmem S;
   for (int i = threadIdx.x; i < 32; i += MT_THREADS) reinterpret_cast<uint4*>(S.pairs)[i] = V.tri_table[160 + i];
-  for (int i = threadIdx.x; i < 256; i += MT_THREADS)
+  for (int i = threadIdx.x; i < 256; i += MT_THREADS) {
     S.ntri[i] = (uint8_t)packed_ntri(reinterpret_cast<const uint64_t*>(V.tri_table)[i]);
+    S.rnear[i] = refine_near(i);
+  }
   if (threadIdx.x == 0) {
     S.nrec = 0;
     S.nsblk = 0;
@@ -310,28 +353,40 @@ __global__ void __launch_bounds__(MT_THREADS, MT_CTAS_PER_SM) k_mesh_types(Vol V
 // (consecutive entries mostly come from one block: they share edges and neighbour rows).  The
 // chunk's missing vertices are deduplicated in a shared hash of edge ids, so each is claimed
 // once per chunk, and every reservation on a pool or list (vertex ids, runs of each length,
-// zero-reference and released-run list slots) is made once per chunk from a CTA-wide scan:
-// a counter hit by every warp of the pass would serialise at its L2 slice.
-constexpr int MC_THREADS = 256;
+// released-run and recycling-candidate list slots) is made once per chunk from a CTA-wide
+// scan: a counter hit by every warp of the pass would serialise at its L2 slice.  A changed
+// cube moves each vertex's reference count (its degree) by the change in how many of the cube's
+// triangles use that vertex's edge, old type to new type, one reduction per edge whose use
+// changes (about 2.4x fewer than one per triangle corner on the floor workload), and nobody
+// waits for it; the vertices of the edges the cube stops using are listed as recycling
+// candidates, and gc recycles exactly the candidates whose count is zero (its claim CAS(0, -1)
+// skips the others).
+constexpr int MC_THREADS = 128;
 constexpr int MC_WARPS = MC_THREADS / 32;
-constexpr int MC_CTAS_PER_SM = 4;
-constexpr int MC_HASH = 4096;  // > 12 edges x MC_THREADS: an insert always finds a slot
+constexpr int MC_CTAS_PER_SM = 6;
+constexpr int MC_HASH = 2048;  // > 12 edges x MC_THREADS: an insert always finds a slot
+constexpr int MC_HASH_LOG2 = 11;
 
-// Quantities a chunk reserves, per warp: owned claims, zero-reference vertices, released runs,
-// new runs of length 1..5.
-enum ChunkQty { Q_CLAIM = 0, Q_ZERO, Q_RUN_REL, Q_RUN1, Q_COUNT = Q_RUN1 + 5 };
+// Quantities a chunk reserves, per warp: distinct missing edges (claims), recycling candidates,
+// released runs, new runs of length 1..5.
+enum ChunkQty { Q_CLAIM = 0, Q_CAND, Q_RUN_REL, Q_RUN1, Q_COUNT = Q_RUN1 + 5 };
 
 struct __align__(16) CubesSmem {
   alignas(16) uint64_t tri64[256];
   alignas(16) uint16_t emask[256];
+  alignas(16) uint64_t euse[256];  // per type, 3 bits per cube edge: triangles using the edge
   int sev[12 * MC_THREADS];  // per lane and cube edge: vertex id, -1 not used, <= -3 hash slot tag
   uint32_t hkey[MC_HASH];    // missing edge id + 1 (0 empty)
   int hval[MC_HASH];         // its vertex id once claimed
-  uint16_t ulist[12 * MC_THREADS];  // hash slots of the chunk's distinct missing edges
+  uint32_t ulist[12 * MC_THREADS];  // distinct missing edges: hash slot | inserting lane << 16
   int nuniq;
+  // per lane: its cube's block's neighbour row (slot 0, unused in the table, holds the block
+  // itself), read by the claims
+  alignas(16) int4 lr0[MC_THREADS];
+  alignas(16) int4 lr1[MC_THREADS];
   int wq[Q_COUNT][MC_WARPS];  // per quantity: warp totals, then their exclusive prefixes
-  int base[Q_COUNT];          // the chunk's first slot per quantity (pools: first stack index)
-  int from_stack[Q_COUNT];    // pools: entries the stack supplied; the rest from bump + ...
+  int base[Q_COUNT];          // the chunk's first slot per quantity (pools: stack top seen)
+  int from_stack[Q_COUNT];    // pools: entries the stack supplied; the rest from the bump range
   int bump[Q_COUNT];
   int red[4][MC_WARPS];
 };
@@ -394,10 +449,8 @@ __device__ __forceinline__ void chunk_reserve(const Vol& V, CubesSmem& S) {
     }
     int base = 0, fs = 0, bump = 0;
     if (tot > 0) {
-      if (q == Q_ZERO) {
-        base = atomicAdd(&V.ctl->c[C_N_DEAD], tot);
-      } else if (q == Q_RUN_REL) {
-        base = atomicAdd(&V.ctl->c[C_N_DEADRUN], tot);
+      if (q == Q_RUN_REL || q == Q_CAND) {
+        base = atomicAdd(&V.ctl->c[q == Q_RUN_REL ? C_N_DEADRUN : C_N_DEAD], tot);
       } else {  // a pool: vertex ids, or runs of length L (from the stack, then the bump range)
         const int L = q - Q_RUN1 + 1;
         const int ctop = q == Q_CLAIM ? C_VTX_TOP : run_top(L);
@@ -430,6 +483,29 @@ __device__ __forceinline__ int chunk_pool_id(const Vol& V, const CubesSmem& S, i
   return (int)b;
 }
 
+// Exclusive prefix of `cnt` over the lanes that call together and one atomicAdd of their total
+// on `counter` (by the first of them); returns this lane's first slot.
+__device__ __forceinline__ int group_reserve(int* counter, int cnt) {
+  cg::coalesced_group g = cg::coalesced_threads();
+  const int incl = cg::inclusive_scan(g, cnt, cg::plus<int>());
+  const int tot = g.shfl(incl, (int)g.size() - 1);
+  int base = 0;
+  if (g.thread_rank() == 0 && tot > 0) base = atomicAdd(counter, tot);
+  return g.shfl(base, 0) + incl - cnt;
+}
+
+// Vertex id of cube edge k in the old triangles tr (the cube's run under its old type, packed
+// triangle word w, nold triangles); -1 if no old triangle uses the edge.
+__device__ __forceinline__ int old_vertex(const int4* tr, uint64_t w, int nold, int k) {
+  int v = -1;
+#pragma unroll
+  for (int q = 14; q >= 0; --q) {
+    const int t = q / 3, j = q % 3;
+    if (t < nold && packed_edge(w, t, j) == k) v = j == 0 ? tr[t].x : (j == 1 ? tr[t].y : tr[t].z);
+  }
+  return v;
+}
+
 // Warp-exclusive prefix of x (full warp) and the warp's total, recorded for quantity q.
 __device__ __forceinline__ int warp_prefix(CubesSmem& S, int q, int x) {
   const int lane = threadIdx.x & 31;
@@ -443,37 +519,44 @@ __device__ __forceinline__ int warp_prefix(CubesSmem& S, int q, int x) {
   return incl - x;
 }
 
-// One distinct missing edge of a chunk (hash slot h, the i-th of the chunk): an id from the
-// chunk's reservation published with atomicCAS on the owner's edge slot; the winner attaches
-// the vertex and evaluates it from the new TSDF (the voxel loads travel with the CAS), a
-// loser (another chunk claimed the edge first) takes the published id and hands its spare to
-// gc.  The result goes to hval[h].  Returns whether a vertex was created.
+// One distinct missing edge of a chunk (the i-th; `ent` = hash slot | inserting lane << 16):
+// an id from the chunk's reservation published with atomicCAS on the owner's edge slot; the
+// winner attaches the vertex and evaluates it from the new TSDF (the owner cube's corners lie in
+// the inserting lane's block and its upper neighbours, whose indices are staged, so the voxel
+// loads travel with the id's), a loser (another chunk claimed the edge first) takes the
+// published id and hands its spare to gc.  The result goes to hval.  Returns whether a vertex
+// was created.
 template <bool CE>
-__device__ __forceinline__ bool claim_edge(const Vol& V, CubesSmem& S, int i, int h) {
+__device__ __forceinline__ bool claim_edge(const Vol& V, CubesSmem& S, int i, uint32_t ent) {
+  const int h = (int)(ent & 0xFFFFu), ln = (int)(ent >> 16);
   const uint32_t e = S.hkey[h] - 1u;
   const int b = (int)(e / EPB), rem = (int)(e - (uint32_t)b * EPB), vox = rem / 3, a = rem - 3 * vox;
+  const int4 r0 = S.lr0[ln], r1 = S.lr1[ln];
+  const int blk = r0.x;
+  const int4 key = __ldcg(&V.bkey[blk]);
+  // the owner block's offset from the inserting lane's block, hence the owner voxel's halo
+  // coordinates (0..8) in that block's frame
+  int o = 0;
+#pragma unroll
+  for (int k = 7; k >= 1; --k) o = nb_select(blk, r0, r1, k) == b ? k : o;
+  const int x = (o & 1) * BS + (vox & 7), y = ((o >> 1) & 1) * BS + ((vox >> 3) & 7), z = ((o >> 2) & 1) * BS + (vox >> 6);
   const int id = chunk_pool_id(V, S, Q_CLAIM, V.vtx_free, i, 1, V.max_vertices, P_VERTICES);
-  const int4 key = __ldcg(&V.bkey[b]);
-  const int4 r0 = __ldcg(reinterpret_cast<const int4*>(V.nbr + (size_t)b * 16));
-  const int4 r1 = __ldcg(reinterpret_cast<const int4*>(V.nbr + (size_t)b * 16 + 4));
+  const int ax = a == 0, ay = a == 1, az = a == 2;
+  const float d0 = global_halo(V, blk, r0, r1, x, y, z);
+  const float d1 = global_halo(V, blk, r0, r1, x + ax, y + ay, z + az);
+  float q0[3], q1[3];
+#pragma unroll
+  for (int bb = 0; bb < 3; ++bb) {
+    const int bx = bb == 0, by = bb == 1, bz = bb == 2;
+    q0[bb] = bb == a ? 0.0f : global_halo(V, blk, r0, r1, x + bx, y + by, z + bz);
+    q1[bb] = bb == a ? 0.0f : global_halo(V, blk, r0, r1, x + ax + bx, y + ay + by, z + az + bz);
+  }
   if (id < 0) {
     S.hval[h] = -1;
     return false;
   }
   int* sp = edge_slot_ptr<CE>(V, b, vox, a, true);
   const int prev = sp ? atomicCAS(sp, -1, id) : -3;
-  // the owner cube's corner values (voxel (x, y, z) of block b, halo coordinates 0..9)
-  const int x = vox & 7, y = (vox >> 3) & 7, z = vox >> 6;
-  const int ax = a == 0, ay = a == 1, az = a == 2;
-  const float d0 = global_halo(V, b, r0, r1, x, y, z);
-  const float d1 = global_halo(V, b, r0, r1, x + ax, y + ay, z + az);
-  float q0[3], q1[3];
-#pragma unroll
-  for (int bb = 0; bb < 3; ++bb) {
-    const int bx = bb == 0, by = bb == 1, bz = bb == 2;
-    q0[bb] = bb == a ? 0.0f : global_halo(V, b, r0, r1, x + bx, y + by, z + bz);
-    q1[bb] = bb == a ? 0.0f : global_halo(V, b, r0, r1, x + ax + bx, y + ay + by, z + az + bz);
-  }
   if (prev != -1) {  // another chunk claimed the edge first (or no edge record could be made)
     S.hval[h] = prev >= 0 ? prev : -1;
     V.vref[id] = 0;
@@ -509,14 +592,15 @@ __device__ __forceinline__ void cubes_chunk(const Vol& V, CubesSmem& S, int j0, 
   const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
   const uint64_t wnew = S.tri64[nw];
   const int nold = packed_ntri(S.tri64[od]), nnew = packed_ntri(wnew);
-  // the old run's start and the block's upper neighbours
+  // the old run's start, the block's key and upper neighbours
   const int obase = nold > 0 ? __ldcg(&V.tri_base[ci]) : -1;
   const int4 r0 = act ? __ldcg(reinterpret_cast<const int4*>(V.nbr + (size_t)blk * 16)) : make_int4(-1, -1, -1, -1);
   const int4 r1 = act ? __ldcg(reinterpret_cast<const int4*>(V.nbr + (size_t)blk * 16 + 4)) : make_int4(-1, -1, -1, -1);
-  // the vertex ids on the edges the new triangles use (-1 missing); the old triangles
+  S.lr0[threadIdx.x] = make_int4(blk, r0.y, r0.z, r0.w);
+  S.lr1[threadIdx.x] = r1;
+  // the vertex ids on the edges the new triangles use (-1 missing)
   const unsigned em = S.emask[nw];
   const bool rel = nold > 0 && obase >= 0;
-  int4 tr[5];
   {
     int ev[12];
 #pragma unroll
@@ -538,27 +622,14 @@ __device__ __forceinline__ void cubes_chunk(const Vol& V, CubesSmem& S, int j0, 
       }
     }
 #pragma unroll
-    for (int t = 0; t < 5; ++t) tr[t] = rel && t < nold ? __ldcg(&V.tris[obase + t]) : make_int4(-1, -1, -1, -1);
-#pragma unroll
     for (int k = 0; k < 12; ++k) sev[k * MC_THREADS] = ev[k];
   }
-  // the old triangles' references down (issued back to back)
-  unsigned zero = 0;
-  {
-    int old[15];
+  // the old triangles; the edges the cube stops using (their vertices are recycling candidates)
+  int4 tr[5];
 #pragma unroll
-    for (int k = 0; k < 15; ++k) {
-      const int4 tt = tr[k / 3];
-      const int v = k % 3 == 0 ? tt.x : (k % 3 == 1 ? tt.y : tt.z);
-      old[k] = atom_add_if(V.vref + (v >= 0 ? v : 0), -1, v >= 0);
-    }
-#pragma unroll
-    for (int k = 0; k < 15; ++k) {
-      const int4 tt = tr[k / 3];
-      const int v = k % 3 == 0 ? tt.x : (k % 3 == 1 ? tt.y : tt.z);
-      if (v >= 0 && old[k] == 1) zero |= 1u << k;
-    }
-  }
+  for (int t = 0; t < 5; ++t) tr[t] = rel && t < nold ? __ldcg(&V.tris[obase + t]) : make_int4(-1, -1, -1, -1);
+  const uint64_t wold = S.tri64[od];
+  const unsigned cand = rel ? (unsigned)(S.emask[od] & ~em) : 0u;
   __syncthreads();  // the hash is empty
   // missing edges into the chunk's hash: the first lane to insert an edge lists it for a claim;
   // every missing edge's slot becomes a tag resolved after the claims
@@ -570,18 +641,17 @@ __device__ __forceinline__ void cubes_chunk(const Vol& V, CubesSmem& S, int j0, 
     const int hx = x + (ob & 1), hy = y + ((ob >> 1) & 1), hz = z + ((ob >> 2) & 1);
     const int b = nb_select(blk, r0, r1, (hx >> 3) | ((hy >> 3) << 1) | ((hz >> 3) << 2));
     const uint32_t e = edge_id(b, (hx & 7) + 8 * (hy & 7) + 64 * (hz & 7), ob >> 3);
-    uint32_t h = (e * 0x9E3779B1u) >> (32 - 12);  // MC_HASH = 2^12
+    uint32_t h = (e * 0x9E3779B1u) >> (32 - MC_HASH_LOG2);
     for (int p = 0; p < MC_HASH; ++p) {
       const uint32_t prev = atomicCAS(&S.hkey[h], 0u, e + 1u);
-      if (prev == 0u) S.ulist[atomicAdd(&S.nuniq, 1)] = (uint16_t)h;
+      if (prev == 0u) S.ulist[atomicAdd(&S.nuniq, 1)] = h | ((uint32_t)threadIdx.x << 16);
       if (prev == 0u || prev == e + 1u) break;
       h = (h + 1) & (MC_HASH - 1);
     }
     sev[k * MC_THREADS] = -3 - (int)h;
   }
-  // per-lane amounts, their warp prefixes, then the chunk's reservations
-  const int zc = __popc(zero);
-  const int pz = warp_prefix(S, Q_ZERO, zc);
+  // per-warp amounts, then the chunk's reservations
+  const int pc = warp_prefix(S, Q_CAND, __popc(cand));
   const unsigned relm = __ballot_sync(0xffffffffu, rel);
   if (lane == 0) S.wq[Q_RUN_REL][warp] = __popc(relm);
   int prun = 0;
@@ -594,20 +664,18 @@ __device__ __forceinline__ void cubes_chunk(const Vol& V, CubesSmem& S, int j0, 
   __syncthreads();
   chunk_reserve(V, S);
   __syncthreads();
-  // the old triangles released: the zero-reference vertices and the run listed for gc
+  // the old triangles released: cleared, the run and the recycling candidates listed for gc
   if (rel) {
-    int slot = S.base[Q_ZERO] + S.wq[Q_ZERO][warp] + pz;
-    for (unsigned zz = zero; zz; zz &= zz - 1, ++slot) {
-      const int k = __ffs(zz) - 1;
-      const int4 tt = k < 3 ? tr[0] : (k < 6 ? tr[1] : (k < 9 ? tr[2] : (k < 12 ? tr[3] : tr[4])));
-      const int v = k % 3 == 0 ? tt.x : (k % 3 == 1 ? tt.y : tt.z);
-      if (slot < V.list_cap_dead) V.dead[slot] = v;
-      else set_status(V, ST_POOL_FULL, P_DEAD_VERTEX_LIST);
-    }
     for (int t = 0; t < nold; ++t) V.tris[obase + t] = make_int4(-1, -1, -1, -1);
     const int rs = S.base[Q_RUN_REL] + S.wq[Q_RUN_REL][warp] + __popc(relm & ((1u << lane) - 1u));
     if (rs < V.list_cap_deadrun) V.deadrun[rs] = make_int2(obase, nold);
     else set_status(V, ST_POOL_FULL, P_DEAD_RUN_LIST);
+    int slot = S.base[Q_CAND] + S.wq[Q_CAND][warp] + pc;
+    for (unsigned m = cand; m; m &= m - 1, ++slot) {
+      const int v = old_vertex(tr, wold, nold, __ffs(m) - 1);
+      if (slot < V.list_cap_dead) V.dead[slot] = v;
+      else set_status(V, ST_POOL_FULL, P_DEAD_VERTEX_LIST);
+    }
     cnt.released += nold;
   }
   // the new run
@@ -639,11 +707,25 @@ __device__ __forceinline__ void cubes_chunk(const Vol& V, CubesSmem& S, int j0, 
           V.tris[base + t] = make_int4(-1, -1, -1, ci);
           continue;
         }
-        atomicAdd(&V.vref[vs[0]], 1);
-        atomicAdd(&V.vref[vs[1]], 1);
-        atomicAdd(&V.vref[vs[2]], 1);
         V.tris[base + t] = make_int4(vs[0], vs[1], vs[2], ci);
       }
+    }
+    // each edge's reference change: (triangles of the new type using it) - (of the old type);
+    // a new edge whose vertex could not be made carries no triangle and no reference
+    const uint64_t un = S.euse[nw], uo = rel ? S.euse[od] : 0ull;
+#pragma unroll 1
+    for (unsigned m = (rel ? S.emask[od] : 0u) | (base >= 0 ? em : 0u); m; m &= m - 1) {
+      const int k = __ffs(m) - 1;
+      const int d = (int)((un >> (3 * k)) & 7) * (base >= 0) - (int)((uo >> (3 * k)) & 7);
+      if (d == 0) continue;
+      int v;
+      if (base >= 0 && ((em >> k) & 1u)) {
+        v = sev[k * MC_THREADS];
+        v = v <= -3 ? S.hval[-3 - v] : v;
+      } else {
+        v = old_vertex(tr, wold, nold, k);
+      }
+      if (v >= 0) atomicAdd(&V.vref[v], d);
     }
   }
   __syncthreads();  // the chunk's shared state is free for the next chunk
@@ -658,6 +740,13 @@ __global__ void __launch_bounds__(MC_THREADS, MC_CTAS_PER_SM) k_mesh_cubes(Vol V
     const uint4 w = V.tri_table[i];
     if (i < 128) reinterpret_cast<uint4*>(S.tri64)[i] = w;
     else reinterpret_cast<uint4*>(S.emask)[i - 128] = w;
+  }
+  // per type, how many of its triangles use each cube edge
+  for (int c = threadIdx.x; c < 256; c += MC_THREADS) {
+    const uint64_t w = reinterpret_cast<const uint64_t*>(V.tri_table)[c];
+    uint64_t u = 0;
+    for (int q = 0; q < 3 * packed_ntri(w); ++q) u += 1ull << (3 * packed_edge(w, q / 3, q % 3));
+    S.euse[c] = u;
   }
   __syncthreads();
   grid_dependency_wait();
@@ -686,5 +775,6 @@ __global__ void __launch_bounds__(MC_THREADS, MC_CTAS_PER_SM) k_mesh_cubes(Vol V
 }
 
 constexpr size_t MC_SMEM = sizeof(CubesSmem);
+static_assert(MC_CTAS_PER_SM * (MC_SMEM + 1024) <= 233472, "k_mesh_cubes: CTAs per SM do not fit the SM's shared memory");
 
 }  // namespace vmk
