@@ -62,25 +62,24 @@ CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.ac
 # come from the library's device counters, per frame):
 #   k_alloc       4 B per depth pixel + 16 B hash bucket per collected block
 #   k_integrate   16 B per voxel of the collected blocks (d, W read + write) + 20 B per block
-#   k_mesh_types  11 B per voxel of the update set (d, W read; type read; previous type write;
-#                 vertex flags read) + 36 B per refreshed vertex (slot read, position + normal
-#                 write) + 9 B per changed cube (type write, list record write)
-#   k_mesh_cubes  16 B per changed cube (list record read, run start read + write) + 52 B per
-#                 emitted triangle (16 B record, 3 vertex slots, 3 reference-count updates) +
-#                 56 B per released triangle (record read + write, 3 reference-count updates) +
-#                 52 B per created vertex (slot claim, position, normal, count, edge, flags)
+#   k_mesh        11 B per voxel of the update set (d, W read; type read; previous type
+#                 write; vertex flags read) + 9 B per changed cube (type write, run slot read +
+#                 write) + 28 B per emitted triangle (16 B record, 3 vertex slots) + 32 B per
+#                 released triangle (record read + clear) + 8 B per reference-count update
+#                 (read-modify-write of a 4-byte count; one per edge whose use changes) + 36 B per
+#                 refreshed vertex (slot read, position + normal write) + 52 B per created vertex
 #   k_gc_vertices 29 B per freed vertex (list entry, edge, count, edge slot, flag byte, block
 #                 count, stack slot); the released runs' few bytes are left out (a lower bound)
 #   k_gc_blocks   29 B per block pool slot ever used (key, epoch, counts, near flag)
 BYTES_MODEL = {
     "k_alloc": lambda s: 4 * s["pixels"] + 16 * s["frame_blocks"],
     "k_integrate": lambda s: 16 * 512 * s["frame_blocks"] + 20 * s["frame_blocks"],
-    "k_mesh_types": lambda s: 11 * 512 * s["update_blocks"] + 36 * s["refreshed"] + 9 * s["changed"],
-    "k_mesh_cubes": lambda s: 16 * s["changed"] + 52 * s["emitted"] + 56 * s["released"] + 52 * s["created"],
+    "k_mesh": lambda s: (11 * 512 * s["update_blocks"] + 9 * s["changed"] + 28 * s["emitted"] + 32 * s["released"]
+                         + 8 * s["refupd"] + 36 * s["refreshed"] + 52 * s["created"]),
     "k_gc_vertices": lambda s: 29 * s["freed_vertices"],
     "k_gc_blocks": lambda s: 29 * s["high_water"],
 }
-FRAME_KERNELS = ["k_alloc", "k_integrate", "k_mesh_types", "k_mesh_cubes", "k_gc_vertices", "k_gc_blocks"]
+FRAME_KERNELS = ["k_alloc", "k_integrate", "k_mesh", "k_gc_vertices", "k_gc_blocks"]
 
 
 def frame_bytes(c):
@@ -243,9 +242,7 @@ def run_reference(args, rank, world):
 
 
 def mesh_bytes(c):
-    """Bytes of the batched step's one-kernel mesh pass: both split kernels' models, less the
-    changed-cube list it does not write (8 B per changed cube each way)."""
-    return BYTES_MODEL["k_mesh_types"](c) + BYTES_MODEL["k_mesh_cubes"](c) - 16 * c["changed"]
+    return BYTES_MODEL["k_mesh"](c)
 
 
 def run_batched(args, stream, flush, peak):
@@ -305,8 +302,9 @@ def run_batched(args, stream, flush, peak):
         batch.step_all(*tick_args(k), graph=True)
     kms = batch.kernel_ms()
     after = [v.stats() for v in vols]
-    work = dict(update_blocks=0, frame_blocks=0, changed=0, emitted=0, released=0, refreshed=0, created=0)
+    work = dict(update_blocks=0, frame_blocks=0, changed=0, emitted=0, released=0, refreshed=0, created=0, refupd=0)
     for a0, a1 in zip(before, after):
+        work["refupd"] += a1["reference_updates"] - a0["reference_updates"]
         work["update_blocks"] += (a1["meshed_blocks"] - a0["meshed_blocks"]) % (1 << 32)
         work["frame_blocks"] += (a1["collected_blocks"] - a0["collected_blocks"]) % (1 << 32)
         work["changed"] += a1["changed_cubes"] - a0["changed_cubes"]
@@ -540,6 +538,7 @@ def measure(args, scene, vc, W, K, stream, flush, peak, peak_kind, world, rank, 
                                  released=st["released_triangles"] - prev["released_triangles"],
                                  refreshed=st["refreshed_vertices"] - prev["refreshed_vertices"],
                                  created=st["created_vertices"] - prev["created_vertices"],
+                                 refupd=st["reference_updates"] - prev["reference_updates"],
                                  freed_vertices=st["freed_vertices"] - prev["freed_vertices"],
                                  freed_blocks=st["freed_blocks"] - prev["freed_blocks"],
                                  high_water=st["block_high_water"], pixels=Wd * H))

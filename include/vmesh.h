@@ -88,9 +88,7 @@ typedef struct {
  * (max_triangles), the per-frame collected-block list (min(max_blocks, hash_buckets)), the
  * update-set list (max_blocks), the zero-reference vertex list (2 max_vertices), the
  * released-run list (max_triangles), a free stack, the hash table, the edge-record pool
- * (max_vertices records, one per voxel that owns a vertex), the changed-cube list of a mesh
- * pass (max_triangles records: a cube is listed when its effective type changes and either
- * type has triangles). */
+ * (max_vertices records, one per voxel that owns a vertex). */
 typedef enum {
   VM_POOL_NONE = 0,
   VM_POOL_BLOCKS,
@@ -102,8 +100,7 @@ typedef enum {
   VM_POOL_DEAD_RUN_LIST,
   VM_POOL_FREE_STACK,
   VM_POOL_HASH,
-  VM_POOL_EDGE_RECORDS,
-  VM_POOL_CHANGED_LIST
+  VM_POOL_EDGE_RECORDS
 } vm_pool;
 
 /* Per-call counters, filled by vm_get_stats (which synchronises). */
@@ -132,6 +129,8 @@ typedef struct {
                                   ids are reused) */
   int64_t triangle_high_water; /* triangle pool slots ever used (below emitted_triangles once
                                   released runs are reused) */
+  int64_t reference_updates;   /* reference-count updates of the mesh passes so far (one per
+                                  edge of a changed cube whose use changes) */
 } vm_frame_stats;
 
 /* Flags of vm_update_mesh / vm_step. */

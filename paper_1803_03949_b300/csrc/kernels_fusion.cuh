@@ -410,14 +410,14 @@ __device__ __forceinline__ void integrate_share(const Vol& V, const FrameParams&
 }
 
 // At the start of integrate call `frame` over n collected blocks (one thread; nothing in the
-// call reads what it writes): statistics, the next call's collected count emptied, the
-// changed-cube list of the mesh pass that follows emptied.
+// call reads what it writes): statistics, the next call's collected count emptied, the mesh
+// pass's block hand-out counter reset for the pass that follows.
 __device__ __forceinline__ void integrate_begin(const Vol& V, int n, uint32_t frame) {
   V.ctl->c[C_ST_FRAME_BLOCKS] = n;
   reinterpret_cast<unsigned*>(V.ctl->c)[C_ST_COLLECTED] += (unsigned)n;  // wraps modulo 2^32
   V.ctl->c[touched_count(frame + 1)] = 0;
   V.ctl->c[C_FRAME] = (int)(frame + 1);
-  V.ctl->c[C_N_CHANGED] = 0;
+  V.ctl->c[C_MESH_NEXT] = 0;
 }
 
 // Every collected block, one per CTA iteration (FUSE = false: resolve only, for analytic

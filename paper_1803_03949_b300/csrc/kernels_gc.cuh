@@ -235,7 +235,7 @@ __device__ __forceinline__ bool gc_candidate(const Vol& V, int blk, uint32_t epo
 // cubes reach into it) has triangles: its bucket becomes a tombstone, its voxels are
 // cleared, its neighbours forget it, its index returns to the pool.  Returns (in every lane)
 // whether the block was freed.
-__device__ __forceinline__ void gc_release_block(const Vol& V, int blk);
+__device__ __forceinline__ void gc_release_block(const Vol& V, int blk, bool tomb);
 __device__ __forceinline__ bool gc_free_block(const Vol& V, int blk) {
   const int lane = threadIdx.x & 31;
   bool lower_tri = false;
@@ -244,13 +244,14 @@ __device__ __forceinline__ bool gc_free_block(const Vol& V, int blk) {
     lower_tri = nbk >= 0 && V.bntri[nbk] != 0;
   }
   if (__any_sync(0xffffffffu, lower_tri)) return false;
-  gc_release_block(V, blk);
+  gc_release_block(V, blk, true);
   return true;
 }
 
-// Free block `blk` (the calling warp; its checks passed): its bucket becomes a tombstone,
-// its voxels are cleared, its neighbours forget it, its index returns to the pool.
-__device__ __forceinline__ void gc_release_block(const Vol& V, int blk) {
+// Free block `blk` (the calling warp; its checks passed): its bucket becomes a tombstone (not
+// while the table is being rebuilt: then the block is simply not reinserted), its voxels are
+// cleared, its neighbours forget it, its index returns to the pool.
+__device__ __forceinline__ void gc_release_block(const Vol& V, int blk, bool tomb = true) {
   const int lane = threadIdx.x & 31;
   const int bucket = V.bkey[blk].w;
   float4* tw = reinterpret_cast<float4*>(V.tw + (size_t)blk * BV);
@@ -266,21 +267,41 @@ __device__ __forceinline__ void gc_release_block(const Vol& V, int blk) {
   __syncwarp();
   if (lane < 16) V.nbr[blk * 16 + lane] = -1;
   if (lane == 0) {
-    V.keys[bucket] = KEY_TOMB;
-    V.vals[bucket] = -1;
+    if (tomb) {
+      V.keys[bucket] = KEY_TOMB;
+      V.vals[bucket] = -1;
+    }
     V.bkey[blk] = make_int4(0, 0, 0, -1);
     V.bnear[blk] = 0;
     pool_push(V, V.blk_free, C_BLK_TOP, V.max_blocks, blk);
   }
 }
 
-__device__ __forceinline__ void gc_flush_blocks(const Vol& V, int& freed) {
+__device__ __forceinline__ void gc_flush_blocks(const Vol& V, int& freed, bool tomb = true) {
   if ((threadIdx.x & 31) == 0 && freed) {
     atomicSub(&V.ctl->c[C_LIVE_BLOCKS], freed);
-    atomicAdd(&V.ctl->c[C_TOMBS], freed);
+    if (tomb) atomicAdd(&V.ctl->c[C_TOMBS], freed);
     atomicAdd(&V.ctl->c[C_ST_FREED_BLOCKS], freed);
   }
   freed = 0;
+}
+
+// Insert live block `blk` (key k) into a table under rebuild: the first empty bucket from its
+// home bucket, claimed with atomicCAS (every key is distinct); its index and bucket recorded.
+__device__ __forceinline__ void rehash_insert(const Vol& V, int blk, int4 k) {
+  const uint64_t key = pack_key(k.x, k.y, k.z);
+  uint32_t s = (uint32_t)mix64(key) & V.hmask;
+  for (uint32_t p = 0; p <= V.hmask; ++p) {
+    const unsigned long long old =
+        atomicCAS((unsigned long long*)&V.keys[s], (unsigned long long)KEY_EMPTY, (unsigned long long)key);
+    if (old == KEY_EMPTY) {
+      V.vals[s] = blk;
+      V.bkey[blk].w = (int)s;
+      return;
+    }
+    s = (s + 1) & V.hmask;
+  }
+  set_status(V, ST_HASH_FULL, P_HASH);
 }
 
 __device__ __forceinline__ void gc_rehash_now(const Vol& V, bool need);
@@ -334,10 +355,19 @@ __global__ void __launch_bounds__(GCV_THREADS, GCV_CTAS_PER_SM) k_gc_vertices(Vo
   const long long live = __ldcg(&V.ctl->c[C_LIVE_BLOCKS]), tomb = __ldcg(&V.ctl->c[C_TOMBS]);
   int freed = 0;
   const int stride = gridDim.x * blockDim.x, m = max(n, nr);
-  // the hash is quiet during this kernel: the first CTA the lists do not reach (else the last)
-  // rebuilds it when live plus dead buckets passed half the table
-  if ((int)blockIdx.x == min((m + GCV_THREADS * GCV_PER_LIST - 1) / (GCV_THREADS * GCV_PER_LIST), (int)gridDim.x - 1))
-    gc_rehash_now(V, gc_rehash_needed(V, live, tomb));
+  // The hash is quiet from here until the block gc that follows: when live plus dead buckets
+  // passed half the table, every CTA clears a share of it here and the block gc reinserts the
+  // live blocks (the kernel boundary is the grid-wide barrier between the two halves).  All
+  // CTAs read the same counts, so they agree on the decision.
+  // (the counts change only in the block gc, which resets them after the rebuild)
+  const bool rehash = gc_rehash_needed(V, live, tomb);
+  if (blockIdx.x == 0 && threadIdx.x == 0) V.ctl->c[C_REHASH] = rehash ? 1 : 0;
+  if (rehash)
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s <= V.hmask; s += gridDim.x * blockDim.x) {
+      V.keys[s] = KEY_EMPTY;
+      V.vals[s] = -1;
+      V.stamp[s] = 0;
+    }
   // the CTA's passes together (CTA-wide reservations)
   for (int b0 = blockIdx.x * blockDim.x; b0 < m; b0 += stride * GCV_PER_LIST) {
     gc_vertices_pass<CE>(V, b0 + (threadIdx.x & ~31), stride, n, nr, freed, &sh);
@@ -356,10 +386,16 @@ __global__ void __launch_bounds__(GCV_THREADS, GCV_CTAS_PER_SM) k_gc_vertices(Vo
   allow_dependent_launch();
 }
 
-// Block recycling: a lane per pool slot tests it, the warp frees the candidates (the tombstones
-// it leaves are cleared by the next vertex gc's rebuild check).
+// Block recycling: a lane per pool slot tests it, the warp frees the candidates.  When the vertex
+// gc before it cleared the hash for a rebuild, freed blocks leave no tombstone and each warp
+// reinserts the live blocks of its slots after its frees.
 __global__ void __launch_bounds__(256) k_gc_blocks(Vol V, int consumed) {
   grid_dependency_wait();
+  const bool rehash = __ldcg(&V.ctl->c[C_REHASH]) != 0;
+  if (rehash && blockIdx.x == 0 && threadIdx.x == 0) {  // no tombstone survives the rebuild
+    V.ctl->c[C_TOMBS] = 0;
+    V.ctl->c[C_ST_REHASHES] += 1;
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     gc_lists_reset(V);
     if (consumed) V.ctl->c[C_N_UPDATE] = 0;  // the update set (read by nothing here) emptied
@@ -390,13 +426,18 @@ __global__ void __launch_bounds__(256) k_gc_blocks(Vol V, int consumed) {
         const int c = __shfl_sync(0xffffffffu, cb, 8 * gg);
         if (c < 0) break;
         if (((kept >> (8 * gg)) & 0xFFu) == 0) {
-          gc_release_block(V, base + c);
+          gc_release_block(V, base + c, !rehash);
           ++freed;
         }
       }
     }
+    __syncwarp();  // lane 0's frees visible to the lane that reads the slot
+    if (rehash && blk < hw) {
+      const int4 k = V.bkey[blk];
+      if (k.w >= 0) rehash_insert(V, blk, k);
+    }
   }
-  gc_flush_blocks(V, freed);
+  gc_flush_blocks(V, freed, !rehash);
 }
 
 }  // namespace vmk

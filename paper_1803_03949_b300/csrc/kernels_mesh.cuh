@@ -25,10 +25,16 @@
 //      the edge pops an id and publishes it with atomicCAS on the owner's edge slot; a
 //      thread that loses the race takes the winner's id and returns its own through the
 //      recycling list, so nobody waits and every vertex exists once; per released run the
-//      reference counts of its old triangles down; per refresh edge the vertex's position
-//      and normal from the new TSDF;
+//      old triangles cleared and the vertices of the edges the cube stops using listed as
+//      recycling candidates (their references dropped); per refresh edge the vertex's
+//      position and normal from the new TSDF;
 //   e. the released runs queued for recycling; per changed cube its new run (from the pop
-//      and its rank), its new triangles written and their references counted.
+//      and its rank), its new triangles written, and each of its edges' reference change.
+// Reference counts (a vertex's degree, Sec. V-E) move once per edge whose use changes: by
+// (triangles of the new type using the edge) - (triangles of the old type using it), with
+// reductions nobody waits for; gc recycles exactly the listed candidates whose count is zero
+// (its claim CAS(0, -1) skips the others).  On the floor workload that is 2.4x fewer atomics
+// than one per triangle corner, and the L2 atomics were the mesh pass's largest cost.
 // The paper resolves concurrent vertex creation with an atomic first-claimer lock or with
 // grouped serial launches (Sec. V-C); publishing the id with the claim replaces both.
 #pragma once
@@ -83,6 +89,7 @@ struct __align__(16) MeshSmem {
   alignas(16) uint64_t tri64[256];
   alignas(16) uint16_t emask[256];  // the cube edges each type's triangles use (bit k: edge k)
   alignas(16) uint16_t pairs[256];  // the halo's neighbour voxel pairs (halo_pairs)
+  alignas(16) uint64_t euse[256];   // per type, triangles using each cube edge (edge_use)
   int nb[8];
   int dtri;
   int nchg, ncand, nref, ndr;  // changed cubes, claim edges, refresh edges, released runs
@@ -318,8 +325,29 @@ __device__ __forceinline__ int nth_marked(const unsigned* mark, const int* count
 
 // Counters a mesh pass accumulates per CTA.
 struct MeshCounts {
-  int changed = 0, created = 0, emitted = 0, released = 0, refreshed = 0, dtri = 0;
+  int changed = 0, created = 0, emitted = 0, released = 0, refreshed = 0, dtri = 0, refupd = 0;
 };
+
+// Per type, how many of its triangles use each cube edge (3 bits per edge: a fan apex edge is
+// used by up to 5).
+__device__ __forceinline__ uint64_t edge_use(uint64_t w) {
+  uint64_t u = 0;
+  for (int q = 0; q < 3 * packed_ntri(w); ++q) u += 1ull << (3 * packed_edge(w, q / 3, q % 3));
+  return u;
+}
+__device__ __forceinline__ int use_of(uint64_t u, int k) { return (int)((u >> (3 * k)) & 7); }
+
+// Vertex id of cube edge k in the old triangles tr (the cube's run under its old type, packed
+// triangle word w, nold triangles); -1 if no old triangle uses the edge.
+__device__ __forceinline__ int old_vertex(const int4* tr, uint64_t w, int nold, int k) {
+  int v = -1;
+#pragma unroll
+  for (int q = 14; q >= 0; --q) {
+    const int t = q / 3, j = q % 3;
+    if (t < nold && packed_edge(w, t, j) == k) v = j == 0 ? tr[t].x : (j == 1 ? tr[t].y : tr[t].z);
+  }
+  return v;
+}
 
 // One update-set block `blk` through stages a-e, the calling CTA of MESH_THREADS with its
 // shared staging area S (S.tri64 already holds the triangle table).
@@ -549,24 +577,14 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem<CE>& S, int bl
       int4 tr[5];
 #pragma unroll
       for (int t = 0; t < 5; ++t) tr[t] = t < nold ? __ldcg(&V.tris[obase + t]) : make_int4(-1, -1, -1, -1);
-      // the 15 reference drops issued back to back, their results read afterwards
-      int old[15];
-#pragma unroll
-      for (int k = 0; k < 15; ++k) {
-        const int4 tt = tr[k / 3];
-        const int v = k % 3 == 0 ? tt.x : (k % 3 == 1 ? tt.y : tt.z);
-        old[k] = atom_add_if(V.vref + (v >= 0 ? v : 0), -1, v >= 0);
-      }
-      unsigned zero = 0;  // references this release dropped to zero
-#pragma unroll
-      for (int k = 0; k < 15; ++k) {
-        const int4 tt = tr[k / 3];
-        const int v = k % 3 == 0 ? tt.x : (k % 3 == 1 ? tt.y : tt.z);
-        if (v >= 0 && old[k] == 1) zero |= 1u << k;
-      }
+      // the edges the cube stops using: their references dropped, their vertices listed as
+      // recycling candidates (one recycling-list reservation for the warp)
+      const int q = i < ndr ? S.rel[i] : 0;
+      const uint64_t wold = i < ndr ? S.tri64[S.chg_old[q]] : 0ull;
+      const unsigned cand = i < ndr ? (unsigned)(S.emask[S.chg_old[q]] & ~S.emask[S.chg_new[q]]) : 0u;
+      const uint64_t uo = i < ndr ? S.euse[S.chg_old[q]] : 0ull;
       for (int t = 0; t < nold; ++t) V.tris[obase + t] = make_int4(-1, -1, -1, -1);
-      // the unreferenced vertices go to the recycling list
-      const int nz = __popc(zero);
+      const int nz = __popc(cand);
       int incl = nz;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -576,14 +594,15 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem<CE>& S, int bl
       int slot = 0;
       if (lane == 31 && incl > 0) slot = atomicAdd(&V.ctl->c[C_N_DEAD], incl);
       slot = __shfl_sync(0xffffffffu, slot, 31) + incl - nz;
-      while (zero) {
-        const int b = __ffs(zero) - 1;
-        zero &= zero - 1;
-        const int4 tt = b < 3 ? tr[0] : (b < 6 ? tr[1] : (b < 9 ? tr[2] : (b < 12 ? tr[3] : tr[4])));
-        const int k = b % 3;
-        if (slot < V.list_cap_dead) V.dead[slot] = k == 0 ? tt.x : (k == 1 ? tt.y : tt.z);
+      for (unsigned m = cand; m; m &= m - 1, ++slot) {
+        const int k = __ffs(m) - 1;
+        const int v = old_vertex(tr, wold, nold, k);  // -1 only after the vertex pool ran out
+        if (v >= 0) {
+          atomicAdd(&V.vref[v], -use_of(uo, k));
+          ++cnt.refupd;
+        }
+        if (slot < V.list_cap_dead) V.dead[slot] = v;  // gc skips -1
         else set_status(V, ST_POOL_FULL, P_DEAD_VERTEX_LIST);
-        ++slot;
       }
       cnt.released += nold;
     } else {
@@ -643,9 +662,27 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem<CE>& S, int bl
     }
     const int ci = blk * BV + c;
     V.tri_base[ci] = base;
+    const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
+    // the references of the edges the new type uses: (its triangles using the edge, none when
+    // its run could not be had) - (the old type's, when it had a run); the edges only the old
+    // type used were handled by the release
+    {
+      const uint64_t un = base >= 0 ? S.euse[S.chg_new[q]] : 0ull;
+      const uint64_t uo = S.chg_base[q] >= 0 ? S.euse[S.chg_old[q]] : 0ull;
+#pragma unroll 1
+      for (unsigned m = S.emask[S.chg_new[q]]; m; m &= m - 1) {
+        const int k = __ffs(m) - 1;
+        const int d = use_of(un, k) - use_of(uo, k);
+        if (d == 0) continue;
+        const int ob = owner_bits(k);
+        const int v = S.evid[edge_slot(x + (ob & 1), y + ((ob >> 1) & 1), z + ((ob >> 2) & 1), ob >> 3)];
+        if (v < 0) continue;
+        atomicAdd(&V.vref[v], d);
+        ++cnt.refupd;
+      }
+    }
     if (base < 0) continue;
     cnt.emitted += nt;
-    const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
 #pragma unroll 1
     for (int t = 0; t < nt; ++t) {
       int vs[3];
@@ -659,8 +696,6 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem<CE>& S, int bl
         V.tris[base + t] = make_int4(-1, -1, -1, ci);
         continue;
       }
-#pragma unroll
-      for (int jj = 0; jj < 3; ++jj) atomicAdd(&V.vref[vs[jj]], 1);
       V.tris[base + t] = make_int4(vs[0], vs[1], vs[2], ci);
     }
   }
@@ -681,6 +716,7 @@ __device__ __forceinline__ void mesh_tables(MeshSmem<CE>& S, const uint4* tables
     else if (i < 160) reinterpret_cast<uint4*>(S.emask)[i - 128] = w;
     else reinterpret_cast<uint4*>(S.pairs)[i - 160] = w;
   }
+  for (int c = threadIdx.x; c < 256; c += MESH_THREADS) S.euse[c] = edge_use(reinterpret_cast<const uint64_t*>(tables)[c]);
 }
 
 // Flush a CTA's counters into the volume's statistics.
@@ -689,6 +725,7 @@ __device__ __forceinline__ void mesh_flush(const Vol& V, MeshCounts& c) {
   if (c.emitted) counter_add(V, C_ST_EMITTED, c.emitted);
   if (c.released) counter_add(V, C_ST_RELEASED, c.released);
   if (c.refreshed) counter_add(V, C_ST_REFRESHED, c.refreshed);
+  if (c.refupd) counter_add(V, C_ST_REFUPD, c.refupd);
   if (c.dtri) counter_add(V, C_LIVE_TRIS, c.dtri);
   if (c.created) {
     counter_add(V, C_LIVE_VERTS, c.created);
@@ -701,6 +738,30 @@ __device__ __forceinline__ void mesh_flush(const Vol& V, MeshCounts& c) {
 __device__ __forceinline__ void mesh_begin(const Vol& V, int n) {
   V.ctl->c[C_ST_UPDATE_BLOCKS] = n;
   reinterpret_cast<unsigned*>(V.ctl->c)[C_ST_MESHED] += (unsigned)n;  // wraps modulo 2^32
+}
+
+// Every update-set block, one per CTA iteration.
+// mode: M_UPDATE (types from the current TSDF; t_{i-1} := previous effective type; refresh
+// the positions and normals of the block's existing vertices), M_REFINE (Eqs. 3-5 with the
+// stored t_{i-1}).
+template <bool CE>
+__global__ void __launch_bounds__(MESH_THREADS, mesh_ctas_per_sm(CE)) k_mesh(Vol V, int mode) {
+  __shared__ MeshSmem<CE> S;
+  mesh_tables(S, V.tri_table);
+  grid_dependency_wait();
+  const int n = min(__ldcg(&V.ctl->c[C_N_UPDATE]), V.list_cap_update);
+  if (blockIdx.x == 0 && threadIdx.x == 0) mesh_begin(V, n);
+  MeshCounts cnt;
+  // one block per CTA, then the blocks beyond the grid go to whichever CTA is free first
+  // (the cost of a block varies tenfold with its changes)
+  for (int i = blockIdx.x, k = 0; i < n; k ^= 1) {
+    mesh_block<CE>(V, S, V.update[i], mode, cnt);
+    if (threadIdx.x == 0) S.next[k] = (int)gridDim.x + atomicAdd(&V.ctl->c[C_MESH_NEXT], 1);
+    __syncthreads();
+    i = S.next[k];
+  }
+  mesh_flush(V, cnt);
+  allow_dependent_launch();
 }
 
 }  // namespace vmk

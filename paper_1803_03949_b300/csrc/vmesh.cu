@@ -17,7 +17,6 @@
 #include "kernels_io.cuh"
 #include "kernels_memory.cuh"
 #include "kernels_mesh.cuh"
-#include "kernels_mesh_split.cuh"
 #include "mc_table.h"
 #include "vmesh_device.cuh"
 
@@ -25,9 +24,8 @@ using namespace vmk;
 
 namespace {
 
-enum KernelId { K_ALLOC = 0, K_INTEGRATE, K_LIST_ALL, K_MESH_TYPES, K_MESH_CUBES, K_GC_VERTICES, K_GC_BLOCKS, K_COUNT_ };
-const char* kKernelNames[K_COUNT_] = {"k_alloc",      "k_integrate",   "k_list_all", "k_mesh_types",
-                                      "k_mesh_cubes", "k_gc_vertices", "k_gc_blocks"};
+enum KernelId { K_ALLOC = 0, K_INTEGRATE, K_LIST_ALL, K_MESH, K_GC_VERTICES, K_GC_BLOCKS, K_COUNT_ };
+const char* kKernelNames[K_COUNT_] = {"k_alloc", "k_integrate", "k_list_all", "k_mesh", "k_gc_vertices", "k_gc_blocks"};
 
 // Every allocated block joins the update set (full extraction).
 __global__ void __launch_bounds__(256) k_list_all(Vol V) {
@@ -275,21 +273,15 @@ vm_status enqueue_list_all(vm_volume* v) {
   return launch(v, K_LIST_ALL, [&] { k_list_all<<<grid_for(v, 4), 256, 0, v->cur>>>(v->V); });
 }
 
-// A mesh pass: the types kernel over the update set, then the changed-cube kernel over the
-// list the first one wrote.  after_integrate: the pass directly follows an integrate call,
-// whose first CTA empties the changed-cube list; otherwise it is emptied here.
+// after_integrate: the pass directly follows an integrate call, whose first CTA resets the
+// pass's block hand-out counter; otherwise it is reset here.
 vm_status enqueue_mesh_pass(vm_volume* v, int mode, bool after_integrate) {
   const bool ce = (v->p.flags & VM_PARAM_COMPACT_EDGES) != 0;
-  if (!after_integrate && cudaMemsetAsync(&v->V.ctl->c[C_N_CHANGED], 0, sizeof(int), v->cur) != cudaSuccess)
+  if (!after_integrate && cudaMemsetAsync(&v->V.ctl->c[C_MESH_NEXT], 0, sizeof(int), v->cur) != cudaSuccess)
     return VM_ERR_CUDA;
-  vm_status st = launch(v, K_MESH_TYPES, [&] {
-    launch_dependent(ce ? k_mesh_types<true> : k_mesh_types<false>, grid_for(v, MT_CTAS_PER_SM), MT_THREADS, 0, v->cur,
+  return launch(v, K_MESH, [&] {
+    launch_dependent(ce ? k_mesh<true> : k_mesh<false>, grid_for(v, mesh_ctas_per_sm(ce)), MESH_THREADS, 0, v->cur,
                      v->V, mode);
-  });
-  if (st) return st;
-  return launch(v, K_MESH_CUBES, [&] {
-    launch_dependent(ce ? k_mesh_cubes<true> : k_mesh_cubes<false>, grid_for(v, MC_CTAS_PER_SM), MC_THREADS, MC_SMEM,
-                     v->cur, v->V);
   });
 }
 
@@ -432,12 +424,8 @@ vm_status vm_create_volume(const vm_params* p, void* cuda_stream, vm_volume** ou
   cudaDeviceGetAttribute(&v->num_sms, cudaDevAttrMultiProcessorCount, dev);
   if (v->num_sms <= 0) v->num_sms = 148;
   // the mesh kernel keeps ~32 KB of shared memory per CTA: ask for the largest carveout
-  cudaFuncSetAttribute(k_mesh_types<false>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-  cudaFuncSetAttribute(k_mesh_types<true>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-  cudaFuncSetAttribute(k_mesh_cubes<false>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-  cudaFuncSetAttribute(k_mesh_cubes<true>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-  cudaFuncSetAttribute(k_mesh_cubes<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MC_SMEM);
-  cudaFuncSetAttribute(k_mesh_cubes<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MC_SMEM);
+  cudaFuncSetAttribute(k_mesh<false>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  cudaFuncSetAttribute(k_mesh<true>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   cudaFuncSetAttribute(kb_mesh<false>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   cudaFuncSetAttribute(kb_mesh<true>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   (void)cudaGetLastError();
@@ -463,7 +451,6 @@ vm_status vm_create_volume(const vm_params* p, void* cuda_stream, vm_volume** ou
   V.list_cap_update = (int)p->max_blocks;
   V.list_cap_dead = (int)((2ull * p->max_vertices) < (1ull << 31) - 1 ? 2ull * p->max_vertices : (1ull << 31) - 1);
   V.list_cap_deadrun = (int)p->max_triangles;
-  V.list_cap_chg = (int)p->max_triangles;
   const size_t NB = p->max_blocks, NV = p->max_vertices, NT = p->max_triangles;
   const bool compact = (p->flags & VM_PARAM_COMPACT_EDGES) != 0;
   bool ok = dalloc(v, &V.keys, hb, 0xFF) && dalloc(v, &V.vals, hb, 0xFF) && dalloc(v, &V.stamp, hb, 0) &&
@@ -480,7 +467,6 @@ vm_status vm_create_volume(const vm_params* p, void* cuda_stream, vm_volume** ou
             dalloc(v, &V.blk_free, NB, 0) && dalloc(v, &V.vtx_free, NV, 0) &&
             dalloc(v, &V.touched, (size_t)V.list_cap_touched, 0) && dalloc(v, &V.update, NB, 0) &&
             dalloc(v, &V.dead, (size_t)V.list_cap_dead, 0) && dalloc(v, &V.deadrun, (size_t)V.list_cap_deadrun, 0) &&
-            dalloc(v, &V.chg, (size_t)V.list_cap_chg, 0) &&
             dalloc(v, &V.ctl, 1, 0);
   for (int L = 0; L < 5 && ok; ++L) ok = dalloc(v, &V.run_free[L], (size_t)V.run_cap[L], 0);
   uint4* tt = nullptr;
@@ -822,6 +808,7 @@ vm_status vm_get_stats(vm_volume* v, vm_frame_stats* s) {
   s->full_pool = c[C_STATUS_POOL];
   s->vertex_high_water = c[C_VTX_BUMP] < (int)v->p.max_vertices ? c[C_VTX_BUMP] : (int)v->p.max_vertices;
   s->triangle_high_water = c[C_TRI_BUMP] < (int)v->p.max_triangles ? c[C_TRI_BUMP] : (int)v->p.max_triangles;
+  s->reference_updates = (uint32_t)c[C_ST_REFUPD];
   return VM_OK;
 }
 

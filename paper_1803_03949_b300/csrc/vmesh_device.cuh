@@ -22,9 +22,8 @@
 //             to 2^21 blocks; NO_EDGE = unattached)
 //   triangles tris int4[NT] (three vertex ids, owning cube id; x < 0 = free)
 //   free lists block / vertex stacks and five triangle-run stacks (run length 1..5)
-//   work lists collected buckets, update set, changed cubes of a mesh pass, zero-reference
-//             vertices, released triangle runs, plus a control block (counters, status, frame
-//             parameters).
+//   work lists collected buckets, update set, zero-reference (recycling-candidate) vertices,
+//             released triangle runs, plus a control block (counters, status, frame parameters).
 #pragma once
 
 #include <cooperative_groups.h>
@@ -89,9 +88,9 @@ enum Counter {
   C_ST_EMITTED = 35 * CLINE,
   C_ST_RELEASED = 36 * CLINE,
   C_ST_REFRESHED = 37 * CLINE,
-  C_UNUSED38 = 38 * CLINE,
+  C_MESH_NEXT = 38 * CLINE,  // next update-set block a mesh pass hands out (beyond one per CTA)
   C_N_TOUCHED1 = 39 * CLINE,  // buckets collected by an odd-numbered integrate call (touched_count)
-  C_N_CHANGED = 40 * CLINE,  // changed-cube records of the current mesh pass
+  C_ST_REFUPD = 40 * CLINE,  // reference-count updates of the mesh passes
   C_COUNT = 41 * CLINE
 };
 
@@ -127,7 +126,7 @@ struct Vol {
   uint32_t hmask;
   int max_blocks, max_vertices, max_triangles;
   int run_cap[5];
-  int list_cap_touched, list_cap_update, list_cap_dead, list_cap_deadrun, list_cap_chg;
+  int list_cap_touched, list_cap_update, list_cap_dead, list_cap_deadrun;
 
   uint64_t* keys;
   int* vals;
@@ -170,7 +169,6 @@ struct Vol {
   int* update;        // update-set blocks
   int* dead;          // zero-reference vertex ids
   int2* deadrun;      // released triangle runs (start, length)
-  int2* chg;          // changed cubes of the current mesh pass: (cube id, new type | old type << 8)
 
   // differentiable path (null unless allocated): per voxel the integrations since the
   // checkpoint, the checkpoint weight and dL/dd; the blocks each recorded call collected
@@ -215,7 +213,7 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {  // murmur3 finaliser
 // Which capacity ran out (the first one, kept beside the status; values of the C ABI's
 // vm_pool enum).
 enum PoolCode { P_NONE = 0, P_BLOCKS, P_VERTICES, P_TRIANGLES, P_COLLECTED_LIST, P_UPDATE_LIST, P_DEAD_VERTEX_LIST,
-                P_DEAD_RUN_LIST, P_FREE_STACK, P_HASH, P_EDGE_RECORDS, P_CHANGED_LIST };
+                P_DEAD_RUN_LIST, P_FREE_STACK, P_HASH, P_EDGE_RECORDS };
 __device__ __forceinline__ void set_status(const Vol& V, int st, int pool = P_NONE) {
   atomicCAS(&V.ctl->c[C_STATUS], 0, st);
   if (pool != P_NONE) atomicCAS(&V.ctl->c[C_STATUS_POOL], 0, pool);
@@ -226,9 +224,7 @@ __device__ __forceinline__ int list_pool_code(int c_count) {
              : (c_count == C_N_UPDATE
                     ? P_UPDATE_LIST
                     : (c_count == C_N_DEADREC ? P_EDGE_RECORDS
-                                              : (c_count == C_N_DEADRUN ? P_DEAD_RUN_LIST
-                                                                        : (c_count == C_N_CHANGED ? P_CHANGED_LIST
-                                                                                                  : P_DEAD_VERTEX_LIST))));
+                                              : (c_count == C_N_DEADRUN ? P_DEAD_RUN_LIST : P_DEAD_VERTEX_LIST)));
 }
 
 // Hash lookup: bucket holding `key`, or -1, and its value (loaded with the key, so a hit at

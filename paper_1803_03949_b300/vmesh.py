@@ -43,10 +43,10 @@ class vm_frame_stats(ctypes.Structure):
         "frame_blocks", "new_blocks", "update_blocks", "changed_cubes", "live_blocks", "live_vertices",
         "live_triangles", "freed_blocks", "freed_vertices", "created_vertices", "hash_tombstones",
         "block_high_water", "rehashes", "emitted_triangles", "released_triangles", "refreshed_vertices",
-        "collected_blocks", "meshed_blocks", "full_pool", "vertex_high_water", "triangle_high_water")]
+        "collected_blocks", "meshed_blocks", "full_pool", "vertex_high_water", "triangle_high_water", "reference_updates")]
 
 POOLS = ["none", "blocks", "vertices", "triangles", "collected_list", "update_list", "dead_vertex_list", "dead_run_list",
-         "free_stack", "hash", "edge_records", "changed_list"]
+         "free_stack", "hash", "edge_records"]
 
 
 class vm_mesh_memory(ctypes.Structure):
@@ -325,7 +325,7 @@ class Volume:
         return dict(keys=keys, grad=grad)
 
     # --------------------------------------------------------------- timing
-    KERNELS = ["k_alloc", "k_integrate", "k_list_all", "k_mesh_types", "k_mesh_cubes", "k_gc_vertices", "k_gc_blocks"]
+    KERNELS = ["k_alloc", "k_integrate", "k_list_all", "k_mesh", "k_gc_vertices", "k_gc_blocks"]
 
     def enable_timing(self, on=True):
         """on: True (every kernel), False (none) or a list of kernel names to time."""
