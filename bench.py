@@ -56,7 +56,7 @@ NOMINAL_HBM_GBS = 8000.0  # HBM3e bandwidth quoted for B300 (the measured copy r
 L2_FLUSH_BYTES = 256 << 20
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,clocks.mem")
 
 # Algorithmic bytes per launch of the per-frame kernels (the minimum each must move; counts
 # come from the library's device counters, per frame):
@@ -89,7 +89,10 @@ def frame_bytes(c):
 # DRAM traffic of a kernel (dram__bytes_read.sum + dram__bytes_write.sum) relative to its byte
 # model, from the ncu captures summarised in profiles/, per workload (kernels unchanged since
 # the capture only).  The reported traffic scales the ratio to this run's mean launch.
-TRAFFIC_RATIO = {}
+TRAFFIC_RATIO = {
+    ("floor", "k_mesh"): (377.5 / 195.2, "profiles/k_mesh_floor640x480.md: one launch's dram bytes (frame 8, "
+                          "15,287 update-set blocks) over its byte model, scaled to this run's mean launch"),
+}
 
 
 def load_peaks():
@@ -135,14 +138,16 @@ class ClockSampler:
                 f.write(self.text)
 
     def summary(self):
-        rows = [r.split(",") for r in self.text.strip().splitlines() if r.count(",") >= 8]
+        rows = [r.split(",") for r in self.text.strip().splitlines() if r.count(",") >= 9]
         if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+            return {"sm_mhz": None, "sm_max_mhz": None, "mem_mhz": None, "reasons": ["unsampled"], "samples": 0}
         sm = [float(r[1]) for r in rows]
         mx = max(float(r[2]) for r in rows)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows)}
+        mem = statistics.median(float(r[9]) for r in rows)  # the memory clock (boxes differ in HBM rate)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "mem_mhz": mem, "reasons": reasons,
+                "samples": len(rows)}
 
 
 def dist_init():
