@@ -92,7 +92,7 @@ struct __align__(16) MeshSmem {
   alignas(16) uint64_t euse[256];   // per type, triangles using each cube edge (edge_use)
   int nb[8];
   int dtri;
-  int nchg, ncand, nref, ndr;  // changed cubes, claim edges, refresh edges, released runs
+  int nchg, ndr;               // changed cubes, released runs
   int unext;                   // next free unit of stage d
   int next[2];                 // the CTA's next update-set block (alternating slots)
   int nrun[5];           // new runs per length L = 1..5 (stage b), then their pop (stage d):
@@ -100,14 +100,21 @@ struct __align__(16) MeshSmem {
   int dr_base;                             // first recycling-list slot of the released runs
   uint16_t chg_cube[BV];                   // changed cubes of the block
   uint8_t chg_new[BV], chg_old[BV];
-  uint16_t chg_rrank[BV];                  // rank among the block's new runs of its length
-  uint16_t rel[BV];                        // changed cubes (list slots) with a released run
+  union {
+    struct {                  // from stage b2 on:
+      uint16_t rrank[BV];     // per changed cube, its rank among the block's new runs of its length
+      uint16_t rel[BV];       // changed cubes (list slots) with a released run
+    } ch;
+    struct {                  // stages a-b: per halo row (y, z), bit x: d < 0, |d| < eps, unusable
+      uint32_t neg[HALO * HALO], sml[HALO * HALO], inv[HALO * HALO];
+    } rm;
+  } u;
   int chg_base[BV];                        // run of the released triangles, -1 none
   unsigned cmark[EDGE_WORDS];  // edges the new triangles use whose vertex may be missing (claims)
   unsigned lmark[EDGE_WORDS];  // the block's own edges that carry a vertex
   unsigned rmark[EDGE_WORDS];  // lmark without cmark: the refreshes
-  int ccount[EDGE_WORDS];      // exclusive prefixes of cmark's and rmark's bits over the words
-  int rcount[EDGE_WORDS];
+  int ccount[EDGE_WORDS];      // per word, the claim | refresh << 16 bits of the words before it in its row of 32
+  int wtot[3];                 // per row of 32 words, its claim | refresh << 16 bits
   alignas(16) int rec[CE ? BV : 4];        // compact layout: the block's edge records (voxel -> record, -1 none)
   int evid[EDGE_SLOTS];                    // vertex id per edge slot (own slots from stage a)
 };
@@ -184,6 +191,20 @@ __device__ __forceinline__ float halo_value(float d, float w) { return w > 0.0f 
 
 __device__ __forceinline__ float halo_at(const float* halo, int x, int y, int z) {
   return halo[x + HALO * y + HALO * HALO * z];
+}
+
+// Bit j of a 4-bit value to bit 8 j (bit i lands on i + 7 m for the terms m of the product,
+// which is a multiple of 8 only for m = i).
+__device__ __forceinline__ uint32_t spread4(uint32_t x) { return (x * 0x00204081u) & 0x01010101u; }
+
+// The 8-bit corner masks (Bourke corner order) of 4 cubes consecutive along x, byte j for the
+// cube at x0 + j, from 5-bit windows (bits x0 .. x0 + 4) of the masks of the 4 halo rows through
+// their corners: w00 row (y, z), w10 (y + 1, z), w01 (y, z + 1), w11 (y + 1, z + 1).  Corners
+// 0, 1 are bits (x, x + 1) of row 00; 3, 2 of row 10; 4, 5 of row 01; 7, 6 of row 11.
+__device__ __forceinline__ uint32_t cube_bits4(uint32_t w00, uint32_t w10, uint32_t w01, uint32_t w11) {
+  return spread4(w00 & 15u) | spread4((w00 >> 1) & 15u) << 1 | spread4((w10 >> 1) & 15u) << 2 |
+         spread4(w10 & 15u) << 3 | spread4(w01 & 15u) << 4 | spread4((w01 >> 1) & 15u) << 5 |
+         spread4((w11 >> 1) & 15u) << 6 | spread4(w11 & 15u) << 7;
 }
 
 // Vertex on the owned edge g -> g + e_a (Sec. V-C) at global voxel (gx, gy, gz), from the
@@ -311,16 +332,20 @@ __device__ __forceinline__ int warp_reserve(int* counter, int cnt) {
 // Shared-memory slot of the edge owned by the voxel at halo coordinates (x, y, z) along a.
 __device__ __forceinline__ int edge_slot(int x, int y, int z, int a) { return ((z * 9 + y) * 9 + x) * 3 + a; }
 
-// Edge slot of the i-th set bit of a shared bitmap, from the exclusive prefix of its words'
-// bit counts (binary search for the word, then the bit within it).
-__device__ __forceinline__ int nth_marked(const unsigned* mark, const int* count, int i) {
-  int lo = 0, hi = EDGE_WORDS - 1;
+// Edge slot of the i-th set bit of a shared bitmap (the claim bits: sh = 0, the refresh bits:
+// sh = 16): its row of 32 words from the rows' totals, then a binary search of the word among the
+// row's prefixes, then the bit within the word.
+__device__ __forceinline__ int nth_marked(const unsigned* mark, const int* count, const int* wtot, int sh, int i) {
+  const int t0 = (wtot[0] >> sh) & 0xFFFF, t1 = t0 + ((wtot[1] >> sh) & 0xFFFF);
+  const int r = (i >= t0) + (i >= t1);
+  const int j = i - (r == 0 ? 0 : (r == 1 ? t0 : t1));
+  int lo = 32 * r, hi = min(32 * r + 31, EDGE_WORDS - 1);
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (count[mid] <= i) lo = mid;
+    if (((count[mid] >> sh) & 0xFFFF) <= j) lo = mid;
     else hi = mid - 1;
   }
-  return lo * 32 + (int)__fns(mark[lo], 0, i - count[lo] + 1);
+  return lo * 32 + (int)__fns(mark[lo], 0, j - ((count[lo] >> sh) & 0xFFFF) + 1);
 }
 
 // Counters a mesh pass accumulates per CTA.
@@ -381,20 +406,23 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem<CE>& S, int bl
     S.cmark[w] = 0;
     S.lmark[w] = 0;
   }
+  for (int w = threadIdx.x; w < 3 * HALO * HALO; w += MESH_THREADS) (&S.u.rm.neg[0])[w] = 0;
   __syncthreads();
   // the neighbours' 488 halo voxels as 244 pairs adjacent along x (16 bytes each)
   float4 qn[2];
-  int qh[2];
+  int qx[2], qrow[2];
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     const int i = threadIdx.x + k * MESH_THREADS;
-    qh[k] = -1;
+    qrow[k] = -1;
+    qx[k] = 0;
     qn[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (i < HALO_PAIRS) {
       const int pc = S.pairs[i];
       const int X = pc & 15, Y = (pc >> 4) & 15, Z = pc >> 8;
       const int b = S.nb[(X >> 3) | ((Y >> 3) << 1) | ((Z >> 3) << 2)];
-      qh[k] = X + HALO * Y + HALO * HALO * Z;
+      qx[k] = X;
+      qrow[k] = Y + HALO * Z;
       if (b >= 0)
         qn[k] = __ldcg(reinterpret_cast<const float4*>(V.tw + (size_t)b * BV + (X & 7) + 8 * (Y & 7) + 64 * (Z & 7)));
     }
@@ -415,12 +443,22 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem<CE>& S, int bl
     if (CE) reinterpret_cast<int4*>(S.rec)[threadIdx.x] = rec4;  // read from stage d on
   }
   const int cx = c0 & 7, cy = (c0 >> 3) & 7, cz = c0 >> 6;
+  const int row = cy + HALO * cz;  // the halo row of the thread's 4 voxels
   {
-    float* h = S.halo + cx + HALO * cy + HALO * HALO * cz;
-    h[0] = halo_value(h01.x, h01.y);
-    h[1] = halo_value(h01.z, h01.w);
-    h[2] = halo_value(h23.x, h23.y);
-    h[3] = halo_value(h23.z, h23.w);
+    const float hv[4] = {halo_value(h01.x, h01.y), halo_value(h01.z, h01.w), halo_value(h23.x, h23.y),
+                         halo_value(h23.z, h23.w)};
+    float* h = S.halo + cx + HALO * row;
+    uint32_t ng = 0, sm = 0, iv = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      h[j] = hv[j];
+      ng |= (uint32_t)(hv[j] < 0.0f) << j;
+      sm |= (uint32_t)(fabsf(hv[j]) < eps) << j;
+      iv |= (uint32_t)isnan(hv[j]) << j;
+    }
+    if (ng) atomicOr(&S.u.rm.neg[row], ng << cx);
+    if (sm) atomicOr(&S.u.rm.sml[row], sm << cx);
+    if (iv) atomicOr(&S.u.rm.inv[row], iv << cx);
     // the 4 voxels' 12 edge slots are consecutive in the shared slot array
     int* es = S.evid + edge_slot(cx, cy, cz, 0);
 #pragma unroll
@@ -428,9 +466,16 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem<CE>& S, int bl
   }
 #pragma unroll
   for (int k = 0; k < 2; ++k)
-    if (qh[k] >= 0) {
-      S.halo[qh[k]] = halo_value(qn[k].x, qn[k].y);
-      S.halo[qh[k] + 1] = halo_value(qn[k].z, qn[k].w);
+    if (qrow[k] >= 0) {
+      const float a = halo_value(qn[k].x, qn[k].y), b = halo_value(qn[k].z, qn[k].w);
+      S.halo[qx[k] + HALO * qrow[k]] = a;
+      S.halo[qx[k] + 1 + HALO * qrow[k]] = b;
+      const uint32_t ng = (uint32_t)(a < 0.0f) | ((uint32_t)(b < 0.0f) << 1);
+      const uint32_t sm = (uint32_t)(fabsf(a) < eps) | ((uint32_t)(fabsf(b) < eps) << 1);
+      const uint32_t iv = (uint32_t)isnan(a) | ((uint32_t)isnan(b) << 1);
+      if (ng) atomicOr(&S.u.rm.neg[qrow[k]], ng << qx[k]);
+      if (sm) atomicOr(&S.u.rm.sml[qrow[k]], sm << qx[k]);
+      if (iv) atomicOr(&S.u.rm.inv[qrow[k]], iv << qx[k]);
     }
   __syncthreads();
   // ---- b. cube types, refresh marks, changed-cube list (the type, previous-type and
@@ -446,23 +491,37 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem<CE>& S, int bl
       atomicOr(&S.lmark[es0 >> 5], live12 << sh);
       if (sh > 20) atomicOr(&S.lmark[(es0 >> 5) + 1], live12 >> (32 - sh));
     }
-    uint32_t new_w = eff_w;
-#pragma unroll 1
-    for (int j = 0; j < 4; ++j) {  // rolled: the kernel's code must stay small (instruction cache)
-      const int x = cx + j, y = cy, z = cz;
-      bool valid = true;
-      int raw = 0, small = 0;
+    // the 4 cubes' raw types at once from 5-bit windows of the row masks (bit k of a cube's
+    // byte is corner k's test: the same decisions as comparing the corners' d one by one); a
+    // cube with an unusable corner is invalid, type 0
+    const uint32_t raw4 = cube_bits4((S.u.rm.neg[row] >> cx) & 31u, (S.u.rm.neg[row + 1] >> cx) & 31u,
+                                     (S.u.rm.neg[row + HALO] >> cx) & 31u, (S.u.rm.neg[row + HALO + 1] >> cx) & 31u);
+    const uint32_t i4 = cube_bits4((S.u.rm.inv[row] >> cx) & 31u, (S.u.rm.inv[row + 1] >> cx) & 31u,
+                                   (S.u.rm.inv[row + HALO] >> cx) & 31u, (S.u.rm.inv[row + HALO + 1] >> cx) & 31u);
+    uint32_t bad = i4 | (i4 >> 4);
+    bad |= bad >> 2;
+    bad = (bad | (bad >> 1)) & 0x01010101u;
+    uint32_t new_w = raw4 & ~(bad * 0xFFu);
+    // refinement (Eqs. 3-5) of the valid cubes with a sign change: types 0 and 255 are never
+    // snapped
+    if (mode & M_REFINE) {
+      uint32_t need = 0;
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const float hv = halo_at(S.halo, x + corner_x(k), y + corner_y(k), z + corner_z(k));
-        valid &= !isnan(hv);
-        raw |= (hv < 0.0f) << k;
-        small |= (fabsf(hv) < eps) << k;
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t t = (new_w >> (8 * j)) & 0xFFu;
+        need |= (uint32_t)(t != 0u && t != 0xFFu) << j;
       }
-      const int prev = (prev_w >> (8 * j)) & 0xFF;
-      int e = valid ? raw : 0;
-      if (valid && (mode & M_REFINE)) e = refine_type(raw, prev, small);
-      new_w = (new_w & ~(0xFFu << (8 * j))) | ((uint32_t)e << (8 * j));
+      if (need) {
+        const uint32_t s4 = cube_bits4((S.u.rm.sml[row] >> cx) & 31u, (S.u.rm.sml[row + 1] >> cx) & 31u,
+                                       (S.u.rm.sml[row + HALO] >> cx) & 31u, (S.u.rm.sml[row + HALO + 1] >> cx) & 31u);
+#pragma unroll 1
+        for (uint32_t m = need; m; m &= m - 1) {
+          const int j = __ffs(m) - 1;
+          const int e = refine_type((int)((new_w >> (8 * j)) & 0xFFu), (int)((prev_w >> (8 * j)) & 0xFFu),
+                                    (int)((s4 >> (8 * j)) & 0xFFu));
+          new_w = (new_w & ~(0xFFu << (8 * j))) | ((uint32_t)e << (8 * j));
+        }
+      }
     }
     if (new_w != eff_w) *reinterpret_cast<uint32_t*>(V.code_eff + ci0) = new_w;
     // the changed cubes into the shared list: one shared atomic per warp
@@ -493,8 +552,8 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem<CE>& S, int bl
     for (int q = threadIdx.x; q < nchg; q += MESH_THREADS) {
       const int c = S.chg_cube[q], e = S.chg_new[q];
       const int nold = packed_ntri(S.tri64[S.chg_old[q]]), nnew = packed_ntri(S.tri64[e]);
-      if (S.chg_base[q] >= 0) S.rel[atomicAdd(&S.ndr, 1)] = (uint16_t)q;
-      if (nnew > 0) S.chg_rrank[q] = (uint16_t)atomicAdd(&S.nrun[nnew - 1], 1);
+      if (S.chg_base[q] >= 0) S.u.ch.rel[atomicAdd(&S.ndr, 1)] = (uint16_t)q;
+      if (nnew > 0) S.u.ch.rrank[q] = (uint16_t)atomicAdd(&S.nrun[nnew - 1], 1);
       dtri += nnew - nold;
       const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
       for (unsigned m = S.emask[e]; m; m &= m - 1) {
@@ -509,29 +568,28 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem<CE>& S, int bl
     if (dtri) atomicAdd(&S.dtri, dtri);
   }
   __syncthreads();
-  // ---- c. count the claim edges (warp 0) and the refresh edges (warp 1) per bitmap word;
-  //         stage d locates the j-th of each from the prefixes
-  if (threadIdx.x < 64) {
-    const int lane = threadIdx.x & 31;
-    const bool refresh = threadIdx.x >= 32;
-    int carry = 0;
-    for (int w0 = 0; w0 < EDGE_WORDS; w0 += 32) {
-      const int w = w0 + lane;
-      unsigned u = 0;
-      if (w < EDGE_WORDS) {
-        u = refresh ? S.lmark[w] & ~S.cmark[w] : S.cmark[w];
-        if (refresh) S.rmark[w] = u;
-      }
-      const int c = __popc(u);
-      int x = c;
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-      }
-      if (w < EDGE_WORDS) (refresh ? S.rcount : S.ccount)[w] = carry + x - c;
-      carry += __shfl_sync(0xffffffffu, x, 31);
+  // ---- c. count the claim and refresh edges per bitmap word, a thread per word (warps 0-2, one
+  //         row of 32 words each, both counts packed as claim | refresh << 16: a row holds at
+  //         most 1024 of each), scanned within the row; stage d locates the j-th of each from
+  //         the rows' totals and the prefixes
+  static_assert(EDGE_WORDS <= 96 && EDGE_WORDS * 32 < 0x10000, "stage c: three rows, 16-bit counts");
+  if (threadIdx.x < 96) {
+    const int w = threadIdx.x, lane = w & 31;
+    unsigned cm = 0, rm = 0;
+    if (w < EDGE_WORDS) {
+      cm = S.cmark[w];
+      rm = S.lmark[w] & ~cm;
+      S.rmark[w] = rm;
     }
-    if (lane == 0) (refresh ? S.nref : S.ncand) = carry;
+    const int c = __popc(cm) | (__popc(rm) << 16);
+    int x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (w < EDGE_WORDS) S.ccount[w] = x - c;
+    if (lane == 31) S.wtot[w >> 5] = x;
   }
   __syncthreads();
   // ---- d. independent work in units of up to 32 items of one kind, so that the lanes of a
@@ -540,7 +598,8 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem<CE>& S, int bl
   //         the releases (round-trip chains) and the refreshes (arithmetic only), 32 per
   //         unit.  Each warp starts on the unit of its index and takes the next free unit
   //         when it is done, so the chains of different warps overlap
-  const int ncand = S.ncand, nref = S.nref, ndr = S.ndr;
+  const int tall = S.wtot[0] + S.wtot[1] + S.wtot[2];
+  const int ncand = tall & 0xFFFF, nref = tall >> 16, ndr = S.ndr;
   const int uc = (ncand + 31) >> 5, ur = (ndr + 31) >> 5;
   const int nunits = 1 + uc + ur + ((nref + 31) >> 5);
   const int lane = threadIdx.x & 31;
@@ -570,7 +629,7 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem<CE>& S, int bl
       const int i = ((u - 1 - uc) << 5) + lane;
       int obase = -1, nold = 0;
       if (i < ndr) {
-        const int q = S.rel[i];
+        const int q = S.u.ch.rel[i];
         obase = S.chg_base[q];
         nold = packed_ntri(S.tri64[S.chg_old[q]]);
       }
@@ -579,7 +638,7 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem<CE>& S, int bl
       for (int t = 0; t < 5; ++t) tr[t] = t < nold ? __ldcg(&V.tris[obase + t]) : make_int4(-1, -1, -1, -1);
       // the edges the cube stops using: their references dropped, their vertices listed as
       // recycling candidates (one recycling-list reservation for the warp)
-      const int q = i < ndr ? S.rel[i] : 0;
+      const int q = i < ndr ? S.u.ch.rel[i] : 0;
       const uint64_t wold = i < ndr ? S.tri64[S.chg_old[q]] : 0ull;
       const unsigned cand = i < ndr ? (unsigned)(S.emask[S.chg_old[q]] & ~S.emask[S.chg_new[q]]) : 0u;
       const uint64_t uo = i < ndr ? S.euse[S.chg_old[q]] : 0ull;
@@ -609,7 +668,7 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem<CE>& S, int bl
       const bool claim = u <= uc;
       const int i = ((claim ? u - 1 : u - 1 - uc - ur) << 5) + lane;
       if (i < (claim ? ncand : nref)) {
-        es = nth_marked(claim ? S.cmark : S.rmark, claim ? S.ccount : S.rcount, i);
+        es = nth_marked(claim ? S.cmark : S.rmark, S.ccount, S.wtot, claim ? 0 : 16, i);
         if (claim) {
           const int o = es / 3;
           const int x = o % 9, y = (o / 9) % 9, z = o / 81;
@@ -641,7 +700,7 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem<CE>& S, int bl
   // ---- e. the released runs queued for recycling; per changed cube its new run, the new
   //         triangles and their references
   for (int r = threadIdx.x; r < ndr; r += MESH_THREADS) {
-    const int q = S.rel[r], slot = S.dr_base + r;
+    const int q = S.u.ch.rel[r], slot = S.dr_base + r;
     if (slot < V.list_cap_deadrun) V.deadrun[slot] = make_int2(S.chg_base[q], packed_ntri(S.tri64[S.chg_old[q]]));
     else set_status(V, ST_POOL_FULL, P_DEAD_RUN_LIST);
   }
@@ -651,7 +710,7 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem<CE>& S, int bl
     const int nt = packed_ntri(tw64);
     int base = -1;
     if (nt > 0) {
-      const int r = S.chg_rrank[q], fs = S.run_fs[nt - 1];
+      const int r = S.u.ch.rrank[q], fs = S.run_fs[nt - 1];
       if (r < fs) {
         base = __ldcg(&V.run_free[nt - 1][S.run_old[nt - 1] - 1 - r]);
       } else {
