@@ -18,9 +18,10 @@ end-to-end figures through the public API (depth from pinned host memory and the
 read back; the same plus the mesh compacted every frame, the "compress" step of Table I),
 the float32 CPU oracle on a bounded sample of the same frames, "full_sequence" (all 2000
 frames of the floor), "room" (the 6 x 4 x 3 m room at 8 mm, the previous headline), and the
-two forms the method grows into: "batched" (independent scenes of uneven sizes, one frame each
-per tick, five launches per tick from one CUDA graph, against the same scenes stepped one
-after another) and "differentiable" (forward and backward of the 60-frame sphere orbit with 50
+two forms the method grows into: "batched" and "batched_small" (32 independent scenes of uneven
+sizes, 4.5k-150k and 0.5k-21k active blocks, one frame each per tick over 500 ticks, five
+launches per tick from one CUDA graph, against the same scenes stepped one after another) and
+"differentiable" (forward and backward of the 60-frame sphere orbit with 50
 leaf depth frames, against the plain path on the same frames).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl vmesh|reference]
@@ -247,20 +248,48 @@ def mesh_bytes(c):
     return BYTES_MODEL["k_mesh"](c)
 
 
-def run_batched(args, stream, flush, peak):
+BATCH_MIXES = {
+    # the room recipe scaled 1-3.5x, voxel 5-10 mm: over 500 ticks the scenes grow to 4.5k-150k
+    # active blocks (BASELINE config 5's 5k-200k)
+    "mixed": dict(scale_range=(1.0, 3.5), voxel_mm=(5, 10)),
+    # small rooms (scaled 0.5-1x, voxel 8-10 mm, 0.5k-21k active blocks): one frame of one scene
+    # leaves most of the GPU idle, the case a batch is for
+    "small": dict(scale_range=(0.5, 1.0), voxel_mm=(8, 10)),
+}
+
+
+def batch_frames(scenes, n, workers=16):
+    """Every scene's frames 0..n-1 on the device, one (n, H, W) tensor per scene, rendered on
+    host threads (the generator releases the interpreter lock) one scene at a time."""
+    import concurrent.futures as cf
+
+    import torch
+
+    out = []
+    with cf.ThreadPoolExecutor(workers) as ex:
+        for sc in scenes:
+            host = np.stack(list(ex.map(sc.depth, range(n))))
+            out.append(torch.from_numpy(host).cuda())
+            del host
+    return out
+
+
+def run_batched(args, stream, flush, peak, mix="mixed"):
     """The batched form (BASELINE config 5 reading): `--batch-scenes` independent room scenes of
-    uneven sizes (floor plan scaled 1-3.5x, voxel 5-10 mm), one 640x480 frame of each per tick,
-    five launches per tick replayed from one CUDA graph, schedules autotuned on the first 6
-    warm-up ticks.  Against it: the same scenes and frames stepped one scene after another
-    through vm_step (one graph per scene) on fresh volumes.  L2 flushed before every tick."""
+    uneven sizes (BATCH_MIXES), one 640x480 frame of each per tick, five launches per tick
+    replayed from one CUDA graph, schedules autotuned on the first 6 warm-up ticks, then
+    `--batch-ticks` timed ticks.  Against it: the same scenes and frames stepped one scene after
+    another through vm_step (one graph per scene) on fresh volumes.  L2 flushed before every tick.
+    Also the empty tick: the same five-launch graph on fresh volumes with all-invalid depth, the
+    fixed cost of the launch structure (what one persistent launch per tick could save at most)."""
     import torch
 
     from paper_1803_03949_b300 import Intrinsics, Scenes, Volume
 
     S, T, Wm, P = args.batch_scenes, args.batch_ticks, max(args.batch_warmup, 8), 5
     n = Wm + T + P
-    scenes = synth.batch_scenes(S, n)
-    dev = [torch.from_numpy(np.stack([sc.depth(k) for k in range(n)])).cuda() for sc in scenes]
+    scenes = synth.batch_scenes(S, n, **BATCH_MIXES[mix])
+    dev = batch_frames(scenes, n)
     Ks = [Intrinsics(sc.W, sc.H, sc.fx, sc.fy, sc.cx, sc.cy) for sc in scenes]
     poses = []
     for sc in scenes:
@@ -276,8 +305,15 @@ def run_batched(args, stream, flush, peak):
     def stat_sum(vols, key):
         return sum(v.stats()[key] for v in vols)
 
+    def active(vols):
+        a = sorted(v.stats()["live_blocks"] for v in vols)
+        return {"min": a[0], "median": a[len(a) // 2], "max": a[-1]}
+
     def timed_ticks(step_tick, k0, k1):
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k1 - k0)]
+        # hold the stream while the host enqueues the first ticks (~0.5 ms of GPU time per tick,
+        # outside every tick's event window), so that no window waits on the host
+        torch.cuda._sleep(int(min(k1 - k0, 200) * 1000000))
         for i, k in enumerate(range(k0, k1)):
             flush.fill_(k)
             evs[i][0].record(stream)
@@ -286,6 +322,18 @@ def run_batched(args, stream, flush, peak):
         torch.cuda.synchronize()
         return [a.elapsed_time(b) for a, b in evs]
 
+    # the empty tick: fresh volumes, every pixel invalid
+    vols = [Volume.from_config(sc.volume, stream=stream) for sc in scenes]
+    batch = Scenes(vols)
+    zero = [torch.zeros_like(d[0]) for d in dev]
+    for k in range(3):
+        batch.step_all(zero, Ks, [pp[k] for pp in poses], graph=True)
+    ms_empty = timed_ticks(lambda k: batch.step_all(zero, Ks, [pp[k] for pp in poses], graph=True), 3, 23)
+    batch.close()
+    for v in vols:
+        v.close()
+    del vols, zero
+
     # batched
     vols = [Volume.from_config(sc.volume, stream=stream) for sc in scenes]
     batch = Scenes(vols)
@@ -293,9 +341,11 @@ def run_batched(args, stream, flush, peak):
     for k in range(Wm):
         batch.step_all(*tick_args(k), graph=True)
     torch.cuda.synchronize()
+    act0 = active(vols)
     c0, u0 = stat_sum(vols, "collected_blocks"), stat_sum(vols, "meshed_blocks")
     ms = timed_ticks(lambda k: batch.step_all(*tick_args(k), graph=True), Wm, Wm + T)
     c1, u1 = stat_sum(vols, "collected_blocks"), stat_sum(vols, "meshed_blocks")
+    act1 = active(vols)
     # per-kernel times on P more ticks (eager launches with events) and their work counters
     before = [v.stats() for v in vols]
     batch.profile(P)
@@ -322,7 +372,6 @@ def run_batched(args, stream, flush, peak):
             roof[name] = {"avg_launch_us": 1000.0 * kms[name], "achieved": gbs, "peak": peak, "unit": "GB/s",
                           "frac": gbs / peak, "bytes_per_launch": model(work) / kms["ticks"]}
     sched = batch.schedule()
-    active = sorted(v.stats()["live_blocks"] for v in vols)
     for v in vols:
         v.check()
     batch.close()
@@ -348,10 +397,13 @@ def run_batched(args, stream, flush, peak):
     del vols, dev
     torch.cuda.empty_cache()
     tot, tot_seq = sum(ms) / 1000.0, sum(ms_seq) / 1000.0
+    mk = BATCH_MIXES[mix]
+    empty_us = 1000.0 * float(np.median(ms_empty))
     return {
-        "workload": "%d room scenes (floor plan 6x4 m scaled 1-3.5x log-uniform, 3 m high, 20 primitives, "
-                    "voxel 5-10 mm, trunc 4 voxels), 640x480 float32 depth, one frame of each per tick; "
-                    "integrate + incremental mesh + refine + gc" % S,
+        "workload": "%d room scenes (floor plan 6x4 m scaled %g-%gx log-uniform, 3 m high, 20 primitives, "
+                    "voxel %d-%d mm, trunc 4 voxels, 4.5 m sensor range), 640x480 float32 depth, one frame of each "
+                    "per tick; integrate + incremental mesh + refine + gc"
+                    % (S, mk["scale_range"][0], mk["scale_range"][1], mk["voxel_mm"][0], mk["voxel_mm"][1]),
         "scenes": S, "ticks": T, "warmup_ticks": Wm, "value": S * T / tot, "unit": "scene-frames/s",
         "ms_per_tick": 1000.0 * tot / T, "voxels_per_s": 512 * ((c1 - c0) % (1 << 32)) / tot,
         "mean_blocks_per_tick": ((c1 - c0) % (1 << 32)) / T, "mean_update_blocks_per_tick": ((u1 - u0) % (1 << 32)) / T,
@@ -359,10 +411,13 @@ def run_batched(args, stream, flush, peak):
         "sequential": {"value": S * T / tot_seq, "unit": "scene-frames/s", "ms_per_tick": 1000.0 * tot_seq / T,
                        "how": "the same frames through vm_step, one CUDA graph per scene, scenes one after another"},
         "speedup_vs_sequential": tot_seq / tot,
+        "empty_tick": {"us": empty_us, "share_of_tick": empty_us / (1000.0 * 1000.0 * tot / T),
+                       "how": "median of 20 ticks of the same five-launch graph on fresh volumes with all-invalid "
+                              "depth: the launch structure's fixed cost, the most one persistent launch could save"},
         "schedule": sched["schedule"], "tuned_ms_per_option": sched["tuned_ms"],
         "kernel_ms_per_tick": {k: v for k, v in kms.items() if k != "ticks"}, "profiled_ticks": kms["ticks"],
         "roofline": roof,
-        "active_blocks": {"min": active[0], "median": active[len(active) // 2], "max": active[-1]},
+        "active_blocks": {"timed_start": act0, "timed_end": act1},
     }
 
 
@@ -779,7 +834,8 @@ def run_vmesh(args, rank, world, local):
                                     "sample": "frames 0..%d of the room sequence (%.1f s)" % (timed - 1, secs),
                                     "voxels_per_s": cvps}
         line["room"] = room
-        line["batched"] = run_batched(args, stream, flush, peak)
+        line["batched"] = run_batched(args, stream, flush, peak, "mixed")
+        line["batched_small"] = run_batched(args, stream, flush, peak, "small")
         line["differentiable"] = run_differentiable(args, stream)
     print(json.dumps(line), flush=True)
 
@@ -808,7 +864,7 @@ def main():
     ap.add_argument("--room-warmup", type=int, default=10)
     ap.add_argument("--room-cpu-frames", type=int, default=200)
     ap.add_argument("--batch-scenes", type=int, default=32)
-    ap.add_argument("--batch-ticks", type=int, default=60)
+    ap.add_argument("--batch-ticks", type=int, default=500)
     ap.add_argument("--batch-warmup", type=int, default=10)
     ap.add_argument("--diff-reps", type=int, default=21)
     args = ap.parse_args()

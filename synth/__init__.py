@@ -186,26 +186,28 @@ def floor_scene(num_frames: int = 2000, seed: int = SEED_BASE + 3) -> Scene:
     return sc
 
 
-def batch_scenes(num_scenes: int = 32, num_frames: int = 100, seed: int = SEED_BASE + 5) -> list:
+def batch_scenes(num_scenes: int = 32, num_frames: int = 100, seed: int = SEED_BASE + 5,
+                 scale_range=(1.0, 3.5), voxel_mm=(5, 10), height: float = 3.0, pool_shift: int = 0) -> list:
     """Independent scenes of uneven sizes for the batched workload: the room recipe with its
-    6 x 4 m floor plan scaled by a log-uniform factor in [1, 3.5] (height 3 m, 20 primitives),
-    voxel l drawn from {5, 6, ..., 10} mm, truncation 4 l,
-    640 x 480 depth with the room noise model and a 4.5 m sensor range (farther depth reads as
-    invalid, as on a structured-light camera); each scene has its own seed and trajectory."""
+    6 x 4 m floor plan scaled by a log-uniform factor in `scale_range` (default [1, 3.5]; height
+    3 m, 20 primitives), voxel l drawn from {voxel_mm[0], ..., voxel_mm[1]} mm (default 5-10),
+    truncation 4 l, 640 x 480 depth with the room noise model and a 4.5 m sensor range (farther
+    depth reads as invalid, as on a structured-light camera); each scene has its own seed and
+    trajectory.  Pools: 2^18 blocks at l <= 6 mm, 2^17 at <= 8 mm, else 2^16, times 2^pool_shift."""
     lib = _load()
     rng = np.random.default_rng(seed)
     out = []
     for i in range(num_scenes):
-        scale = float(np.exp(rng.uniform(0.0, np.log(3.5))))
-        l = int(rng.integers(5, 11)) * 1e-3
+        scale = float(np.exp(rng.uniform(np.log(scale_range[0]), np.log(scale_range[1]))))
+        l = int(rng.integers(voxel_mm[0], voxel_mm[1] + 1)) * 1e-3
         sx, sy = 6.0 * scale, 4.0 * scale
         nprims = 20
-        h = lib.synth_create_room(seed + 1000 * (i + 1), num_frames, 640, 480, 525.0, 525.0, 319.5, 239.5, sx, sy, 3.0,
-                                  nprims, 0.0012, 0.02)
-        mb = 1 << 18 if l <= 0.006 else (1 << 17 if l <= 0.008 else 1 << 16)
+        h = lib.synth_create_room(seed + 1000 * (i + 1), num_frames, 640, 480, 525.0, 525.0, 319.5, 239.5, sx, sy,
+                                  height, nprims, 0.0012, 0.02)
+        mb = (1 << 18 if l <= 0.006 else (1 << 17 if l <= 0.008 else 1 << 16)) << pool_shift
         vol = VolumeConfig(voxel_size=l, trunc=4 * l, hash_buckets=4 * mb, max_blocks=mb, max_vertices=64 * mb,
                            max_triangles=128 * mb)
-        sc = Scene(h, lib, "room_%.1fx%.1fx3_640x480_l%dmm" % (sx, sy, round(l * 1000)), vol)
+        sc = Scene(h, lib, "room_%.1fx%.1fx%g_640x480_l%dmm" % (sx, sy, height, round(l * 1000)), vol)
         sc.max_range = 4.5
         out.append(sc)
     return out
