@@ -570,8 +570,10 @@ def measure(args, scene, vc, W, K, stream, flush, peak, peak_kind, world, rank, 
                     vol.mesh_size_async(res_host)
                     d2h = 8
                 else:
-                    m = vol.download(device=True)  # counts (two 4-byte reads) + on-device compaction
-                    d2h = 16
+                    # the statistics block (high-water marks that size the outputs, 41 x 128 B), then
+                    # counts + on-device compaction in one call (the two 4-byte counts come back)
+                    m = vol.download(device=True)
+                    d2h = 41 * 128 + 8
                     del m
             evs[i][1].record(stream)
         torch.cuda.synchronize()
@@ -691,9 +693,9 @@ def measure(args, scene, vc, W, K, stream, flush, peak, peak_kind, world, rank, 
         out["e2e_compress"] = {"value": world * K / (reduce_max(sum(ms4), world) / 1000.0), "unit": UNIT,
                                "h2d_bytes_per_step": 4 * Wd * H, "d2h_bytes_per_step": d2h,
                                "path": "as e2e, plus the live mesh compacted every frame into dense device arrays "
-                                       "(vm_mesh_counts, then vm_download_mesh with on_device = 1: positions, "
-                                       "normals, triangles, edge keys, reference counts), the host waiting for "
-                                       "the counts"}
+                                       "(vm_get_stats for the pools' high-water marks that size the outputs, "
+                                       "then vm_download_mesh_into: counts, scan and compaction of positions, "
+                                       "normals, triangles, edge keys and reference counts, one synchronisation)"}
     torch.cuda.empty_cache()
     return out
 

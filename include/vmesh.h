@@ -207,6 +207,19 @@ vm_status vm_mesh_counts(vm_volume* vol, int64_t* n_vertices, int64_t* n_triangl
 vm_status vm_download_mesh(vm_volume* vol, float* pos, float* nrm, int32_t* tris, uint64_t* edge_keys,
                            int32_t* refcount, int on_device);
 
+/* The vm_download_mesh compaction (Sec. VI "compress") into caller-allocated DEVICE buffers
+ * with capacities, without a separate vm_mesh_counts call: the counts, their scan and both
+ * compactions are enqueued back to back and the call synchronises once.  pos, nrm, tris (and
+ * the optional edge_keys, refcount) have the vm_download_mesh layout and hold at least
+ * cap_vertices / cap_triangles entries; *n_vertices and *n_triangles receive the live counts.
+ * Nothing at or past a capacity is written; when a count exceeds its capacity the call
+ * returns VM_ERR_INVALID_ARG and the outputs are unspecified (call again with the counts as
+ * capacities).  The pools' high-water marks (vm_frame_stats.vertex_high_water,
+ * triangle_high_water) always bound the counts. */
+vm_status vm_download_mesh_into(vm_volume* vol, float* pos, float* nrm, int32_t* tris, uint64_t* edge_keys,
+                                int32_t* refcount, int64_t cap_vertices, int64_t cap_triangles,
+                                int64_t* n_vertices, int64_t* n_triangles);
+
 /* Enqueues (without waiting) a copy of the live vertex and triangle counts, 2 x int32,
  * to dst: pinned host memory when on_device == 0 (valid once the stream reaches the
  * copy), device memory otherwise.  The counts include zero-reference vertices that the

@@ -31,37 +31,50 @@ __global__ void __launch_bounds__(256) k_count_live(Vol V, int* cta_counts) {
   if (threadIdx.x == 0) cta_counts[blockIdx.x] = s;
 }
 
-// Exclusive scan of n counts in place by one CTA of 1024 threads; the total to *total.
+// Exclusive scan of n counts in place by one CTA of 1024 threads; the total to *total.  Each
+// pass covers 16 consecutive counts per thread (their loads in flight together), a serial scan
+// of them, then a scan of the threads' totals over the CTA (two barriers per 16384 counts).
 __device__ __forceinline__ void scan_in_cta(int* cta_counts, int n, int* total) {
-  __shared__ int carry;
+  constexpr int PER = 16, SPAN = PER * 1024;
   __shared__ int warp_sums[32];
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (int base = 0; base < n; base += 1024) {
-    int i = base + threadIdx.x;
-    int v = i < n ? cta_counts[i] : 0;
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int x = v;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int carry = 0;  // the same in every thread
+  for (int base = 0; base < n; base += SPAN) {
+    const int i0 = base + threadIdx.x * PER;
+    int v[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) v[k] = i0 + k < n ? cta_counts[i0 + k] : 0;
+    int tsum = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int c = v[k];
+      v[k] = tsum;
+      tsum += c;
+    }
+    int x = tsum;
+#pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      int y = __shfl_up_sync(0xffffffffu, x, o);
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
     if (lane == 31) warp_sums[w] = x;
     __syncthreads();
     if (w == 0) {
-      int s = warp_sums[lane];
+      int t = warp_sums[lane];
+#pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, s, o);
-        if (lane >= o) s += y;
+        const int y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
       }
-      warp_sums[lane] = s;
+      warp_sums[lane] = t;
     }
     __syncthreads();
-    int incl = x + (w > 0 ? warp_sums[w - 1] : 0);
-    if (i < n) cta_counts[i] = carry + incl - v;
-    __syncthreads();
-    if (threadIdx.x == 1023) carry += incl;
-    __syncthreads();
+    const int off = carry + (w > 0 ? warp_sums[w - 1] : 0) + x - tsum;
+#pragma unroll
+    for (int k = 0; k < PER; ++k)
+      if (i0 + k < n) cta_counts[i0 + k] = off + v[k];
+    carry += warp_sums[31];
+    __syncthreads();  // warp_sums is rewritten by the next pass
   }
   if (threadIdx.x == 0) *total = carry;
 }
@@ -121,9 +134,10 @@ __device__ __forceinline__ uint64_t edge_key_of(const Vol& V, uint32_t e) {
          ((uint64_t)(uint32_t)(gz + (1 << 19)) << 2) | (uint64_t)a;
 }
 
-// Download, phase 3 (vertices): stable compaction; remap[v] = new index (or -1).
+// Download, phase 3 (vertices): stable compaction; remap[v] = new index (or -1).  Outputs at or
+// past index `cap` are not written.
 __global__ void __launch_bounds__(256) k_compact_vertices(Vol V, const int* cta_offsets, int* remap, float* pos,
-                                                          float* nrm, uint64_t* keys, int* refcount) {
+                                                          float* nrm, uint64_t* keys, int* refcount, int cap) {
   const int n = live_slots<false>(V);
   const int nch = (n + SCAN_ITEMS - 1) / SCAN_ITEMS;
   __shared__ int warp_tot[8];
@@ -143,7 +157,7 @@ __global__ void __launch_bounds__(256) k_compact_vertices(Vol V, const int* cta_
       for (int q = 0; q < w; ++q) off += warp_tot[q];
       off += __popc(b & ((1u << lane) - 1));
       if (v < n) remap[v] = live ? off : -1;
-      if (live) {
+      if (live && off < cap) {
         float4 p = V.vpos[v], q4 = V.vnrm[v];
         pos[3 * (size_t)off] = p.x; pos[3 * (size_t)off + 1] = p.y; pos[3 * (size_t)off + 2] = p.z;
         nrm[3 * (size_t)off] = q4.x; nrm[3 * (size_t)off + 1] = q4.y; nrm[3 * (size_t)off + 2] = q4.z;
@@ -161,41 +175,64 @@ __global__ void __launch_bounds__(256) k_compact_vertices(Vol V, const int* cta_
   }
 }
 
-// Download, phase 3 (triangles): stable compaction with vertex indices remapped.
+// Download, phase 3 (triangles): stable compaction with vertex indices remapped.  A chunk's
+// 1024 slots are 4 rounds of 256; all four rounds' loads, then all their vertex remaps, are in
+// flight together, with one barrier for the warps' counts of every round.  Outputs at or past
+// index `cap` are not written.
 __global__ void __launch_bounds__(256) k_compact_triangles(Vol V, const int* cta_offsets, const int* remap,
-                                                           int* tris_out) {
+                                                           int* tris_out, int cap) {
+  constexpr int R = SCAN_ITEMS / 256;
   const int n = live_slots<true>(V);
   const int nch = (n + SCAN_ITEMS - 1) / SCAN_ITEMS;
-  __shared__ int warp_tot[8];
-  __shared__ int running;
+  __shared__ int warp_tot[R][8];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1;
   for (int ch = blockIdx.x; ch < nch; ch += gridDim.x) {
     const int base = ch * SCAN_ITEMS;
-    if (threadIdx.x == 0) running = cta_offsets[ch];
-    __syncthreads();
-    for (int j0 = 0; j0 < SCAN_ITEMS; j0 += 256) {
-      int t = base + j0 + threadIdx.x;
-      int4 tr = t < n ? V.tris[t] : make_int4(-1, -1, -1, -1);
-      bool live = tr.x >= 0;
-      unsigned b = __ballot_sync(0xffffffffu, live);
-      if (lane == 0) warp_tot[w] = __popc(b);
-      __syncthreads();
-      int off = running;
-      for (int q = 0; q < w; ++q) off += warp_tot[q];
-      off += __popc(b & ((1u << lane) - 1));
-      if (live) {
-        tris_out[3 * (size_t)off] = remap[tr.x];
-        tris_out[3 * (size_t)off + 1] = tr.y >= 0 ? remap[tr.y] : -1;
-        tris_out[3 * (size_t)off + 2] = tr.z >= 0 ? remap[tr.z] : -1;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        int s = 0;
-        for (int q = 0; q < 8; ++q) s += warp_tot[q];
-        running += s;
-      }
-      __syncthreads();
+    int4 tr[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int t = base + k * 256 + threadIdx.x;
+      tr[k] = t < n ? __ldcs(reinterpret_cast<const int4*>(V.tris) + t) : make_int4(-1, -1, -1, -1);
     }
+    unsigned b[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      b[k] = __ballot_sync(0xffffffffu, tr[k].x >= 0);
+      if (lane == 0) warp_tot[k][w] = __popc(b[k]);
+    }
+    const int running = __ldg(cta_offsets + ch);
+    __syncthreads();
+    int off[R], acc = running;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      int pre = 0, tot = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int c = warp_tot[k][q];
+        pre += q < w ? c : 0;
+        tot += c;
+      }
+      off[k] = acc + pre + __popc(b[k] & lt);
+      acc += tot;
+    }
+    int r[R][3];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const bool live = tr[k].x >= 0;
+      r[k][0] = live ? __ldg(remap + tr[k].x) : -1;
+      r[k][1] = live && tr[k].y >= 0 ? __ldg(remap + tr[k].y) : -1;
+      r[k][2] = live && tr[k].z >= 0 ? __ldg(remap + tr[k].z) : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+      if (tr[k].x >= 0 && off[k] < cap) {
+        int* o = tris_out + 3 * (size_t)off[k];
+        o[0] = r[k][0];
+        o[1] = r[k][1];
+        o[2] = r[k][2];
+      }
+    __syncthreads();  // warp_tot is rewritten by the next chunk
   }
 }
 

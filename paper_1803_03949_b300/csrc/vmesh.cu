@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <climits>
 #include <vector>
 
 #include "vmesh.h"
@@ -734,8 +735,8 @@ vm_status vm_download_mesh(vm_volume* v, float* pos, float* nrm, int32_t* tris, 
   const int grid = grid_for(v, 8);
   if (on_device) {  // counts, offsets and both compactions in stream order; one synchronisation
     if ((st = enqueue_live_counts(v))) return st;
-    k_compact_vertices<<<grid, 256, 0, v->stream>>>(v->V, v->cta_counts, v->remap, pos, nrm, keys, refcount);
-    k_compact_triangles<<<grid, 256, 0, v->stream>>>(v->V, v->cta_counts_t, v->remap, tris);
+    k_compact_vertices<<<grid, 256, 0, v->stream>>>(v->V, v->cta_counts, v->remap, pos, nrm, keys, refcount, INT_MAX);
+    k_compact_triangles<<<grid, 256, 0, v->stream>>>(v->V, v->cta_counts_t, v->remap, tris, INT_MAX);
     if (cudaGetLastError() != cudaSuccess) return VM_ERR_CUDA;
     return sync_status(v);
   }
@@ -762,8 +763,8 @@ vm_status vm_download_mesh(vm_volume* v, float* pos, float* nrm, int32_t* tris, 
     cleanup();
     return VM_ERR_OOM;
   }
-  k_compact_vertices<<<grid, 256, 0, v->stream>>>(v->V, v->cta_counts, v->remap, dpos, dnrm, dkeys, dref);
-  k_compact_triangles<<<grid, 256, 0, v->stream>>>(v->V, v->cta_counts_t, v->remap, dtris);
+  k_compact_vertices<<<grid, 256, 0, v->stream>>>(v->V, v->cta_counts, v->remap, dpos, dnrm, dkeys, dref, nv);
+  k_compact_triangles<<<grid, 256, 0, v->stream>>>(v->V, v->cta_counts_t, v->remap, dtris, nt);
   bool ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(v->stream) == cudaSuccess;
   ok = ok && cudaMemcpy(pos, dpos, (size_t)nv * 12, cudaMemcpyDeviceToHost) == cudaSuccess &&
        cudaMemcpy(nrm, dnrm, (size_t)nv * 12, cudaMemcpyDeviceToHost) == cudaSuccess &&
@@ -772,6 +773,26 @@ vm_status vm_download_mesh(vm_volume* v, float* pos, float* nrm, int32_t* tris, 
        (!refcount || cudaMemcpy(refcount, dref, (size_t)nv * 4, cudaMemcpyDeviceToHost) == cudaSuccess);
   cleanup();
   return ok ? VM_OK : VM_ERR_CUDA;
+}
+
+vm_status vm_download_mesh_into(vm_volume* v, float* pos, float* nrm, int32_t* tris, uint64_t* keys,
+                                int32_t* refcount, int64_t cap_v, int64_t cap_t, int64_t* nv, int64_t* nt) {
+  if (!v || !pos || !nrm || !tris || !nv || !nt || cap_v < 0 || cap_t < 0) return VM_ERR_INVALID_ARG;
+  vm_status st = ensure_scan_scratch(v);
+  if (st) return st;
+  const int grid = grid_for(v, 8);
+  const int cv = (int)std::min<int64_t>(cap_v, INT_MAX), ct = (int)std::min<int64_t>(cap_t, INT_MAX);
+  int tot[2] = {0, 0};
+  if ((st = enqueue_live_counts(v))) return st;
+  k_compact_vertices<<<grid, 256, 0, v->stream>>>(v->V, v->cta_counts, v->remap, pos, nrm, keys, refcount, cv);
+  k_compact_triangles<<<grid, 256, 0, v->stream>>>(v->V, v->cta_counts_t, v->remap, tris, ct);
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(tot, v->scan_total, sizeof(tot), cudaMemcpyDeviceToHost, v->stream) != cudaSuccess)
+    return VM_ERR_CUDA;
+  if ((st = sync_status(v))) return st;
+  *nv = tot[0];
+  *nt = tot[1];
+  return (tot[0] > cap_v || tot[1] > cap_t) ? VM_ERR_INVALID_ARG : VM_OK;
 }
 
 vm_status vm_mesh_size_async(vm_volume* v, int32_t* dst, int on_device) {

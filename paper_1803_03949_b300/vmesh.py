@@ -60,7 +60,8 @@ _lib = None
 EXPORTS = ["vm_create_volume", "vm_destroy_volume", "vm_set_stream", "vm_integrate_depth", "vm_update_mesh",
            "vm_refine_mesh", "vm_gc", "vm_step", "vm_mesh_counts", "vm_download_mesh", "vm_get_stats",
            "vm_last_error", "vm_num_blocks", "vm_export_blocks", "vm_set_blocks", "vm_enable_timing",
-           "vm_kernel_times", "vm_mesh_size_async", "vm_download_mesh_noalloc", "vm_diff_begin", "vm_diff_end",
+           "vm_kernel_times", "vm_mesh_size_async", "vm_download_mesh_noalloc", "vm_download_mesh_into", "vm_diff_begin",
+           "vm_diff_end",
            "vm_grad_vertices", "vm_grad_depth", "vm_export_grad", "vm_batch_create", "vm_batch_destroy",
            "vm_batch_step", "vm_batch_tune", "vm_batch_schedule", "vm_batch_set_schedule", "vm_batch_profile",
            "vm_batch_kernel_ms", "vm_mesh_memory_stats"]
@@ -97,6 +98,7 @@ def load_library(path: str = LIB_PATH):
         "vm_kernel_times": [vp, P(ctypes.c_char_p), P(ctypes.c_double), P(i64), i, P(i)],
         "vm_mesh_size_async": [vp, vp, i],
         "vm_download_mesh_noalloc": [vp, vp, vp, vp, vp, vp, i64, i64, P(i64), P(i64)],
+        "vm_download_mesh_into": [vp, vp, vp, vp, vp, vp, i64, i64, P(i64), P(i64)],
         "vm_diff_begin": [vp, i],
         "vm_diff_end": [vp],
         "vm_grad_vertices": [vp, i64, vp, vp, vp],
@@ -259,22 +261,32 @@ class Volume:
         refcount (nv,) i32) as numpy arrays (host path) or torch CUDA tensors (device path)."""
         import torch
 
-        nv, nt = self.mesh_counts()
         if device:
+            # buffers sized by the pools' high-water marks (they bound the live counts), then one
+            # call that counts, compacts and synchronises once; the outputs are views of the
+            # counted length
+            st = self.stats()
+            cv, ct = max(st["vertex_high_water"], 1), max(st["triangle_high_water"], 1)  # non-empty buffers
             dev = torch.device("cuda")
-            pos = torch.empty((nv, 3), dtype=torch.float32, device=dev)
-            nrm = torch.empty((nv, 3), dtype=torch.float32, device=dev)
-            tris = torch.empty((nt, 3), dtype=torch.int32, device=dev)
-            keys = torch.empty((nv,), dtype=torch.int64, device=dev)
-            ref = torch.empty((nv,), dtype=torch.int32, device=dev)
-        else:
-            pos = np.empty((nv, 3), np.float32)
-            nrm = np.empty((nv, 3), np.float32)
-            tris = np.empty((nt, 3), np.int32)
-            keys = np.empty((nv,), np.uint64)
-            ref = np.empty((nv,), np.int32)
-        _check(self._lib.vm_download_mesh(self._h, _ptr(pos), _ptr(nrm), _ptr(tris), _ptr(keys), _ptr(ref),
-                                          int(device)), "vm_download_mesh")
+            pos = torch.empty((cv, 3), dtype=torch.float32, device=dev)
+            nrm = torch.empty((cv, 3), dtype=torch.float32, device=dev)
+            tris = torch.empty((ct, 3), dtype=torch.int32, device=dev)
+            keys = torch.empty((cv,), dtype=torch.int64, device=dev)
+            ref = torch.empty((cv,), dtype=torch.int32, device=dev)
+            nv, nt = ctypes.c_int64(), ctypes.c_int64()
+            _check(self._lib.vm_download_mesh_into(self._h, _ptr(pos), _ptr(nrm), _ptr(tris), _ptr(keys), _ptr(ref),
+                                                   cv, ct, ctypes.byref(nv), ctypes.byref(nt)),
+                   "vm_download_mesh_into")
+            nv, nt = nv.value, nt.value
+            return dict(pos=pos[:nv], nrm=nrm[:nv], tris=tris[:nt], keys=keys[:nv], refcount=ref[:nv])
+        nv, nt = self.mesh_counts()
+        pos = np.empty((nv, 3), np.float32)
+        nrm = np.empty((nv, 3), np.float32)
+        tris = np.empty((nt, 3), np.int32)
+        keys = np.empty((nv,), np.uint64)
+        ref = np.empty((nv,), np.int32)
+        _check(self._lib.vm_download_mesh(self._h, _ptr(pos), _ptr(nrm), _ptr(tris), _ptr(keys), _ptr(ref), 0),
+               "vm_download_mesh")
         return dict(pos=pos, nrm=nrm, tris=tris, keys=keys, refcount=ref)
 
     def blocks(self) -> dict:
