@@ -550,22 +550,25 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem<CE>& S, int bl
   {
     int dtri = 0;
     for (int q = threadIdx.x; q < nchg; q += MESH_THREADS) {
-      const int c = S.chg_cube[q], e = S.chg_new[q];
+      const int e = S.chg_new[q];
       const int nold = packed_ntri(S.tri64[S.chg_old[q]]), nnew = packed_ntri(S.tri64[e]);
       if (S.chg_base[q] >= 0) S.u.ch.rel[atomicAdd(&S.ndr, 1)] = (uint16_t)q;
       if (nnew > 0) S.u.ch.rrank[q] = (uint16_t)atomicAdd(&S.nrun[nnew - 1], 1);
       dtri += nnew - nold;
-      const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
-      for (unsigned m = S.emask[e]; m; m &= m - 1) {
-        const int ob = owner_bits(__ffs(m) - 1);
-        const int ox = x + (ob & 1), oy = y + ((ob >> 1) & 1), oz = z + ((ob >> 2) & 1);
-        const int es = edge_slot(ox, oy, oz, ob >> 3);
-        // an existing vertex of the block's own voxels needs nothing more (its slot is
-        // staged); a neighbour's edge or a missing vertex needs a claim in stage d
-        if ((ox | oy | oz) >= 8 || S.evid[es] < 0) atomicOr(&S.cmark[es >> 5], 1u << (es & 31));
-      }
     }
     if (dtri) atomicAdd(&S.dtri, dtri);
+    // the edges the new triangles use, a (changed cube, cube edge) pair per thread: an existing
+    // vertex of the block's own voxels needs nothing more (its slot is staged); a neighbour's
+    // edge or a missing vertex needs a claim in stage d
+    for (int i = threadIdx.x; i < 12 * nchg; i += MESH_THREADS) {
+      const int q = i / 12, k = i - 12 * q;
+      if (!((S.emask[S.chg_new[q]] >> k) & 1)) continue;
+      const int c = S.chg_cube[q];
+      const int ob = owner_bits(k);
+      const int ox = (c & 7) + (ob & 1), oy = ((c >> 3) & 7) + ((ob >> 1) & 1), oz = (c >> 6) + ((ob >> 2) & 1);
+      const int es = edge_slot(ox, oy, oz, ob >> 3);
+      if ((ox | oy | oz) >= 8 || S.evid[es] < 0) atomicOr(&S.cmark[es >> 5], 1u << (es & 31));
+    }
   }
   __syncthreads();
   // ---- c. count the claim and refresh edges per bitmap word, a thread per word (warps 0-2, one
@@ -708,25 +711,30 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem<CE>& S, int bl
     const int c = S.chg_cube[q];
     const uint64_t tw64 = S.tri64[S.chg_new[q]];
     const int nt = packed_ntri(tw64);
+    // the new run: popped from the free stack (a run start, never negative) or the bump range
+    // (none past the pool's end); whether the cube got one is known before the stack entry
+    // arrives, so the reference updates below do not wait for it
     int base = -1;
+    bool got = false;
     if (nt > 0) {
       const int r = S.u.ch.rrank[q], fs = S.run_fs[nt - 1];
       if (r < fs) {
         base = __ldcg(&V.run_free[nt - 1][S.run_old[nt - 1] - 1 - r]);
+        got = true;
       } else {
         const long long b = (long long)S.run_bump[nt - 1] + (long long)(r - fs) * nt;
         if (b + nt > V.max_triangles) set_status(V, ST_POOL_FULL, P_TRIANGLES);
         else base = (int)b;
+        got = base >= 0;
       }
     }
     const int ci = blk * BV + c;
-    V.tri_base[ci] = base;
     const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
     // the references of the edges the new type uses: (its triangles using the edge, none when
     // its run could not be had) - (the old type's, when it had a run); the edges only the old
     // type used were handled by the release
     {
-      const uint64_t un = base >= 0 ? S.euse[S.chg_new[q]] : 0ull;
+      const uint64_t un = got ? S.euse[S.chg_new[q]] : 0ull;
       const uint64_t uo = S.chg_base[q] >= 0 ? S.euse[S.chg_old[q]] : 0ull;
 #pragma unroll 1
       for (unsigned m = S.emask[S.chg_new[q]]; m; m &= m - 1) {
@@ -740,6 +748,7 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem<CE>& S, int bl
         ++cnt.refupd;
       }
     }
+    V.tri_base[ci] = base;
     if (base < 0) continue;
     cnt.emitted += nt;
 #pragma unroll 1
