@@ -78,9 +78,9 @@ struct GcvCta {
 // lane j takes entries b + j + k * stride (k < GCV_PER_LIST) of each.  A listed vertex is
 // claimed with CAS(0 -> -1), so a vertex listed twice, or one that regained a reference after
 // it was listed, is freed at most once and only when unreferenced; a vertex still attached to
-// its edge is detached.  Three round trips for all entries: the list entries; the vertices'
-// edges and claims, with one free-stack reservation per run length; one free-stack
-// reservation for the freed vertices.  The reservations are the warp's own (sh null) or the
+// its edge is detached.  Three round trips for all entries: the list entries; the claims, with
+// one free-stack reservation per run length; one free-stack reservation for the freed vertices,
+// while the claimed vertices' edges load.  The reservations are the warp's own (sh null) or the
 // CTA's (sh: the whole CTA calls the pass together; two barriers).
 template <bool CE>
 __device__ __forceinline__ void gc_vertices_pass(const Vol& V, int b, int stride, int n, int nr, int& freed,
@@ -95,14 +95,17 @@ __device__ __forceinline__ void gc_vertices_pass(const Vol& V, int b, int stride
     vid[k] = i < n ? __ldcg(&V.dead[i]) : -1;
     run[k] = i < nr ? __ldcg(&V.deadrun[i]) : make_int2(0, 0);
   }
-  uint32_t e[K];
   int old[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const int v = vid[k] >= 0 ? vid[k] : 0;
-    e[k] = __ldcg(&V.vedge[v]);  // no gc thread writes it
     old[k] = atom_cas_if(V.vref + v, 0, -1, vid[k] >= 0);
   }
+  // the edge of each claimed vertex (most listed vertices are still referenced and keep theirs;
+  // no gc thread writes it), loaded while the reservations below are made
+  uint32_t e[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) e[k] = (vid[k] >= 0 && old[k] == 0) ? __ldcg(&V.vedge[vid[k]]) : NO_EDGE;
   // released runs: per length L (8 bits at 8 (L - 1)) this lane's count, its exclusive prefix
   // over the warp, and one free-stack reservation per length (lanes 0..4)
   unsigned long long rc = 0;
