@@ -23,7 +23,7 @@ struct BatchFrames {
 
 // Batch control: the last-CTA ticket of the block gc, and the mesh pass's block hand-out
 // counter (reset by the fusion's first CTA).
-enum BatchDone { BD_MESH = 0, BD_GC_BLOCKS, BD_COUNT };
+enum BatchDone { BD_MESH = 0, BD_COUNT };
 
 // pre[s] = sum of count(t) over scenes t < s, pre[n] = total (shared memory, whole CTA).
 template <typename F>
@@ -150,6 +150,25 @@ __global__ void __launch_bounds__(GCV_THREADS) kb_gc_vertices(const Vol* __restr
   });
   scene_prefix(nscenes, pre_e,
                [&](int t) { return (min(__ldcg(&vols[t].ctl->c[C_N_DEADREC]), vols[t].max_vertices) + 31) >> 5; });
+  // hash rebuilds: a scene whose live plus dead buckets passed half its table (the counts its
+  // previous block gc left: every CTA reads the same, nothing changes them in this kernel) has
+  // the table cleared by the whole grid here and its live blocks reinserted by the block gc
+  __shared__ int rehash[MAX_SCENES];
+  if (threadIdx.x < nscenes) {
+    const Vol& V = vols[threadIdx.x];
+    rehash[threadIdx.x] = gc_rehash_needed(V, __ldcg(&V.ctl->c[C_LIVE_BLOCKS]), __ldcg(&V.ctl->c[C_TOMBS])) ? 1 : 0;
+    if (blockIdx.x == 0) V.ctl->c[C_REHASH] = rehash[threadIdx.x];
+  }
+  __syncthreads();
+  for (int t = 0; t < nscenes; ++t)
+    if (rehash[t]) {
+      const Vol& V = vols[t];
+      for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b <= V.hmask; b += gridDim.x * blockDim.x) {
+        V.keys[b] = KEY_EMPTY;
+        V.vals[b] = -1;
+        V.stamp[b] = 0;
+      }
+    }
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -180,16 +199,26 @@ __global__ void __launch_bounds__(GCV_THREADS) kb_gc_vertices(const Vol* __restr
 }
 
 // Block recycling of every scene: a lane per pool slot in use tests it, the warp frees the
-// candidates.  The last CTA finishes the scenes one after another (a hash rebuild takes the
-// whole CTA).
-__global__ void __launch_bounds__(256) kb_gc_blocks(const Vol* __restrict__ vols, int nscenes, int consumed,
-                                                    int* bdone) {
+// candidates.  A scene whose table the vertex gc cleared for a rebuild frees without tombstones,
+// and each warp reinserts the live blocks of its slots of that scene after its frees.
+__global__ void __launch_bounds__(256) kb_gc_blocks(const Vol* __restrict__ vols, int nscenes, int consumed) {
   grid_dependency_wait();
-  if (blockIdx.x == 0)
-    for (int t = threadIdx.x; t < nscenes; t += blockDim.x) gc_lists_reset(vols[t]);
   __shared__ int pre[MAX_SCENES + 1];
   __shared__ uint32_t sepoch[MAX_SCENES];
-  if (threadIdx.x < nscenes) sepoch[threadIdx.x] = (uint32_t)__ldcg(&vols[threadIdx.x].ctl->c[C_EPOCH]);
+  __shared__ int rehash[MAX_SCENES];
+  if (threadIdx.x < nscenes) {
+    const Vol& V = vols[threadIdx.x];
+    sepoch[threadIdx.x] = (uint32_t)__ldcg(&V.ctl->c[C_EPOCH]);
+    rehash[threadIdx.x] = __ldcg(&V.ctl->c[C_REHASH]);
+    if (blockIdx.x == 0) {
+      gc_lists_reset(V);
+      if (consumed) V.ctl->c[C_N_UPDATE] = 0;  // the update set (read by nothing here) emptied
+      if (rehash[threadIdx.x]) {                 // no tombstone survives the rebuild
+        V.ctl->c[C_TOMBS] = 0;
+        V.ctl->c[C_ST_REHASHES] += 1;
+      }
+    }
+  }
   scene_prefix(nscenes, pre, [&](int t) { return min(__ldcg(&vols[t].ctl->c[C_BLK_BUMP]), vols[t].max_blocks); });
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -208,13 +237,16 @@ __global__ void __launch_bounds__(256) kb_gc_blocks(const Vol* __restrict__ vols
       const int b = __ffs(m) - 1;
       m &= m - 1;
       const int sb = __shfl_sync(0xffffffffu, s, b);
-      int freed = gc_free_block(vols[sb], base + b - pre[sb]);
-      gc_flush_blocks(vols[sb], freed);
+      const bool tomb = !rehash[sb];
+      int freed = gc_free_block(vols[sb], base + b - pre[sb], tomb);
+      gc_flush_blocks(vols[sb], freed, tomb);
     }
-  }
-  if (last_block_at(bdone + BD_GC_BLOCKS)) {
-    for (int t = 0; t < nscenes; ++t) gc_blocks_finish(vols[t], consumed);
-    if (threadIdx.x == 0) bdone[BD_GC_BLOCKS] = 0;
+    __syncwarp();  // lane 0's frees visible to the lane that reads the slot
+    if (g < total && rehash[s]) {
+      const int blk = g - pre[s];
+      const int4 k = vols[s].bkey[blk];
+      if (k.w >= 0) rehash_insert(vols[s], blk, k);
+    }
   }
 }
 

@@ -191,36 +191,6 @@ __device__ __forceinline__ void gc_lists_reset(const Vol& V) {
 // A spare edge record of a lost claim back to its free stack.
 __device__ __forceinline__ void gc_record(const Vol& V, int rec) { pool_push(V, V.rec_free, C_REC_TOP, V.max_vertices, rec); }
 
-// Rebuild the hash without tombstones (one CTA): empty every bucket, then re-insert every
-// live block from the block array (bkey holds its key; its new bucket is written back).
-// Block indices, and with them the update-set marks, do not change.
-__device__ void rehash_in_cta(const Vol& V) {
-  for (uint32_t s = threadIdx.x; s <= V.hmask; s += blockDim.x) {
-    V.keys[s] = KEY_EMPTY;
-    V.vals[s] = -1;
-    V.stamp[s] = 0;
-  }
-  __threadfence();
-  __syncthreads();
-  const int hw = min(__ldcg(&V.ctl->c[C_BLK_BUMP]), V.max_blocks);
-  for (int blk = threadIdx.x; blk < hw; blk += blockDim.x) {
-    const int4 k = V.bkey[blk];
-    if (k.w < 0) continue;
-    const uint64_t key = pack_key(k.x, k.y, k.z);
-    uint32_t s = (uint32_t)mix64(key) & V.hmask;
-    for (uint32_t p = 0; p <= V.hmask; ++p) {
-      const unsigned long long old = atomicCAS((unsigned long long*)&V.keys[s], (unsigned long long)KEY_EMPTY,
-                                               (unsigned long long)key);
-      if (old == KEY_EMPTY) break;
-      s = (s + 1) & V.hmask;
-    }
-    V.vals[s] = blk;
-    V.bkey[blk].w = (int)s;
-  }
-  __threadfence();
-  __syncthreads();
-}
-
 // Block slot `blk` (one lane) may be freed when it was not collected in the current epoch,
 // has no triangles and owns no vertex, and all of its voxels have W = 0 or d >= mu.
 // `consumed`: the update set has been meshed since it was collected (else its blocks are
@@ -239,7 +209,7 @@ __device__ __forceinline__ bool gc_candidate(const Vol& V, int blk, uint32_t epo
 // cleared, its neighbours forget it, its index returns to the pool.  Returns (in every lane)
 // whether the block was freed.
 __device__ __forceinline__ void gc_release_block(const Vol& V, int blk, bool tomb);
-__device__ __forceinline__ bool gc_free_block(const Vol& V, int blk) {
+__device__ __forceinline__ bool gc_free_block(const Vol& V, int blk, bool tomb = true) {
   const int lane = threadIdx.x & 31;
   bool lower_tri = false;
   if (lane >= 1 && lane < 8) {
@@ -247,7 +217,7 @@ __device__ __forceinline__ bool gc_free_block(const Vol& V, int blk) {
     lower_tri = nbk >= 0 && V.bntri[nbk] != 0;
   }
   if (__any_sync(0xffffffffu, lower_tri)) return false;
-  gc_release_block(V, blk, true);
+  gc_release_block(V, blk, tomb);
   return true;
 }
 
@@ -307,41 +277,10 @@ __device__ __forceinline__ void rehash_insert(const Vol& V, int blk, int4 k) {
   set_status(V, ST_HASH_FULL, P_HASH);
 }
 
-__device__ __forceinline__ void gc_rehash_now(const Vol& V, bool need);
-
 // Whether the hash needs a rebuild: live plus dead buckets (the live-block and tombstone
 // counts) past half the table.
 __device__ __forceinline__ bool gc_rehash_needed(const Vol& V, long long live, long long tomb) {
   return (live + tomb) * 2 > (long long)V.hmask + 1 && tomb > 0;
-}
-
-// Rebuild the hash (the whole CTA) when it needs it.  The table must be quiet: no kernel
-// inserts, frees or looks up blocks meanwhile.
-__device__ __forceinline__ void gc_rehash_if_needed(const Vol& V) {
-  __shared__ int need;
-  if (threadIdx.x == 0) need = gc_rehash_needed(V, V.ctl->c[C_LIVE_BLOCKS], V.ctl->c[C_TOMBS]);
-  __syncthreads();
-  gc_rehash_now(V, need);
-}
-
-// The rebuild itself when `need` (the whole CTA; `need` uniform over it).
-__device__ __forceinline__ void gc_rehash_now(const Vol& V, bool need) {
-  if (need) {
-    rehash_in_cta(V);
-    if (threadIdx.x == 0) {
-      V.ctl->c[C_TOMBS] = 0;
-      V.ctl->c[C_ST_REHASHES] += 1;
-    }
-  }
-  __syncthreads();
-}
-
-// After the last CTA of a batched block gc (the whole CTA): the rebuild check; with
-// `consumed`, empty the update set.
-__device__ __forceinline__ void gc_blocks_finish(const Vol& V, int consumed) {
-  gc_rehash_if_needed(V);
-  if (threadIdx.x == 0 && consumed) V.ctl->c[C_N_UPDATE] = 0;
-  __syncthreads();
 }
 
 // Zero-reference vertices and released triangle runs (and, CE, spare edge records) back to

@@ -1315,7 +1315,7 @@ vm_status batch_enqueue(vm_batch* b, cudaStream_t st, const int* sc, int flags, 
     launch_dependent(b->compact ? kb_gc_vertices<true> : kb_gc_vertices<false>, b->num_sms * sc[3], 256, 0, st,
                      (const Vol*)b->d_vols, b->n);
     if (rec) cudaEventRecord(rec->ev[4], st);
-    launch_dependent(kb_gc_blocks, b->num_sms * sc[4], 256, 0, st, (const Vol*)b->d_vols, b->n, 1, b->d_done);
+    launch_dependent(kb_gc_blocks, b->num_sms * sc[4], 256, 0, st, (const Vol*)b->d_vols, b->n, 1);
   } else if (rec) {
     cudaEventRecord(rec->ev[4], st);
   }

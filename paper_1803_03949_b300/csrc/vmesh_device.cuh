@@ -333,24 +333,6 @@ __device__ __forceinline__ uint8_t atomic_and_u8(uint8_t* p, uint8_t bits) {
   return (uint8_t)(atomicAnd(w, ~((unsigned)(uint8_t)~bits << sh)) >> sh);
 }
 
-// Last-block-done ticket: returns true in exactly one CTA of the grid, after every
-// other CTA has finished its work (threadfence reduction pattern; no waiting).
-__device__ __forceinline__ bool last_block_at(int* done) {
-  __shared__ bool s_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int t = atomicAdd(done, 1);
-    s_last = (t == (int)(gridDim.x * gridDim.y * gridDim.z) - 1);
-  }
-  __syncthreads();
-  if (s_last) {
-    __threadfence();
-    return true;
-  }
-  return false;
-}
-
 // Programmatic dependent launch: a kernel launched with programmatic stream serialization
 // may start while the previous kernel drains; it waits here (the hardware grid-dependency
 // wait, which returns once the previous grid has completed and its memory is visible)

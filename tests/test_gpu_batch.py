@@ -139,3 +139,34 @@ def test_batch_arguments_are_checked():
     b.step_all([torch.from_numpy(s.depth(0)).cuda()], [intrinsics(s)], [poses32(s.pose(0))])
     v.check()
     b.close()
+
+
+def test_batch_hash_rebuilds_under_block_churn():
+    """Scenes whose hash tables are small enough that recycled blocks' tombstones force rebuilds
+    (the batched vertex gc clears a scene's table with the whole grid, the batched block gc
+    reinserts its live blocks), next to a scene with a large table that never rebuilds: each
+    equals the scene stepped alone, and the small-table scene the oracle."""
+    import dataclasses
+
+    frames = 10
+    s0 = synth.small_room_scene(num_frames=frames, seed=synth.SEED_BASE + 51)
+    s1 = synth.small_room_scene(num_frames=frames, seed=synth.SEED_BASE + 52)
+    s2 = synth.small_room_scene(num_frames=frames, seed=synth.SEED_BASE + 53)
+    s0.volume = dataclasses.replace(s0.volume, hash_buckets=1 << 10)  # ~500 live blocks: rebuilds from frame 2
+    s2.volume = dataclasses.replace(s2.volume, hash_buckets=1 << 11)
+    scenes = [s0, s1, s2]
+    b, vols = _run_batch(scenes, frames, graph=True)
+    for s, v in zip(scenes, vols):
+        _same_state(v, _run_single(s, frames))
+    assert vols[0].stats()["rehashes"] > 0 and vols[0].stats()["freed_blocks"] > 0
+    assert vols[1].stats()["rehashes"] == 0
+    o = oracle.Volume.from_config(s0.volume, prec="f32")
+    K = (s0.fx, s0.fy, s0.cx, s0.cy)
+    for k in range(frames):
+        Twc, Tcw = poses32(s0.pose(k))
+        o.integrate(s0.depth(k), K, Twc.astype(np.float64), Tcw.astype(np.float64))
+        o.update_mesh(refine=True)
+        o.gc()
+    compare_blocks(vols[0].blocks(), o.blocks())
+    compare_mesh(vols[0].download(), o.mesh(), s0.volume.voxel_size)
+    b.close()
