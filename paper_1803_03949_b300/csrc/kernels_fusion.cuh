@@ -425,12 +425,19 @@ __device__ __forceinline__ void integrate_begin(const Vol& V, int n, uint32_t fr
 // collection).
 template <bool FUSE>
 __global__ void __launch_bounds__(INTEG_THREADS, INTEG_CTAS_PER_SM) k_integrate(Vol V, const FrameParams* __restrict__ fpp) {
+  // the frame's parameters in shared memory: there they cannot alias the voxels the kernel
+  // writes, so they are not reloaded from global memory after every block's stores
+  __shared__ FrameParams sfp;
+  static_assert(sizeof(FrameParams) % 4 == 0 && sizeof(FrameParams) / 4 <= INTEG_THREADS, "FrameParams copy");
   grid_dependency_wait();
-  const uint32_t frame = fpp->frame;
+  if (threadIdx.x < sizeof(FrameParams) / 4)
+    reinterpret_cast<uint32_t*>(&sfp)[threadIdx.x] = __ldcg(reinterpret_cast<const uint32_t*>(fpp) + threadIdx.x);
+  __syncthreads();
+  const uint32_t frame = sfp.frame;
   const int n = min(__ldcg(&V.ctl->c[touched_count(frame)]), V.list_cap_touched);
   const uint32_t epoch = (uint32_t)__ldcg(&V.ctl->c[C_EPOCH]);
   if (blockIdx.x == 0 && threadIdx.x == 0) integrate_begin(V, n, frame);
-  integrate_share<FUSE>(V, *fpp, blockIdx.x, gridDim.x, n, frame, epoch);
+  integrate_share<FUSE>(V, sfp, blockIdx.x, gridDim.x, n, frame, epoch);
   allow_dependent_launch();
 }
 
