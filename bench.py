@@ -803,7 +803,7 @@ def run_vmesh(args, rank, world, local):
     if rank != 0:
         return
     cpu = None
-    if not args.skip_cpu_baseline:
+    if not args.skip_cpu_baseline and world == 1:  # the CPU baseline is an N = 1 figure
         fps, cvps, secs, timed = oracle_frames(scene_for(0), FLOOR_FRAMES, budget_s=args.cpu_seconds)
         cpu = {"value": fps, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "frames 0..%d of the same floor sequence, integrate+update(refine)+gc each (%.1f s of "
@@ -828,7 +828,9 @@ def run_vmesh(args, rank, world, local):
         "clocks": head.pop("clocks"),
     }
     line.update(head)  # voxels_per_s, mean blocks, work per frame
-    if not args.skip_forms:
+    # the other workloads and forms are single-GPU figures: with several ranks they would hold every
+    # GPU while rank 0 alone ran them
+    if not args.skip_forms and world == 1:
         if not args.skip_full_sequence:
             line["full_sequence"] = run_full_sequence(args, stream, flush)
         rs = room_scene_for(0, args.room_warmup + args.room_steps)
