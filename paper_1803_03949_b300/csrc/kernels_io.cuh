@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(256) k_compact_vertices(Vol V, const int* cta_
       off += __popc(b & ((1u << lane) - 1));
       if (v < n) remap[v] = live ? off : -1;
       if (live && off < cap) {
-        float4 p = V.vpos[v], q4 = V.vnrm[v];
+        float4 p = V.vrec[2 * (size_t)v], q4 = V.vrec[2 * (size_t)v + 1];
         pos[3 * (size_t)off] = p.x; pos[3 * (size_t)off + 1] = p.y; pos[3 * (size_t)off + 2] = p.z;
         nrm[3 * (size_t)off] = q4.x; nrm[3 * (size_t)off + 1] = q4.y; nrm[3 * (size_t)off + 2] = q4.z;
         if (keys) keys[off] = edge_key_of(V, V.vedge[v]);

@@ -691,8 +691,8 @@ __device__ __forceinline__ void mesh_block(const Vol& V, MeshSmem<CE>& S, int bl
       const int o = es / 3;
       float4 p, nn;
       edge_vertex(S.halo, l, key, o % 9, (o / 9) % 9, o / 81, es - 3 * o, &p, &nn);
-      V.vpos[vid] = p;
-      V.vnrm[vid] = nn;
+      V.vrec[2 * (size_t)vid] = p;  // position and normal: one 32-byte sector
+      V.vrec[2 * (size_t)vid + 1] = nn;
     }
     __syncwarp();
     int next = 0;

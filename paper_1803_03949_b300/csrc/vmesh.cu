@@ -463,7 +463,7 @@ vm_status vm_create_volume(const vm_params* p, void* cuda_stream, vm_volume** ou
             (compact ? dalloc(v, &V.edge_rec, NB * BV, 0xFF) && dalloc(v, &V.erec, NV * 3, 0xFF) &&
                            dalloc(v, &V.rec_free, NV, 0) && dalloc(v, &V.dead_rec, NV, 0)
                      : dalloc(v, &V.edge_vtx, NB * BV * 3, 0xFF)) &&
-            dalloc(v, &V.tri_base, NB * BV, 0xFF) && dalloc(v, &V.vpos, NV, 0) && dalloc(v, &V.vnrm, NV, 0) &&
+            dalloc(v, &V.tri_base, NB * BV, 0xFF) && dalloc(v, &V.vrec, 2 * (size_t)NV, 0) &&
             dalloc(v, &V.vref, NV, 0xFF) && dalloc(v, &V.vedge, NV, 0xFF) && dalloc(v, &V.tris, NT, 0xFF) &&
             dalloc(v, &V.blk_free, NB, 0) && dalloc(v, &V.vtx_free, NV, 0) &&
             dalloc(v, &V.touched, (size_t)V.list_cap_touched, 0) && dalloc(v, &V.update, NB, 0) &&
@@ -1127,7 +1127,7 @@ __global__ void __launch_bounds__(256) k_na_vertex_compact(Vol V, const unsigned
     if (v >= n) break;
     const int off = na_remap(mask, wprefix, v);
     if (off < 0) continue;
-    const float4 p = V.vpos[v], q = V.vnrm[v];
+    const float4 p = V.vrec[2 * (size_t)v], q = V.vrec[2 * (size_t)v + 1];
     pos[3 * (size_t)off] = p.x; pos[3 * (size_t)off + 1] = p.y; pos[3 * (size_t)off + 2] = p.z;
     nrm[3 * (size_t)off] = q.x; nrm[3 * (size_t)off + 1] = q.y; nrm[3 * (size_t)off + 2] = q.z;
     if (keys) keys[off] = edge_key_of(V, V.vedge[v]);

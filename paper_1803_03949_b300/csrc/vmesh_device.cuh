@@ -17,7 +17,8 @@
 //             (19 B per cube), edge_rec i32[NB*512] (the voxel's edge record, -1 none) into
 //             erec i32[NV*3], one record per voxel that owns a vertex, from a pool with its
 //             own free stack
-//   vertices  vpos float4[NV], vnrm float4[NV], vref i32[NV] (reference count, -1 free),
+//   vertices  vrec float4[2 NV] (per vertex its position, then its normal: one 32-byte sector, so a
+//             refresh writes whole sectors), vref i32[NV] (reference count, -1 free),
 //             vedge u32[NV] (owning edge id = block*1536 + voxel*3 + axis, below 2^32 for up
 //             to 2^21 blocks; NO_EDGE = unattached)
 //   triangles tris int4[NT] (three vertex ids, owning cube id; x < 0 = free)
@@ -152,8 +153,7 @@ struct Vol {
   int* dead_rec;  // spare records of lost claims (recycled by gc)
   int* tri_base;
 
-  float4* vpos;
-  float4* vnrm;
+  float4* vrec;  // vertex v: position vrec[2 v], normal vrec[2 v + 1]
   int* vref;
   uint32_t* vedge;
 
