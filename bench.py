@@ -91,7 +91,7 @@ def frame_bytes(c):
 # model, from the ncu captures summarised in profiles/, per workload (kernels unchanged since
 # the capture only).  The reported traffic scales the ratio to this run's mean launch.
 TRAFFIC_RATIO = {
-    ("floor", "k_mesh"): (377.2 / 195.2, "profiles/k_mesh_floor640x480.md: one launch's dram bytes (frame 8, "
+    ("floor", "k_mesh"): (287.6 / 195.2, "profiles/k_mesh_floor640x480.md: one launch's dram bytes (frame 8, "
                           "15,287 update-set blocks) over its byte model, scaled to this run's mean launch"),
 }
 
