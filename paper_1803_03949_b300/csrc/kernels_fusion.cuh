@@ -14,7 +14,8 @@ constexpr int ALLOC_TILE_W = 64;     // pixels per tile row (batched collection)
 constexpr int ALLOC_TILE_W1 = 32;    // pixels per tile row (k_alloc: 600 tiles of a 640 x 480
                                      // frame spread over the SMs more evenly than 300)
 constexpr int ALLOC_TILE_H = 16;     // tile rows
-constexpr int ALLOC_PPT = 2;         // vertically adjacent pixels per thread (k_alloc)
+constexpr int ALLOC_PPT = 1;         // vertically adjacent pixels per thread (k_alloc; 1 measured
+                                     // faster than 2 and 4: the walks of one thread are serial)
 constexpr int ALLOC_THREADS = ALLOC_TILE_W1 * ALLOC_TILE_H / ALLOC_PPT;
 constexpr int ALLOC_SET_LOG2 = 10;
 constexpr int ALLOC_SET = 1 << ALLOC_SET_LOG2;  // CTA-local set of block keys
@@ -253,12 +254,12 @@ __device__ __forceinline__ void alloc_begin(const Vol& V, int advance_epoch) {
   }
 }
 
-// One CTA per 32 x 16 pixel tile, two vertically adjacent pixels per thread (a 640 x 480
-// frame is one wave of CTAs).  The frame's parameters arrive as a launch argument; the
-// first CTA stores them in the control block for the kernels that follow and starts the
-// epoch.  No CTA waits for the others: the kernel ends with its last tile.  Registers are
-// bounded for 5 CTAs per SM (740 on 148 SMs, over the 600 tiles of a 640 x 480 frame).
-__global__ void __launch_bounds__(ALLOC_THREADS, 5) k_alloc(Vol V, const __grid_constant__ FrameParams fp,
+// One CTA per 32 x 16 pixel tile, a pixel per thread (512 threads; a 640 x 480 frame is 600
+// CTAs).  The frame's parameters arrive as a launch argument; the first CTA stores them in the
+// control block for the kernels that follow and starts the epoch.  No CTA waits for the
+// others: the kernel ends with its last tile.  Registers are bounded for 3 CTAs per SM (40;
+// bounding them for 4 spills and measured slower).
+__global__ void __launch_bounds__(ALLOC_THREADS, 3) k_alloc(Vol V, const __grid_constant__ FrameParams fp,
                                                          int advance_epoch) {
   __shared__ unsigned long long set[ALLOC_SET];
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
