@@ -792,6 +792,14 @@ def run_vmesh(args, rank, world, local):
         raise SystemExit("--warmup + --steps must not exceed the floor's %d frames" % FLOOR_FRAMES)
     sc = scene_for(rank)
     vc = floor_config(args, sc)
+    if args.only_room:  # the room's value pass alone (profiling captures)
+        args.no_kernel_timing = True
+        args.no_e2e = True
+        rs = room_scene_for(rank, W + K)
+        r = measure(args, rs, rs.volume, W, K, stream, flush, peak, peak_kind, world, rank, local, "room")
+        if rank == 0:
+            print(json.dumps({"room_value_only": r}), flush=True)
+        return
     if args.only_headline:  # the headline's value pass alone (profiling captures)
         args.no_kernel_timing = True
         args.no_e2e = True
@@ -882,6 +890,7 @@ def main():
                     help="time frames without per-kernel event nodes (no roofline)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the two end-to-end passes")
     ap.add_argument("--only-headline", action="store_true", help="run only the headline's value pass")
+    ap.add_argument("--only-room", action="store_true", help="run only the room's value pass (--steps, --warmup)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle's timed sample")
     ap.add_argument("--reference-seconds", type=float, default=150.0, help="budget of the reference arm's timing")
     ap.add_argument("--skip-forms", action="store_true",
